@@ -1,0 +1,120 @@
+"""Synthetic multilevel block-Toeplitz problems shaped like the paper's arrays.
+
+The paper's impedance matrices come from RWG meshes of real antennas, which
+are not available; these lattices stand in for them (same structure: an
+Nx x Ny regular array of identical elements, b basis functions per element,
+element-pair blocks that depend only on the lattice offset, Sec. II-A).
+
+Units are wavelengths (lambda = 1, k = 2*pi).  For seed s the generator draws,
+in this order, u_i in [0,1)^2 (b pairs, x then y per basis), w_i ~ U(0.5, 1)
+and alpha_i ~ U(0, pi).  Basis i of element (mx, my) sits at
+(mx*d, my*d) + d*u_i.  The coupling between observation basis i of element m
+and source basis j of element n, with lattice offset Delta = m - n, is
+
+    Z_Delta[i][j] = w_i w_j cos(alpha_i - alpha_j) exp(-1j k r) / (4 pi r),
+    r = max(|Delta*d + p_i - p_j|, a),  a = 0.01,
+
+plus a self-loading of 50+30j ohm on every diagonal entry of Z_0.  The
+construction is reciprocal: Z_{-Delta} = Z_Delta^T exactly (Sec. II-D states
+the MoM matrix is symmetric).
+
+Block layout: complex array [2Ny-1][2Nx-1][b][b], offset (dx, dy) at index
+(dy + Ny - 1, dx + Nx - 1), rows = observation basis.
+Vector layout: complex array [nrhs][Ny][Nx][b]; element e = mx + Nx*my and
+global unknown e*b + i, as in the two-level ordering of Eq. (2).
+"""
+from dataclasses import dataclass
+
+import numpy as np
+
+from .rng import SplitMix64
+
+K_WAVENUMBER = 2.0 * np.pi
+R_FLOOR = 0.01
+SELF_LOAD = 50.0 + 30.0j
+
+
+@dataclass(frozen=True)
+class LatticeSpec:
+    nx: int
+    ny: int
+    b: int
+    d: float = 0.5
+    seed: int = 0
+
+    @property
+    def n_el(self):
+        return self.nx * self.ny
+
+    @property
+    def n(self):
+        return self.nx * self.ny * self.b
+
+
+def element_geometry(b, d, seed=0):
+    """Basis positions p (b,2), weights w (b,) and orientations alpha (b,)."""
+    g = SplitMix64(seed)
+    u = g.uniform(2 * b).reshape(b, 2)
+    w = g.uniform(b, 0.5, 1.0)
+    alpha = g.uniform(b, 0.0, np.pi)
+    return d * u, w, alpha
+
+
+def offset_blocks(spec, dtype=np.complex128):
+    """All (2Nx-1)(2Ny-1) offset blocks of the lattice, layout [2Ny-1][2Nx-1][b][b].
+
+    Entries are computed in float64; with dtype=complex64 they are rounded once
+    at the end (the rounded values then define the problem).
+    """
+    nx, ny, b, d = spec.nx, spec.ny, spec.b, spec.d
+    p, w, alpha = element_geometry(b, d, spec.seed)
+    coef = np.outer(w, w) * np.cos(alpha[:, None] - alpha[None, :])
+    pij = p[:, None, :] - p[None, :, :]  # (b, b, 2): p_i - p_j
+    dxs = np.arange(-(nx - 1), nx, dtype=np.float64) * d
+    out = np.empty((2 * ny - 1, 2 * nx - 1, b, b), dtype=dtype)
+    for iy, dy in enumerate(range(-(ny - 1), ny)):
+        rx = dxs[:, None, None] + pij[None, :, :, 0]
+        ry = dy * d + pij[None, :, :, 1]
+        r = np.maximum(np.sqrt(rx * rx + ry * ry), R_FLOOR)
+        blk = coef[None] * np.exp(-1j * K_WAVENUMBER * r) / (4.0 * np.pi * r)
+        if dy == 0:
+            blk[nx - 1] += SELF_LOAD * np.eye(b)
+        out[iy] = blk
+    return out
+
+
+def scan_phase(nx, ny, d, theta_deg, phi_deg):
+    """Progressive port phase a[my][mx] = exp(-j k d sin(theta) (mx cos(phi) + my sin(phi)))."""
+    th = np.deg2rad(theta_deg)
+    ph = np.deg2rad(phi_deg)
+    mx = np.arange(nx)[None, :]
+    my = np.arange(ny)[:, None]
+    return np.exp(-1j * K_WAVENUMBER * d * np.sin(th) * (mx * np.cos(ph) + my * np.sin(ph)))
+
+
+def excitation(spec, angles, port_basis=0):
+    """Delta-gap port excitation V [nrhs][Ny][Nx][b]: the scan phase on basis
+    `port_basis` of each element, zero elsewhere.  `angles` is a list of
+    (theta_deg, phi_deg); (0, 0) is broadside (all ports 1)."""
+    nx, ny, b = spec.nx, spec.ny, spec.b
+    v = np.zeros((len(angles), ny, nx, b), dtype=np.complex128)
+    for q, (th, ph) in enumerate(angles):
+        v[q, :, :, port_basis] = scan_phase(nx, ny, spec.d, th, ph)
+    return v
+
+
+def config_c1():
+    """4x4 lattice, spacing 0.5, b = 32, one broadside RHS, complex128 blocks."""
+    return LatticeSpec(4, 4, 32, 0.5, 0), [(0.0, 0.0)]
+
+
+def config_c2():
+    """32x32 lattice, spacing 0.5, b = 128, blocks stored complex64, 2 RHS:
+    broadside and a 45 degree E-plane (x) scan."""
+    return LatticeSpec(32, 32, 128, 0.5, 0), [(0.0, 0.0), (45.0, 0.0)]
+
+
+def config_c3_angles():
+    """8 x 8 scan grid: theta_p = p*60/7 (p = 0..7), phi_q = q*90/8 (q = 0..7),
+    RHS index p*8 + q."""
+    return [(p * 60.0 / 7.0, q * 90.0 / 8.0) for p in range(8) for q in range(8)]
