@@ -1,0 +1,381 @@
+"""Benchmark: solves/s of the MBT array solver on one B300 (or N replicas).
+
+Workload: the 32 x 32 lattice, b = 128 basis functions per element
+(N = 131072 unknowns), offset blocks stored complex64, two right-hand sides
+(broadside and a 45 degree E-plane scan), restarted GMRES(50) on the
+preconditioned normal equations with FP64 refinement to a relative residual
+of 1e-10.  One step = the whole hot path on one problem: block ingest, the
+block-bin transform, preconditioner build and factorisation, the solve and
+the port quantities.  value = right-hand sides solved per second (solves/s).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank solves its own replica of the problem (the work
+shards by independent problems; no collective on the data path).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "solves/s at rel. Z_a err <=1e-8 vs plain FP64 GPU solve; p50/p99 latency; HBM GB/s"
+WORKLOAD = ("32x32 lattice, b=128 (N=131072), offset blocks complex64, 2 RHS (broadside, 45deg E-plane), "
+            "preconditioned GMRES(50) + FP64 refinement to rel. residual 1e-10")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=2, help="steps of the plain FP64 solve (0 = skip)")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0, help="bounded oracle sample (0 = skip)")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_inputs():
+    from synth import config_c2, offset_blocks, excitation
+    spec, angles = config_c2()
+    blocks = offset_blocks(spec, np.complex64)
+    V = excitation(spec, angles)
+    return spec, blocks, V
+
+
+def bin_product_bytes(spec, nr):
+    """Algorithmic bytes of one c64 bin-product launch: the stored bins once
+    (one b x b block per {k,-k} pair) plus the bin vectors in and out."""
+    def smooth(n):
+        m = n
+        while True:
+            k = m
+            for r in (2, 3, 5):
+                while k % r == 0:
+                    k //= r
+            if k == 1:
+                return m
+            m += 1
+    mx, my = smooth(2 * spec.nx - 1), smooth(2 * spec.ny - 1)
+    B = mx * my
+    pairs = sum(1 for ky in range(my) for kx in range(mx)
+                if ky * mx + kx <= ((my - ky) % my) * mx + ((mx - kx) % mx))
+    ldb = spec.b + (spec.b % 2)
+    return pairs * spec.b * ldb * 8 + 2 * B * nr * spec.b * 8, pairs, B
+
+
+def cpu_oracle_sample(spec, blocks, V, seconds):
+    """Time the oracle (oracle-I: GMRES on Z I = V with the direct offset-sum
+    product, complex128) on RHS 0 of the workload for a bounded wall time;
+    extrapolate to one full solve from the measured time per iteration and
+    the observed geometric residual reduction per iteration."""
+    from oracle import iterative
+    cores = len(os.sched_getaffinity(0))
+    b128 = blocks.astype(np.complex128)
+    hist = []
+    t0 = time.perf_counter()
+
+    class Stop(Exception):
+        pass
+
+    def cb(q, it, rel):
+        hist.append((time.perf_counter() - t0, it, rel))
+        if time.perf_counter() - t0 > seconds:
+            raise Stop()
+
+    try:
+        iterative.gmres(b128, spec.nx, spec.ny, V[:1], tol=1e-10, restart=60, max_iter=500, callback=cb)
+        converged = True
+    except Stop:
+        converged = False
+    if not hist:
+        return None
+    t_iter = hist[-1][0] / hist[-1][1]
+    if converged:
+        iters = hist[-1][1]
+    else:
+        rho = hist[-1][2] ** (1.0 / hist[-1][1])
+        iters = int(np.ceil(np.log(1e-10) / np.log(rho))) if 0 < rho < 1 else float("inf")
+    per_solve = t_iter * iters
+    return {"value": 1.0 / per_solve, "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "sample": (f"oracle-I (complex128 GMRES, direct offset-sum product, block Jacobi) on RHS 0 of the same "
+                       f"32x32 b=128 problem for {hist[-1][0]:.1f} s: {hist[-1][1]} iterations at "
+                       f"{t_iter:.2f} s each, residual {hist[-1][2]:.2e}; "
+                       + ("converged" if converged else f"extrapolated to {iters} iterations for 1e-10")),
+            "s_per_iteration": t_iter, "iterations_for_1e-10": iters}
+
+
+def run_reference(args, world, rank):
+    """Reference arm: the CPU oracle as it stands, on the host cores."""
+    if rank != 0:
+        return
+    spec, blocks, V = make_inputs()
+    per_step = max(5.0, min(30.0, 120.0 / max(1, args.steps + args.warmup)))
+    vals = []
+    cb = None
+    for s in range(args.warmup + args.steps):
+        cb = cpu_oracle_sample(spec, blocks, V, per_step)
+        if s >= args.warmup and cb:
+            vals.append(cb["value"])
+    value = float(np.mean(vals)) if vals else None
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * 2 / value if value else None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+            "cpu_baseline": {k: cb[k] for k in ("kind", "cores", "sample")} | {"value": value} if cb else None,
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    import torch
+    import paper_2608_17844_b300 as m
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    spec, blocks, V = make_inputs()
+    nr = V.shape[0]
+    stream = torch.cuda.current_stream()
+    blocks_d = torch.from_numpy(blocks).cuda()
+    V_d = torch.from_numpy(V).cuda()
+    I_d = torch.zeros_like(V_d)
+    za_d = torch.zeros(V.shape[:3], dtype=torch.complex128, device="cuda")
+    gam_d = torch.zeros_like(za_d)
+
+    h = m.moma_create_array(spec.nx, spec.ny, spec.b, m.MOMA_PREC_MIXED, stream=stream)
+    infos = []
+
+    def step():
+        m.moma_set_blocks(h, blocks_d)
+        infos.append(m.moma_solve(h, V_d, I_d))
+        m.moma_active_impedance(h, I_d, V_d, za_d, gam_d)
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    m.moma_profile(h, True)
+    launches0 = m.moma_launch_count(h)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    step_ms = []
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        e_a = torch.cuda.Event(enable_timing=True)
+        e_b = torch.cuda.Event(enable_timing=True)
+        e_a.record(stream)
+        step()
+        e_b.record(stream)
+        step_ms.append((e_a, e_b))
+    ev1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    total_ms = ev0.elapsed_time(ev1)
+    launches = m.moma_launch_count(h) - launches0
+    stats = {k: m.moma_kernel_stats(h, k) for k in m.KERNEL_IDS}
+    m.moma_profile(h, False)
+    steps_ms = [a.elapsed_time(b) for a, b in step_ms]
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * nr * args.steps / (total_ms / 1000.0)
+
+    # Phase breakdown of one step (set-up vs solve), same stream, events.
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    e[0].record(stream)
+    m.moma_set_blocks(h, blocks_d)
+    e[1].record(stream)
+    info = m.moma_solve(h, V_d, I_d)
+    e[2].record(stream)
+    m.moma_active_impedance(h, I_d, V_d, za_d, gam_d)
+    e[3].record(stream)
+    torch.cuda.synchronize()
+    phases = {"set_blocks_ms": e[0].elapsed_time(e[1]), "solve_ms": e[1].elapsed_time(e[2]),
+              "ports_ms": e[2].elapsed_time(e[3]), "solve_info": info}
+
+    # Roofline of the dominant kernel: the c64 bin product.
+    n_bin, ms_bin = stats["bin_c64"]
+    alg_bytes, pairs, B = bin_product_bytes(spec, nr)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6400.0)
+    achieved = alg_bytes / (ms_bin / n_bin / 1000.0) / 1e9 if n_bin else None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak if achieved else None, "traffic": None,
+                "kernel": "bin_pair_kernel<float> (c64 per-bin product, Z and Z^H legs)",
+                "alg_bytes_per_launch": alg_bytes, "launches": n_bin, "avg_launch_us": 1000.0 * ms_bin / n_bin if n_bin else None,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback 6.4 TB/s"}
+    kernel_share = {k: {"launches": n, "ms": ms} for k, (n, ms) in stats.items()}
+
+    # Plain FP64 GPU solve on the same problem (the comparison solver).
+    fp64 = None
+    if args.fp64_steps > 0:
+        h64 = m.moma_create_array(spec.nx, spec.ny, spec.b, m.MOMA_PREC_FP64, stream=stream)
+        I64 = torch.zeros_like(V_d)
+        m.moma_set_blocks(h64, blocks_d)
+        m.moma_solve(h64, V_d, I64)
+        torch.cuda.synchronize()
+        a_ = torch.cuda.Event(enable_timing=True)
+        b_ = torch.cuda.Event(enable_timing=True)
+        a_.record(stream)
+        for _ in range(args.fp64_steps):
+            m.moma_set_blocks(h64, blocks_d)
+            inf64 = m.moma_solve(h64, V_d, I64)
+            m.moma_active_impedance(h64, I64, V_d, za_d, gam_d)
+        b_.record(stream)
+        torch.cuda.synchronize()
+        ms64 = a_.elapsed_time(b_) / args.fp64_steps
+        m.moma_destroy(h64)
+        fp64 = {"value": nr / (ms64 / 1000.0), "unit": "solves/s", "ms_per_step": ms64, "info": inf64,
+                "speedup_mixed_vs_fp64": value / world / (nr / (ms64 / 1000.0))}
+
+    # End to end through the C ABI with host buffers (pinned), copies inside.
+    e2e = None
+    if not args.no_e2e:
+        hb = torch.from_numpy(blocks).pin_memory()
+        hV = torch.from_numpy(V).pin_memory()
+        hI = torch.zeros_like(hV).pin_memory()
+        hz = torch.zeros(V.shape[:3], dtype=torch.complex128).pin_memory()
+        hg = torch.zeros_like(hz).pin_memory()
+
+        def host_step():
+            m.moma_set_blocks(h, hb)
+            m.moma_solve(h, hV, hI)
+            m.moma_active_impedance(h, hI, hV, hz, hg)
+
+        host_step()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            host_step()
+        barrier()
+        dt = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([dt], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": world * nr * args.steps / dt, "unit": "solves/s",
+               "h2d_bytes_per_step": int(blocks.nbytes + 2 * V.nbytes + V.nbytes),
+               "d2h_bytes_per_step": int(V.nbytes + 2 * hz.numel() * 16)}
+
+    za = za_d.cpu().numpy()
+    from oracle.ports import named_elements
+    ports = {n: [complex(za[q, ey, ex]) for q in range(nr)] for n, (ex, ey) in named_elements(spec.nx, spec.ny).items()}
+    m.moma_destroy(h)
+
+    cpu = None
+    if rank == 0 and args.cpu_seconds > 0:
+        cpu = cpu_oracle_sample(spec, blocks, V, args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64 (FP32) inner + f64 refinement",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "rhs_per_step": nr * world, "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (c64 blocks 520 MB; stored bins 269 MB c64 + 537 MB c128)"},
+            "step_ms": {"p50": statistics.median(steps_ms), "p99": float(np.percentile(steps_ms, 99)),
+                        "min": min(steps_ms), "max": max(steps_ms)},
+            "phases": phases, "roofline": roofline, "kernels": kernel_share, "cpu_baseline": cpu,
+            "e2e": e2e, "gpu_launches": launches, "clocks": clk, "fp64_plain": fp64,
+            "ports_Za": {k: [f"{z.real:.10f}{z.imag:+.10f}j" for z in v] for k, v in ports.items()},
+        }
+        print(json.dumps(line, default=str), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

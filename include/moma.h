@@ -1,0 +1,178 @@
+/*
+ * moma.h -- C ABI of the B300 solver for regular finite arrays whose Method
+ * of Moments matrix is multilevel block-Toeplitz (MBT).
+ *
+ * Problem (Sec. II-A and Eq. 15 of arXiv 2608.17844): an Nx x Ny lattice of
+ * identical elements, b basis functions per element.  The impedance matrix Z
+ * couples observation element m and source element n through a b x b block
+ * that depends only on the lattice offset m - n, so Z is fully described by
+ * its (2Nx-1)(2Ny-1) unique offset blocks (Eq. 1, Fig. 1).  The library
+ * solves Z I = V and forms the port quantities (Eqs. 16-19).
+ *
+ * Method: Z is applied as a 2D lattice FFT convolution of its circulant
+ * embedding (Eq. 3), with Z^H served from the same stored bins through the
+ * Hermitian commutation property (Eq. 6).  The system is solved through the
+ * preconditioned normal equations P^{-1} Z^H Z I = P^{-1} Z^H V (Sec. III-A)
+ * with P the block diagonal of Z^H Z (Eq. 37), Cholesky-factored once, using
+ * restarted GMRES inside an FP64 iterative-refinement loop on V - Z I.
+ *
+ * Conventions shared by every entry point
+ *  - Complex numbers are interleaved (re, im): "c128" = two doubles,
+ *    "c64" = two floats.
+ *  - Offset blocks: [2Ny-1][2Nx-1][b][b] row-major; offset (dx, dy) sits at
+ *    index (dy + Ny - 1, dx + Nx - 1); row = observation basis.
+ *  - Vectors: [nrhs][Ny][Nx][b] row-major; element e = mx + Nx*my, unknown
+ *    e*b + i (the two-level ordering of Eq. 2).
+ *  - Every buffer argument may be host or device memory of the current CUDA
+ *    device; the library inspects the pointer.  The caller owns all buffers
+ *    it passes; the library never keeps a caller pointer past the call.
+ *  - All GPU work runs on the stream given at creation.  Calls return after
+ *    their results are visible to the caller (host results copied, device
+ *    results complete on that stream).
+ *  - Status codes are returned; moma_last_error() gives a thread-local
+ *    message for the last failing call on that thread.  No C++ exception
+ *    crosses the ABI.  Calls on one handle are not thread-safe; distinct
+ *    handles are independent.
+ */
+#ifndef MOMA_H
+#define MOMA_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MOMA_OK = 0,
+    MOMA_ERR_ARG = 1,           /* invalid argument (sizes, null pointers, enum values) */
+    MOMA_ERR_STATE = 2,         /* call order violated, e.g. solve before set_blocks */
+    MOMA_ERR_OOM = 3,           /* device allocation failed */
+    MOMA_ERR_CUDA = 4,          /* a CUDA runtime call failed */
+    MOMA_ERR_NOT_PD = 5,        /* a preconditioner block lost positive definiteness */
+    MOMA_ERR_NOT_CONVERGED = 6, /* iteration limits reached before the tolerance */
+    MOMA_ERR_BREAKDOWN = 7,     /* Krylov breakdown with the residual above tolerance */
+    MOMA_ERR_NONFINITE = 8,     /* NaN/Inf in an input or a result */
+    MOMA_ERR_TIMEOUT = 9        /* a bounded device wait gave up */
+} moma_status;
+
+typedef enum { MOMA_C128 = 0, MOMA_C64 = 1 } moma_dtype;
+
+typedef enum {
+    MOMA_PREC_FP64 = 0,  /* plain: every stage in FP64 / complex128 */
+    MOMA_PREC_MIXED = 1  /* inner GMRES, FFTs and bin products in FP32/c64;
+                            FP64 for the refinement residual V - Z I, the
+                            Hessenberg least squares and the Cholesky factor */
+} moma_precision;
+
+typedef enum {
+    MOMA_OP_Z = 0,      /* y = Z x                         (Eq. 3)            */
+    MOMA_OP_ZH = 1,     /* y = Z^H x, bins conjugate-transposed on the fly (Eq. 6) */
+    MOMA_OP_NORMAL = 2  /* y = P^{-1} Z^H Z x              (Sec. III-A)      */
+} moma_op;
+
+typedef struct moma_array moma_array; /* opaque; owns all device state */
+
+typedef struct {
+    int precision; /* moma_precision */
+    int mx, my;    /* circulant sizes; 0 = smallest 2^a 3^b 5^c >= 2N-1.
+                      Any M >= 2N-1 embeds Z exactly (Sec. II-A uses 2N-1). */
+    int restart;   /* GMRES restart length m; 0 = 50 */
+} moma_options;
+
+typedef struct {
+    double tol;       /* per-RHS relative true residual ||V - Z I|| / ||V||; 0 = 1e-10 */
+    double inner_tol; /* relative reduction of the inner preconditioned residual per
+                         refinement step; 0 = 1e-5 (mixed) or tol/10 (FP64) */
+    int max_outer;    /* refinement steps (each one GMRES cycle); 0 = 30 */
+    int warm_start;   /* nonzero: I holds an initial guess on entry */
+} moma_solve_opts;
+
+typedef struct {
+    int outer_iters;         /* refinement steps taken (true-residual evaluations - 1) */
+    int inner_iters;         /* total Arnoldi steps over all refinement steps */
+    int converged;           /* 1 if every column met tol */
+    double max_rel_residual; /* max over columns of the final FP64 ||V - Z I|| / ||V|| */
+    double first_inner_reduction; /* max over columns of the inner residual estimate after
+                                     the first inner cycle, relative to its start */
+} moma_solve_info;
+
+/* Create a solver for an nx x ny lattice with b bases per element.
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream).
+ * Allocates the device store for the transformed bins (c128, plus c64 in
+ * MIXED mode), the factored preconditioner and the workspaces.
+ * Errors: MOMA_ERR_ARG (nx, ny, b < 1, bad options), MOMA_ERR_OOM. */
+moma_status moma_create_array(int nx, int ny, int b, const moma_options *opt,
+                              void *cuda_stream, moma_array **out);
+
+/* Load the offset blocks (Eq. 1) and build everything derived from them:
+ * the transformed first column of the circulant embedding, one block per
+ * (k, -k) bin pair since Zhat_{-k} = Zhat_k^T (Eqs. 3, 6, 11); the blocks
+ * of P = blockdiag(Z^H Z) by summed-area box sums of the offset Gram
+ * products Z_D^H Z_D (Eq. 37); their Cholesky factors P_e = L_e L_e^H
+ * (Sec. III-A) and the inverse factors used to apply P^{-1}.
+ * blocks: [2Ny-1][2Nx-1][b][b] of dtype (moma_dtype), host or device.
+ * Errors: MOMA_ERR_NONFINITE (NaN/Inf in blocks), MOMA_ERR_NOT_PD. */
+moma_status moma_set_blocks(moma_array *a, const void *blocks, int dtype);
+
+/* Apply an operator to nrhs vectors x -> y (layout [nrhs][Ny][Nx][b]).
+ * dtype MOMA_C128 computes in FP64 from the c128 bins; MOMA_C64 in FP32
+ * from the c64 bins (MIXED arrays only).  MOMA_OP_NORMAL needs set_blocks. */
+moma_status moma_matvec(moma_array *a, int op, int nrhs, const void *x, void *y, int dtype);
+
+/* y = P^{-1} x with the factored block-diagonal preconditioner (Eq. 38
+ * without margin, applied through L_e^{-H} L_e^{-1}). */
+moma_status moma_apply_precond(moma_array *a, int nrhs, const void *x, void *y, int dtype);
+
+/* Copy one transformed bin Zhat_k (b x b, c128 or c64) for circulant
+ * frequency (kx, ky), resolving the pair storage (transposes if k is the
+ * stored partner).  Inspection aid for tests. */
+moma_status moma_get_bin(moma_array *a, int kx, int ky, int dtype, void *out);
+
+/* Copy the preconditioner block P_e (b x b c128, full Hermitian) of element
+ * (ex, ey) as built from Eq. 37.  Inspection aid for tests. */
+moma_status moma_get_precond_block(moma_array *a, int ex, int ey, void *out);
+
+/* Solve Z I = V (Eq. 15) for nrhs right-hand sides.
+ * V, I: c128 [nrhs][Ny][Nx][b], host or device.  I is output (and the
+ * initial guess if opts->warm_start).  opts, info may be NULL.
+ * rel_residual: optional [nrhs] doubles receiving each column's final
+ * FP64 relative residual.
+ * Errors: MOMA_ERR_STATE (no blocks), MOMA_ERR_NONFINITE (V or iterate),
+ * MOMA_ERR_NOT_CONVERGED (limits reached; I holds the best iterate). */
+moma_status moma_solve(moma_array *a, int nrhs, const void *V, void *I,
+                       const moma_solve_opts *opts, moma_solve_info *info,
+                       double *rel_residual);
+
+/* Port quantities (Eqs. 16-19): with delta-gap ports on basis port_basis,
+ * I_p,e = I[q][e][port_basis], V_p,e likewise from V, and
+ *   Z_a,e = V_p,e / I_p,e      (Eq. 17 with Z_p I_p = V_p, Eq. 18)
+ *   Gamma_e = (Z_a,e - z0) / (Z_a,e + z0), z0 real (Eq. 19).
+ * I, V: c128 [nrhs][Ny][Nx][b]; Za, Gamma: c128 [nrhs][Ny][Nx]; Gamma may
+ * be NULL.  Errors: MOMA_ERR_NONFINITE if some I_p = 0 (that Z_a is NaN). */
+moma_status moma_active_impedance(moma_array *a, int nrhs, const void *I, const void *V,
+                                  int port_basis, double z0, void *Za, void *Gamma);
+
+/* Per-kernel timing over the calls made since moma_profile(a, 1), measured
+ * with CUDA events recorded on the array's stream around each launch of a
+ * kernel family.  kernel: 0 = c64 bin product, 1 = c128 bin product,
+ * 2 = preconditioner apply, 3 = c64 lattice FFT passes, 4 = block-bin
+ * transform (set-up), 5 = c128 lattice FFT passes.  Writes the number of
+ * timed launches and their total milliseconds.  moma_profile(a, 0) stops
+ * timing; either call resets the counters. */
+moma_status moma_profile(moma_array *a, int enable);
+moma_status moma_kernel_stats(moma_array *a, int kernel, long long *launches, double *total_ms);
+
+/* Number of kernel launches issued on the array's stream since creation. */
+long long moma_launch_count(moma_array *a);
+
+/* Device bytes held by the array (bins, preconditioner, workspaces). */
+size_t moma_device_bytes(const moma_array *a);
+
+void moma_destroy(moma_array *a);
+const char *moma_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MOMA_H */

@@ -1,0 +1,115 @@
+// Column FFT engine for the lattice transforms of the MLFFT (Eq. 2:
+// F^[2] = F_{Ny} (x) (F_{Nx} (x) I_b), i.e. independent 1D DFTs along the
+// x and y lattice axes with the basis index untouched).
+//
+// One thread owns one 1D line of length M held in shared memory with a
+// stride of `ld` elements (column m of thread t at col[m * ld + t]), so no
+// synchronisation is needed between stages and consecutive threads touch
+// consecutive words (conflict-free).  M = r_0 r_1 ... r_{k-1} with radices
+// in {2, 3, 4, 5}.
+//
+//  * dif(): natural-order input -> output X[k] at position pos[k]
+//    (decimation in frequency; stage s splits the current sub-problem of
+//    length Ms into r_s sub-problems, twiddle after the butterfly).
+//  * dit(): input x[n] at position pos[n] -> natural-order output
+//    (decimation in time; the mirror image, twiddle before the butterfly).
+// pos[] is the mixed-radix digit reversal: with n = r_0 n' + n_0,
+// pos(n) = n_0 (M / r_0) + pos'(n') on the remaining radices.
+//
+// Forward kernel is exp(-2 pi i k n / M) (the sign of Eq. 11); the inverse
+// is taken as conj(DFT(conj(.))) / M.
+#pragma once
+#include "common.cuh"
+
+#define MOMA_FFT_MAXST 16
+
+struct FftPlan {
+  int M;
+  int nst;
+  int radix[MOMA_FFT_MAXST];
+};
+
+// Radix-r forward DFT in registers: b[k] = sum_n a[n] w_r^{nk}.
+// tw[t] = exp(-2 pi i t / M); w_r = tw[M / r].
+template <typename C>
+MOMA_HD void butterfly(C *a, int r, const C *tw, int M) {
+  using R = decltype(a[0].x);
+  if (r == 2) {
+    C t = a[0];
+    a[0] = cadd(t, a[1]);
+    a[1] = csub(t, a[1]);
+  } else if (r == 4) {
+    C s02 = cadd(a[0], a[2]), d02 = csub(a[0], a[2]);
+    C s13 = cadd(a[1], a[3]), d13 = csub(a[1], a[3]);
+    a[0] = cadd(s02, s13);
+    a[2] = csub(s02, s13);
+    a[1] = cadd(d02, cmul_mi(d13));
+    a[3] = csub(d02, cmul_mi(d13));
+  } else if (r == 3) {
+    const R s = -tw[M / 3].y;  // sin(2 pi / 3)
+    C t1 = cadd(a[1], a[2]);
+    C t2 = csub(a[0], cscale(t1, (R)0.5));
+    C d = csub(a[1], a[2]);
+    C t3 = cscale(cmul_mi(d), s);
+    a[0] = cadd(a[0], t1);
+    a[1] = cadd(t2, t3);
+    a[2] = csub(t2, t3);
+  } else {  // r == 5
+    const C w1 = tw[M / 5], w2 = tw[(2 * M) / 5];
+    const R c1 = w1.x, s1 = -w1.y, c2 = w2.x, s2 = -w2.y;
+    C t1 = cadd(a[1], a[4]), t2 = cadd(a[2], a[3]);
+    C t3 = csub(a[1], a[4]), t4 = csub(a[2], a[3]);
+    C a0 = a[0];
+    C p1 = cadd(a0, cadd(cscale(t1, c1), cscale(t2, c2)));
+    C p2 = cadd(a0, cadd(cscale(t1, c2), cscale(t2, c1)));
+    C q1 = cadd(cscale(t3, s1), cscale(t4, s2));
+    C q2 = csub(cscale(t3, s2), cscale(t4, s1));
+    a[0] = cadd(a0, cadd(t1, t2));
+    a[1] = cadd(p1, cmul_mi(q1));
+    a[4] = csub(p1, cmul_mi(q1));
+    a[2] = cadd(p2, cmul_mi(q2));
+    a[3] = csub(p2, cmul_mi(q2));
+  }
+}
+
+template <typename C>
+MOMA_HD void fft_dif(C *col, int ld, const FftPlan &pl, const C *tw) {
+  const int M = pl.M;
+  int Ms = M, G = 1;
+  for (int s = 0; s < pl.nst; ++s) {
+    const int r = pl.radix[s], Mp = Ms / r;
+    for (int g = 0; g < G; ++g) {
+      C *seg = col + (size_t)g * Ms * ld;
+      for (int k = 0; k < Mp; ++k) {
+        C a[5];
+        for (int n = 0; n < r; ++n) a[n] = seg[(n * Mp + k) * ld];
+        butterfly(a, r, tw, M);
+        seg[k * ld] = a[0];
+        for (int n = 1; n < r; ++n) seg[(n * Mp + k) * ld] = cmul(a[n], tw[k * n * G]);
+      }
+    }
+    Ms = Mp;
+    G *= r;
+  }
+}
+
+template <typename C>
+MOMA_HD void fft_dit(C *col, int ld, const FftPlan &pl, const C *tw) {
+  const int M = pl.M;
+  int Ms = 1;
+  for (int s = pl.nst - 1; s >= 0; --s) {
+    const int r = pl.radix[s], Mp = Ms;
+    Ms *= r;
+    const int G = M / Ms;
+    for (int g = 0; g < G; ++g) {
+      C *seg = col + (size_t)g * Ms * ld;
+      for (int k = 0; k < Mp; ++k) {
+        C a[5];
+        a[0] = seg[k * ld];
+        for (int n = 1; n < r; ++n) a[n] = cmul(seg[(n * Mp + k) * ld], tw[k * n * G]);
+        butterfly(a, r, tw, M);
+        for (int n = 0; n < r; ++n) seg[(n * Mp + k) * ld] = a[n];
+      }
+    }
+  }
+}

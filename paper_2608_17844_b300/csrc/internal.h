@@ -1,0 +1,87 @@
+// Host-side declarations shared by the translation units of libmoma.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "fft.cuh"
+
+namespace moma {
+
+// ---------------------------------------------------------------- FFT ----
+// Device tables of one transform length: twiddles (both precisions) and
+// the digit-reversal permutation.
+struct FftTables {
+  FftPlan plan;
+  double2 *tw64 = nullptr;  // [M]
+  float2 *tw32 = nullptr;   // [M]
+  int *pos = nullptr;       // [M]
+};
+
+FftPlan make_plan(int M);
+std::vector<int> digit_reversal(const FftPlan &pl);
+bool smooth_235(int m);
+int next_smooth(int n);
+
+// A batch of 1D transforms along one axis of a strided array.  Line
+// (o1, o2), inner index j, axis position m sits at
+//   base + o1*s1 + o2*s2 + m*sm + j        (element units).
+struct AxisPass {
+  const void *in = nullptr;
+  void *out = nullptr;
+  void *out2 = nullptr;    // optional second output (always c64)
+  long long in_s1 = 0, in_s2 = 0, in_sm = 0;
+  long long out_s1 = 0, out_s2 = 0, out_sm = 0;
+  int n1 = 1, n2 = 1, ninner = 0;
+  int nin = 0;             // loaded points (the rest of the M-line is zero)
+  int nout = 0;            // stored points
+  int in_mode = 0;         // 0: point m <- axis index m; 1: circulant gather of 2N-1 offsets
+  int out_mode = 0;        // 0: point k -> axis index k; 1: k -> slot_of[k*slot_mul + o1]
+  const int *slot_of = nullptr;
+  int slot_mul = 0;
+  int remap_b = 0, remap_ld = 0;  // out_mode 1: inner j -> (j / remap_b) * remap_ld + j % remap_b
+  int inverse = 0;         // conj(DFT(conj x)) / M
+  int refft_keep = 0;      // >0: inverse, keep points < refft_keep, zero the rest, forward again
+  int in_c128 = 1, out_c128 = 1;  // element types of in / out
+};
+
+// Launch one axis pass computing in precision R (float or double).
+template <typename R>
+void launch_axis_pass(const AxisPass &p, const FftTables &t, cudaStream_t st);
+
+// --------------------------------------------------------- bin product ----
+struct BinProduct {
+  const void *Z = nullptr;    // pair storage [Bp][b][ldb]
+  const int2 *pairs = nullptr;  // [Bp] (ka, kb), ka <= kb
+  const void *x = nullptr;    // bins [B][nr][b]
+  void *y = nullptr;          // bins [B][nr][b]
+  int Bp = 0, b = 0, ldb = 0, nr = 0;
+  int herm = 0;
+  unsigned *err = nullptr;
+};
+template <typename R>
+void launch_bin_product(const BinProduct &p, int num_sms, cudaStream_t st);
+
+// ------------------------------------------------------ preconditioner ----
+// G_D = Z_D^H Z_D for every offset, output FP64 [nD][b][b].
+template <typename R>
+void launch_gram(const void *blocks, int blocks_c128, int nD, int b, double2 *G, cudaStream_t st);
+// In-place 2D inclusive prefix sum over the (2Ny-1) x (2Nx-1) offset grid.
+void launch_sat(double2 *S, int ndy, int ndx, int bb, cudaStream_t st);
+// Box sums + Cholesky: L_e (packed lower, column-major, FP64) for each element.
+void launch_box_cholesky(const double2 *S, int nx, int ny, int b, double2 *Lpk, unsigned *err, cudaStream_t st);
+// Full P_e (b x b, FP64) of one element from the summed-area table.
+void launch_box_one(const double2 *S, int nx, int ny, int b, int ex, int ey, double2 *out, cudaStream_t st);
+// Inverse factor X_e = L_e^{-1}, packed row-major lower, in precision R.
+template <typename R>
+void launch_tri_inverse(const double2 *Lpk, int nel, int b, void *X, size_t x_stride, cudaStream_t st);
+// y_e = X_e^H X_e x_e for each element.
+template <typename R>
+void launch_precond_apply(const void *X, size_t x_stride, int nel, int b, int nr, const void *x, void *y,
+                          unsigned *err, cudaStream_t st);
+
+// ------------------------------------------------------------- Krylov ----
+struct ArnoldiCtl;  // device-side control block (krylov.cu)
+}  // namespace moma

@@ -1,0 +1,376 @@
+// Restarted GMRES on the preconditioned normal equations (Sec. III-A:
+// P^{-1} Z^H Z I = P^{-1} Z^H V) inside an FP64 iterative-refinement loop.
+//
+// All nr right-hand sides run side by side, each with its own Krylov basis,
+// Hessenberg matrix and convergence state (column q freezes when its
+// residual estimate reaches its tolerance).  Orthogonalisation is classical
+// Gram-Schmidt with one re-orthogonalisation pass (CGS2), fused so that the
+// basis is swept three times per step:
+//   pass 1: h1 = V^H w
+//   pass 2: w -= V h1, then h2 = V^H w       (same sweep)
+//   pass 3: w -= V h2, then ||w||^2, Givens  (same sweep)
+// Each pass ends with a "last block done" reduction: every CTA writes its
+// partial sums, the last CTA to arrive (atomic ticket) adds them in a fixed
+// order, so results are deterministic and no CTA ever waits on another.
+// Dot products and norms accumulate in FP64; the Hessenberg matrix, the
+// Givens rotations and the small least-squares solve are FP64.
+#include "krylov.h"
+
+namespace moma {
+
+constexpr int KT = 256;   // threads per CTA
+constexpr int KEPT = 4;   // elements per thread
+constexpr int KG = 8;     // dot products reduced together
+
+// Block-wide sum of NV double2 values held by every thread; result valid in
+// thread 0 for all NV values (red must hold 8 * NV double2).
+template <int NV>
+MOMA_DEV void block_sum(double2 (&v)[NV], double2 *red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) v[i] = warp_sum(v[i]);
+  if (lane == 0)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) red[w * NV + i] = v[i];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      double2 s = red[i];
+      for (int ww = 1; ww < KT / 32; ++ww) s = cadd(s, red[ww * NV + i]);
+      v[i] = s;
+    }
+  }
+  __syncthreads();
+}
+
+// Givens step for column j of RHS q (thread-serial, FP64).
+MOMA_DEV void givens_step(const KrylovCtl &c, int q, int j, double wnorm) {
+  const int m = c.m;
+  double2 *h = c.hacc + (size_t)q * (m + 1);
+  double *cs = c.cs + (size_t)q * m;
+  double2 *sn = c.sn + (size_t)q * m;
+  double2 *g = c.g + (size_t)q * (m + 1);
+  h[j + 1] = make_double2(wnorm, 0.0);
+  for (int i = 0; i < j; ++i) {
+    const double2 a = h[i], bb = h[i + 1];
+    h[i] = cadd(cscale(a, cs[i]), cmul(sn[i], bb));
+    h[i + 1] = csub(cscale(bb, cs[i]), cmul(cconj(sn[i]), a));
+  }
+  const double2 f = h[j];
+  const double af = hypot(f.x, f.y);
+  const double t = hypot(af, wnorm);
+  if (af == 0.0) {
+    cs[j] = 0.0;
+    sn[j] = make_double2(1.0, 0.0);
+    h[j] = make_double2(wnorm, 0.0);
+  } else {
+    cs[j] = af / t;
+    const double2 ph = cscale(f, 1.0 / af);
+    sn[j] = cscale(ph, wnorm / t);  // (f/|f|) conj(g) / t with g = wnorm real
+    h[j] = cscale(ph, t);
+  }
+  h[j + 1] = make_double2(0.0, 0.0);
+  const double2 gj = g[j];
+  g[j + 1] = cscale(cmul(cconj(sn[j]), gj), -1.0);
+  g[j] = cscale(gj, cs[j]);
+  double2 *rc = c.Rm + ((size_t)q * m + j) * (m + 1);
+  for (int i = 0; i <= j; ++i) rc[i] = h[i];
+  const double res = hypot(g[j + 1].x, g[j + 1].y);
+  c.res[q] = res;
+  const bool conv = res <= c.tol[q];
+  // Lucky breakdown: the new direction vanished, the current space is invariant.
+  const bool breakdown = !(wnorm > 1e-300) || wnorm <= 1e-14 * c.beta[q];
+  if (conv || breakdown || j + 1 >= m || !isfinite(res)) {
+    c.kq[q] = j + 1;
+    c.active[q] = 0;
+    atomicSub(c.nact, 1);
+    c.inv_norm[q] = 0.0;
+    if (!isfinite(res)) atomicOr(c.err, DEVERR_NONFINITE);
+  } else {
+    c.inv_norm[q] = 1.0 / wnorm;
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(KT) cgs_kernel(KrylovCtl c, typename Cplx<R>::T *V, size_t vstride, int N, int j,
+                                                  int flags) {
+  using C = typename Cplx<R>::T;
+  __shared__ double2 red[8 * KG];
+  __shared__ C hs[MOMA_MAX_RESTART + 1];
+  __shared__ int last;
+  const int q = blockIdx.y, chunk = blockIdx.x, tid = threadIdx.x;
+  if (!c.active[q]) return;
+  const int m = c.m;
+  const size_t qoff = (size_t)q * N;
+  C *w = V + (size_t)(j + 1) * vstride + qoff;
+  const int n0 = chunk * KT * KEPT;
+
+  C wv[KEPT];
+#pragma unroll
+  for (int t = 0; t < KEPT; ++t) {
+    const int n = n0 + tid + KT * t;
+    wv[t] = n < N ? w[n] : czero<C>();
+  }
+  if (flags & KF_UPDATE) {
+    for (int i = tid; i <= j; i += KT) hs[i] = cvt<C>(c.hcur[(size_t)q * (m + 1) + i]);
+    __syncthreads();
+    for (int i = 0; i <= j; ++i) {
+      const C hi = hs[i];
+      const C *vi = V + (size_t)i * vstride + qoff;
+#pragma unroll
+      for (int t = 0; t < KEPT; ++t) {
+        const int n = n0 + tid + KT * t;
+        if (n < N) wv[t] = csub(wv[t], cmul(vi[n], hi));
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < KEPT; ++t) {
+      const int n = n0 + tid + KT * t;
+      if (n < N) w[n] = wv[t];
+    }
+  }
+  double2 *part = c.partial + ((size_t)q * gridDim.x + chunk) * (m + 1);
+  if (flags & KF_DOTS) {
+    for (int i0 = 0; i0 <= j; i0 += KG) {
+      double2 acc[KG];
+#pragma unroll
+      for (int ii = 0; ii < KG; ++ii) acc[ii] = make_double2(0, 0);
+#pragma unroll
+      for (int ii = 0; ii < KG; ++ii) {
+        const int i = i0 + ii;
+        if (i <= j) {
+          const C *vi = V + (size_t)i * vstride + qoff;
+#pragma unroll
+          for (int t = 0; t < KEPT; ++t) {
+            const int n = n0 + tid + KT * t;
+            if (n < N) acc[ii] = cfmac(cvt<double2>(vi[n]), cvt<double2>(wv[t]), acc[ii]);
+          }
+        }
+      }
+      block_sum<KG>(acc, red);
+      if (tid == 0)
+        for (int ii = 0; ii < KG && i0 + ii <= j; ++ii) part[i0 + ii] = acc[ii];
+    }
+  }
+  if (flags & KF_NORM) {
+    double2 acc[1] = {make_double2(0, 0)};
+#pragma unroll
+    for (int t = 0; t < KEPT; ++t) {
+      const double2 v = cvt<double2>(wv[t]);
+      acc[0].x += v.x * v.x + v.y * v.y;
+    }
+    block_sum<1>(acc, red);
+    if (tid == 0) part[0] = acc[0];
+  }
+
+  // Last-block reduction over the chunks of this RHS, in chunk order.
+  __threadfence();
+  if (tid == 0) last = (atomicAdd(&c.counters[q], 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const double2 *pq = c.partial + (size_t)q * gridDim.x * (m + 1);
+  if (flags & KF_DOTS) {
+    for (int i = tid; i <= j; i += KT) {
+      double2 s = make_double2(0, 0);
+      for (int ch = 0; ch < (int)gridDim.x; ++ch) s = cadd(s, pq[(size_t)ch * (m + 1) + i]);
+      double2 *ha = c.hacc + (size_t)q * (m + 1) + i;
+      *ha = (flags & KF_ACCUM) ? cadd(*ha, s) : s;
+      c.hcur[(size_t)q * (m + 1) + i] = s;
+    }
+  }
+  if ((flags & KF_NORM) && tid == 0) {
+    double s = 0;
+    for (int ch = 0; ch < (int)gridDim.x; ++ch) s += pq[(size_t)ch * (m + 1)].x;
+    const double nrm = sqrt(s);
+    if (flags & KF_INIT) {
+      c.beta[q] = nrm;
+      c.g[(size_t)q * (m + 1)] = make_double2(nrm, 0.0);
+      c.tol[q] = c.inner_tol * nrm;
+      c.res[q] = nrm;
+      if (nrm > 0.0 && isfinite(nrm)) {
+        c.inv_norm[q] = 1.0 / nrm;
+      } else {
+        if (!isfinite(nrm)) atomicOr(c.err, DEVERR_NONFINITE);
+        c.inv_norm[q] = 0.0;
+        c.active[q] = 0;
+        c.kq[q] = 0;
+        atomicSub(c.nact, 1);
+      }
+    } else {
+      givens_step(c, q, j, nrm);
+    }
+  }
+  if (tid == 0) c.counters[q] = 0;
+}
+
+// V[slot] *= inv_norm[q] (zero for frozen columns).
+template <typename R>
+__global__ void scale_kernel(KrylovCtl c, typename Cplx<R>::T *v, size_t vstride, int N, int nr) {
+  const size_t total = (size_t)nr * N;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const int q = (int)(idx / N);
+    v[idx] = cscale(v[idx], (decltype(v[0].x))c.inv_norm[q]);
+  }
+}
+
+// y = R^{-1} g per RHS (FP64 back substitution on the rotated Hessenberg).
+__global__ void backsolve_kernel(KrylovCtl c, int nr) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nr) return;
+  const int m = c.m, k = c.kq[q];
+  double2 *y = c.y + (size_t)q * m;
+  const double2 *g = c.g + (size_t)q * (m + 1);
+  for (int i = k - 1; i >= 0; --i) {
+    double2 s = g[i];
+    for (int jj = i + 1; jj < k; ++jj) s = csub(s, cmul(c.Rm[((size_t)q * m + jj) * (m + 1) + i], y[jj]));
+    const double2 d = c.Rm[((size_t)q * m + i) * (m + 1) + i];
+    const double den = d.x * d.x + d.y * d.y;
+    y[i] = cscale(cmul(s, cconj(d)), 1.0 / den);
+  }
+}
+
+// I[q] += scale[q] * sum_{i<kq} V[i][q] y[q][i]   (FP64 accumulation).
+template <typename R>
+__global__ void lincomb_kernel(KrylovCtl c, const typename Cplx<R>::T *V, size_t vstride, int N, int nr,
+                               double2 *I, const double *scale) {
+  const size_t total = (size_t)nr * N;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const int q = (int)(idx / N);
+    const int k = c.kq[q];
+    if (k == 0) continue;
+    const double2 *y = c.y + (size_t)q * c.m;
+    double2 s = make_double2(0, 0);
+    for (int i = 0; i < k; ++i) s = cfma(cvt<double2>(V[(size_t)i * vstride + idx]), y[i], s);
+    I[idx] = cadd(I[idx], cscale(s, scale[q]));
+  }
+}
+
+// ---------------------------------------------------------------- FP64 ----
+// r = V - y (y may be null: r = V); per-RHS ||r|| into out_norm; optional
+// copy of r scaled by 1/||r|| happens in a second kernel.  Last-block
+// reduction as above.
+__global__ void __launch_bounds__(KT) resid_kernel(const double2 *V, const double2 *y, double2 *r, int N,
+                                                   double *partial, unsigned *counters, double *out_norm) {
+  __shared__ double2 red[8];
+  __shared__ int last;
+  const int q = blockIdx.y, chunk = blockIdx.x, tid = threadIdx.x;
+  const size_t qoff = (size_t)q * N;
+  const int n0 = chunk * KT * KEPT;
+  double2 acc[1] = {make_double2(0, 0)};
+#pragma unroll
+  for (int t = 0; t < KEPT; ++t) {
+    const int n = n0 + tid + KT * t;
+    if (n < N) {
+      double2 v = V[qoff + n];
+      if (y) v = csub(v, y[qoff + n]);
+      if (r) r[qoff + n] = v;
+      acc[0].x += v.x * v.x + v.y * v.y;
+    }
+  }
+  block_sum<1>(acc, red);
+  if (tid == 0) partial[(size_t)q * gridDim.x + chunk] = acc[0].x;
+  __threadfence();
+  if (tid == 0) last = (atomicAdd(&counters[q], 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (tid == 0) {
+    double s = 0;
+    for (int ch = 0; ch < (int)gridDim.x; ++ch) s += partial[(size_t)q * gridDim.x + ch];
+    out_norm[q] = sqrt(s);
+    counters[q] = 0;
+  }
+}
+
+// dst[q] = src[q] / rnorm[q] in precision R, zero for columns with mask[q] == 0.
+template <typename R>
+__global__ void to_inner_kernel(const double2 *src, typename Cplx<R>::T *dst, int N, int nr, const double *rnorm,
+                                const int *mask) {
+  using C = typename Cplx<R>::T;
+  const size_t total = (size_t)nr * N;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const int q = (int)(idx / N);
+    dst[idx] = mask[q] ? cvt<C>(cscale(src[idx], 1.0 / rnorm[q])) : czero<C>();
+  }
+}
+
+// Port quantities (Eqs. 16-19).
+__global__ void ports_kernel(const double2 *I, const double2 *V, int nel, int b, int nr, int pb, double z0,
+                             double2 *Za, double2 *Gam, unsigned *err) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nel * nr) return;
+  const double2 ip = I[(size_t)idx * b + pb];
+  const double2 vp = V[(size_t)idx * b + pb];
+  const double den = ip.x * ip.x + ip.y * ip.y;
+  double2 za;
+  if (den == 0.0 || !isfinite(den)) {
+    za = make_double2(nan(""), nan(""));
+    atomicOr(err, DEVERR_NONFINITE);
+  } else {
+    za = cscale(cmul(vp, cconj(ip)), 1.0 / den);
+  }
+  Za[idx] = za;
+  if (Gam) {
+    const double2 num = make_double2(za.x - z0, za.y), dd = make_double2(za.x + z0, za.y);
+    const double d2 = dd.x * dd.x + dd.y * dd.y;
+    Gam[idx] = cscale(cmul(num, cconj(dd)), 1.0 / d2);
+  }
+}
+
+static int grid_for(size_t total) {
+  size_t g = (total + 255) / 256;
+  if (g > 4096) g = 4096;
+  return (int)(g < 1 ? 1 : g);
+}
+
+int krylov_chunks(int N) { return (N + KT * KEPT - 1) / (KT * KEPT); }
+
+template <typename R>
+void launch_cgs(const KrylovCtl &c, void *V, size_t vstride, int N, int nr, int j, int flags, cudaStream_t st) {
+  dim3 grid(krylov_chunks(N), nr);
+  cgs_kernel<R><<<grid, KT, 0, st>>>(c, reinterpret_cast<typename Cplx<R>::T *>(V), vstride, N, j, flags);
+}
+template <typename R>
+void launch_scale(const KrylovCtl &c, void *v, size_t vstride, int N, int nr, cudaStream_t st) {
+  scale_kernel<R><<<grid_for((size_t)nr * N), 256, 0, st>>>(c, reinterpret_cast<typename Cplx<R>::T *>(v), vstride,
+                                                              N, nr);
+}
+void launch_backsolve(const KrylovCtl &c, int nr, cudaStream_t st) {
+  backsolve_kernel<<<(nr + 63) / 64, 64, 0, st>>>(c, nr);
+}
+template <typename R>
+void launch_lincomb(const KrylovCtl &c, const void *V, size_t vstride, int N, int nr, double2 *I,
+                    const double *scale, cudaStream_t st) {
+  lincomb_kernel<R><<<grid_for((size_t)nr * N), 256, 0, st>>>(
+      c, reinterpret_cast<const typename Cplx<R>::T *>(V), vstride, N, nr, I, scale);
+}
+void launch_resid(const double2 *V, const double2 *y, double2 *r, int N, int nr, double *partial, unsigned *counters,
+                  double *out_norm, cudaStream_t st) {
+  dim3 grid(krylov_chunks(N), nr);
+  resid_kernel<<<grid, KT, 0, st>>>(V, y, r, N, partial, counters, out_norm);
+}
+template <typename R>
+void launch_to_inner(const double2 *src, void *dst, int N, int nr, const double *rnorm, const int *mask,
+                     cudaStream_t st) {
+  to_inner_kernel<R><<<grid_for((size_t)nr * N), 256, 0, st>>>(src, reinterpret_cast<typename Cplx<R>::T *>(dst), N,
+                                                                 nr, rnorm, mask);
+}
+void launch_ports(const double2 *I, const double2 *V, int nel, int b, int nr, int pb, double z0, double2 *Za,
+                  double2 *Gam, unsigned *err, cudaStream_t st) {
+  ports_kernel<<<(nel * nr + 255) / 256, 256, 0, st>>>(I, V, nel, b, nr, pb, z0, Za, Gam, err);
+}
+
+template void launch_cgs<float>(const KrylovCtl &, void *, size_t, int, int, int, int, cudaStream_t);
+template void launch_cgs<double>(const KrylovCtl &, void *, size_t, int, int, int, int, cudaStream_t);
+template void launch_scale<float>(const KrylovCtl &, void *, size_t, int, int, cudaStream_t);
+template void launch_scale<double>(const KrylovCtl &, void *, size_t, int, int, cudaStream_t);
+template void launch_lincomb<float>(const KrylovCtl &, const void *, size_t, int, int, double2 *, const double *,
+                                    cudaStream_t);
+template void launch_lincomb<double>(const KrylovCtl &, const void *, size_t, int, int, double2 *, const double *,
+                                     cudaStream_t);
+template void launch_to_inner<float>(const double2 *, void *, int, int, const double *, const int *, cudaStream_t);
+template void launch_to_inner<double>(const double2 *, void *, int, int, const double *, const int *, cudaStream_t);
+
+}  // namespace moma

@@ -1,0 +1,866 @@
+// C ABI of libmoma: handle management, device memory, and the host-side
+// orchestration of the set-up and solve pipelines (see include/moma.h).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "moma.h"
+#include "krylov.h"
+
+using namespace moma;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+struct MomaError : std::runtime_error {
+  moma_status st;
+  MomaError(moma_status s, const std::string &m) : std::runtime_error(m), st(s) {}
+};
+
+#define CK(call)                                                                                      \
+  do {                                                                                                \
+    cudaError_t e_ = (call);                                                                          \
+    if (e_ != cudaSuccess) {                                                                          \
+      cudaGetLastError();                                                                             \
+      throw MomaError(e_ == cudaErrorMemoryAllocation ? MOMA_ERR_OOM : MOMA_ERR_CUDA,                \
+                      std::string(#call) + ": " + cudaGetErrorString(e_));                            \
+    }                                                                                                 \
+  } while (0)
+
+bool is_device_ptr(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Grow-only device buffer.
+struct DevBuf {
+  void *p = nullptr;
+  size_t cap = 0;
+  void ensure(size_t bytes, size_t &total) {
+    if (bytes <= cap) return;
+    if (p) {
+      cudaFree(p);
+      total -= cap;
+      p = nullptr;
+      cap = 0;
+    }
+    void *q = nullptr;
+    CK(cudaMalloc(&q, bytes));
+    p = q;
+    cap = bytes;
+    total += bytes;
+  }
+  void release(size_t &total) {
+    if (p) cudaFree(p);
+    total -= cap;
+    p = nullptr;
+    cap = 0;
+  }
+  template <typename T> T *as() const { return reinterpret_cast<T *>(p); }
+};
+
+__global__ void nonfinite_kernel(const void *p, size_t n_real, int is_double, unsigned *err) {
+  bool bad = false;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n_real; i += (size_t)gridDim.x * blockDim.x) {
+    const double v = is_double ? reinterpret_cast<const double *>(p)[i] : (double)reinterpret_cast<const float *>(p)[i];
+    if (!isfinite(v)) bad = true;
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(err, DEVERR_NONFINITE);
+}
+
+enum { PK_BIN64 = 0, PK_BIN128 = 1, PK_PREC = 2, PK_FFT64 = 3, PK_BLOCKFFT = 4, PK_FFT128 = 5, PK_N = 6 };
+
+}  // namespace
+
+struct moma_array {
+  int nx = 0, ny = 0, b = 0, nel = 0, N = 0;
+  int Mx = 0, My = 0, B = 0, Bp = 0, ldb = 0;
+  int prec = MOMA_PREC_MIXED, m = 50;
+  cudaStream_t st = nullptr;
+  int dev = 0, num_sms = 148;
+  size_t dev_bytes = 0;
+  long long launches = 0;
+
+  FftTables fx, fy;
+  DevBuf tabs;      // twiddles / permutations of both plans
+  DevBuf pairs, slot_of;
+  DevBuf Z128, Z64;  // pair storage [Bp][b][ldb]
+  DevBuf Xinv;       // inverse factors, packed row-major, inner precision
+  size_t x_stride = 0;
+  bool have_blocks = false;
+
+  // set-up workspace
+  DevBuf blk, T, S, Lpk;
+  // solve workspace
+  int ws_nr = 0;
+  DevBuf lat_in, lat_tmp, t1, bx, by, Vk;
+  DevBuf Iw, Vw, rw, yw;
+  DevBuf kbuf;  // Krylov control arrays
+  KrylovCtl ctl{};
+  double *rnorm = nullptr, *vnorm = nullptr, *rpart = nullptr;
+  unsigned *rcount = nullptr;
+  int *mask = nullptr;
+  DevBuf errbuf;
+  unsigned *err = nullptr;
+  DevBuf one_blk;
+  DevBuf portsb;  // Z_a and Gamma results [2][nr][nel]
+
+  // pinned host mirrors
+  int *h_nact = nullptr;  // ring of polled nact values
+  double *h_norms = nullptr;
+  unsigned *h_err = nullptr;
+  std::vector<cudaEvent_t> poll_ev;
+
+  // profiling
+  bool prof = false;
+  struct EvPair { cudaEvent_t a, b; int kind; };
+  std::vector<EvPair> ev_pending;
+  std::vector<cudaEvent_t> ev_free;
+  long long st_launch[PK_N] = {0};
+  double st_ms[PK_N] = {0};
+
+  cudaEvent_t ev_get() {
+    if (!ev_free.empty()) {
+      cudaEvent_t e = ev_free.back();
+      ev_free.pop_back();
+      return e;
+    }
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e));
+    return e;
+  }
+  void flush_events() {
+    for (auto &p : ev_pending) {
+      float ms = 0;
+      if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+        st_ms[p.kind] += ms;
+        st_launch[p.kind] += 1;
+      } else {
+        cudaGetLastError();
+      }
+      ev_free.push_back(p.a);
+      ev_free.push_back(p.b);
+    }
+    ev_pending.clear();
+  }
+  template <typename F> void timed(int kind, F &&f) {
+    if (!prof) {
+      f();
+      return;
+    }
+    cudaEvent_t a = ev_get(), b2 = ev_get();
+    CK(cudaEventRecord(a, st));
+    f();
+    CK(cudaEventRecord(b2, st));
+    ev_pending.push_back({a, b2, kind});
+    if (ev_pending.size() > 8192) flush_events();
+  }
+};
+
+namespace {
+
+void check_launch(moma_array *a) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) throw MomaError(MOMA_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+  a->launches += 1;
+}
+
+void build_tables(moma_array *a) {
+  a->fx.plan = make_plan(a->Mx);
+  a->fy.plan = make_plan(a->My);
+  auto px = digit_reversal(a->fx.plan), py = digit_reversal(a->fy.plan);
+  const int Ms[2] = {a->Mx, a->My};
+  size_t bytes = 0;
+  for (int M : Ms) bytes += (size_t)M * (sizeof(double2) + sizeof(float2) + sizeof(int)) + 256;
+  a->tabs.ensure(bytes, a->dev_bytes);
+  std::vector<unsigned char> host(bytes, 0);
+  size_t off = 0;
+  FftTables *tt[2] = {&a->fx, &a->fy};
+  const std::vector<int> *pp[2] = {&px, &py};
+  for (int d = 0; d < 2; ++d) {
+    const int M = Ms[d];
+    double2 *t64 = reinterpret_cast<double2 *>(host.data() + off);
+    tt[d]->tw64 = reinterpret_cast<double2 *>(a->tabs.as<unsigned char>() + off);
+    off += (size_t)M * sizeof(double2);
+    float2 *t32 = reinterpret_cast<float2 *>(host.data() + off);
+    tt[d]->tw32 = reinterpret_cast<float2 *>(a->tabs.as<unsigned char>() + off);
+    off += (size_t)M * sizeof(float2);
+    int *ps = reinterpret_cast<int *>(host.data() + off);
+    tt[d]->pos = reinterpret_cast<int *>(a->tabs.as<unsigned char>() + off);
+    off += (size_t)M * sizeof(int);
+    off = (off + 255) & ~size_t(255);
+    for (int t = 0; t < M; ++t) {
+      const double ang = -2.0 * M_PI * (double)t / (double)M;
+      t64[t] = make_double2(std::cos(ang), std::sin(ang));
+      t32[t] = make_float2((float)t64[t].x, (float)t64[t].y);
+      ps[t] = (*pp[d])[t];
+    }
+  }
+  CK(cudaMemcpy(a->tabs.p, host.data(), bytes, cudaMemcpyHostToDevice));
+
+  // Bin pairs {k, -k}; the smaller index is stored.
+  std::vector<int> slot(a->B, -1);
+  std::vector<int2> pr;
+  for (int ky = 0; ky < a->My; ++ky)
+    for (int kx = 0; kx < a->Mx; ++kx) {
+      const int k = ky * a->Mx + kx;
+      const int nk = ((a->My - ky) % a->My) * a->Mx + ((a->Mx - kx) % a->Mx);
+      if (k <= nk) {
+        slot[k] = (int)pr.size();
+        pr.push_back(make_int2(k, nk));
+      }
+    }
+  a->Bp = (int)pr.size();
+  a->pairs.ensure(pr.size() * sizeof(int2), a->dev_bytes);
+  a->slot_of.ensure(slot.size() * sizeof(int), a->dev_bytes);
+  CK(cudaMemcpy(a->pairs.p, pr.data(), pr.size() * sizeof(int2), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(a->slot_of.p, slot.data(), slot.size() * sizeof(int), cudaMemcpyHostToDevice));
+}
+
+// ----------------------------------------------------- axis pass builders --
+AxisPass pass_fx(moma_array *a, int nr, const void *in, void *out, int in128, int out128) {
+  AxisPass p;
+  p.in = in; p.out = out; p.n1 = nr; p.n2 = a->ny; p.ninner = a->b;
+  p.in_s1 = (long long)a->ny * a->nx * a->b; p.in_s2 = (long long)a->nx * a->b; p.in_sm = a->b; p.nin = a->nx;
+  p.out_s1 = (long long)a->ny * a->Mx * a->b; p.out_s2 = (long long)a->Mx * a->b; p.out_sm = a->b; p.nout = a->Mx;
+  p.in_c128 = in128; p.out_c128 = out128;
+  return p;
+}
+AxisPass pass_fy(moma_array *a, int nr, const void *in, void *out, int c128) {
+  AxisPass p;
+  p.in = in; p.out = out; p.n1 = nr; p.n2 = a->Mx; p.ninner = a->b;
+  p.in_s1 = (long long)a->ny * a->Mx * a->b; p.in_s2 = a->b; p.in_sm = (long long)a->Mx * a->b; p.nin = a->ny;
+  p.out_s1 = a->b; p.out_s2 = (long long)nr * a->b; p.out_sm = (long long)a->Mx * nr * a->b; p.nout = a->My;
+  p.in_c128 = p.out_c128 = c128;
+  return p;
+}
+AxisPass pass_iy(moma_array *a, int nr, const void *in, void *out, int c128) {
+  AxisPass p;
+  p.in = in; p.out = out; p.n1 = nr; p.n2 = a->Mx; p.ninner = a->b; p.inverse = 1;
+  p.in_s1 = a->b; p.in_s2 = (long long)nr * a->b; p.in_sm = (long long)a->Mx * nr * a->b; p.nin = a->My;
+  p.out_s1 = (long long)a->ny * a->Mx * a->b; p.out_s2 = a->b; p.out_sm = (long long)a->Mx * a->b; p.nout = a->ny;
+  p.in_c128 = p.out_c128 = c128;
+  return p;
+}
+AxisPass pass_ix(moma_array *a, int nr, const void *in, void *out, int c128, bool mask_refft) {
+  AxisPass p;
+  p.in = in; p.out = out; p.n1 = nr; p.n2 = a->ny; p.ninner = a->b; p.inverse = 1;
+  p.in_s1 = (long long)a->ny * a->Mx * a->b; p.in_s2 = (long long)a->Mx * a->b; p.in_sm = a->b; p.nin = a->Mx;
+  if (mask_refft) {
+    p.refft_keep = a->nx;
+    p.out_s1 = p.in_s1; p.out_s2 = p.in_s2; p.out_sm = p.in_sm; p.nout = a->Mx;
+  } else {
+    p.out_s1 = (long long)a->ny * a->nx * a->b; p.out_s2 = (long long)a->nx * a->b; p.out_sm = a->b; p.nout = a->nx;
+  }
+  p.in_c128 = p.out_c128 = c128;
+  return p;
+}
+
+template <typename R> constexpr int is64() { return sizeof(R) == 8 ? 1 : 0; }
+
+template <typename R>
+void axis(moma_array *a, const AxisPass &p, const FftTables &t) {
+  a->timed(is64<R>() ? PK_FFT128 : PK_FFT64, [&] { launch_axis_pass<R>(p, t, a->st); });
+  check_launch(a);
+}
+
+template <typename R>
+void binprod(moma_array *a, int nr, const void *x, void *y, int herm) {
+  BinProduct P;
+  P.Z = is64<R>() ? a->Z128.p : a->Z64.p;
+  P.pairs = a->pairs.as<int2>();
+  P.x = x; P.y = y; P.Bp = a->Bp; P.b = a->b; P.ldb = a->ldb; P.nr = nr; P.herm = herm; P.err = a->err;
+  a->timed(is64<R>() ? PK_BIN128 : PK_BIN64, [&] { launch_bin_product<R>(P, a->num_sms, a->st); });
+  check_launch(a);
+}
+
+template <typename R>
+void precond(moma_array *a, int nr, const void *x, void *y) {
+  a->timed(PK_PREC, [&] { launch_precond_apply<R>(a->Xinv.p, a->x_stride, a->nel, a->b, nr, x, y, a->err, a->st); });
+  check_launch(a);
+}
+
+// lattice -> bins (Fx then Fy); in may be c128 when R is double.
+template <typename R>
+void lattice_to_bins(moma_array *a, int nr, const void *in, int in128) {
+  axis<R>(a, pass_fx(a, nr, in, a->t1.p, in128, is64<R>()), a->fx);
+  axis<R>(a, pass_fy(a, nr, a->t1.p, a->bx.p, is64<R>()), a->fy);
+}
+template <typename R>
+void bins_to_lattice(moma_array *a, int nr, const void *bins, void *out) {
+  axis<R>(a, pass_iy(a, nr, bins, a->t1.p, is64<R>()), a->fy);
+  axis<R>(a, pass_ix(a, nr, a->t1.p, out, is64<R>(), false), a->fx);
+}
+
+// y = Z x (herm = 0) or Z^H x (herm = 1), lattice in/out in precision R.
+template <typename R>
+void apply_z(moma_array *a, int nr, const void *x, void *y, int herm) {
+  lattice_to_bins<R>(a, nr, x, is64<R>());
+  binprod<R>(a, nr, a->bx.p, a->by.p, herm);
+  bins_to_lattice<R>(a, nr, a->by.p, y);
+}
+
+// y = P^{-1} Z^H M Z x, M the restriction to the lattice (mask between legs).
+template <typename R>
+void apply_normal(moma_array *a, int nr, const void *x, void *y) {
+  lattice_to_bins<R>(a, nr, x, is64<R>());
+  binprod<R>(a, nr, a->bx.p, a->by.p, 0);
+  axis<R>(a, pass_iy(a, nr, a->by.p, a->t1.p, is64<R>()), a->fy);
+  axis<R>(a, pass_ix(a, nr, a->t1.p, a->t1.p, is64<R>(), true), a->fx);
+  axis<R>(a, pass_fy(a, nr, a->t1.p, a->bx.p, is64<R>()), a->fy);
+  binprod<R>(a, nr, a->bx.p, a->by.p, 1);
+  bins_to_lattice<R>(a, nr, a->by.p, a->lat_tmp.p);
+  precond<R>(a, nr, a->lat_tmp.p, y);
+}
+
+// y = P^{-1} Z^H x.
+template <typename R>
+void apply_zh_p(moma_array *a, int nr, const void *x, void *y) {
+  apply_z<R>(a, nr, x, a->lat_tmp.p, 1);
+  precond<R>(a, nr, a->lat_tmp.p, y);
+}
+
+void sync_and_check(moma_array *a) {
+  CK(cudaMemcpyAsync(a->h_err, a->err, sizeof(unsigned), cudaMemcpyDeviceToHost, a->st));
+  CK(cudaStreamSynchronize(a->st));
+  const unsigned e = *a->h_err;
+  if (e) {
+    CK(cudaMemsetAsync(a->err, 0, sizeof(unsigned), a->st));
+    CK(cudaStreamSynchronize(a->st));
+    if (e & DEVERR_TIMEOUT) throw MomaError(MOMA_ERR_TIMEOUT, "a bounded device wait gave up");
+    if (e & DEVERR_NOT_PD) throw MomaError(MOMA_ERR_NOT_PD, "a preconditioner block is not positive definite");
+    if (e & DEVERR_NONFINITE) throw MomaError(MOMA_ERR_NONFINITE, "non-finite value in input or result");
+  }
+}
+
+void check_finite(moma_array *a, const void *p, size_t n_real, int is_double) {
+  if (n_real == 0) return;
+  size_t g = (n_real + 255) / 256;
+  if (g > 2048) g = 2048;
+  nonfinite_kernel<<<(int)g, 256, 0, a->st>>>(p, n_real, is_double, a->err);
+  check_launch(a);
+}
+
+void ensure_ws(moma_array *a, int nr) {
+  if (nr <= a->ws_nr) return;
+  const size_t c = sizeof(double2);
+  const size_t lat = (size_t)nr * a->N;
+  const size_t tsz = (size_t)nr * a->ny * a->Mx * a->b;
+  const size_t bsz = (size_t)a->B * nr * a->b;
+  a->lat_in.ensure(lat * c, a->dev_bytes);
+  a->lat_tmp.ensure(lat * c, a->dev_bytes);
+  a->t1.ensure(tsz * c, a->dev_bytes);
+  a->bx.ensure(bsz * c, a->dev_bytes);
+  a->by.ensure(bsz * c, a->dev_bytes);
+  const size_t esz = a->prec == MOMA_PREC_FP64 ? sizeof(double2) : sizeof(float2);
+  a->Vk.ensure((size_t)(a->m + 1) * lat * esz, a->dev_bytes);
+  a->Iw.ensure(lat * c, a->dev_bytes);
+  a->Vw.ensure(lat * c, a->dev_bytes);
+  a->rw.ensure(lat * c, a->dev_bytes);
+  a->yw.ensure(lat * c, a->dev_bytes);
+  // Krylov control arrays
+  const int m = a->m, nch = krylov_chunks(a->N);
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off = (off + bytes + 255) & ~size_t(255); return o; };
+  const size_t o_active = take(nr * sizeof(int)), o_kq = take(nr * sizeof(int)), o_nact = take(sizeof(int));
+  const size_t o_beta = take(nr * sizeof(double)), o_tol = take(nr * sizeof(double)), o_res = take(nr * sizeof(double));
+  const size_t o_inv = take(nr * sizeof(double)), o_cnt = take(nr * sizeof(unsigned) * 2);
+  const size_t o_part = take((size_t)nr * nch * (m + 1) * c), o_hacc = take((size_t)nr * (m + 1) * c);
+  const size_t o_hcur = take((size_t)nr * (m + 1) * c), o_R = take((size_t)nr * m * (m + 1) * c);
+  const size_t o_cs = take((size_t)nr * m * sizeof(double)), o_sn = take((size_t)nr * m * c);
+  const size_t o_g = take((size_t)nr * (m + 1) * c), o_y = take((size_t)nr * m * c);
+  const size_t o_rn = take(nr * sizeof(double)), o_vn = take(nr * sizeof(double));
+  const size_t o_rp = take((size_t)nr * nch * sizeof(double)), o_mask = take(nr * sizeof(int));
+  a->kbuf.ensure(off, a->dev_bytes);
+  unsigned char *base = a->kbuf.as<unsigned char>();
+  CK(cudaMemset(base, 0, off));
+  KrylovCtl &k = a->ctl;
+  k.m = m;
+  k.active = reinterpret_cast<int *>(base + o_active);
+  k.kq = reinterpret_cast<int *>(base + o_kq);
+  k.nact = reinterpret_cast<int *>(base + o_nact);
+  k.beta = reinterpret_cast<double *>(base + o_beta);
+  k.tol = reinterpret_cast<double *>(base + o_tol);
+  k.res = reinterpret_cast<double *>(base + o_res);
+  k.inv_norm = reinterpret_cast<double *>(base + o_inv);
+  k.counters = reinterpret_cast<unsigned *>(base + o_cnt);
+  k.partial = reinterpret_cast<double2 *>(base + o_part);
+  k.hacc = reinterpret_cast<double2 *>(base + o_hacc);
+  k.hcur = reinterpret_cast<double2 *>(base + o_hcur);
+  k.Rm = reinterpret_cast<double2 *>(base + o_R);
+  k.cs = reinterpret_cast<double *>(base + o_cs);
+  k.sn = reinterpret_cast<double2 *>(base + o_sn);
+  k.g = reinterpret_cast<double2 *>(base + o_g);
+  k.y = reinterpret_cast<double2 *>(base + o_y);
+  k.err = a->err;
+  a->rnorm = reinterpret_cast<double *>(base + o_rn);
+  a->vnorm = reinterpret_cast<double *>(base + o_vn);
+  a->rpart = reinterpret_cast<double *>(base + o_rp);
+  a->rcount = k.counters + nr;
+  a->mask = reinterpret_cast<int *>(base + o_mask);
+  if (a->h_norms) cudaFreeHost(a->h_norms);
+  CK(cudaMallocHost(&a->h_norms, (size_t)3 * nr * sizeof(double) + 64));
+  a->ws_nr = nr;
+}
+
+// Stage a caller buffer on the device: returns a device pointer (the
+// caller's own if it is device memory, else `tmp` after a copy).
+const void *stage_in(moma_array *a, const void *src, size_t bytes, DevBuf &tmp) {
+  if (is_device_ptr(src)) return src;
+  tmp.ensure(bytes, a->dev_bytes);
+  CK(cudaMemcpyAsync(tmp.p, src, bytes, cudaMemcpyHostToDevice, a->st));
+  return tmp.p;
+}
+
+void copy_out(moma_array *a, void *dst, const void *src, size_t bytes) {
+  CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, a->st));
+}
+
+template <typename R>
+void build_preconditioner(moma_array *a, const void *blk, int blk128) {
+  const int nD = (2 * a->nx - 1) * (2 * a->ny - 1), bb = a->b * a->b;
+  a->S.ensure((size_t)nD * bb * sizeof(double2), a->dev_bytes);
+  launch_gram<R>(blk, blk128, nD, a->b, a->S.as<double2>(), a->st);
+  check_launch(a);
+  launch_sat(a->S.as<double2>(), 2 * a->ny - 1, 2 * a->nx - 1, bb, a->st);
+  check_launch(a);
+  const size_t npk = (size_t)a->b * (a->b + 1) / 2;
+  a->Lpk.ensure((size_t)a->nel * npk * sizeof(double2), a->dev_bytes);
+  launch_box_cholesky(a->S.as<double2>(), a->nx, a->ny, a->b, a->Lpk.as<double2>(), a->err, a->st);
+  check_launch(a);
+  using C = typename Cplx<R>::T;
+  size_t xs = npk;
+  while ((xs * sizeof(C)) % 16) ++xs;
+  a->x_stride = xs;
+  a->Xinv.ensure((size_t)a->nel * xs * sizeof(C), a->dev_bytes);
+  launch_tri_inverse<R>(a->Lpk.as<double2>(), a->nel, a->b, a->Xinv.p, xs, a->st);
+  check_launch(a);
+}
+
+void set_blocks_impl(moma_array *a, const void *blocks, int dtype) {
+  if (dtype != MOMA_C128 && dtype != MOMA_C64) throw MomaError(MOMA_ERR_ARG, "blocks dtype must be MOMA_C128 or MOMA_C64");
+  if (!blocks) throw MomaError(MOMA_ERR_ARG, "blocks is NULL");
+  const int nD = (2 * a->nx - 1) * (2 * a->ny - 1), bb = a->b * a->b;
+  const size_t esz = dtype == MOMA_C128 ? sizeof(double2) : sizeof(float2);
+  const void *blk = stage_in(a, blocks, (size_t)nD * bb * esz, a->blk);
+  a->have_blocks = false;
+  check_finite(a, blk, (size_t)nD * bb * 2, dtype == MOMA_C128);
+  sync_and_check(a);
+
+  // Transformed first column of the circulant embedding (Eqs. 3, 11), FP64.
+  a->T.ensure((size_t)(2 * a->ny - 1) * a->Mx * bb * sizeof(double2), a->dev_bytes);
+  AxisPass px;
+  px.in = blk; px.out = a->T.p; px.n1 = 2 * a->ny - 1; px.n2 = 1; px.ninner = bb;
+  px.in_s1 = (long long)(2 * a->nx - 1) * bb; px.in_sm = bb; px.nin = 2 * a->nx - 1; px.in_mode = 1;
+  px.out_s1 = (long long)a->Mx * bb; px.out_sm = bb; px.nout = a->Mx;
+  px.in_c128 = dtype == MOMA_C128; px.out_c128 = 1;
+  a->timed(PK_BLOCKFFT, [&] { launch_axis_pass<double>(px, a->fx, a->st); });
+  check_launch(a);
+  AxisPass py;
+  py.in = a->T.p; py.out = a->Z128.p; py.out2 = a->prec == MOMA_PREC_MIXED ? a->Z64.p : nullptr;
+  py.n1 = a->Mx; py.n2 = 1; py.ninner = bb;
+  py.in_s1 = bb; py.in_sm = (long long)a->Mx * bb; py.nin = 2 * a->ny - 1; py.in_mode = 1;
+  py.out_mode = 1; py.slot_of = a->slot_of.as<int>(); py.slot_mul = a->Mx;
+  py.out_sm = (long long)a->b * a->ldb; py.remap_b = a->b; py.remap_ld = a->ldb; py.nout = a->My;
+  py.in_c128 = 1; py.out_c128 = 1;
+  a->timed(PK_BLOCKFFT, [&] { launch_axis_pass<double>(py, a->fy, a->st); });
+  check_launch(a);
+
+  // Preconditioner (Eq. 37) and its factorisation (Sec. III-A).
+  if (a->prec == MOMA_PREC_FP64) build_preconditioner<double>(a, blk, dtype == MOMA_C128);
+  else build_preconditioner<float>(a, blk, dtype == MOMA_C128);
+  sync_and_check(a);
+  a->have_blocks = true;
+}
+
+template <typename R>
+void gmres_cycle(moma_array *a, int nr, const std::vector<int> &act, int *inner_iters, double *first_red) {
+  using C = typename Cplx<R>::T;
+  const size_t vstride = (size_t)nr * a->N;
+  C *V = a->Vk.as<C>();
+  KrylovCtl c = a->ctl;
+  // Inner right-hand side P^{-1} Z^H r~ into slot 0; its norm starts the cycle.
+  apply_zh_p<R>(a, nr, a->lat_in.p, V);
+  int nact = 0;
+  for (int q = 0; q < nr; ++q) nact += act[q] ? 1 : 0;
+  a->h_nact[MOMA_MAX_RESTART + 4] = nact;  // pinned staging slot
+  CK(cudaMemcpyAsync(c.active, a->mask, nr * sizeof(int), cudaMemcpyDeviceToDevice, a->st));
+  CK(cudaMemsetAsync(c.kq, 0, nr * sizeof(int), a->st));
+  CK(cudaMemcpyAsync(c.nact, a->h_nact + MOMA_MAX_RESTART + 4, sizeof(int), cudaMemcpyHostToDevice, a->st));
+  launch_cgs<R>(c, V, vstride, a->N, nr, -1, KF_NORM | KF_INIT, a->st);
+  check_launch(a);
+  launch_scale<R>(c, V, vstride, a->N, nr, a->st);
+  check_launch(a);
+
+  const int lag = 2;
+  if ((int)a->poll_ev.size() < a->m + 1) {
+    while ((int)a->poll_ev.size() < a->m + 1) {
+      cudaEvent_t e;
+      CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      a->poll_ev.push_back(e);
+    }
+  }
+  int steps = 0;
+  for (int j = 0; j < a->m; ++j) {
+    apply_normal<R>(a, nr, V + (size_t)j * vstride, V + (size_t)(j + 1) * vstride);
+    launch_cgs<R>(c, V, vstride, a->N, nr, j, KF_DOTS, a->st);
+    check_launch(a);
+    launch_cgs<R>(c, V, vstride, a->N, nr, j, KF_UPDATE | KF_DOTS | KF_ACCUM, a->st);
+    check_launch(a);
+    launch_cgs<R>(c, V, vstride, a->N, nr, j, KF_UPDATE | KF_NORM, a->st);
+    check_launch(a);
+    launch_scale<R>(c, V + (size_t)(j + 1) * vstride, vstride, a->N, nr, a->st);
+    check_launch(a);
+    CK(cudaMemcpyAsync(a->h_nact + j, c.nact, sizeof(int), cudaMemcpyDeviceToHost, a->st));
+    CK(cudaEventRecord(a->poll_ev[j], a->st));
+    steps = j + 1;
+    if (j >= lag) {
+      CK(cudaEventSynchronize(a->poll_ev[j - lag]));
+      if (a->h_nact[j - lag] == 0) break;
+    }
+  }
+  CK(cudaStreamSynchronize(a->st));
+  int done_at = steps;
+  for (int j = 0; j < steps; ++j)
+    if (a->h_nact[j] == 0) { done_at = j + 1; break; }
+  *inner_iters += done_at;
+  if (first_red) {
+    std::vector<double> res(nr), beta(nr);
+    CK(cudaMemcpy(res.data(), c.res, nr * sizeof(double), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(beta.data(), c.beta, nr * sizeof(double), cudaMemcpyDeviceToHost));
+    double mx = 0;
+    for (int q = 0; q < nr; ++q)
+      if (act[q] && beta[q] > 0) mx = std::max(mx, res[q] / beta[q]);
+    *first_red = mx;
+  }
+  launch_backsolve(c, nr, a->st);
+  check_launch(a);
+  launch_lincomb<R>(c, V, vstride, a->N, nr, a->Iw.as<double2>(), a->rnorm, a->st);
+  check_launch(a);
+}
+
+template <typename R>
+void solve_impl(moma_array *a, int nr, const void *Vin, void *Iout, const moma_solve_opts *o, moma_solve_info *info,
+                double *relres) {
+  const double tol = (o && o->tol > 0) ? o->tol : 1e-10;
+  const double itol = (o && o->inner_tol > 0) ? o->inner_tol : (is64<R>() ? tol * 0.1 : 1e-5);
+  const int max_outer = (o && o->max_outer > 0) ? o->max_outer : 30;
+  const bool warm = o && o->warm_start;
+  const size_t bytes = (size_t)nr * a->N * sizeof(double2);
+  a->ctl.inner_tol = itol;
+
+  // Inputs into the solver's own buffers.
+  CK(cudaMemcpyAsync(a->Vw.p, Vin, bytes, cudaMemcpyDefault, a->st));
+  if (warm) CK(cudaMemcpyAsync(a->Iw.p, Iout, bytes, cudaMemcpyDefault, a->st));
+  else CK(cudaMemsetAsync(a->Iw.p, 0, bytes, a->st));
+  check_finite(a, a->Vw.p, (size_t)nr * a->N * 2, 1);
+  launch_resid(a->Vw.as<double2>(), nullptr, nullptr, a->N, nr, a->rpart, a->rcount, a->vnorm, a->st);
+  check_launch(a);
+  sync_and_check(a);
+
+  std::vector<double> vn(nr), rn(nr), rel(nr);
+  std::vector<int> mask(nr);
+  CK(cudaMemcpy(vn.data(), a->vnorm, nr * sizeof(double), cudaMemcpyDeviceToHost));
+  int outer = 0, inner = 0;
+  double first_red = -1;
+  bool converged = false;
+  for (;;) {
+    // True residual r = V - Z I in FP64 (c128 bins); I = 0 needs no product.
+    if (outer == 0 && !warm) {
+      launch_resid(a->Vw.as<double2>(), nullptr, a->rw.as<double2>(), a->N, nr, a->rpart, a->rcount, a->rnorm, a->st);
+    } else {
+      apply_z<double>(a, nr, a->Iw.p, a->yw.p, 0);
+      launch_resid(a->Vw.as<double2>(), a->yw.as<double2>(), a->rw.as<double2>(), a->N, nr, a->rpart, a->rcount,
+                   a->rnorm, a->st);
+    }
+    check_launch(a);
+    CK(cudaMemcpyAsync(a->h_norms, a->rnorm, nr * sizeof(double), cudaMemcpyDeviceToHost, a->st));
+    sync_and_check(a);
+    std::memcpy(rn.data(), a->h_norms, nr * sizeof(double));
+    int nact = 0;
+    for (int q = 0; q < nr; ++q) {
+      if (!std::isfinite(rn[q])) throw MomaError(MOMA_ERR_NONFINITE, "non-finite residual");
+      rel[q] = vn[q] > 0 ? rn[q] / vn[q] : 0.0;
+      mask[q] = rel[q] > tol ? 1 : 0;
+      nact += mask[q];
+    }
+    if (nact == 0) { converged = true; break; }
+    if (outer >= max_outer) break;
+    CK(cudaMemcpyAsync(a->mask, mask.data(), nr * sizeof(int), cudaMemcpyHostToDevice, a->st));
+    launch_to_inner<R>(a->rw.as<double2>(), a->lat_in.p, a->N, nr, a->rnorm, a->mask, a->st);
+    check_launch(a);
+    gmres_cycle<R>(a, nr, mask, &inner, outer == 0 ? &first_red : nullptr);
+    sync_and_check(a);
+    ++outer;
+  }
+  copy_out(a, Iout, a->Iw.p, bytes);
+  CK(cudaStreamSynchronize(a->st));
+  double mx = 0;
+  for (int q = 0; q < nr; ++q) mx = std::max(mx, rel[q]);
+  if (relres) std::memcpy(relres, rel.data(), nr * sizeof(double));
+  if (info) {
+    info->outer_iters = outer;
+    info->inner_iters = inner;
+    info->converged = converged ? 1 : 0;
+    info->max_rel_residual = mx;
+    info->first_inner_reduction = first_red;
+  }
+  if (!converged) throw MomaError(MOMA_ERR_NOT_CONVERGED, "solve reached max_outer before tol");
+}
+
+template <typename F> moma_status guarded(F &&f) {
+  try {
+    f();
+    return MOMA_OK;
+  } catch (const MomaError &e) {
+    g_last_error = e.what();
+    return e.st;
+  } catch (const std::bad_alloc &) {
+    g_last_error = "host allocation failed";
+    return MOMA_ERR_OOM;
+  } catch (const std::exception &e) {
+    g_last_error = e.what();
+    return MOMA_ERR_ARG;
+  }
+}
+
+void destroy_impl(moma_array *a) {
+  DevBuf *bufs[] = {&a->tabs, &a->pairs, &a->slot_of, &a->Z128, &a->Z64, &a->Xinv, &a->blk, &a->T, &a->S,
+                    &a->Lpk, &a->lat_in, &a->lat_tmp, &a->t1, &a->bx, &a->by, &a->Vk, &a->Iw, &a->Vw,
+                    &a->rw, &a->yw, &a->kbuf, &a->errbuf, &a->one_blk, &a->portsb};
+  for (DevBuf *b : bufs) b->release(a->dev_bytes);
+  if (a->h_nact) cudaFreeHost(a->h_nact);
+  if (a->h_norms) cudaFreeHost(a->h_norms);
+  if (a->h_err) cudaFreeHost(a->h_err);
+  for (auto e : a->poll_ev) cudaEventDestroy(e);
+  for (auto &p : a->ev_pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+  for (auto e : a->ev_free) cudaEventDestroy(e);
+  delete a;
+}
+
+}  // namespace
+
+// ===================================================================== ABI ==
+extern "C" {
+
+const char *moma_last_error(void) { return g_last_error.c_str(); }
+
+moma_status moma_create_array(int nx, int ny, int b, const moma_options *opt, void *cuda_stream, moma_array **out) {
+  if (out) *out = nullptr;
+  moma_array *a = nullptr;
+  moma_status s = guarded([&] {
+    if (!out) throw MomaError(MOMA_ERR_ARG, "out is NULL");
+    if (nx < 1 || ny < 1 || b < 1) throw MomaError(MOMA_ERR_ARG, "nx, ny, b must be >= 1");
+    if ((long long)nx * ny * b > (1ll << 31) / 4) throw MomaError(MOMA_ERR_ARG, "lattice too large");
+    a = new moma_array();
+    a->nx = nx; a->ny = ny; a->b = b; a->nel = nx * ny; a->N = nx * ny * b;
+    a->st = reinterpret_cast<cudaStream_t>(cuda_stream);
+    const int prec = opt ? opt->precision : MOMA_PREC_MIXED;
+    if (prec != MOMA_PREC_FP64 && prec != MOMA_PREC_MIXED) throw MomaError(MOMA_ERR_ARG, "bad precision");
+    // The factored preconditioner block of one element is staged whole in
+    // shared memory (packed triangle): b <= 128 in FP64, b <= 160 in c64.
+    if (b > (prec == MOMA_PREC_FP64 ? 128 : 160)) throw MomaError(MOMA_ERR_ARG, "b too large for this build");
+    a->prec = prec;
+    a->m = (opt && opt->restart > 0) ? opt->restart : 50;
+    if (a->m > MOMA_MAX_RESTART) throw MomaError(MOMA_ERR_ARG, "restart too large");
+    const int mx = (opt && opt->mx > 0) ? opt->mx : next_smooth(2 * nx - 1);
+    const int my = (opt && opt->my > 0) ? opt->my : next_smooth(2 * ny - 1);
+    if (mx < 2 * nx - 1 || my < 2 * ny - 1) throw MomaError(MOMA_ERR_ARG, "circulant size must be >= 2N-1");
+    if (!smooth_235(mx) || !smooth_235(my)) throw MomaError(MOMA_ERR_ARG, "circulant sizes must be 2^a 3^b 5^c");
+    if ((size_t)std::max(mx, my) * 16 * 32 > 190 * 1024) throw MomaError(MOMA_ERR_ARG, "circulant size too large");
+    a->Mx = mx; a->My = my; a->B = mx * my;
+    a->ldb = (b % 2) ? b + 1 : b;  // rows of the pair storage are 16-byte multiples in c64
+    CK(cudaGetDevice(&a->dev));
+    CK(cudaDeviceGetAttribute(&a->num_sms, cudaDevAttrMultiProcessorCount, a->dev));
+    build_tables(a);
+    a->Z128.ensure((size_t)a->Bp * b * a->ldb * sizeof(double2), a->dev_bytes);
+    CK(cudaMemset(a->Z128.p, 0, a->Z128.cap));
+    if (prec == MOMA_PREC_MIXED) {
+      a->Z64.ensure((size_t)a->Bp * b * a->ldb * sizeof(float2), a->dev_bytes);
+      CK(cudaMemset(a->Z64.p, 0, a->Z64.cap));
+    }
+    a->errbuf.ensure(256, a->dev_bytes);
+    CK(cudaMemset(a->errbuf.p, 0, 256));
+    a->err = a->errbuf.as<unsigned>();
+    CK(cudaMallocHost(&a->h_nact, (MOMA_MAX_RESTART + 8) * sizeof(int)));
+    CK(cudaMallocHost(&a->h_err, 64));
+    *out = a;
+  });
+  if (s != MOMA_OK && a) destroy_impl(a);
+  return s;
+}
+
+moma_status moma_set_blocks(moma_array *a, const void *blocks, int dtype) {
+  if (!a) { g_last_error = "array is NULL"; return MOMA_ERR_ARG; }
+  return guarded([&] { set_blocks_impl(a, blocks, dtype); });
+}
+
+moma_status moma_matvec(moma_array *a, int op, int nrhs, const void *x, void *y, int dtype) {
+  if (!a) { g_last_error = "array is NULL"; return MOMA_ERR_ARG; }
+  return guarded([&] {
+    if (!a->have_blocks) throw MomaError(MOMA_ERR_STATE, "set_blocks must precede matvec");
+    if (op < MOMA_OP_Z || op > MOMA_OP_NORMAL) throw MomaError(MOMA_ERR_ARG, "bad op");
+    if (nrhs < 0 || (nrhs > 0 && (!x || !y))) throw MomaError(MOMA_ERR_ARG, "bad nrhs or NULL buffer");
+    if (dtype != MOMA_C128 && dtype != MOMA_C64) throw MomaError(MOMA_ERR_ARG, "bad dtype");
+    const bool d64 = dtype == MOMA_C128;
+    if (!d64 && a->prec != MOMA_PREC_MIXED) throw MomaError(MOMA_ERR_ARG, "c64 operators need a MIXED array");
+    if (op == MOMA_OP_NORMAL && d64 != (a->prec == MOMA_PREC_FP64))
+      throw MomaError(MOMA_ERR_ARG, "the normal operator runs in the array's inner precision");
+    if (nrhs == 0) return;
+    ensure_ws(a, nrhs);
+    const size_t bytes = (size_t)nrhs * a->N * (d64 ? sizeof(double2) : sizeof(float2));
+    CK(cudaMemcpyAsync(a->Vw.p, x, bytes, cudaMemcpyDefault, a->st));
+    if (d64) {
+      if (op == MOMA_OP_NORMAL) apply_normal<double>(a, nrhs, a->Vw.p, a->yw.p);
+      else apply_z<double>(a, nrhs, a->Vw.p, a->yw.p, op == MOMA_OP_ZH);
+    } else {
+      if (op == MOMA_OP_NORMAL) apply_normal<float>(a, nrhs, a->Vw.p, a->yw.p);
+      else apply_z<float>(a, nrhs, a->Vw.p, a->yw.p, op == MOMA_OP_ZH);
+    }
+    copy_out(a, y, a->yw.p, bytes);
+    sync_and_check(a);
+  });
+}
+
+moma_status moma_apply_precond(moma_array *a, int nrhs, const void *x, void *y, int dtype) {
+  if (!a) { g_last_error = "array is NULL"; return MOMA_ERR_ARG; }
+  return guarded([&] {
+    if (!a->have_blocks) throw MomaError(MOMA_ERR_STATE, "set_blocks must precede apply_precond");
+    const bool d64 = dtype == MOMA_C128;
+    if ((dtype != MOMA_C128 && dtype != MOMA_C64) || d64 != (a->prec == MOMA_PREC_FP64))
+      throw MomaError(MOMA_ERR_ARG, "the preconditioner is stored in the array's inner precision");
+    if (nrhs < 0 || (nrhs > 0 && (!x || !y))) throw MomaError(MOMA_ERR_ARG, "bad nrhs or NULL buffer");
+    if (nrhs == 0) return;
+    ensure_ws(a, nrhs);
+    const size_t bytes = (size_t)nrhs * a->N * (d64 ? sizeof(double2) : sizeof(float2));
+    CK(cudaMemcpyAsync(a->Vw.p, x, bytes, cudaMemcpyDefault, a->st));
+    if (d64) precond<double>(a, nrhs, a->Vw.p, a->yw.p);
+    else precond<float>(a, nrhs, a->Vw.p, a->yw.p);
+    copy_out(a, y, a->yw.p, bytes);
+    sync_and_check(a);
+  });
+}
+
+moma_status moma_get_bin(moma_array *a, int kx, int ky, int dtype, void *out) {
+  if (!a) { g_last_error = "array is NULL"; return MOMA_ERR_ARG; }
+  return guarded([&] {
+    if (!a->have_blocks) throw MomaError(MOMA_ERR_STATE, "no blocks");
+    if (kx < 0 || kx >= a->Mx || ky < 0 || ky >= a->My || !out) throw MomaError(MOMA_ERR_ARG, "bad bin");
+    if (dtype != MOMA_C128 && !(dtype == MOMA_C64 && a->prec == MOMA_PREC_MIXED))
+      throw MomaError(MOMA_ERR_ARG, "bad dtype");
+    const int k = ky * a->Mx + kx;
+    const int nk = ((a->My - ky) % a->My) * a->Mx + ((a->Mx - kx) % a->Mx);
+    const int canon = std::min(k, nk);
+    std::vector<int> slot(a->B);
+    CK(cudaMemcpy(slot.data(), a->slot_of.p, a->B * sizeof(int), cudaMemcpyDeviceToHost));
+    const int s = slot[canon];
+    const size_t esz = dtype == MOMA_C128 ? 16 : 8;
+    const int b = a->b, ldb = a->ldb;
+    std::vector<unsigned char> blk((size_t)b * ldb * esz), res((size_t)b * b * esz);
+    const void *src = dtype == MOMA_C128 ? a->Z128.p : a->Z64.p;
+    CK(cudaMemcpy(blk.data(), (const unsigned char *)src + (size_t)s * b * ldb * esz, blk.size(),
+                  cudaMemcpyDeviceToHost));
+    const bool transpose = k != canon;
+    for (int i = 0; i < b; ++i)
+      for (int j = 0; j < b; ++j) {
+        const int si = transpose ? j : i, sj = transpose ? i : j;
+        std::memcpy(&res[((size_t)i * b + j) * esz], &blk[((size_t)si * ldb + sj) * esz], esz);
+      }
+    if (is_device_ptr(out)) CK(cudaMemcpy(out, res.data(), res.size(), cudaMemcpyHostToDevice));
+    else std::memcpy(out, res.data(), res.size());
+  });
+}
+
+moma_status moma_get_precond_block(moma_array *a, int ex, int ey, void *out) {
+  if (!a) { g_last_error = "array is NULL"; return MOMA_ERR_ARG; }
+  return guarded([&] {
+    if (!a->have_blocks) throw MomaError(MOMA_ERR_STATE, "no blocks");
+    if (ex < 0 || ex >= a->nx || ey < 0 || ey >= a->ny || !out) throw MomaError(MOMA_ERR_ARG, "bad element");
+    const size_t bytes = (size_t)a->b * a->b * sizeof(double2);
+    a->one_blk.ensure(bytes, a->dev_bytes);
+    launch_box_one(a->S.as<double2>(), a->nx, a->ny, a->b, ex, ey, a->one_blk.as<double2>(), a->st);
+    check_launch(a);
+    copy_out(a, out, a->one_blk.p, bytes);
+    sync_and_check(a);
+  });
+}
+
+moma_status moma_solve(moma_array *a, int nrhs, const void *V, void *I, const moma_solve_opts *opts,
+                       moma_solve_info *info, double *rel_residual) {
+  if (!a) { g_last_error = "array is NULL"; return MOMA_ERR_ARG; }
+  if (info) std::memset(info, 0, sizeof(*info));
+  return guarded([&] {
+    if (!a->have_blocks) throw MomaError(MOMA_ERR_STATE, "set_blocks must precede solve");
+    if (nrhs < 0 || (nrhs > 0 && (!V || !I))) throw MomaError(MOMA_ERR_ARG, "bad nrhs or NULL buffer");
+    if (nrhs == 0) {
+      if (info) info->converged = 1;
+      return;
+    }
+    ensure_ws(a, nrhs);
+    if (a->prec == MOMA_PREC_FP64) solve_impl<double>(a, nrhs, V, I, opts, info, rel_residual);
+    else solve_impl<float>(a, nrhs, V, I, opts, info, rel_residual);
+  });
+}
+
+moma_status moma_active_impedance(moma_array *a, int nrhs, const void *I, const void *V, int port_basis, double z0,
+                                  void *Za, void *Gamma) {
+  if (!a) { g_last_error = "array is NULL"; return MOMA_ERR_ARG; }
+  return guarded([&] {
+    if (nrhs < 0 || (nrhs > 0 && (!I || !V || !Za))) throw MomaError(MOMA_ERR_ARG, "bad nrhs or NULL buffer");
+    if (port_basis < 0 || port_basis >= a->b) throw MomaError(MOMA_ERR_ARG, "port_basis out of range");
+    if (nrhs == 0) return;
+    ensure_ws(a, nrhs);
+    const size_t bytes = (size_t)nrhs * a->N * sizeof(double2);
+    CK(cudaMemcpyAsync(a->rw.p, I, bytes, cudaMemcpyDefault, a->st));
+    CK(cudaMemcpyAsync(a->Vw.p, V, bytes, cudaMemcpyDefault, a->st));
+    a->portsb.ensure((size_t)2 * nrhs * a->nel * sizeof(double2), a->dev_bytes);
+    double2 *za = a->portsb.as<double2>();
+    double2 *ga = Gamma ? za + (size_t)nrhs * a->nel : nullptr;
+    launch_ports(a->rw.as<double2>(), a->Vw.as<double2>(), a->nel, a->b, nrhs, port_basis, z0, za, ga, a->err, a->st);
+    check_launch(a);
+    copy_out(a, Za, za, (size_t)nrhs * a->nel * sizeof(double2));
+    if (Gamma) copy_out(a, Gamma, ga, (size_t)nrhs * a->nel * sizeof(double2));
+    sync_and_check(a);
+  });
+}
+
+moma_status moma_profile(moma_array *a, int enable) {
+  if (!a) { g_last_error = "array is NULL"; return MOMA_ERR_ARG; }
+  return guarded([&] {
+    CK(cudaStreamSynchronize(a->st));
+    a->flush_events();
+    for (int k = 0; k < PK_N; ++k) { a->st_launch[k] = 0; a->st_ms[k] = 0; }
+    a->prof = enable != 0;
+  });
+}
+
+moma_status moma_kernel_stats(moma_array *a, int kernel, long long *launches, double *total_ms) {
+  if (!a) { g_last_error = "array is NULL"; return MOMA_ERR_ARG; }
+  return guarded([&] {
+    if (kernel < 0 || kernel >= PK_N) throw MomaError(MOMA_ERR_ARG, "bad kernel id");
+    a->flush_events();
+    if (launches) *launches = a->st_launch[kernel];
+    if (total_ms) *total_ms = a->st_ms[kernel];
+  });
+}
+
+long long moma_launch_count(moma_array *a) { return a ? a->launches : 0; }
+size_t moma_device_bytes(const moma_array *a) { return a ? a->dev_bytes : 0; }
+
+void moma_destroy(moma_array *a) {
+  if (!a) return;
+  cudaStreamSynchronize(a->st);
+  destroy_impl(a);
+}
+
+}  // extern "C"

@@ -1,0 +1,393 @@
+// Block-diagonal preconditioner of the normal equations (Sec. III-A).
+//
+// Eq. 37: the diagonal block of element e is
+//     P_e = sum_j (Z_{j,e})^H Z_{j,e} = sum_{D in W(e)} G_D,   G_D = Z_D^H Z_D,
+// where D = j - e runs over the offsets that keep j inside the lattice:
+// W(e) = [-ex, Nx-1-ex] x [-ey, Ny-1-ey].  Following the paper's recipe
+// (precompute all block products, then sum subsets), G is formed once per
+// offset and P_e is read off a 2D summed-area table of G with four corner
+// lookups, so the cost is O((2Nx-1)(2Ny-1) b^3) instead of O(Nel^2 b^3).
+// P_e = L_e L_e^H by Cholesky in FP64 (Sec. III-A), and P^{-1} is applied
+// as X_e^H X_e with X_e = L_e^{-1} stored packed.
+#include "internal.h"
+
+namespace moma {
+
+// ------------------------------------------------------------- Gram ------
+// G_D[i][j] = sum_k conj(Z_D[k][i]) Z_D[k][j]; 64 x 64 output tile per CTA,
+// 16 x 16 threads with 4 x 4 micro-tiles, k staged in chunks of 16.
+constexpr int GT = 64, GK = 16;
+
+template <typename R, typename Cin>
+__global__ void __launch_bounds__(256) gram_kernel(const Cin *__restrict__ blocks, int b, double2 *__restrict__ G) {
+  using C = typename Cplx<R>::T;
+  __shared__ C As[GK][GT];
+  __shared__ C Bs[GK][GT];
+  const int D = blockIdx.z;
+  const int i0 = blockIdx.y * GT, j0 = blockIdx.x * GT;
+  const Cin *Zd = blocks + (size_t)D * b * b;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  C acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[a][c] = czero<C>();
+
+  for (int k0 = 0; k0 < b; k0 += GK) {
+    for (int idx = threadIdx.x; idx < GK * GT; idx += 256) {
+      const int kk = idx / GT, cc = idx % GT;
+      const int k = k0 + kk;
+      As[kk][cc] = (k < b && i0 + cc < b) ? cvt<C>(Zd[(size_t)k * b + i0 + cc]) : czero<C>();
+      Bs[kk][cc] = (k < b && j0 + cc < b) ? cvt<C>(Zd[(size_t)k * b + j0 + cc]) : czero<C>();
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < GK; ++kk) {
+      C av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = As[kk][ty + 16 * a];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) bv[c] = Bs[kk][tx + 16 * c];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[a][c] = cfmac(av[a], bv[c], acc[a][c]);
+    }
+    __syncthreads();
+  }
+  double2 *Gd = G + (size_t)D * b * b;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int i = i0 + ty + 16 * a, j = j0 + tx + 16 * c;
+      if (i < b && j < b) Gd[(size_t)i * b + j] = cvt<double2>(acc[a][c]);
+    }
+}
+
+template <typename R>
+void launch_gram(const void *blocks, int blocks_c128, int nD, int b, double2 *G, cudaStream_t st) {
+  dim3 grid((b + GT - 1) / GT, (b + GT - 1) / GT, nD);
+  if (blocks_c128)
+    gram_kernel<R, double2><<<grid, 256, 0, st>>>(reinterpret_cast<const double2 *>(blocks), b, G);
+  else
+    gram_kernel<R, float2><<<grid, 256, 0, st>>>(reinterpret_cast<const float2 *>(blocks), b, G);
+}
+template void launch_gram<float>(const void *, int, int, int, double2 *, cudaStream_t);
+template void launch_gram<double>(const void *, int, int, int, double2 *, cudaStream_t);
+
+// ------------------------------------------------------ summed-area table --
+// S[y][x][e] <- sum_{y' <= y, x' <= x} S[y'][x'][e], in place, FP64.
+__global__ void sat_x_kernel(double2 *S, int ndx, int bb) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= bb) return;
+  double2 *row = S + (size_t)blockIdx.y * ndx * bb + e;
+  double2 run = make_double2(0, 0);
+  for (int x = 0; x < ndx; ++x) {
+    run = cadd(run, row[(size_t)x * bb]);
+    row[(size_t)x * bb] = run;
+  }
+}
+__global__ void sat_y_kernel(double2 *S, int ndy, int ndx, int bb) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= bb) return;
+  double2 *col = S + (size_t)blockIdx.y * bb + e;
+  double2 run = make_double2(0, 0);
+  for (int y = 0; y < ndy; ++y) {
+    run = cadd(run, col[(size_t)y * ndx * bb]);
+    col[(size_t)y * ndx * bb] = run;
+  }
+}
+void launch_sat(double2 *S, int ndy, int ndx, int bb, cudaStream_t st) {
+  sat_x_kernel<<<dim3((bb + 255) / 256, ndy), 256, 0, st>>>(S, ndx, bb);
+  sat_y_kernel<<<dim3((bb + 255) / 256, ndx), 256, 0, st>>>(S, ndy, ndx, bb);
+}
+
+// Entry (i, k) of P_e from the summed-area table: box over offset indices
+// x' in [Nx-1-ex, 2Nx-2-ex], y' in [Ny-1-ey, 2Ny-2-ey].
+MOMA_DEV double2 box_entry(const double2 *S, int ndx, int bb, int x0, int x1, int y0, int y1, int ent) {
+  auto at = [&](int y, int x) -> double2 {
+    if (x < 0 || y < 0) return make_double2(0, 0);
+    return S[((size_t)y * ndx + x) * bb + ent];
+  };
+  double2 v = at(y1, x1);
+  v = csub(v, at(y0 - 1, x1));
+  v = csub(v, at(y1, x0 - 1));
+  v = cadd(v, at(y0 - 1, x0 - 1));
+  return v;
+}
+
+MOMA_HD size_t colpk(int i, int k, int b) {  // packed column-major lower, i >= k
+  return (size_t)k * b - (size_t)k * (k - 1) / 2 + (i - k);
+}
+MOMA_HD size_t rowpk(int i, int k) {  // packed row-major lower, i >= k
+  return (size_t)i * (i + 1) / 2 + k;
+}
+
+// ------------------------------------------------------- box + Cholesky ---
+// One CTA per element.  The packed lower triangle of P_e is assembled from
+// the summed-area table and factored right-looking, column by column, in
+// FP64; L_e (packed column-major) is written to Lpk.
+template <bool IN_SMEM>
+__global__ void __launch_bounds__(256) box_cholesky_kernel(const double2 *__restrict__ S, int nx, int ny, int b,
+                                                           double2 *__restrict__ Lpk, unsigned *err) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int e = blockIdx.x, ex = e % nx, ey = e / nx;
+  const size_t npk = (size_t)b * (b + 1) / 2;
+  double2 *A = IN_SMEM ? reinterpret_cast<double2 *>(smraw) : Lpk + (size_t)e * npk;
+  const int ndx = 2 * nx - 1, bb = b * b;
+  const int x0 = nx - 1 - ex, x1 = 2 * nx - 2 - ex, y0 = ny - 1 - ey, y1 = 2 * ny - 2 - ey;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+
+  for (int k = 0; k < b; ++k)
+    for (int i = k + tid; i < b; i += blockDim.x) A[colpk(i, k, b)] = box_entry(S, ndx, bb, x0, x1, y0, y1, i * b + k);
+  __syncthreads();
+
+  __shared__ int bad;
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  for (int j = 0; j < b; ++j) {
+    const double d = A[colpk(j, j, b)].x;
+    if (!(d > 0.0) || !isfinite(d)) {  // uniform: every thread reads the same value
+      if (tid == 0) atomicOr(err, DEVERR_NOT_PD);
+      bad = 1;
+      break;
+    }
+    const double l = sqrt(d), inv_l = 1.0 / l;
+    __syncthreads();  // everyone has read d before the column is overwritten
+    for (int i = j + tid; i < b; i += blockDim.x) {
+      const size_t q = colpk(i, j, b);
+      A[q] = (i == j) ? make_double2(l, 0.0) : cscale(A[q], inv_l);
+    }
+    __syncthreads();
+    for (int k = j + 1 + w; k < b; k += blockDim.x / 32) {
+      const double2 lkj = cconj(A[colpk(k, j, b)]);
+      for (int i = k + lane; i < b; i += 32) {
+        const size_t q = colpk(i, k, b);
+        A[q] = csub(A[q], cmul(A[colpk(i, j, b)], lkj));
+      }
+    }
+    __syncthreads();
+  }
+  if (IN_SMEM && !bad) {
+    double2 *dst = Lpk + (size_t)e * npk;
+    for (size_t q = tid; q < npk; q += blockDim.x) dst[q] = A[q];
+  }
+}
+
+void launch_box_cholesky(const double2 *S, int nx, int ny, int b, double2 *Lpk, unsigned *err, cudaStream_t st) {
+  const size_t bytes = (size_t)b * (b + 1) / 2 * sizeof(double2);
+  const int nel = nx * ny;
+  if (bytes <= 200 * 1024) {
+    static int configured = 0;
+    if (!configured) {
+      cudaFuncSetAttribute(box_cholesky_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+      configured = 1;
+    }
+    box_cholesky_kernel<true><<<nel, 256, bytes, st>>>(S, nx, ny, b, Lpk, err);
+  } else {
+    box_cholesky_kernel<false><<<nel, 256, 0, st>>>(S, nx, ny, b, Lpk, err);
+  }
+}
+
+// Full P_e of one element (debug / inspection).
+__global__ void box_one_kernel(const double2 *S, int nx, int ny, int b, int ex, int ey, double2 *out) {
+  const int ndx = 2 * nx - 1, bb = b * b;
+  const int x0 = nx - 1 - ex, x1 = 2 * nx - 2 - ex, y0 = ny - 1 - ey, y1 = 2 * ny - 2 - ey;
+  for (int ent = blockIdx.x * blockDim.x + threadIdx.x; ent < bb; ent += gridDim.x * blockDim.x)
+    out[ent] = box_entry(S, ndx, bb, x0, x1, y0, y1, ent);
+}
+void launch_box_one(const double2 *S, int nx, int ny, int b, int ex, int ey, double2 *out, cudaStream_t st) {
+  box_one_kernel<<<(b * b + 255) / 256, 256, 0, st>>>(S, nx, ny, b, ex, ey, out);
+}
+
+// ---------------------------------------------------- inverse factor -----
+// X = L^{-1} by rows: X[i][k] = (delta_ik - sum_{k<=m<i} L[i][m] X[m][k]) / L[i][i].
+// L is staged in shared memory (packed column-major, precision R); X rows are
+// written packed row-major to global memory (stride x_stride elements per
+// element) and re-read from there (L1/L2 resident).
+template <typename R>
+__global__ void __launch_bounds__(256) tri_inverse_kernel(const double2 *__restrict__ Lpk, int b,
+                                                          typename Cplx<R>::T *X, size_t x_stride) {
+  using C = typename Cplx<R>::T;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C *L = reinterpret_cast<C *>(smraw);
+  const int e = blockIdx.x;
+  const size_t npk = (size_t)b * (b + 1) / 2;
+  const double2 *Le = Lpk + (size_t)e * npk;
+  C *Xe = X + (size_t)e * x_stride;
+  for (size_t q = threadIdx.x; q < npk; q += blockDim.x) L[q] = cvt<C>(Le[q]);
+  for (size_t q = npk + threadIdx.x; q < x_stride; q += blockDim.x) Xe[q] = czero<C>();  // pad
+  __syncthreads();
+  // Threads own columns k; the sum over m runs in the same order on every
+  // thread so L[i][m] is a broadcast and X[m][k] reads are contiguous in k.
+  for (int i = 0; i < b; ++i) {
+    const R inv = (R)1 / L[colpk(i, i, b)].x;
+    for (int k0 = 0; k0 <= i; k0 += blockDim.x) {
+      const int k = k0 + threadIdx.x;
+      C acc = czero<C>();
+      for (int m = k0; m < i; ++m)
+        if (m >= k) acc = cfma(L[colpk(i, m, b)], Xe[rowpk(m, k)], acc);
+      if (k <= i) {
+        C v = (k == i) ? mk((R)1, (R)0) : czero<C>();
+        Xe[rowpk(i, k)] = cscale(csub(v, acc), inv);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename R>
+void launch_tri_inverse(const double2 *Lpk, int nel, int b, void *X, size_t x_stride, cudaStream_t st) {
+  using C = typename Cplx<R>::T;
+  const size_t bytes = (size_t)b * (b + 1) / 2 * sizeof(C);
+  static int configured = 0;
+  if (!configured) {
+    cudaFuncSetAttribute(tri_inverse_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    configured = 1;
+  }
+  tri_inverse_kernel<R><<<nel, 256, bytes, st>>>(Lpk, b, reinterpret_cast<C *>(X), x_stride);
+}
+template void launch_tri_inverse<float>(const double2 *, int, int, void *, size_t, cudaStream_t);
+template void launch_tri_inverse<double>(const double2 *, int, int, void *, size_t, cudaStream_t);
+
+// ------------------------------------------------------------ apply ------
+// y_e = X_e^H (X_e x_e).  One CTA per element; X_e arrives in shared memory
+// with one bulk copy.  Phase 1: warps own rows i of X, lanes own columns
+// k <= i (warp-reduced row products).  Phase 2: the same rows, lanes
+// accumulate conj(X[i][k]) t_i into per-warp column partials, reduced
+// across warps at the end.
+constexpr int PA_THREADS = 256, PA_WARPS = 8;
+
+template <typename R, int NR, int U>
+__global__ void __launch_bounds__(PA_THREADS) precond_apply_kernel(const typename Cplx<R>::T *__restrict__ X,
+                                                                   size_t x_stride, int nel, int b, int nr,
+                                                                   const typename Cplx<R>::T *__restrict__ x,
+                                                                   typename Cplx<R>::T *__restrict__ y,
+                                                                   unsigned *err) {
+  using C = typename Cplx<R>::T;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smraw);
+  C *Xs = reinterpret_cast<C *>(smraw + 128);
+  C *xs = Xs + x_stride;              // [b][NR]
+  C *ts = xs + (size_t)b * NR;        // [b][NR]
+  C *zp = ts + (size_t)b * NR;        // [PA_WARPS][b][NR]
+  const int e = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const uint32_t bytes = (uint32_t)(x_stride * sizeof(C));
+    fence_proxy_async();
+    mbar_expect_tx(bar, bytes);
+    bulk_g2s(Xs, X + (size_t)e * x_stride, bytes, bar);
+  }
+  const bool ok = mbar_wait_bounded(bar, 0, 2000000000ull);
+  if (__syncthreads_or(!ok)) {
+    if (tid == 0) {
+      atomicOr(err, DEVERR_TIMEOUT);
+      mbar_wait_bounded(bar, 0, 2000000000ull);
+    }
+    return;
+  }
+
+  for (int q0 = 0; q0 < nr; q0 += NR) {
+    for (int idx = tid; idx < b * NR; idx += PA_THREADS) {
+      const int k = idx / NR, q = q0 + idx % NR;
+      xs[idx] = q < nr ? x[((size_t)q * nel + e) * b + k] : czero<C>();
+    }
+    __syncthreads();
+    for (int i = w; i < b; i += PA_WARPS) {
+      const C *row = Xs + rowpk(i, 0);
+      C p[NR];
+#pragma unroll
+      for (int qq = 0; qq < NR; ++qq) p[qq] = czero<C>();
+      for (int k = lane; k <= i; k += 32) {
+        const C xv = row[k];
+#pragma unroll
+        for (int qq = 0; qq < NR; ++qq) p[qq] = cfma(xv, xs[k * NR + qq], p[qq]);
+      }
+#pragma unroll
+      for (int qq = 0; qq < NR; ++qq) {
+        const C v = warp_sum(p[qq]);
+        if (lane == 0) ts[i * NR + qq] = v;
+      }
+    }
+    __syncthreads();
+    C acc[U][NR];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int qq = 0; qq < NR; ++qq) acc[u][qq] = czero<C>();
+    for (int i = w; i < b; i += PA_WARPS) {
+      const C *row = Xs + rowpk(i, 0);
+      C tv[NR];
+#pragma unroll
+      for (int qq = 0; qq < NR; ++qq) tv[qq] = ts[i * NR + qq];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int k = lane + 32 * u;
+        if (k <= i) {
+          const C xv = row[k];
+#pragma unroll
+          for (int qq = 0; qq < NR; ++qq) acc[u][qq] = cfmac(xv, tv[qq], acc[u][qq]);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int k = lane + 32 * u;
+      if (k < b)
+#pragma unroll
+        for (int qq = 0; qq < NR; ++qq) zp[((size_t)w * b + k) * NR + qq] = acc[u][qq];
+    }
+    __syncthreads();
+    for (int idx = tid; idx < b * NR; idx += PA_THREADS) {
+      C v = czero<C>();
+      for (int ww = 0; ww < PA_WARPS; ++ww) v = cadd(v, zp[(size_t)ww * b * NR + idx]);
+      const int k = idx / NR, q = q0 + idx % NR;
+      if (q < nr) y[((size_t)q * nel + e) * b + k] = v;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename R, int NR, int U>
+static void apply_launch(const void *X, size_t x_stride, int nel, int b, int nr, const void *x, void *y,
+                         unsigned *err, cudaStream_t st) {
+  using C = typename Cplx<R>::T;
+  const size_t smem = 128 + x_stride * sizeof(C) + (size_t)(2 + PA_WARPS) * b * NR * sizeof(C);
+  static int configured = 0;
+  if (!configured) {
+    cudaFuncSetAttribute(precond_apply_kernel<R, NR, U>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    configured = 1;
+  }
+  precond_apply_kernel<R, NR, U><<<nel, PA_THREADS, smem, st>>>(
+      reinterpret_cast<const C *>(X), x_stride, nel, b, nr, reinterpret_cast<const C *>(x),
+      reinterpret_cast<C *>(y), err);
+}
+
+template <typename R, int NR>
+static void apply_u(const void *X, size_t xs, int nel, int b, int nr, const void *x, void *y, unsigned *err,
+                    cudaStream_t st) {
+  const int U = (b + 31) / 32;
+  if (U <= 1) apply_launch<R, NR, 1>(X, xs, nel, b, nr, x, y, err, st);
+  else if (U <= 2) apply_launch<R, NR, 2>(X, xs, nel, b, nr, x, y, err, st);
+  else if (U <= 4) apply_launch<R, NR, 4>(X, xs, nel, b, nr, x, y, err, st);
+  else apply_launch<R, NR, 8>(X, xs, nel, b, nr, x, y, err, st);
+}
+
+template <typename R>
+void launch_precond_apply(const void *X, size_t x_stride, int nel, int b, int nr, const void *x, void *y,
+                          unsigned *err, cudaStream_t st) {
+  if (nr == 1) apply_u<R, 1>(X, x_stride, nel, b, nr, x, y, err, st);
+  else apply_u<R, 2>(X, x_stride, nel, b, nr, x, y, err, st);
+}
+template void launch_precond_apply<float>(const void *, size_t, int, int, int, const void *, void *, unsigned *,
+                                          cudaStream_t);
+template void launch_precond_apply<double>(const void *, size_t, int, int, int, const void *, void *, unsigned *,
+                                           cudaStream_t);
+
+}  // namespace moma

@@ -1,0 +1,225 @@
+"""ctypes binding of libmoma (include/moma.h): the same entry points, with
+argument marshalling only.  Every computation runs in the CUDA library;
+there is no Python or CPU fallback -- a missing library raises.
+
+Buffers may be numpy arrays (host memory) or torch tensors (host or CUDA
+memory); they must be C-contiguous complex128 or complex64 arrays in the
+layouts of moma.h.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmoma.so")
+
+MOMA_OK = 0
+STATUS = {
+    0: "MOMA_OK", 1: "MOMA_ERR_ARG", 2: "MOMA_ERR_STATE", 3: "MOMA_ERR_OOM", 4: "MOMA_ERR_CUDA",
+    5: "MOMA_ERR_NOT_PD", 6: "MOMA_ERR_NOT_CONVERGED", 7: "MOMA_ERR_BREAKDOWN", 8: "MOMA_ERR_NONFINITE",
+    9: "MOMA_ERR_TIMEOUT",
+}
+MOMA_C128, MOMA_C64 = 0, 1
+MOMA_PREC_FP64, MOMA_PREC_MIXED = 0, 1
+MOMA_OP_Z, MOMA_OP_ZH, MOMA_OP_NORMAL = 0, 1, 2
+KERNEL_IDS = {"bin_c64": 0, "bin_c128": 1, "precond": 2, "fft_c64": 3, "block_fft": 4, "fft_c128": 5}
+
+# Every symbol include/moma.h declares, for the export check.
+EXPORTS = [
+    "moma_create_array", "moma_set_blocks", "moma_matvec", "moma_apply_precond", "moma_get_bin",
+    "moma_get_precond_block", "moma_solve", "moma_active_impedance", "moma_profile", "moma_kernel_stats",
+    "moma_launch_count", "moma_device_bytes", "moma_destroy", "moma_last_error",
+]
+
+
+class MomaError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class moma_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("mx", ctypes.c_int), ("my", ctypes.c_int), ("restart", ctypes.c_int)]
+
+
+class moma_solve_opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int),
+                ("warm_start", ctypes.c_int)]
+
+
+class moma_solve_info(ctypes.Structure):
+    _fields_ = [("outer_iters", ctypes.c_int), ("inner_iters", ctypes.c_int), ("converged", ctypes.c_int),
+                ("max_rel_residual", ctypes.c_double), ("first_inner_reduction", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """Load libmoma.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_2608_17844_b300.build`")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    L.moma_create_array.argtypes = [i, i, i, ctypes.POINTER(moma_options), vp, ctypes.POINTER(vp)]
+    L.moma_set_blocks.argtypes = [vp, vp, i]
+    L.moma_matvec.argtypes = [vp, i, i, vp, vp, i]
+    L.moma_apply_precond.argtypes = [vp, i, vp, vp, i]
+    L.moma_get_bin.argtypes = [vp, i, i, i, vp]
+    L.moma_get_precond_block.argtypes = [vp, i, i, vp]
+    L.moma_solve.argtypes = [vp, i, vp, vp, ctypes.POINTER(moma_solve_opts), ctypes.POINTER(moma_solve_info),
+                             ctypes.POINTER(d)]
+    L.moma_active_impedance.argtypes = [vp, i, vp, vp, i, d, vp, vp]
+    L.moma_profile.argtypes = [vp, i]
+    L.moma_kernel_stats.argtypes = [vp, i, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(d)]
+    L.moma_launch_count.argtypes = [vp]
+    L.moma_launch_count.restype = ctypes.c_longlong
+    L.moma_device_bytes.argtypes = [vp]
+    L.moma_device_bytes.restype = ctypes.c_size_t
+    L.moma_destroy.argtypes = [vp]
+    L.moma_destroy.restype = None
+    L.moma_last_error.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name not in ("moma_launch_count", "moma_device_bytes", "moma_destroy", "moma_last_error"):
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(st):
+    if st != MOMA_OK:
+        raise MomaError(st, lib().moma_last_error().decode())
+
+
+def _ptr_dtype(a):
+    """(pointer, moma_dtype) of a C-contiguous complex numpy array or torch tensor."""
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        if a.dtype == np.complex128:
+            return a.ctypes.data, MOMA_C128
+        if a.dtype == np.complex64:
+            return a.ctypes.data, MOMA_C64
+        raise TypeError(f"unsupported dtype {a.dtype}")
+    import torch
+    if isinstance(a, torch.Tensor):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        if a.dtype == torch.complex128:
+            return a.data_ptr(), MOMA_C128
+        if a.dtype == torch.complex64:
+            return a.data_ptr(), MOMA_C64
+        raise TypeError(f"unsupported dtype {a.dtype}")
+    raise TypeError(type(a))
+
+
+def _stream_handle(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    return getattr(stream, "cuda_stream", stream)
+
+
+def moma_create_array(nx, ny, b, precision=MOMA_PREC_MIXED, mx=0, my=0, restart=0, stream=None):
+    h = ctypes.c_void_p()
+    opt = moma_options(precision, mx, my, restart)
+    _check(lib().moma_create_array(nx, ny, b, ctypes.byref(opt), _stream_handle(stream), ctypes.byref(h)))
+    return h
+
+
+def moma_set_blocks(h, blocks):
+    p, dt = _ptr_dtype(blocks)
+    _check(lib().moma_set_blocks(h, p, dt))
+
+
+def moma_matvec(h, op, x, y):
+    px, dt = _ptr_dtype(x)
+    py, dty = _ptr_dtype(y)
+    if dt != dty:
+        raise TypeError("x and y must have the same dtype")
+    _check(lib().moma_matvec(h, op, x.shape[0], px, py, dt))
+
+
+def moma_apply_precond(h, x, y):
+    px, dt = _ptr_dtype(x)
+    py, _ = _ptr_dtype(y)
+    _check(lib().moma_apply_precond(h, x.shape[0], px, py, dt))
+
+
+def moma_get_bin(h, kx, ky, out):
+    p, dt = _ptr_dtype(out)
+    _check(lib().moma_get_bin(h, kx, ky, dt, p))
+
+
+def moma_get_precond_block(h, ex, ey, out):
+    p, _ = _ptr_dtype(out)
+    _check(lib().moma_get_precond_block(h, ex, ey, p))
+
+
+def moma_solve(h, V, I, tol=0.0, inner_tol=0.0, max_outer=0, warm_start=False, rel_residual=None):
+    """Returns the moma_solve_info as a dict; raises MomaError on failure
+    (the exception carries .info for MOMA_ERR_NOT_CONVERGED)."""
+    pv, dv = _ptr_dtype(V)
+    pi, di = _ptr_dtype(I)
+    if dv != MOMA_C128 or di != MOMA_C128:
+        raise TypeError("V and I are complex128")
+    opts = moma_solve_opts(tol, inner_tol, max_outer, 1 if warm_start else 0)
+    info = moma_solve_info()
+    rr = None
+    if rel_residual is not None:
+        rr = rel_residual.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    st = lib().moma_solve(h, V.shape[0], pv, pi, ctypes.byref(opts), ctypes.byref(info), rr)
+    if st != MOMA_OK:
+        e = MomaError(st, lib().moma_last_error().decode())
+        e.info = info.as_dict()
+        raise e
+    return info.as_dict()
+
+
+def moma_active_impedance(h, I, V, Za, Gamma=None, port_basis=0, z0=50.0):
+    pi, _ = _ptr_dtype(I)
+    pv, _ = _ptr_dtype(V)
+    pz, _ = _ptr_dtype(Za)
+    pg = _ptr_dtype(Gamma)[0] if Gamma is not None else None
+    _check(lib().moma_active_impedance(h, I.shape[0], pi, pv, port_basis, z0, pz, pg))
+
+
+def moma_profile(h, enable):
+    _check(lib().moma_profile(h, 1 if enable else 0))
+
+
+def moma_kernel_stats(h, kernel):
+    n = ctypes.c_longlong()
+    ms = ctypes.c_double()
+    kid = KERNEL_IDS[kernel] if isinstance(kernel, str) else kernel
+    _check(lib().moma_kernel_stats(h, kid, ctypes.byref(n), ctypes.byref(ms)))
+    return n.value, ms.value
+
+
+def moma_launch_count(h):
+    return lib().moma_launch_count(h)
+
+
+def moma_device_bytes(h):
+    return lib().moma_device_bytes(h)
+
+
+def moma_destroy(h):
+    if h:
+        lib().moma_destroy(h)
+
+
+def moma_last_error():
+    return lib().moma_last_error().decode()

@@ -11,3 +11,21 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA device (B300) and the built library")
     config.addinivalue_line("markers", "slow: larger CPU cases")
+
+
+@pytest.fixture(scope="session")
+def moma_lib():
+    """The in-tree libmoma.so, built if missing or stale."""
+    from paper_2608_17844_b300 import build as _build
+    _build.build()
+    import paper_2608_17844_b300 as pkg
+    return pkg
+
+
+@pytest.fixture(scope="session")
+def cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    torch.cuda.init()
+    return torch

@@ -1,0 +1,65 @@
+"""Full-size parity on the 32 x 32 lattice, b = 128 (N = 131072), blocks
+stored complex64, broadside + 45 degree E-plane RHS -- the workload the
+benchmark times, in the same launch configuration.
+
+The dense oracle cannot hold this Z (275 GB), so the checks are:
+  * the residual certificate: ||V - Z I|| / ||V|| recomputed on the CPU in
+    complex128 with the oracle's direct offset sum (no FFT) <= 1e-10;
+  * Z_a of the centre, edge and corner elements against oracle-I (GMRES on
+    the original system, tol 1e-13) within 1e-8;
+  * the plain FP64 GPU solve reaches the same tolerance.
+"""
+import numpy as np
+import pytest
+
+from synth import config_c2, offset_blocks, excitation
+from oracle import mbt, ports, iterative
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def c2():
+    spec, angles = config_c2()
+    blocks64 = offset_blocks(spec, np.complex64)
+    return spec, blocks64, excitation(spec, angles)
+
+
+def _solve(m, spec, blocks64, V, prec):
+    h = m.moma_create_array(spec.nx, spec.ny, spec.b, prec)
+    try:
+        m.moma_set_blocks(h, blocks64)
+        I = np.zeros_like(V)
+        rr = np.zeros(V.shape[0])
+        info = m.moma_solve(h, V, I, rel_residual=rr)
+        za = np.zeros(V.shape[:3], np.complex128)
+        gam = np.zeros_like(za)
+        m.moma_active_impedance(h, I, V, za, gam)
+        return I, za, gam, info, rr
+    finally:
+        m.moma_destroy(h)
+
+
+def test_c2_mixed_certified_and_ports_match_oracle(moma_lib, cuda, c2):
+    spec, blocks64, V = c2
+    I, za, gam, info, rr = _solve(moma_lib, spec, blocks64, V, 1)
+    assert info["converged"] == 1 and rr.max() <= 1e-10
+    blocks = blocks64.astype(np.complex128)
+    res = V - mbt.matvec(blocks, spec.nx, spec.ny, I)
+    cert = np.linalg.norm(res.reshape(2, -1), axis=1) / np.linalg.norm(V.reshape(2, -1), axis=1)
+    print("C2 mixed: info", info, "certified residual", cert)
+    assert cert.max() <= 1e-10
+    i_ref, oinfo = iterative.gmres(blocks, spec.nx, spec.ny, V, tol=1e-13, restart=60)
+    za_ref = ports.active_impedance(i_ref, V)
+    for name, (ex, ey) in ports.named_elements(spec.nx, spec.ny).items():
+        err = np.abs(za[:, ey, ex] - za_ref[:, ey, ex]) / np.abs(za_ref[:, ey, ex])
+        print(f"C2 {name}: Za={za[:, ey, ex]} rel err {err}")
+        assert err.max() <= 1e-8
+    assert np.allclose(gam, ports.reflection(za), rtol=1e-12)
+
+
+def test_c2_plain_fp64_reaches_tolerance(moma_lib, cuda, c2):
+    spec, blocks64, V = c2
+    I, za, gam, info, rr = _solve(moma_lib, spec, blocks64, V, 0)
+    print("C2 fp64: info", info)
+    assert info["converged"] == 1 and rr.max() <= 1e-10
