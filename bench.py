@@ -35,12 +35,14 @@ WORKLOAD = ("32x32 lattice, b=128 (N=131072), offset blocks complex64, 2 RHS (br
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=2, help="steps of the plain FP64 solve (0 = skip)")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="bounded oracle sample (0 = skip)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--lattice", type=int, nargs=3, metavar=("NX", "NY", "B"), default=None,
+                    help="override the lattice (profiling of smaller cases; not the benchmark workload)")
     return ap.parse_args()
 
 
@@ -77,6 +79,12 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
+    def wait_first(self, timeout=5.0):
+        t0 = time.time()
+        while self.proc is not None and not self.lines and time.time() - t0 < timeout:
+            time.sleep(0.05)
+        self.lines.clear()
+
     def stop(self):
         if self.proc is None:
             return None
@@ -106,9 +114,11 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def make_inputs():
-    from synth import config_c2, offset_blocks, excitation
+def make_inputs(lattice=None):
+    from synth import config_c2, offset_blocks, excitation, LatticeSpec
     spec, angles = config_c2()
+    if lattice:
+        spec = LatticeSpec(lattice[0], lattice[1], lattice[2], spec.d, spec.seed)
     blocks = offset_blocks(spec, np.complex64)
     V = excitation(spec, angles)
     return spec, blocks, V
@@ -180,7 +190,7 @@ def run_reference(args, world, rank):
     """Reference arm: the CPU oracle as it stands, on the host cores."""
     if rank != 0:
         return
-    spec, blocks, V = make_inputs()
+    spec, blocks, V = make_inputs(args.lattice)
     per_step = max(5.0, min(30.0, 120.0 / max(1, args.steps + args.warmup)))
     vals = []
     cb = None
@@ -218,7 +228,7 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    spec, blocks, V = make_inputs()
+    spec, blocks, V = make_inputs(args.lattice)
     nr = V.shape[0]
     stream = torch.cuda.current_stream()
     blocks_d = torch.from_numpy(blocks).cuda()
@@ -242,6 +252,7 @@ def main():
     launches0 = m.moma_launch_count(h)
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
+    clocks.wait_first()
     step_ms = []
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -364,7 +375,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c64 (FP32) inner + f64 refinement",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "rhs_per_step": nr * world, "parallelism": f"replicas x{world}",
+            "config": {"workload": WORKLOAD if not args.lattice else f"profiling lattice {args.lattice}",
+                       "rhs_per_step": nr * world, "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (c64 blocks 520 MB; stored bins 269 MB c64 + 537 MB c128)"},
             "step_ms": {"p50": statistics.median(steps_ms), "p99": float(np.percentile(steps_ms, 99)),
                         "min": min(steps_ms), "max": max(steps_ms)},

@@ -157,7 +157,10 @@ moma_status moma_active_impedance(moma_array *a, int nrhs, const void *I, const 
  * with CUDA events recorded on the array's stream around each launch of a
  * kernel family.  kernel: 0 = c64 bin product, 1 = c128 bin product,
  * 2 = preconditioner apply, 3 = c64 lattice FFT passes, 4 = block-bin
- * transform (set-up), 5 = c128 lattice FFT passes.  Writes the number of
+ * transform (set-up), 5 = c128 lattice FFT passes, 6 = offset Gram
+ * products, 7 = summed-area table, 8 = box sums + Cholesky, 9 = inverse
+ * factors, 10 = Arnoldi/Givens/update kernels, 11 = residual and
+ * conversion kernels.  Writes the number of
  * timed launches and their total milliseconds.  moma_profile(a, 0) stops
  * timing; either call resets the counters. */
 moma_status moma_profile(moma_array *a, int enable);

@@ -31,6 +31,11 @@ FftPlan make_plan(int M) {
   while (m % 3 == 0) { p.radix[p.nst++] = 3; m /= 3; }
   while (m % 5 == 0) { p.radix[p.nst++] = 5; m /= 5; }
   if (m != 1 || p.nst > MOMA_FFT_MAXST) throw std::runtime_error("FFT length is not 2^a 3^b 5^c");
+  int span = M;
+  for (int s = 0; s < p.nst; ++s) {
+    p.span[s] = span;
+    span /= p.radix[s];
+  }
   return p;
 }
 
@@ -51,14 +56,20 @@ struct AxisKernelArgs {
   FftPlan pl;
 };
 
+// One CTA transforms 32 consecutive lines (inner indices j0 .. j0+31) of
+// one (o1, o2) slice; G = blockDim.x / 32 threads cooperate on each line,
+// splitting its loads, butterflies and stores, with a barrier between
+// stages.  Line jj lives in shared memory at col[m * 32 + jj], so a warp
+// (32 lines, same sub-thread) touches 32 consecutive words.
 template <typename R, typename Cin, typename Cout>
 __global__ void axis_kernel(AxisKernelArgs A, const typename Cplx<R>::T *__restrict__ tw_g,
                             const int *__restrict__ pos_g) {
   using C = typename Cplx<R>::T;
   extern __shared__ __align__(16) unsigned char smraw[];
   const AxisPass &p = A.p;
+  if (p.live && *p.live == 0) return;
   const int M = A.pl.M;
-  const int ld = blockDim.x;
+  constexpr int ld = 32;
   C *tw = reinterpret_cast<C *>(smraw);
   int *pos = reinterpret_cast<int *>(tw + M);
   C *col = reinterpret_cast<C *>(smraw + ((M * sizeof(C) + M * sizeof(int) + 15) & ~size_t(15)));
@@ -66,60 +77,102 @@ __global__ void axis_kernel(AxisKernelArgs A, const typename Cplx<R>::T *__restr
     tw[i] = tw_g[i];
     pos[i] = pos_g[i];
   }
-  __syncthreads();
-
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= p.ninner) return;  // lines are private: no block-wide sync below
+  const int jj = threadIdx.x & 31, g = threadIdx.x >> 5, G = blockDim.x >> 5;
+  const int j = blockIdx.x * 32 + jj;
+  const bool act = j < p.ninner;
   const int o1 = blockIdx.y % p.n1, o2 = blockIdx.y / p.n1;
-  C *c = col + threadIdx.x;
+  C *c = col + jj;
   const Cin *src = reinterpret_cast<const Cin *>(p.in) + (long long)o1 * p.in_s1 + (long long)o2 * p.in_s2 + j;
 
-  // Gather the line (zero padded).  in_mode 1 places the 2N-1 offsets of a
+  // Gather this thread's points m = g, g + G, ... (zero padded), UL loads
+  // in flight at a time.  in_mode 1 places the 2N-1 offsets of a
   // block-Toeplitz first column at circulant positions D mod M.
   const int Nc = (p.nin + 1) / 2;
-#pragma unroll 4
-  for (int m = 0; m < M; ++m) {
-    int idx = -1;
-    if (p.in_mode == 0) {
-      if (m < p.nin) idx = m;
-    } else {
-      if (m < Nc) idx = m + Nc - 1;
-      else if (m >= M - Nc + 1) idx = m - M + Nc - 1;
+  const long long jin = (act && p.inner_in_map) ? (long long)p.inner_in_map[j] - j : 0;
+  constexpr int UL = sizeof(R) == 4 ? 16 : 8;
+  for (int m0 = g; m0 < M; m0 += G * UL) {
+    C v[UL];
+#pragma unroll
+    for (int u = 0; u < UL; ++u) {
+      const int m = m0 + u * G;
+      int idx = -1;
+      if (act && m < M) {
+        if (p.in_mode == 0) {
+          if (m < p.nin) idx = m;
+        } else {
+          if (m < Nc) idx = m + Nc - 1;
+          else if (m >= M - Nc + 1) idx = m - M + Nc - 1;
+        }
+      }
+      v[u] = idx >= 0 ? cvt<C>(src[(long long)idx * p.in_sm + jin]) : czero<C>();
     }
-    C v = czero<C>();
-    if (idx >= 0) v = cvt<C>(src[(long long)idx * p.in_sm]);
-    if (p.inverse) v = cconj(v);
-    c[m * ld] = v;
+#pragma unroll
+    for (int u = 0; u < UL; ++u) {
+      const int m = m0 + u * G;
+      if (m < M) c[m * ld] = p.inverse ? cconj(v[u]) : v[u];
+    }
   }
-
-  fft_dif(c, ld, A.pl, tw);
+  __syncthreads();
+  for (int s = 0; s < A.pl.nst; ++s) {
+    dif_stage(c, ld, A.pl, tw, s, g, G);
+    __syncthreads();
+  }
   const R inv_m = (R)1 / (R)M;
   bool natural = false;
   if (p.refft_keep > 0) {
-    for (int m = 0; m < M; ++m) {
+    for (int m = g; m < M; m += G) {
       const int q = pos[m] * ld;
       c[q] = (m < p.refft_keep) ? cscale(cconj(c[q]), inv_m) : czero<C>();
     }
-    fft_dit(c, ld, A.pl, tw);
+    __syncthreads();
+    for (int s = A.pl.nst - 1; s >= 0; --s) {
+      dit_stage(c, ld, A.pl, tw, s, g, G);
+      __syncthreads();
+    }
     natural = true;
   }
+  if (!act) return;
 
   Cout *dst = reinterpret_cast<Cout *>(p.out);
   float2 *dst2 = reinterpret_cast<float2 *>(p.out2);
-  for (int k = 0; k < p.nout; ++k) {
+  int ti = 0, tj = 0;
+  if (p.out_mode == 2) {
+    const int2 t = p.tri[j];
+    ti = t.x;
+    tj = t.y;
+  }
+  for (int k = g; k < p.nout; k += G) {
     C v = natural ? c[k * ld] : c[pos[k] * ld];
     if (p.inverse && !natural) v = cscale(cconj(v), inv_m);
-    long long off;
+    long long off, off2 = -1;
     if (p.out_mode == 0) {
       off = (long long)o1 * p.out_s1 + (long long)o2 * p.out_s2 + (long long)k * p.out_sm + j;
-    } else {
+    } else if (p.out_mode == 1) {
       const int slot = p.slot_of[k * p.slot_mul + o1];
       if (slot < 0) continue;
-      const long long jj = p.remap_b > 0 ? (long long)(j / p.remap_b) * p.remap_ld + (j % p.remap_b) : j;
-      off = (long long)slot * p.out_sm + jj;
+      const long long jx = p.remap_b > 0 ? (long long)(j / p.remap_b) * p.remap_ld + (j % p.remap_b) : j;
+      off = (long long)slot * p.out_sm + jx;
+    } else {
+      // Symmetric scatter: line j carries entry (ti, tj), ti <= tj, of every
+      // bin.  A stored (canonical) bin takes it at (ti, tj); the partner bin
+      // -k is the transpose, so its value lands at (tj, ti) of the stored
+      // block; a self-paired bin takes both.
+      const int2 bs = p.bin_slot[k * p.slot_mul + o1];
+      const long long base = (long long)bs.x * p.out_sm;
+      if (bs.y == 1) {
+        off = base + (long long)tj * p.remap_ld + ti;
+      } else {
+        off = base + (long long)ti * p.remap_ld + tj;
+        if (bs.y == 2 && ti != tj) off2 = base + (long long)tj * p.remap_ld + ti;
+      }
     }
-    dst[off] = cvt<Cout>(v);
+    const Cout o = cvt<Cout>(v);
+    dst[off] = o;
     if (dst2) dst2[off] = cvt<float2>(v);
+    if (off2 >= 0) {
+      dst[off2] = o;
+      if (dst2) dst2[off2] = cvt<float2>(v);
+    }
   }
 }
 
@@ -127,21 +180,22 @@ template <typename R, typename Cin, typename Cout>
 static void launch_typed(const AxisPass &p, const FftTables &t, cudaStream_t st) {
   using C = typename Cplx<R>::T;
   const int M = t.plan.M;
-  int tj = 128;
-  while (tj > 32 && (size_t)M * tj * sizeof(C) > 96 * 1024) tj /= 2;
-  while (tj > 32 && tj / 2 >= p.ninner) tj /= 2;
+  // G threads per line: about 16 points each, at most 8.
+  int G = M / 16;
+  if (G < 1) G = 1;
+  if (G > 8) G = 8;
   const size_t head = ((size_t)M * sizeof(C) + (size_t)M * sizeof(int) + 15) & ~size_t(15);
-  const size_t smem = head + (size_t)M * tj * sizeof(C);
+  const size_t smem = head + (size_t)M * 32 * sizeof(C);
   static int configured = 0;
   if (!configured) {
     cudaFuncSetAttribute(axis_kernel<R, Cin, Cout>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     configured = 1;
   }
-  dim3 grid((p.ninner + tj - 1) / tj, p.n1 * p.n2);
+  dim3 grid((p.ninner + 31) / 32, p.n1 * p.n2);
   AxisKernelArgs a{p, t.plan};
   const C *tw = nullptr;
   if constexpr (sizeof(R) == 8) tw = t.tw64; else tw = t.tw32;
-  axis_kernel<R, Cin, Cout><<<grid, tj, smem, st>>>(a, tw, t.pos);
+  axis_kernel<R, Cin, Cout><<<grid, 32 * G, smem, st>>>(a, tw, t.pos);
 }
 
 template <typename R>

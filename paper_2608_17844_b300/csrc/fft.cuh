@@ -27,6 +27,7 @@ struct FftPlan {
   int M;
   int nst;
   int radix[MOMA_FFT_MAXST];
+  int span[MOMA_FFT_MAXST];  // span[s] = radix[s] * radix[s+1] * ... (span[0] = M)
 };
 
 // Radix-r forward DFT in registers: b[k] = sum_n a[n] w_r^{nk}.
@@ -72,44 +73,46 @@ MOMA_HD void butterfly(C *a, int r, const C *tw, int M) {
   }
 }
 
+// One stage of the transform, restricted to the butterflies bt = g, g + ng,
+// ... of that stage (ng cooperating threads share a line; the stages must
+// be separated by a barrier).  Stage s works on sub-problems of length
+// span[s] = r_s r_{s+1} ... r_{k-1}; there are M / span[s] of them.
 template <typename C>
-MOMA_HD void fft_dif(C *col, int ld, const FftPlan &pl, const C *tw) {
-  const int M = pl.M;
-  int Ms = M, G = 1;
-  for (int s = 0; s < pl.nst; ++s) {
-    const int r = pl.radix[s], Mp = Ms / r;
-    for (int g = 0; g < G; ++g) {
-      C *seg = col + (size_t)g * Ms * ld;
-      for (int k = 0; k < Mp; ++k) {
-        C a[5];
-        for (int n = 0; n < r; ++n) a[n] = seg[(n * Mp + k) * ld];
-        butterfly(a, r, tw, M);
-        seg[k * ld] = a[0];
-        for (int n = 1; n < r; ++n) seg[(n * Mp + k) * ld] = cmul(a[n], tw[k * n * G]);
-      }
-    }
-    Ms = Mp;
-    G *= r;
+MOMA_HD void dif_stage(C *col, int ld, const FftPlan &pl, const C *tw, int s, int g, int ng) {
+  const int M = pl.M, r = pl.radix[s], Ms = pl.span[s], Mp = Ms / r, G = M / Ms;
+  const int nbt = M / r;
+  for (int bt = g; bt < nbt; bt += ng) {
+    const int seg = bt / Mp, k = bt - seg * Mp;
+    C *base = col + (size_t)seg * Ms * ld;
+    C a[5];
+    for (int n = 0; n < r; ++n) a[n] = base[(n * Mp + k) * ld];
+    butterfly(a, r, tw, M);
+    base[k * ld] = a[0];
+    for (int n = 1; n < r; ++n) base[(n * Mp + k) * ld] = cmul(a[n], tw[k * n * G]);
   }
 }
 
 template <typename C>
-MOMA_HD void fft_dit(C *col, int ld, const FftPlan &pl, const C *tw) {
-  const int M = pl.M;
-  int Ms = 1;
-  for (int s = pl.nst - 1; s >= 0; --s) {
-    const int r = pl.radix[s], Mp = Ms;
-    Ms *= r;
-    const int G = M / Ms;
-    for (int g = 0; g < G; ++g) {
-      C *seg = col + (size_t)g * Ms * ld;
-      for (int k = 0; k < Mp; ++k) {
-        C a[5];
-        a[0] = seg[k * ld];
-        for (int n = 1; n < r; ++n) a[n] = cmul(seg[(n * Mp + k) * ld], tw[k * n * G]);
-        butterfly(a, r, tw, M);
-        for (int n = 0; n < r; ++n) seg[(n * Mp + k) * ld] = a[n];
-      }
-    }
+MOMA_HD void dit_stage(C *col, int ld, const FftPlan &pl, const C *tw, int s, int g, int ng) {
+  const int M = pl.M, r = pl.radix[s], Ms = pl.span[s], Mp = Ms / r, G = M / Ms;
+  const int nbt = M / r;
+  for (int bt = g; bt < nbt; bt += ng) {
+    const int seg = bt / Mp, k = bt - seg * Mp;
+    C *base = col + (size_t)seg * Ms * ld;
+    C a[5];
+    a[0] = base[k * ld];
+    for (int n = 1; n < r; ++n) a[n] = cmul(base[(n * Mp + k) * ld], tw[k * n * G]);
+    butterfly(a, r, tw, M);
+    for (int n = 0; n < r; ++n) base[(n * Mp + k) * ld] = a[n];
   }
+}
+
+// Single-thread transforms (one thread owns the whole line).
+template <typename C>
+MOMA_HD void fft_dif(C *col, int ld, const FftPlan &pl, const C *tw) {
+  for (int s = 0; s < pl.nst; ++s) dif_stage(col, ld, pl, tw, s, 0, 1);
+}
+template <typename C>
+MOMA_HD void fft_dit(C *col, int ld, const FftPlan &pl, const C *tw) {
+  for (int s = pl.nst - 1; s >= 0; --s) dit_stage(col, ld, pl, tw, s, 0, 1);
 }

@@ -38,13 +38,17 @@ struct AxisPass {
   int nin = 0;             // loaded points (the rest of the M-line is zero)
   int nout = 0;            // stored points
   int in_mode = 0;         // 0: point m <- axis index m; 1: circulant gather of 2N-1 offsets
-  int out_mode = 0;        // 0: point k -> axis index k; 1: k -> slot_of[k*slot_mul + o1]
+  int out_mode = 0;        // 0: point k -> axis index k; 1: k -> slot_of[k*slot_mul + o1]; 2: symmetric scatter
   const int *slot_of = nullptr;
   int slot_mul = 0;
   int remap_b = 0, remap_ld = 0;  // out_mode 1: inner j -> (j / remap_b) * remap_ld + j % remap_b
+  const int *inner_in_map = nullptr;  // if set: input inner offset of line j is inner_in_map[j]
+  const int2 *bin_slot = nullptr;     // out_mode 2: per bin (stored slot, 0 direct | 1 transposed | 2 both)
+  const int2 *tri = nullptr;          // out_mode 2: inner j -> block entry (i, j), i <= j
   int inverse = 0;         // conj(DFT(conj x)) / M
   int refft_keep = 0;      // >0: inverse, keep points < refft_keep, zero the rest, forward again
   int in_c128 = 1, out_c128 = 1;  // element types of in / out
+  const int *live = nullptr;       // if set and *live == 0 the pass does nothing
 };
 
 // Launch one axis pass computing in precision R (float or double).
@@ -60,6 +64,7 @@ struct BinProduct {
   int Bp = 0, b = 0, ldb = 0, nr = 0;
   int herm = 0;
   unsigned *err = nullptr;
+  const int *live = nullptr;  // if set and *live == 0 the product does nothing
 };
 template <typename R>
 void launch_bin_product(const BinProduct &p, int num_sms, cudaStream_t st);
@@ -80,7 +85,7 @@ void launch_tri_inverse(const double2 *Lpk, int nel, int b, void *X, size_t x_st
 // y_e = X_e^H X_e x_e for each element.
 template <typename R>
 void launch_precond_apply(const void *X, size_t x_stride, int nel, int b, int nr, const void *x, void *y,
-                          unsigned *err, cudaStream_t st);
+                          unsigned *err, const int *live, cudaStream_t st);
 
 // ------------------------------------------------------------- Krylov ----
 struct ArnoldiCtl;  // device-side control block (krylov.cu)

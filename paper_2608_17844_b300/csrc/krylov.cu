@@ -131,11 +131,13 @@ __global__ void __launch_bounds__(KT) cgs_kernel(KrylovCtl c, typename Cplx<R>::
     }
   }
   double2 *part = c.partial + ((size_t)q * gridDim.x + chunk) * (m + 1);
+  // Each thread sums its KEPT products in the vector precision; the partials
+  // are reduced across threads, CTAs and chunks in FP64.
   if (flags & KF_DOTS) {
     for (int i0 = 0; i0 <= j; i0 += KG) {
-      double2 acc[KG];
+      C accr[KG];
 #pragma unroll
-      for (int ii = 0; ii < KG; ++ii) acc[ii] = make_double2(0, 0);
+      for (int ii = 0; ii < KG; ++ii) accr[ii] = czero<C>();
 #pragma unroll
       for (int ii = 0; ii < KG; ++ii) {
         const int i = i0 + ii;
@@ -144,22 +146,23 @@ __global__ void __launch_bounds__(KT) cgs_kernel(KrylovCtl c, typename Cplx<R>::
 #pragma unroll
           for (int t = 0; t < KEPT; ++t) {
             const int n = n0 + tid + KT * t;
-            if (n < N) acc[ii] = cfmac(cvt<double2>(vi[n]), cvt<double2>(wv[t]), acc[ii]);
+            if (n < N) accr[ii] = cfmac(vi[n], wv[t], accr[ii]);
           }
         }
       }
+      double2 acc[KG];
+#pragma unroll
+      for (int ii = 0; ii < KG; ++ii) acc[ii] = cvt<double2>(accr[ii]);
       block_sum<KG>(acc, red);
       if (tid == 0)
         for (int ii = 0; ii < KG && i0 + ii <= j; ++ii) part[i0 + ii] = acc[ii];
     }
   }
   if (flags & KF_NORM) {
-    double2 acc[1] = {make_double2(0, 0)};
+    decltype(wv[0].x) nr2 = 0;
 #pragma unroll
-    for (int t = 0; t < KEPT; ++t) {
-      const double2 v = cvt<double2>(wv[t]);
-      acc[0].x += v.x * v.x + v.y * v.y;
-    }
+    for (int t = 0; t < KEPT; ++t) nr2 += wv[t].x * wv[t].x + wv[t].y * wv[t].y;
+    double2 acc[1] = {make_double2((double)nr2, 0)};
     block_sum<1>(acc, red);
     if (tid == 0) part[0] = acc[0];
   }

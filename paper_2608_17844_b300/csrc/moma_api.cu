@@ -78,7 +78,10 @@ __global__ void nonfinite_kernel(const void *p, size_t n_real, int is_double, un
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(err, DEVERR_NONFINITE);
 }
 
-enum { PK_BIN64 = 0, PK_BIN128 = 1, PK_PREC = 2, PK_FFT64 = 3, PK_BLOCKFFT = 4, PK_FFT128 = 5, PK_N = 6 };
+enum {
+  PK_BIN64 = 0, PK_BIN128 = 1, PK_PREC = 2, PK_FFT64 = 3, PK_BLOCKFFT = 4, PK_FFT128 = 5,
+  PK_GRAM = 6, PK_SAT = 7, PK_CHOL = 8, PK_TRINV = 9, PK_KRYLOV = 10, PK_MISC = 11, PK_N = 12
+};
 
 }  // namespace
 
@@ -94,6 +97,7 @@ struct moma_array {
   FftTables fx, fy;
   DevBuf tabs;      // twiddles / permutations of both plans
   DevBuf pairs, slot_of;
+  DevBuf bin_slot, tri, tri_in;  // symmetric block-transform tables
   DevBuf Z128, Z64;  // pair storage [Bp][b][ldb]
   DevBuf Xinv;       // inverse factors, packed row-major, inner precision
   size_t x_stride = 0;
@@ -114,6 +118,7 @@ struct moma_array {
   unsigned *err = nullptr;
   DevBuf one_blk;
   DevBuf portsb;  // Z_a and Gamma results [2][nr][nel]
+  const int *live = nullptr;  // operator kernels skip their work while *live == 0
 
   // pinned host mirrors
   int *h_nact = nullptr;  // ring of polled nact values
@@ -225,6 +230,34 @@ void build_tables(moma_array *a) {
   a->slot_of.ensure(slot.size() * sizeof(int), a->dev_bytes);
   CK(cudaMemcpy(a->pairs.p, pr.data(), pr.size() * sizeof(int2), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(a->slot_of.p, slot.data(), slot.size() * sizeof(int), cudaMemcpyHostToDevice));
+
+  // Block-transform tables: only entries (i <= j) are transformed; bin k
+  // stores them directly if it is the stored member of its pair, the
+  // partner -k scatters them transposed, a self-paired bin writes both.
+  std::vector<int2> bs(a->B);
+  for (int ky = 0; ky < a->My; ++ky)
+    for (int kx = 0; kx < a->Mx; ++kx) {
+      const int k = ky * a->Mx + kx;
+      const int nk = ((a->My - ky) % a->My) * a->Mx + ((a->Mx - kx) % a->Mx);
+      if (k == nk) bs[k] = make_int2(slot[k], 2);
+      else if (k < nk) bs[k] = make_int2(slot[k], 0);
+      else bs[k] = make_int2(slot[nk], 1);
+    }
+  const int b = a->b, nt = b * (b + 1) / 2;
+  std::vector<int2> tri(nt);
+  std::vector<int> tri_in(nt);
+  int t = 0;
+  for (int i = 0; i < b; ++i)
+    for (int j = i; j < b; ++j, ++t) {
+      tri[t] = make_int2(i, j);
+      tri_in[t] = i * b + j;
+    }
+  a->bin_slot.ensure(bs.size() * sizeof(int2), a->dev_bytes);
+  a->tri.ensure(tri.size() * sizeof(int2), a->dev_bytes);
+  a->tri_in.ensure(tri_in.size() * sizeof(int), a->dev_bytes);
+  CK(cudaMemcpy(a->bin_slot.p, bs.data(), bs.size() * sizeof(int2), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(a->tri.p, tri.data(), tri.size() * sizeof(int2), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(a->tri_in.p, tri_in.data(), tri_in.size() * sizeof(int), cudaMemcpyHostToDevice));
 }
 
 // ----------------------------------------------------- axis pass builders --
@@ -269,7 +302,8 @@ AxisPass pass_ix(moma_array *a, int nr, const void *in, void *out, int c128, boo
 template <typename R> constexpr int is64() { return sizeof(R) == 8 ? 1 : 0; }
 
 template <typename R>
-void axis(moma_array *a, const AxisPass &p, const FftTables &t) {
+void axis(moma_array *a, AxisPass p, const FftTables &t) {
+  p.live = a->live;
   a->timed(is64<R>() ? PK_FFT128 : PK_FFT64, [&] { launch_axis_pass<R>(p, t, a->st); });
   check_launch(a);
 }
@@ -280,13 +314,14 @@ void binprod(moma_array *a, int nr, const void *x, void *y, int herm) {
   P.Z = is64<R>() ? a->Z128.p : a->Z64.p;
   P.pairs = a->pairs.as<int2>();
   P.x = x; P.y = y; P.Bp = a->Bp; P.b = a->b; P.ldb = a->ldb; P.nr = nr; P.herm = herm; P.err = a->err;
+  P.live = a->live;
   a->timed(is64<R>() ? PK_BIN128 : PK_BIN64, [&] { launch_bin_product<R>(P, a->num_sms, a->st); });
   check_launch(a);
 }
 
 template <typename R>
 void precond(moma_array *a, int nr, const void *x, void *y) {
-  a->timed(PK_PREC, [&] { launch_precond_apply<R>(a->Xinv.p, a->x_stride, a->nel, a->b, nr, x, y, a->err, a->st); });
+  a->timed(PK_PREC, [&] { launch_precond_apply<R>(a->Xinv.p, a->x_stride, a->nel, a->b, nr, x, y, a->err, a->live, a->st); });
   check_launch(a);
 }
 
@@ -430,20 +465,20 @@ template <typename R>
 void build_preconditioner(moma_array *a, const void *blk, int blk128) {
   const int nD = (2 * a->nx - 1) * (2 * a->ny - 1), bb = a->b * a->b;
   a->S.ensure((size_t)nD * bb * sizeof(double2), a->dev_bytes);
-  launch_gram<R>(blk, blk128, nD, a->b, a->S.as<double2>(), a->st);
+  a->timed(PK_GRAM, [&] { launch_gram<R>(blk, blk128, nD, a->b, a->S.as<double2>(), a->st); });
   check_launch(a);
-  launch_sat(a->S.as<double2>(), 2 * a->ny - 1, 2 * a->nx - 1, bb, a->st);
+  a->timed(PK_SAT, [&] { launch_sat(a->S.as<double2>(), 2 * a->ny - 1, 2 * a->nx - 1, bb, a->st); });
   check_launch(a);
   const size_t npk = (size_t)a->b * (a->b + 1) / 2;
   a->Lpk.ensure((size_t)a->nel * npk * sizeof(double2), a->dev_bytes);
-  launch_box_cholesky(a->S.as<double2>(), a->nx, a->ny, a->b, a->Lpk.as<double2>(), a->err, a->st);
+  a->timed(PK_CHOL, [&] { launch_box_cholesky(a->S.as<double2>(), a->nx, a->ny, a->b, a->Lpk.as<double2>(), a->err, a->st); });
   check_launch(a);
   using C = typename Cplx<R>::T;
   size_t xs = npk;
   while ((xs * sizeof(C)) % 16) ++xs;
   a->x_stride = xs;
   a->Xinv.ensure((size_t)a->nel * xs * sizeof(C), a->dev_bytes);
-  launch_tri_inverse<R>(a->Lpk.as<double2>(), a->nel, a->b, a->Xinv.p, xs, a->st);
+  a->timed(PK_TRINV, [&] { launch_tri_inverse<R>(a->Lpk.as<double2>(), a->nel, a->b, a->Xinv.p, xs, a->st); });
   check_launch(a);
 }
 
@@ -458,20 +493,25 @@ void set_blocks_impl(moma_array *a, const void *blocks, int dtype) {
   sync_and_check(a);
 
   // Transformed first column of the circulant embedding (Eqs. 3, 11), FP64.
-  a->T.ensure((size_t)(2 * a->ny - 1) * a->Mx * bb * sizeof(double2), a->dev_bytes);
+  // Reciprocity (Z_{-D} = Z_D^T) makes Zhat_{-k} = Zhat_k^T, so only the
+  // b(b+1)/2 entries i <= j are transformed; the y pass scatters each bin's
+  // values into the stored block of its pair (transposed for the partner).
+  const int nt = a->b * (a->b + 1) / 2;
+  a->T.ensure((size_t)(2 * a->ny - 1) * a->Mx * nt * sizeof(double2), a->dev_bytes);
   AxisPass px;
-  px.in = blk; px.out = a->T.p; px.n1 = 2 * a->ny - 1; px.n2 = 1; px.ninner = bb;
+  px.in = blk; px.out = a->T.p; px.n1 = 2 * a->ny - 1; px.n2 = 1; px.ninner = nt;
   px.in_s1 = (long long)(2 * a->nx - 1) * bb; px.in_sm = bb; px.nin = 2 * a->nx - 1; px.in_mode = 1;
-  px.out_s1 = (long long)a->Mx * bb; px.out_sm = bb; px.nout = a->Mx;
+  px.inner_in_map = a->tri_in.as<int>();
+  px.out_s1 = (long long)a->Mx * nt; px.out_sm = nt; px.nout = a->Mx;
   px.in_c128 = dtype == MOMA_C128; px.out_c128 = 1;
   a->timed(PK_BLOCKFFT, [&] { launch_axis_pass<double>(px, a->fx, a->st); });
   check_launch(a);
   AxisPass py;
   py.in = a->T.p; py.out = a->Z128.p; py.out2 = a->prec == MOMA_PREC_MIXED ? a->Z64.p : nullptr;
-  py.n1 = a->Mx; py.n2 = 1; py.ninner = bb;
-  py.in_s1 = bb; py.in_sm = (long long)a->Mx * bb; py.nin = 2 * a->ny - 1; py.in_mode = 1;
-  py.out_mode = 1; py.slot_of = a->slot_of.as<int>(); py.slot_mul = a->Mx;
-  py.out_sm = (long long)a->b * a->ldb; py.remap_b = a->b; py.remap_ld = a->ldb; py.nout = a->My;
+  py.n1 = a->Mx; py.n2 = 1; py.ninner = nt;
+  py.in_s1 = nt; py.in_sm = (long long)a->Mx * nt; py.nin = 2 * a->ny - 1; py.in_mode = 1;
+  py.out_mode = 2; py.bin_slot = a->bin_slot.as<int2>(); py.tri = a->tri.as<int2>(); py.slot_mul = a->Mx;
+  py.out_sm = (long long)a->b * a->ldb; py.remap_ld = a->ldb; py.nout = a->My;
   py.in_c128 = 1; py.out_c128 = 1;
   a->timed(PK_BLOCKFFT, [&] { launch_axis_pass<double>(py, a->fy, a->st); });
   check_launch(a);
@@ -497,9 +537,9 @@ void gmres_cycle(moma_array *a, int nr, const std::vector<int> &act, int *inner_
   CK(cudaMemcpyAsync(c.active, a->mask, nr * sizeof(int), cudaMemcpyDeviceToDevice, a->st));
   CK(cudaMemsetAsync(c.kq, 0, nr * sizeof(int), a->st));
   CK(cudaMemcpyAsync(c.nact, a->h_nact + MOMA_MAX_RESTART + 4, sizeof(int), cudaMemcpyHostToDevice, a->st));
-  launch_cgs<R>(c, V, vstride, a->N, nr, -1, KF_NORM | KF_INIT, a->st);
+  a->timed(PK_KRYLOV, [&] { launch_cgs<R>(c, V, vstride, a->N, nr, -1, KF_NORM | KF_INIT, a->st); });
   check_launch(a);
-  launch_scale<R>(c, V, vstride, a->N, nr, a->st);
+  a->timed(PK_KRYLOV, [&] { launch_scale<R>(c, V, vstride, a->N, nr, a->st); });
   check_launch(a);
 
   const int lag = 2;
@@ -512,14 +552,16 @@ void gmres_cycle(moma_array *a, int nr, const std::vector<int> &act, int *inner_
   }
   int steps = 0;
   for (int j = 0; j < a->m; ++j) {
+    a->live = c.nact;  // steps queued after convergence cost only their launches
     apply_normal<R>(a, nr, V + (size_t)j * vstride, V + (size_t)(j + 1) * vstride);
-    launch_cgs<R>(c, V, vstride, a->N, nr, j, KF_DOTS, a->st);
+    a->live = nullptr;
+    a->timed(PK_KRYLOV, [&] { launch_cgs<R>(c, V, vstride, a->N, nr, j, KF_DOTS, a->st); });
     check_launch(a);
-    launch_cgs<R>(c, V, vstride, a->N, nr, j, KF_UPDATE | KF_DOTS | KF_ACCUM, a->st);
+    a->timed(PK_KRYLOV, [&] { launch_cgs<R>(c, V, vstride, a->N, nr, j, KF_UPDATE | KF_DOTS | KF_ACCUM, a->st); });
     check_launch(a);
-    launch_cgs<R>(c, V, vstride, a->N, nr, j, KF_UPDATE | KF_NORM, a->st);
+    a->timed(PK_KRYLOV, [&] { launch_cgs<R>(c, V, vstride, a->N, nr, j, KF_UPDATE | KF_NORM, a->st); });
     check_launch(a);
-    launch_scale<R>(c, V + (size_t)(j + 1) * vstride, vstride, a->N, nr, a->st);
+    a->timed(PK_KRYLOV, [&] { launch_scale<R>(c, V + (size_t)(j + 1) * vstride, vstride, a->N, nr, a->st); });
     check_launch(a);
     CK(cudaMemcpyAsync(a->h_nact + j, c.nact, sizeof(int), cudaMemcpyDeviceToHost, a->st));
     CK(cudaEventRecord(a->poll_ev[j], a->st));
@@ -543,9 +585,9 @@ void gmres_cycle(moma_array *a, int nr, const std::vector<int> &act, int *inner_
       if (act[q] && beta[q] > 0) mx = std::max(mx, res[q] / beta[q]);
     *first_red = mx;
   }
-  launch_backsolve(c, nr, a->st);
+  a->timed(PK_KRYLOV, [&] { launch_backsolve(c, nr, a->st); });
   check_launch(a);
-  launch_lincomb<R>(c, V, vstride, a->N, nr, a->Iw.as<double2>(), a->rnorm, a->st);
+  a->timed(PK_KRYLOV, [&] { launch_lincomb<R>(c, V, vstride, a->N, nr, a->Iw.as<double2>(), a->rnorm, a->st); });
   check_launch(a);
 }
 
@@ -564,7 +606,7 @@ void solve_impl(moma_array *a, int nr, const void *Vin, void *Iout, const moma_s
   if (warm) CK(cudaMemcpyAsync(a->Iw.p, Iout, bytes, cudaMemcpyDefault, a->st));
   else CK(cudaMemsetAsync(a->Iw.p, 0, bytes, a->st));
   check_finite(a, a->Vw.p, (size_t)nr * a->N * 2, 1);
-  launch_resid(a->Vw.as<double2>(), nullptr, nullptr, a->N, nr, a->rpart, a->rcount, a->vnorm, a->st);
+  a->timed(PK_MISC, [&] { launch_resid(a->Vw.as<double2>(), nullptr, nullptr, a->N, nr, a->rpart, a->rcount, a->vnorm, a->st); });
   check_launch(a);
   sync_and_check(a);
 
@@ -577,11 +619,11 @@ void solve_impl(moma_array *a, int nr, const void *Vin, void *Iout, const moma_s
   for (;;) {
     // True residual r = V - Z I in FP64 (c128 bins); I = 0 needs no product.
     if (outer == 0 && !warm) {
-      launch_resid(a->Vw.as<double2>(), nullptr, a->rw.as<double2>(), a->N, nr, a->rpart, a->rcount, a->rnorm, a->st);
+      a->timed(PK_MISC, [&] { launch_resid(a->Vw.as<double2>(), nullptr, a->rw.as<double2>(), a->N, nr, a->rpart, a->rcount, a->rnorm, a->st); });
     } else {
       apply_z<double>(a, nr, a->Iw.p, a->yw.p, 0);
-      launch_resid(a->Vw.as<double2>(), a->yw.as<double2>(), a->rw.as<double2>(), a->N, nr, a->rpart, a->rcount,
-                   a->rnorm, a->st);
+      a->timed(PK_MISC, [&] { launch_resid(a->Vw.as<double2>(), a->yw.as<double2>(), a->rw.as<double2>(), a->N, nr, a->rpart, a->rcount,
+                   a->rnorm, a->st); });
     }
     check_launch(a);
     CK(cudaMemcpyAsync(a->h_norms, a->rnorm, nr * sizeof(double), cudaMemcpyDeviceToHost, a->st));
@@ -597,7 +639,7 @@ void solve_impl(moma_array *a, int nr, const void *Vin, void *Iout, const moma_s
     if (nact == 0) { converged = true; break; }
     if (outer >= max_outer) break;
     CK(cudaMemcpyAsync(a->mask, mask.data(), nr * sizeof(int), cudaMemcpyHostToDevice, a->st));
-    launch_to_inner<R>(a->rw.as<double2>(), a->lat_in.p, a->N, nr, a->rnorm, a->mask, a->st);
+    a->timed(PK_MISC, [&] { launch_to_inner<R>(a->rw.as<double2>(), a->lat_in.p, a->N, nr, a->rnorm, a->mask, a->st); });
     check_launch(a);
     gmres_cycle<R>(a, nr, mask, &inner, outer == 0 ? &first_red : nullptr);
     sync_and_check(a);
@@ -635,7 +677,7 @@ template <typename F> moma_status guarded(F &&f) {
 }
 
 void destroy_impl(moma_array *a) {
-  DevBuf *bufs[] = {&a->tabs, &a->pairs, &a->slot_of, &a->Z128, &a->Z64, &a->Xinv, &a->blk, &a->T, &a->S,
+  DevBuf *bufs[] = {&a->tabs, &a->pairs, &a->slot_of, &a->bin_slot, &a->tri, &a->tri_in, &a->Z128, &a->Z64, &a->Xinv, &a->blk, &a->T, &a->S,
                     &a->Lpk, &a->lat_in, &a->lat_tmp, &a->t1, &a->bx, &a->by, &a->Vk, &a->Iw, &a->Vw,
                     &a->rw, &a->yw, &a->kbuf, &a->errbuf, &a->one_blk, &a->portsb};
   for (DevBuf *b : bufs) b->release(a->dev_bytes);

@@ -117,61 +117,95 @@ MOMA_DEV double2 box_entry(const double2 *S, int ndx, int bb, int x0, int x1, in
   return v;
 }
 
-MOMA_HD size_t colpk(int i, int k, int b) {  // packed column-major lower, i >= k
-  return (size_t)k * b - (size_t)k * (k - 1) / 2 + (i - k);
-}
-MOMA_HD size_t rowpk(int i, int k) {  // packed row-major lower, i >= k
-  return (size_t)i * (i + 1) / 2 + k;
-}
 
 // ------------------------------------------------------- box + Cholesky ---
 // One CTA per element.  The packed lower triangle of P_e is assembled from
-// the summed-area table and factored right-looking, column by column, in
-// FP64; L_e (packed column-major) is written to Lpk.
+// the summed-area table (row by row, so reads of the table are contiguous)
+// and factored in FP64 by a blocked right-looking Cholesky: a panel of CH_NB
+// columns is factored column by column, then the trailing matrix receives
+// the rank-CH_NB update A(i,k) -= sum_p L(i,p) conj(L(k,p)) in one sweep
+// (warps own columns k, lanes own rows i, four rows per lane in flight).
+// L_e (packed column-major) is written to Lpk.
+constexpr int CH_NB = 8;
+
+MOMA_HD int colbase(int k, int b) { return k * b - k * (k - 1) / 2; }  // start of column k (packed)
+
 template <bool IN_SMEM>
-__global__ void __launch_bounds__(256) box_cholesky_kernel(const double2 *__restrict__ S, int nx, int ny, int b,
+__global__ void __launch_bounds__(512) box_cholesky_kernel(const double2 *__restrict__ S, int nx, int ny, int b,
                                                            double2 *__restrict__ Lpk, unsigned *err) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int e = blockIdx.x, ex = e % nx, ey = e / nx;
-  const size_t npk = (size_t)b * (b + 1) / 2;
+  const int npk = b * (b + 1) / 2;
   double2 *A = IN_SMEM ? reinterpret_cast<double2 *>(smraw) : Lpk + (size_t)e * npk;
   const int ndx = 2 * nx - 1, bb = b * b;
   const int x0 = nx - 1 - ex, x1 = 2 * nx - 2 - ex, y0 = ny - 1 - ey, y1 = 2 * ny - 2 - ey;
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
 
-  for (int k = 0; k < b; ++k)
-    for (int i = k + tid; i < b; i += blockDim.x) A[colpk(i, k, b)] = box_entry(S, ndx, bb, x0, x1, y0, y1, i * b + k);
+  // Assemble: linear index t runs over the lower triangle row by row.
+  for (int t = tid; t < npk; t += blockDim.x) {
+    int i = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+    while (i * (i + 1) / 2 > t) --i;
+    while ((i + 1) * (i + 2) / 2 <= t) ++i;
+    const int k = t - i * (i + 1) / 2;
+    A[colbase(k, b) + i - k] = box_entry(S, ndx, bb, x0, x1, y0, y1, i * b + k);
+  }
   __syncthreads();
 
-  __shared__ int bad;
-  if (tid == 0) bad = 0;
-  __syncthreads();
-  for (int j = 0; j < b; ++j) {
-    const double d = A[colpk(j, j, b)].x;
-    if (!(d > 0.0) || !isfinite(d)) {  // uniform: every thread reads the same value
-      if (tid == 0) atomicOr(err, DEVERR_NOT_PD);
-      bad = 1;
-      break;
+  for (int jb = 0; jb < b; jb += CH_NB) {
+    const int je = min(jb + CH_NB, b);
+    // Panel: columns jb .. je-1, unblocked.
+    for (int j = jb; j < je; ++j) {
+      double2 *cj = A + colbase(j, b) - j;  // cj[i] = A(i, j), i >= j
+      const double d = cj[j].x;
+      if (!(d > 0.0) || !isfinite(d)) {  // uniform: every thread reads the same value
+        if (tid == 0) atomicOr(err, DEVERR_NOT_PD);
+        return;
+      }
+      const double l = sqrt(d), inv_l = 1.0 / l;
+      __syncthreads();  // everyone has read d before the column is overwritten
+      for (int i = j + tid; i < b; i += blockDim.x) cj[i] = (i == j) ? make_double2(l, 0.0) : cscale(cj[i], inv_l);
+      __syncthreads();
+      for (int k = j + 1 + w; k < je; k += nw) {
+        double2 *ck = A + colbase(k, b) - k;
+        const double2 lkj = cconj(cj[k]);
+        for (int i = k + lane; i < b; i += 32) ck[i] = csub(ck[i], cmul(cj[i], lkj));
+      }
+      __syncthreads();
     }
-    const double l = sqrt(d), inv_l = 1.0 / l;
-    __syncthreads();  // everyone has read d before the column is overwritten
-    for (int i = j + tid; i < b; i += blockDim.x) {
-      const size_t q = colpk(i, j, b);
-      A[q] = (i == j) ? make_double2(l, 0.0) : cscale(A[q], inv_l);
-    }
-    __syncthreads();
-    for (int k = j + 1 + w; k < b; k += blockDim.x / 32) {
-      const double2 lkj = cconj(A[colpk(k, j, b)]);
-      for (int i = k + lane; i < b; i += 32) {
-        const size_t q = colpk(i, k, b);
-        A[q] = csub(A[q], cmul(A[colpk(i, j, b)], lkj));
+    // Trailing rank-(je - jb) update.
+    const int np = je - jb;
+    int pb[CH_NB];
+#pragma unroll
+    for (int p = 0; p < CH_NB; ++p) pb[p] = p < np ? colbase(jb + p, b) - (jb + p) : 0;
+    for (int k = je + w; k < b; k += nw) {
+      double2 *ck = A + colbase(k, b) - k;
+      double2 lk[CH_NB];
+#pragma unroll
+      for (int p = 0; p < CH_NB; ++p) lk[p] = p < np ? cconj(A[pb[p] + k]) : make_double2(0, 0);
+      for (int i0 = k + lane; i0 < b; i0 += 128) {
+        double2 acc[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) acc[r] = (i0 + 32 * r < b) ? ck[i0 + 32 * r] : make_double2(0, 0);
+#pragma unroll
+        for (int p = 0; p < CH_NB; ++p) {
+          if (p < np) {
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+              const int i = i0 + 32 * r;
+              if (i < b) acc[r] = csub(acc[r], cmul(A[pb[p] + i], lk[p]));
+            }
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+          if (i0 + 32 * r < b) ck[i0 + 32 * r] = acc[r];
       }
     }
     __syncthreads();
   }
-  if (IN_SMEM && !bad) {
+  if (IN_SMEM) {
     double2 *dst = Lpk + (size_t)e * npk;
-    for (size_t q = tid; q < npk; q += blockDim.x) dst[q] = A[q];
+    for (int q = tid; q < npk; q += blockDim.x) dst[q] = A[q];
   }
 }
 
@@ -184,9 +218,9 @@ void launch_box_cholesky(const double2 *S, int nx, int ny, int b, double2 *Lpk, 
       cudaFuncSetAttribute(box_cholesky_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
       configured = 1;
     }
-    box_cholesky_kernel<true><<<nel, 256, bytes, st>>>(S, nx, ny, b, Lpk, err);
+    box_cholesky_kernel<true><<<nel, 512, bytes, st>>>(S, nx, ny, b, Lpk, err);
   } else {
-    box_cholesky_kernel<false><<<nel, 256, 0, st>>>(S, nx, ny, b, Lpk, err);
+    box_cholesky_kernel<false><<<nel, 512, 0, st>>>(S, nx, ny, b, Lpk, err);
   }
 }
 
@@ -202,38 +236,54 @@ void launch_box_one(const double2 *S, int nx, int ny, int b, int ex, int ey, dou
 }
 
 // ---------------------------------------------------- inverse factor -----
-// X = L^{-1} by rows: X[i][k] = (delta_ik - sum_{k<=m<i} L[i][m] X[m][k]) / L[i][i].
-// L is staged in shared memory (packed column-major, precision R); X rows are
-// written packed row-major to global memory (stride x_stride elements per
-// element) and re-read from there (L1/L2 resident).
-template <typename R>
+// X = L^{-1}, one column per warp: column k solves L x = e_k by forward
+// substitution in axpy form -- at step m the lane holding row m finishes
+// x_m = x_m / L_mm, broadcasts it, and every lane updates its rows i > m
+// with column m of L (contiguous in the packed column-major layout, staged
+// in shared memory in precision R).  x lives in registers (lane owns rows
+// lane + 32u).  X is written packed column-major, so the column store is
+// coalesced.
+template <typename R, int U>
 __global__ void __launch_bounds__(256) tri_inverse_kernel(const double2 *__restrict__ Lpk, int b,
                                                           typename Cplx<R>::T *X, size_t x_stride) {
   using C = typename Cplx<R>::T;
   extern __shared__ __align__(16) unsigned char smraw[];
   C *L = reinterpret_cast<C *>(smraw);
-  const int e = blockIdx.x;
+  const int e = blockIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const size_t npk = (size_t)b * (b + 1) / 2;
   const double2 *Le = Lpk + (size_t)e * npk;
   C *Xe = X + (size_t)e * x_stride;
   for (size_t q = threadIdx.x; q < npk; q += blockDim.x) L[q] = cvt<C>(Le[q]);
   for (size_t q = npk + threadIdx.x; q < x_stride; q += blockDim.x) Xe[q] = czero<C>();  // pad
   __syncthreads();
-  // Threads own columns k; the sum over m runs in the same order on every
-  // thread so L[i][m] is a broadcast and X[m][k] reads are contiguous in k.
-  for (int i = 0; i < b; ++i) {
-    const R inv = (R)1 / L[colpk(i, i, b)].x;
-    for (int k0 = 0; k0 <= i; k0 += blockDim.x) {
-      const int k = k0 + threadIdx.x;
-      C acc = czero<C>();
-      for (int m = k0; m < i; ++m)
-        if (m >= k) acc = cfma(L[colpk(i, m, b)], Xe[rowpk(m, k)], acc);
-      if (k <= i) {
-        C v = (k == i) ? mk((R)1, (R)0) : czero<C>();
-        Xe[rowpk(i, k)] = cscale(csub(v, acc), inv);
+  for (int k = w; k < b; k += nw) {
+    C x[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) x[u] = (lane + 32 * u == k) ? mk((R)1, (R)0) : czero<C>();
+#pragma unroll
+    for (int u0 = 0; u0 < U; ++u0) {
+      for (int lm = 0; lm < 32; ++lm) {
+        const int m = 32 * u0 + lm;
+        if (m >= b) break;
+        if (m < k) continue;
+        const C *Lc = L + colbase(m, b) - m;  // Lc[i] = L(i, m)
+        if (lane == lm) x[u0] = cscale(x[u0], (R)1 / Lc[m].x);
+        C xm;
+        xm.x = __shfl_sync(0xffffffffu, x[u0].x, lm);
+        xm.y = __shfl_sync(0xffffffffu, x[u0].y, lm);
+#pragma unroll
+        for (int u = u0; u < U; ++u) {
+          const int i = lane + 32 * u;
+          if (i > m && i < b) x[u] = csub(x[u], cmul(Lc[i], xm));
+        }
       }
     }
-    __syncthreads();
+    C *Xc = Xe + colbase(k, b) - k;  // Xc[i] = X(i, k)
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = lane + 32 * u;
+      if (i >= k && i < b) Xc[i] = x[u];
+    }
   }
 }
 
@@ -241,22 +291,26 @@ template <typename R>
 void launch_tri_inverse(const double2 *Lpk, int nel, int b, void *X, size_t x_stride, cudaStream_t st) {
   using C = typename Cplx<R>::T;
   const size_t bytes = (size_t)b * (b + 1) / 2 * sizeof(C);
-  static int configured = 0;
-  if (!configured) {
-    cudaFuncSetAttribute(tri_inverse_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-    configured = 1;
-  }
-  tri_inverse_kernel<R><<<nel, 256, bytes, st>>>(Lpk, b, reinterpret_cast<C *>(X), x_stride);
+  const int U = (b + 31) / 32;
+  auto go = [&](auto kern) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    kern<<<nel, 256, bytes, st>>>(Lpk, b, reinterpret_cast<C *>(X), x_stride);
+  };
+  if (U <= 1) go(tri_inverse_kernel<R, 1>);
+  else if (U <= 2) go(tri_inverse_kernel<R, 2>);
+  else if (U <= 4) go(tri_inverse_kernel<R, 4>);
+  else go(tri_inverse_kernel<R, 8>);
 }
 template void launch_tri_inverse<float>(const double2 *, int, int, void *, size_t, cudaStream_t);
 template void launch_tri_inverse<double>(const double2 *, int, int, void *, size_t, cudaStream_t);
 
 // ------------------------------------------------------------ apply ------
-// y_e = X_e^H (X_e x_e).  One CTA per element; X_e arrives in shared memory
-// with one bulk copy.  Phase 1: warps own rows i of X, lanes own columns
-// k <= i (warp-reduced row products).  Phase 2: the same rows, lanes
-// accumulate conj(X[i][k]) t_i into per-warp column partials, reduced
-// across warps at the end.
+// y_e = X_e^H (X_e x_e), X_e = L_e^{-1} packed column-major.  One CTA per
+// element; X_e arrives in shared memory with one bulk copy.
+//  Phase 1, t = X x: warps own columns k, lanes own rows i >= k and
+//    accumulate X(i,k) x_k in registers; partial t is reduced across warps.
+//  Phase 2, z = X^H t: warps own columns k, lanes own rows i >= k, and
+//    z_k = sum_i conj(X(i,k)) t_i is a warp reduction.
 constexpr int PA_THREADS = 256, PA_WARPS = 8;
 
 template <typename R, int NR, int U>
@@ -264,15 +318,16 @@ __global__ void __launch_bounds__(PA_THREADS) precond_apply_kernel(const typenam
                                                                    size_t x_stride, int nel, int b, int nr,
                                                                    const typename Cplx<R>::T *__restrict__ x,
                                                                    typename Cplx<R>::T *__restrict__ y,
-                                                                   unsigned *err) {
+                                                                   unsigned *err, const int *live) {
   using C = typename Cplx<R>::T;
   extern __shared__ __align__(128) unsigned char smraw[];
   uint64_t *bar = reinterpret_cast<uint64_t *>(smraw);
   C *Xs = reinterpret_cast<C *>(smraw + 128);
   C *xs = Xs + x_stride;              // [b][NR]
   C *ts = xs + (size_t)b * NR;        // [b][NR]
-  C *zp = ts + (size_t)b * NR;        // [PA_WARPS][b][NR]
+  C *tp = ts + (size_t)b * NR;        // [PA_WARPS][b][NR]
   const int e = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  if (live && *live == 0) return;
   if (tid == 0) {
     mbar_init(bar, 1);
     fence_mbar_init();
@@ -299,56 +354,59 @@ __global__ void __launch_bounds__(PA_THREADS) precond_apply_kernel(const typenam
       xs[idx] = q < nr ? x[((size_t)q * nel + e) * b + k] : czero<C>();
     }
     __syncthreads();
-    for (int i = w; i < b; i += PA_WARPS) {
-      const C *row = Xs + rowpk(i, 0);
-      C p[NR];
-#pragma unroll
-      for (int qq = 0; qq < NR; ++qq) p[qq] = czero<C>();
-      for (int k = lane; k <= i; k += 32) {
-        const C xv = row[k];
-#pragma unroll
-        for (int qq = 0; qq < NR; ++qq) p[qq] = cfma(xv, xs[k * NR + qq], p[qq]);
-      }
-#pragma unroll
-      for (int qq = 0; qq < NR; ++qq) {
-        const C v = warp_sum(p[qq]);
-        if (lane == 0) ts[i * NR + qq] = v;
-      }
-    }
-    __syncthreads();
     C acc[U][NR];
 #pragma unroll
     for (int u = 0; u < U; ++u)
 #pragma unroll
       for (int qq = 0; qq < NR; ++qq) acc[u][qq] = czero<C>();
-    for (int i = w; i < b; i += PA_WARPS) {
-      const C *row = Xs + rowpk(i, 0);
-      C tv[NR];
+    for (int k = w; k < b; k += PA_WARPS) {
+      const C *col = Xs + colbase(k, b) - k;
+      C xk[NR];
 #pragma unroll
-      for (int qq = 0; qq < NR; ++qq) tv[qq] = ts[i * NR + qq];
+      for (int qq = 0; qq < NR; ++qq) xk[qq] = xs[k * NR + qq];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const int k = lane + 32 * u;
-        if (k <= i) {
-          const C xv = row[k];
+        const int i = lane + 32 * u;
+        if (i >= k && i < b) {
+          const C xv = col[i];
 #pragma unroll
-          for (int qq = 0; qq < NR; ++qq) acc[u][qq] = cfmac(xv, tv[qq], acc[u][qq]);
+          for (int qq = 0; qq < NR; ++qq) acc[u][qq] = cfma(xv, xk[qq], acc[u][qq]);
         }
       }
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int k = lane + 32 * u;
-      if (k < b)
+      const int i = lane + 32 * u;
+      if (i < b)
 #pragma unroll
-        for (int qq = 0; qq < NR; ++qq) zp[((size_t)w * b + k) * NR + qq] = acc[u][qq];
+        for (int qq = 0; qq < NR; ++qq) tp[((size_t)w * b + i) * NR + qq] = acc[u][qq];
     }
     __syncthreads();
     for (int idx = tid; idx < b * NR; idx += PA_THREADS) {
       C v = czero<C>();
-      for (int ww = 0; ww < PA_WARPS; ++ww) v = cadd(v, zp[(size_t)ww * b * NR + idx]);
-      const int k = idx / NR, q = q0 + idx % NR;
-      if (q < nr) y[((size_t)q * nel + e) * b + k] = v;
+      for (int ww = 0; ww < PA_WARPS; ++ww) v = cadd(v, tp[(size_t)ww * b * NR + idx]);
+      ts[idx] = v;
+    }
+    __syncthreads();
+    for (int k = w; k < b; k += PA_WARPS) {
+      const C *col = Xs + colbase(k, b) - k;
+      C p[NR];
+#pragma unroll
+      for (int qq = 0; qq < NR; ++qq) p[qq] = czero<C>();
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int i = lane + 32 * u;
+        if (i >= k && i < b) {
+          const C xv = col[i];
+#pragma unroll
+          for (int qq = 0; qq < NR; ++qq) p[qq] = cfmac(xv, ts[i * NR + qq], p[qq]);
+        }
+      }
+#pragma unroll
+      for (int qq = 0; qq < NR; ++qq) {
+        const C v = warp_sum(p[qq]);
+        if (lane == 0 && q0 + qq < nr) y[((size_t)(q0 + qq) * nel + e) * b + k] = v;
+      }
     }
     __syncthreads();
   }
@@ -356,7 +414,7 @@ __global__ void __launch_bounds__(PA_THREADS) precond_apply_kernel(const typenam
 
 template <typename R, int NR, int U>
 static void apply_launch(const void *X, size_t x_stride, int nel, int b, int nr, const void *x, void *y,
-                         unsigned *err, cudaStream_t st) {
+                         unsigned *err, const int *live, cudaStream_t st) {
   using C = typename Cplx<R>::T;
   const size_t smem = 128 + x_stride * sizeof(C) + (size_t)(2 + PA_WARPS) * b * NR * sizeof(C);
   static int configured = 0;
@@ -366,28 +424,28 @@ static void apply_launch(const void *X, size_t x_stride, int nel, int b, int nr,
   }
   precond_apply_kernel<R, NR, U><<<nel, PA_THREADS, smem, st>>>(
       reinterpret_cast<const C *>(X), x_stride, nel, b, nr, reinterpret_cast<const C *>(x),
-      reinterpret_cast<C *>(y), err);
+      reinterpret_cast<C *>(y), err, live);
 }
 
 template <typename R, int NR>
 static void apply_u(const void *X, size_t xs, int nel, int b, int nr, const void *x, void *y, unsigned *err,
-                    cudaStream_t st) {
+                    const int *live, cudaStream_t st) {
   const int U = (b + 31) / 32;
-  if (U <= 1) apply_launch<R, NR, 1>(X, xs, nel, b, nr, x, y, err, st);
-  else if (U <= 2) apply_launch<R, NR, 2>(X, xs, nel, b, nr, x, y, err, st);
-  else if (U <= 4) apply_launch<R, NR, 4>(X, xs, nel, b, nr, x, y, err, st);
-  else apply_launch<R, NR, 8>(X, xs, nel, b, nr, x, y, err, st);
+  if (U <= 1) apply_launch<R, NR, 1>(X, xs, nel, b, nr, x, y, err, live, st);
+  else if (U <= 2) apply_launch<R, NR, 2>(X, xs, nel, b, nr, x, y, err, live, st);
+  else if (U <= 4) apply_launch<R, NR, 4>(X, xs, nel, b, nr, x, y, err, live, st);
+  else apply_launch<R, NR, 8>(X, xs, nel, b, nr, x, y, err, live, st);
 }
 
 template <typename R>
 void launch_precond_apply(const void *X, size_t x_stride, int nel, int b, int nr, const void *x, void *y,
-                          unsigned *err, cudaStream_t st) {
-  if (nr == 1) apply_u<R, 1>(X, x_stride, nel, b, nr, x, y, err, st);
-  else apply_u<R, 2>(X, x_stride, nel, b, nr, x, y, err, st);
+                          unsigned *err, const int *live, cudaStream_t st) {
+  if (nr == 1) apply_u<R, 1>(X, x_stride, nel, b, nr, x, y, err, live, st);
+  else apply_u<R, 2>(X, x_stride, nel, b, nr, x, y, err, live, st);
 }
 template void launch_precond_apply<float>(const void *, size_t, int, int, int, const void *, void *, unsigned *,
-                                          cudaStream_t);
+                                          const int *, cudaStream_t);
 template void launch_precond_apply<double>(const void *, size_t, int, int, int, const void *, void *, unsigned *,
-                                           cudaStream_t);
+                                           const int *, cudaStream_t);
 
 }  // namespace moma

@@ -28,6 +28,16 @@ int main(int argc, char **argv) {
     col = x;
     fft_dif(col.data(), 1, pl, tw.data());
     for (int k = 0; k < M; ++k) out[k] = col[pos[k]];
+  } else if (!strcmp(mode, "difcoop")) {  // stages split over `keep` cooperating threads
+    col = x;
+    for (int s = 0; s < pl.nst; ++s)
+      for (int g = 0; g < keep; ++g) dif_stage(col.data(), 1, pl, tw.data(), s, g, keep);
+    for (int k = 0; k < M; ++k) out[k] = col[pos[k]];
+  } else if (!strcmp(mode, "ditcoop")) {
+    for (int n = 0; n < M; ++n) col[pos[n]] = x[n];
+    for (int s = pl.nst - 1; s >= 0; --s)
+      for (int g = 0; g < keep; ++g) dit_stage(col.data(), 1, pl, tw.data(), s, g, keep);
+    out = col;
   } else if (!strcmp(mode, "dit")) {  // x[n] at pos[n], natural out
     for (int n = 0; n < M; ++n) col[pos[n]] = x[n];
     fft_dit(col.data(), 1, pl, tw.data());

@@ -43,6 +43,18 @@ def test_forward_matches_numpy(exe, M, mode):
     assert np.allclose(y, ref, rtol=0, atol=1e-13 * max(1.0, np.abs(ref).max()))
 
 
+@pytest.mark.parametrize("M", [4, 15, 48, 64, 80, 96, 128])
+@pytest.mark.parametrize("mode", ["difcoop", "ditcoop"])
+@pytest.mark.parametrize("ng", [2, 3, 4, 8])
+def test_cooperative_stage_split(exe, M, mode, ng):
+    """Stages split over ng cooperating threads give the same transform."""
+    rng = np.random.default_rng(M + ng)
+    x = rng.standard_normal(M) + 1j * rng.standard_normal(M)
+    _, y = _run(exe, x, mode, ng)
+    ref = np.fft.fft(x)
+    assert np.allclose(y, ref, rtol=0, atol=1e-13 * max(1.0, np.abs(ref).max()))
+
+
 @pytest.mark.parametrize("M,keep", [(8, 3), (48, 24), (64, 32), (96, 40), (5, 3), (1, 1)])
 def test_inverse_mask_forward(exe, M, keep):
     rng = np.random.default_rng(7 + M)
