@@ -32,6 +32,18 @@ template <typename C> MOMA_HD C cfmac(C a, C b, C acc) {
   acc.y = fma(a.x, b.y, acc.y); acc.y = fma(-a.y, b.x, acc.y);
   return acc;
 }
+// acc - a*conj(b), four fused multiply-adds
+template <typename C> MOMA_HD C cfms_conj(C a, C b, C acc) {
+  acc.x = fma(-a.x, b.x, acc.x); acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(-a.y, b.x, acc.y); acc.y = fma(a.x, b.y, acc.y);
+  return acc;
+}
+// acc - a*b, four fused multiply-adds
+template <typename C> MOMA_HD C cfms(C a, C b, C acc) {
+  acc.x = fma(-a.x, b.x, acc.x); acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(-a.x, b.y, acc.y); acc.y = fma(-a.y, b.x, acc.y);
+  return acc;
+}
 template <typename C> MOMA_HD C cconj(C a) { a.y = -a.y; return a; }
 template <typename C, typename S> MOMA_HD C cscale(C a, S s) { a.x *= s; a.y *= s; return a; }
 // multiply by -i and +i

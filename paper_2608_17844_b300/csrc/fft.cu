@@ -1,6 +1,7 @@
 // Lattice-axis FFT passes: the building block of the MLFFT (Eq. 2) used
 // both for the one-time transform of the offset blocks into circulant bins
 // (Eqs. 3 and 11) and for the per-iteration transforms of the vectors.
+#include <algorithm>
 #include <cmath>
 #include <stdexcept>
 
@@ -180,10 +181,15 @@ template <typename R, typename Cin, typename Cout>
 static void launch_typed(const AxisPass &p, const FftTables &t, cudaStream_t st) {
   using C = typename Cplx<R>::T;
   const int M = t.plan.M;
-  // G threads per line: about 16 points each, at most 8.
-  int G = M / 16;
-  if (G < 1) G = 1;
-  if (G > 8) G = 8;
+  // G threads per line: about 16 points each; when the batch has few lines
+  // (vector passes at small nrhs) G grows -- up to one butterfly per thread
+  // per stage -- until there are ~24 warps per SM to hide latency.
+  int gmax = 1;
+  for (int s = 0; s < t.plan.nst; ++s) gmax = std::max(gmax, M / t.plan.radix[s]);
+  if (gmax > 32) gmax = 32;
+  int G = std::max(1, std::min(8, M / 16));
+  const long long ctas = (long long)((p.ninner + 31) / 32) * p.n1 * p.n2;
+  while (G * 2 <= gmax && ctas * G < 24LL * 148) G *= 2;
   const size_t head = ((size_t)M * sizeof(C) + (size_t)M * sizeof(int) + 15) & ~size_t(15);
   const size_t smem = head + (size_t)M * 32 * sizeof(C);
   static int configured = 0;

@@ -22,10 +22,10 @@ constexpr int KT = 256;   // threads per CTA
 constexpr int KEPT = 4;   // elements per thread
 constexpr int KG = 8;     // dot products reduced together
 
-// Block-wide sum of NV double2 values held by every thread; result valid in
-// thread 0 for all NV values (red must hold 8 * NV double2).
-template <int NV>
-MOMA_DEV void block_sum(double2 (&v)[NV], double2 *red) {
+// Block-wide sum of NV complex values held by every thread, in the
+// precision of C; result valid in thread 0 (red must hold 8 * NV values).
+template <typename C, int NV>
+MOMA_DEV void block_sum(C (&v)[NV], C *red) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
   for (int i = 0; i < NV; ++i) v[i] = warp_sum(v[i]);
@@ -36,12 +36,21 @@ MOMA_DEV void block_sum(double2 (&v)[NV], double2 *red) {
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
-      double2 s = red[i];
+      C s = red[i];
       for (int ww = 1; ww < KT / 32; ++ww) s = cadd(s, red[ww * NV + i]);
       v[i] = s;
     }
   }
   __syncthreads();
+}
+
+// Sum over the nch chunk partials of value i (stride `stride`), in FP64 and
+// a fixed order: lanes take chunks lane, lane+32, ..., then a warp tree.
+MOMA_DEV double2 chunk_sum(const double2 *pq, int nch, int stride, int i) {
+  const int lane = threadIdx.x & 31;
+  double2 s = make_double2(0, 0);
+  for (int ch = lane; ch < nch; ch += 32) s = cadd(s, pq[(size_t)ch * stride + i]);
+  return warp_sum(s);
 }
 
 // Givens step for column j of RHS q (thread-serial, FP64).
@@ -96,7 +105,7 @@ template <typename R>
 __global__ void __launch_bounds__(KT) cgs_kernel(KrylovCtl c, typename Cplx<R>::T *V, size_t vstride, int N, int j,
                                                   int flags) {
   using C = typename Cplx<R>::T;
-  __shared__ double2 red[8 * KG];
+  __shared__ C red[8 * KG];
   __shared__ C hs[MOMA_MAX_RESTART + 1];
   __shared__ int last;
   const int q = blockIdx.y, chunk = blockIdx.x, tid = threadIdx.x;
@@ -150,21 +159,17 @@ __global__ void __launch_bounds__(KT) cgs_kernel(KrylovCtl c, typename Cplx<R>::
           }
         }
       }
-      double2 acc[KG];
-#pragma unroll
-      for (int ii = 0; ii < KG; ++ii) acc[ii] = cvt<double2>(accr[ii]);
-      block_sum<KG>(acc, red);
+      block_sum<C, KG>(accr, red);
       if (tid == 0)
-        for (int ii = 0; ii < KG && i0 + ii <= j; ++ii) part[i0 + ii] = acc[ii];
+        for (int ii = 0; ii < KG && i0 + ii <= j; ++ii) part[i0 + ii] = cvt<double2>(accr[ii]);
     }
   }
   if (flags & KF_NORM) {
-    decltype(wv[0].x) nr2 = 0;
+    C acc[1] = {czero<C>()};
 #pragma unroll
-    for (int t = 0; t < KEPT; ++t) nr2 += wv[t].x * wv[t].x + wv[t].y * wv[t].y;
-    double2 acc[1] = {make_double2((double)nr2, 0)};
-    block_sum<1>(acc, red);
-    if (tid == 0) part[0] = acc[0];
+    for (int t = 0; t < KEPT; ++t) acc[0].x += wv[t].x * wv[t].x + wv[t].y * wv[t].y;
+    block_sum<C, 1>(acc, red);
+    if (tid == 0) part[0] = cvt<double2>(acc[0]);
   }
 
   // Last-block reduction over the chunks of this RHS, in chunk order.
@@ -174,35 +179,37 @@ __global__ void __launch_bounds__(KT) cgs_kernel(KrylovCtl c, typename Cplx<R>::
   if (!last) return;
   __threadfence();
   const double2 *pq = c.partial + (size_t)q * gridDim.x * (m + 1);
+  const int wid = tid >> 5, lane = tid & 31;
   if (flags & KF_DOTS) {
-    for (int i = tid; i <= j; i += KT) {
-      double2 s = make_double2(0, 0);
-      for (int ch = 0; ch < (int)gridDim.x; ++ch) s = cadd(s, pq[(size_t)ch * (m + 1) + i]);
-      double2 *ha = c.hacc + (size_t)q * (m + 1) + i;
-      *ha = (flags & KF_ACCUM) ? cadd(*ha, s) : s;
-      c.hcur[(size_t)q * (m + 1) + i] = s;
+    for (int i = wid; i <= j; i += KT / 32) {
+      const double2 sm = chunk_sum(pq, gridDim.x, m + 1, i);
+      if (lane == 0) {
+        double2 *ha = c.hacc + (size_t)q * (m + 1) + i;
+        *ha = (flags & KF_ACCUM) ? cadd(*ha, sm) : sm;
+        c.hcur[(size_t)q * (m + 1) + i] = sm;
+      }
     }
   }
-  if ((flags & KF_NORM) && tid == 0) {
-    double s = 0;
-    for (int ch = 0; ch < (int)gridDim.x; ++ch) s += pq[(size_t)ch * (m + 1)].x;
-    const double nrm = sqrt(s);
-    if (flags & KF_INIT) {
-      c.beta[q] = nrm;
-      c.g[(size_t)q * (m + 1)] = make_double2(nrm, 0.0);
-      c.tol[q] = c.inner_tol * nrm;
-      c.res[q] = nrm;
-      if (nrm > 0.0 && isfinite(nrm)) {
-        c.inv_norm[q] = 1.0 / nrm;
+  if ((flags & KF_NORM) && wid == 0) {
+    const double nrm = sqrt(chunk_sum(pq, gridDim.x, m + 1, 0).x);
+    if (lane == 0) {
+      if (flags & KF_INIT) {
+        c.beta[q] = nrm;
+        c.g[(size_t)q * (m + 1)] = make_double2(nrm, 0.0);
+        c.tol[q] = c.inner_tol * nrm;
+        c.res[q] = nrm;
+        if (nrm > 0.0 && isfinite(nrm)) {
+          c.inv_norm[q] = 1.0 / nrm;
+        } else {
+          if (!isfinite(nrm)) atomicOr(c.err, DEVERR_NONFINITE);
+          c.inv_norm[q] = 0.0;
+          c.active[q] = 0;
+          c.kq[q] = 0;
+          atomicSub(c.nact, 1);
+        }
       } else {
-        if (!isfinite(nrm)) atomicOr(c.err, DEVERR_NONFINITE);
-        c.inv_norm[q] = 0.0;
-        c.active[q] = 0;
-        c.kq[q] = 0;
-        atomicSub(c.nact, 1);
+        givens_step(c, q, j, nrm);
       }
-    } else {
-      givens_step(c, q, j, nrm);
     }
   }
   if (tid == 0) c.counters[q] = 0;
@@ -272,18 +279,21 @@ __global__ void __launch_bounds__(KT) resid_kernel(const double2 *V, const doubl
       acc[0].x += v.x * v.x + v.y * v.y;
     }
   }
-  block_sum<1>(acc, red);
+  block_sum<double2, 1>(acc, red);
   if (tid == 0) partial[(size_t)q * gridDim.x + chunk] = acc[0].x;
   __threadfence();
   if (tid == 0) last = (atomicAdd(&counters[q], 1u) == gridDim.x - 1);
   __syncthreads();
   if (!last) return;
   __threadfence();
-  if (tid == 0) {
+  if (tid < 32) {
     double s = 0;
-    for (int ch = 0; ch < (int)gridDim.x; ++ch) s += partial[(size_t)q * gridDim.x + ch];
-    out_norm[q] = sqrt(s);
-    counters[q] = 0;
+    for (int ch = tid; ch < (int)gridDim.x; ch += 32) s += partial[(size_t)q * gridDim.x + ch];
+    s = warp_sum(s);
+    if (tid == 0) {
+      out_norm[q] = sqrt(s);
+      counters[q] = 0;
+    }
   }
 }
 

@@ -122,9 +122,12 @@ MOMA_DEV double2 box_entry(const double2 *S, int ndx, int bb, int x0, int x1, in
 // One CTA per element.  The packed lower triangle of P_e is assembled from
 // the summed-area table (row by row, so reads of the table are contiguous)
 // and factored in FP64 by a blocked right-looking Cholesky: a panel of CH_NB
-// columns is factored column by column, then the trailing matrix receives
-// the rank-CH_NB update A(i,k) -= sum_p L(i,p) conj(L(k,p)) in one sweep
-// (warps own columns k, lanes own rows i, four rows per lane in flight).
+// columns is factored column by column, then the trailing triangle receives
+// the rank-CH_NB update A(i,k) -= sum_p L(i,p) conj(L(k,p)) in one sweep.
+// The trailing triangle is contiguous in the packed column-major layout, so
+// the sweep hands consecutive packed entries to consecutive threads (an
+// (i, k) table in shared memory gives each entry's row and column): every
+// lane does useful FP64 work however short the remaining columns are.
 // L_e (packed column-major) is written to Lpk.
 constexpr int CH_NB = 8;
 
@@ -137,6 +140,7 @@ __global__ void __launch_bounds__(512) box_cholesky_kernel(const double2 *__rest
   const int e = blockIdx.x, ex = e % nx, ey = e / nx;
   const int npk = b * (b + 1) / 2;
   double2 *A = IN_SMEM ? reinterpret_cast<double2 *>(smraw) : Lpk + (size_t)e * npk;
+  short2 *tab = reinterpret_cast<short2 *>(smraw + (IN_SMEM ? (size_t)npk * sizeof(double2) : 0));
   const int ndx = 2 * nx - 1, bb = b * b;
   const int x0 = nx - 1 - ex, x1 = 2 * nx - 2 - ex, y0 = ny - 1 - ey, y1 = 2 * ny - 2 - ey;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
@@ -147,7 +151,9 @@ __global__ void __launch_bounds__(512) box_cholesky_kernel(const double2 *__rest
     while (i * (i + 1) / 2 > t) --i;
     while ((i + 1) * (i + 2) / 2 <= t) ++i;
     const int k = t - i * (i + 1) / 2;
-    A[colbase(k, b) + i - k] = box_entry(S, ndx, bb, x0, x1, y0, y1, i * b + k);
+    const int q = colbase(k, b) + i - k;
+    A[q] = box_entry(S, ndx, bb, x0, x1, y0, y1, i * b + k);
+    tab[q] = make_short2((short)i, (short)k);
   }
   __syncthreads();
 
@@ -167,39 +173,33 @@ __global__ void __launch_bounds__(512) box_cholesky_kernel(const double2 *__rest
       __syncthreads();
       for (int k = j + 1 + w; k < je; k += nw) {
         double2 *ck = A + colbase(k, b) - k;
-        const double2 lkj = cconj(cj[k]);
-        for (int i = k + lane; i < b; i += 32) ck[i] = csub(ck[i], cmul(cj[i], lkj));
+        const double2 lkj = cj[k];
+        for (int i = k + lane; i < b; i += 32) ck[i] = cfms_conj(cj[i], lkj, ck[i]);
       }
       __syncthreads();
     }
-    // Trailing rank-(je - jb) update.
+    // Trailing rank-(je - jb) update over the contiguous packed triangle
+    // starting at (je, je); two entries per thread in flight.
     const int np = je - jb;
     int pb[CH_NB];
 #pragma unroll
     for (int p = 0; p < CH_NB; ++p) pb[p] = p < np ? colbase(jb + p, b) - (jb + p) : 0;
-    for (int k = je + w; k < b; k += nw) {
-      double2 *ck = A + colbase(k, b) - k;
-      double2 lk[CH_NB];
+    const int t0 = je < b ? colbase(je, b) : npk;
+    const int nthr = blockDim.x;
+    for (int t = t0 + tid; t < npk; t += 2 * nthr) {
+      const int t2 = t + nthr;
+      const bool two = t2 < npk;
+      const short2 ik0 = tab[t], ik1 = two ? tab[t2] : ik0;
+      double2 a0 = A[t], a1 = two ? A[t2] : a0;
 #pragma unroll
-      for (int p = 0; p < CH_NB; ++p) lk[p] = p < np ? cconj(A[pb[p] + k]) : make_double2(0, 0);
-      for (int i0 = k + lane; i0 < b; i0 += 128) {
-        double2 acc[4];
-#pragma unroll
-        for (int r = 0; r < 4; ++r) acc[r] = (i0 + 32 * r < b) ? ck[i0 + 32 * r] : make_double2(0, 0);
-#pragma unroll
-        for (int p = 0; p < CH_NB; ++p) {
-          if (p < np) {
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-              const int i = i0 + 32 * r;
-              if (i < b) acc[r] = csub(acc[r], cmul(A[pb[p] + i], lk[p]));
-            }
-          }
+      for (int p = 0; p < CH_NB; ++p) {
+        if (p < np) {
+          a0 = cfms_conj(A[pb[p] + ik0.x], A[pb[p] + ik0.y], a0);
+          a1 = cfms_conj(A[pb[p] + ik1.x], A[pb[p] + ik1.y], a1);
         }
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-          if (i0 + 32 * r < b) ck[i0 + 32 * r] = acc[r];
       }
+      A[t] = a0;
+      if (two) A[t2] = a1;
     }
     __syncthreads();
   }
@@ -210,18 +210,18 @@ __global__ void __launch_bounds__(512) box_cholesky_kernel(const double2 *__rest
 }
 
 void launch_box_cholesky(const double2 *S, int nx, int ny, int b, double2 *Lpk, unsigned *err, cudaStream_t st) {
-  const size_t bytes = (size_t)b * (b + 1) / 2 * sizeof(double2);
+  // Shared memory: the packed triangle (if it fits) and the (i, k) table.
+  const size_t npk = (size_t)b * (b + 1) / 2;
+  const size_t matb = npk * sizeof(double2), tabb = npk * sizeof(short2);
   const int nel = nx * ny;
-  if (bytes <= 200 * 1024) {
-    static int configured = 0;
-    if (!configured) {
-      cudaFuncSetAttribute(box_cholesky_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
-      configured = 1;
-    }
-    box_cholesky_kernel<true><<<nel, 512, bytes, st>>>(S, nx, ny, b, Lpk, err);
-  } else {
-    box_cholesky_kernel<false><<<nel, 512, 0, st>>>(S, nx, ny, b, Lpk, err);
+  static int configured = 0;
+  if (!configured) {
+    cudaFuncSetAttribute(box_cholesky_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+    cudaFuncSetAttribute(box_cholesky_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+    configured = 1;
   }
+  if (matb + tabb <= 200 * 1024) box_cholesky_kernel<true><<<nel, 512, matb + tabb, st>>>(S, nx, ny, b, Lpk, err);
+  else box_cholesky_kernel<false><<<nel, 512, tabb, st>>>(S, nx, ny, b, Lpk, err);
 }
 
 // Full P_e of one element (debug / inspection).
