@@ -145,6 +145,27 @@ def bin_product_bytes(spec, nr):
     return pairs * spec.b * ldb * 8 + 2 * B * nr * spec.b * 8, pairs, B
 
 
+def measured_traffic(alg_bytes, spec, nr):
+    """DRAM bytes per launch of the c64 bin product from the committed ncu
+    capture (profiles/bin_pair_kernel_c64_traffic.txt), scaled from the
+    captured lattice to this launch by the algorithmic bytes; None if the
+    kernel source changed since the capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "bin_pair_kernel_c64_traffic.txt")
+    src = os.path.join(ROOT, "paper_2608_17844_b300", "csrc", "binprod.cu")
+    try:
+        kv = dict(l.strip().split("=", 1) for l in open(path) if "=" in l and not l.startswith("#"))
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    if kv.get("kernel_source_sha256") != sha:
+        return None
+    pairs, bins, nrc, b = (int(kv[k]) for k in ("pairs", "bins", "nrhs", "b"))
+    alg_captured = pairs * b * (b + b % 2) * 8 + 2 * bins * nrc * b * 8
+    measured = int(kv["dram_read_bytes"]) + int(kv["dram_write_bytes"])
+    return measured / alg_captured * alg_bytes
+
+
 def cpu_oracle_sample(spec, blocks, V, seconds):
     """Time the oracle (oracle-I: GMRES on Z I = V with the direct offset-sum
     product, complex128) on RHS 0 of the workload for a bounded wall time;
@@ -302,8 +323,12 @@ def main():
         pass
     hbm_peak = peaks.get("hbm_gbs", 6400.0)
     achieved = alg_bytes / (ms_bin / n_bin / 1000.0) / 1e9 if n_bin else None
+    traffic = measured_traffic(alg_bytes, spec, nr)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak if achieved else None, "traffic": None,
+                "frac": achieved / hbm_peak if achieved else None,
+                "traffic": int(traffic) if traffic else None,
+                "traffic_source": "ncu dram bytes of the 24x24 capture scaled by algorithmic bytes" if traffic
+                else "kernel changed since the ncu capture",
                 "kernel": "bin_pair_kernel<float> (c64 per-bin product, Z and Z^H legs)",
                 "alg_bytes_per_launch": alg_bytes, "launches": n_bin, "avg_launch_us": 1000.0 * ms_bin / n_bin if n_bin else None,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback 6.4 TB/s"}

@@ -161,6 +161,9 @@ __global__ void axis_kernel(AxisKernelArgs A, const typename Cplx<R>::T *__restr
       const int2 bs = p.bin_slot[k * p.slot_mul + o1];
       const long long base = (long long)bs.x * p.out_sm;
       if (bs.y == 1) {
+        // The diagonal of the partner is the stored bin's own diagonal:
+        // written once, by the stored bin, so the result is deterministic.
+        if (ti == tj) continue;
         off = base + (long long)tj * p.remap_ld + ti;
       } else {
         off = base + (long long)ti * p.remap_ld + tj;

@@ -289,3 +289,26 @@ def test_zz_report_raw_errors():
     """Print the raw error of every reduced-precision stage seen above."""
     for k in sorted(RAW_ERRORS):
         print(f"RAW_ERROR {k}: {RAW_ERRORS[k]:.3e}")
+
+
+def test_solves_are_deterministic(moma_lib, cuda):
+    """Fixed reduction orders everywhere: fresh handles and repeated solves
+    on one handle give bitwise identical currents (needed for the
+    alone-versus-in-a-batch comparisons)."""
+    m = moma_lib
+    spec = LatticeSpec(6, 5, 10, 0.5, 4)
+    blocks = offset_blocks(spec, np.complex64)
+    V = excitation(spec, [(0, 0), (25, 40), (50, 10)])
+    outs = []
+    for _ in range(3):
+        h = m.moma_create_array(spec.nx, spec.ny, spec.b, MIXED)
+        try:
+            m.moma_set_blocks(h, blocks)
+            for _ in range(2):
+                I = np.zeros_like(V)
+                m.moma_solve(h, V, I)
+                outs.append(I)
+        finally:
+            m.moma_destroy(h)
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
