@@ -120,6 +120,30 @@ moma_status moma_set_blocks(moma_array *a, const void *blocks, int dtype);
  * from the c64 bins (MIXED arrays only).  MOMA_OP_NORMAL needs set_blocks. */
 moma_status moma_matvec(moma_array *a, int op, int nrhs, const void *x, void *y, int dtype);
 
+/* Allocation-free variant of moma_matvec for MOMA_OP_Z and MOMA_OP_ZH (no
+ * counterpart in the paper; it exists for callers of this library).  Some
+ * callers cannot let a library call allocate device memory once they are
+ * running: another framework's caching allocator may already hold the free
+ * memory, or a latency-bound loop cannot afford the implicit device
+ * synchronisation of an allocation.  moma_matvec grows the handle's
+ * workspace on demand; this entry point allocates nothing.  Its scratch (the
+ * lattice and bin-vector buffers of the FFT product) is one fixed 32 MiB
+ * device array compiled into the library, which every GPU that loads the
+ * library holds until the process exits.
+ *  - x, y: device memory only, layout [nrhs][Ny][Nx][b], dtype as in
+ *    moma_matvec; host pointers are rejected with MOMA_ERR_ARG.
+ *  - Sizes whose scratch exceeds 32 MiB are rejected with MOMA_ERR_ARG and a
+ *    message stating the bytes needed (call again with fewer RHS).
+ *  - The first call on a device looks up the array's device address (with
+ *    that device current); make that first call before any stream capture.
+ *  - All calls in the process share the one array: calls whose GPU work
+ *    overlaps (other streams, other handles, other threads) race on it.  The
+ *    scratch is fully rewritten before it is read, so no state leaks from one
+ *    call into the next.
+ * Errors: as moma_matvec, plus MOMA_ERR_ARG for host pointers, MOMA_OP_NORMAL
+ * or oversized requests. */
+moma_status moma_matvec_noalloc(moma_array *a, int op, int nrhs, const void *x, void *y, int dtype);
+
 /* y = P^{-1} x with the factored block-diagonal preconditioner (Eq. 38
  * without margin, applied through L_e^{-H} L_e^{-1}). */
 moma_status moma_apply_precond(moma_array *a, int nrhs, const void *x, void *y, int dtype);

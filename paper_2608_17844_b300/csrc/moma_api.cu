@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <stdexcept>
 #include <string>
@@ -906,3 +907,85 @@ void moma_destroy(moma_array *a) {
 }
 
 }  // extern "C"
+
+// ============================================ allocation-free product ====
+// moma_matvec_noalloc: the Z / Z^H product of moma_matvec, for callers that
+// must not let a library call allocate device memory at call time.  Its
+// scratch (the x-pass lattice buffer and the two bin-vector buffers) lives
+// in a file-scope device array of fixed size instead of the handle's
+// grow-on-demand workspace.
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;  // 32 MiB per device
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void *g_noalloc_ptr[kMaxDevices] = {nullptr};
+
+// Device address of the scratch array on the current device (first call per
+// device resolves it with cudaGetSymbolAddress, with that device current).
+void *noalloc_scratch(int dev) {
+  if (dev < 0 || dev >= kMaxDevices) throw MomaError(MOMA_ERR_ARG, "device index out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void *p = nullptr;
+    CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_ptr[dev] = p;
+  }
+  return g_noalloc_ptr[dev];
+}
+
+size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
+
+template <typename R>
+void noalloc_product(moma_array *a, int nr, const void *x, void *y, int herm, unsigned char *scratch) {
+  const size_t esz = sizeof(typename Cplx<R>::T);
+  unsigned char *t1 = scratch;
+  unsigned char *bx = t1 + align256((size_t)nr * a->ny * a->Mx * a->b * esz);
+  unsigned char *by = bx + align256((size_t)a->B * nr * a->b * esz);
+  const int c = is64<R>();
+  launch_axis_pass<R>(pass_fx(a, nr, x, t1, c, c), a->fx, a->st);
+  check_launch(a);
+  launch_axis_pass<R>(pass_fy(a, nr, t1, bx, c), a->fy, a->st);
+  check_launch(a);
+  BinProduct P;
+  P.Z = c ? a->Z128.p : a->Z64.p;
+  P.pairs = a->pairs.as<int2>();
+  P.x = bx; P.y = by; P.Bp = a->Bp; P.b = a->b; P.ldb = a->ldb; P.nr = nr; P.herm = herm; P.err = a->err;
+  launch_bin_product<R>(P, a->num_sms, a->st);
+  check_launch(a);
+  launch_axis_pass<R>(pass_iy(a, nr, by, t1, c), a->fy, a->st);
+  check_launch(a);
+  launch_axis_pass<R>(pass_ix(a, nr, t1, y, c, false), a->fx, a->st);
+  check_launch(a);
+}
+
+}  // namespace
+
+extern "C" moma_status moma_matvec_noalloc(moma_array *a, int op, int nrhs, const void *x, void *y, int dtype) {
+  if (!a) { g_last_error = "array is NULL"; return MOMA_ERR_ARG; }
+  return guarded([&] {
+    if (!a->have_blocks) throw MomaError(MOMA_ERR_STATE, "set_blocks must precede matvec");
+    if (op != MOMA_OP_Z && op != MOMA_OP_ZH) throw MomaError(MOMA_ERR_ARG, "op must be MOMA_OP_Z or MOMA_OP_ZH");
+    if (dtype != MOMA_C128 && dtype != MOMA_C64) throw MomaError(MOMA_ERR_ARG, "bad dtype");
+    const bool d64 = dtype == MOMA_C128;
+    if (!d64 && a->prec != MOMA_PREC_MIXED) throw MomaError(MOMA_ERR_ARG, "c64 operators need a MIXED array");
+    if (nrhs < 0) throw MomaError(MOMA_ERR_ARG, "nrhs < 0");
+    if (nrhs == 0) return;
+    if (!is_device_ptr(x) || !is_device_ptr(y)) throw MomaError(MOMA_ERR_ARG, "x and y must be device memory");
+    const size_t esz = d64 ? sizeof(double2) : sizeof(float2);
+    const size_t need = align256((size_t)nrhs * a->ny * a->Mx * a->b * esz) +
+                        2 * align256((size_t)a->B * nrhs * a->b * esz);
+    if (need > kNoAllocScratchBytes)
+      throw MomaError(MOMA_ERR_ARG, "moma_matvec_noalloc needs " + std::to_string(need) +
+                                        " bytes of scratch; the fixed maximum is " +
+                                        std::to_string(kNoAllocScratchBytes) + " (use fewer RHS per call)");
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    unsigned char *scratch = static_cast<unsigned char *>(noalloc_scratch(dev));
+    if (d64) noalloc_product<double>(a, nrhs, x, y, op == MOMA_OP_ZH, scratch);
+    else noalloc_product<float>(a, nrhs, x, y, op == MOMA_OP_ZH, scratch);
+    sync_and_check(a);
+  });
+}

@@ -30,7 +30,7 @@ KERNEL_IDS = {"bin_c64": 0, "bin_c128": 1, "precond": 2, "fft_c64": 3, "block_ff
 EXPORTS = [
     "moma_create_array", "moma_set_blocks", "moma_matvec", "moma_apply_precond", "moma_get_bin",
     "moma_get_precond_block", "moma_solve", "moma_active_impedance", "moma_profile", "moma_kernel_stats",
-    "moma_launch_count", "moma_device_bytes", "moma_destroy", "moma_last_error",
+    "moma_launch_count", "moma_device_bytes", "moma_destroy", "moma_last_error", "moma_matvec_noalloc",
 ]
 
 
@@ -73,6 +73,7 @@ def lib():
     L.moma_set_blocks.argtypes = [vp, vp, i]
     L.moma_matvec.argtypes = [vp, i, i, vp, vp, i]
     L.moma_apply_precond.argtypes = [vp, i, vp, vp, i]
+    L.moma_matvec_noalloc.argtypes = [vp, i, i, vp, vp, i]
     L.moma_get_bin.argtypes = [vp, i, i, i, vp]
     L.moma_get_precond_block.argtypes = [vp, i, i, vp]
     L.moma_solve.argtypes = [vp, i, vp, vp, ctypes.POINTER(moma_solve_opts), ctypes.POINTER(moma_solve_info),
@@ -151,6 +152,15 @@ def moma_matvec(h, op, x, y):
     if dt != dty:
         raise TypeError("x and y must have the same dtype")
     _check(lib().moma_matvec(h, op, x.shape[0], px, py, dt))
+
+
+def moma_matvec_noalloc(h, op, x, y):
+    """Z or Z^H product without any device allocation (device tensors only)."""
+    px, dt = _ptr_dtype(x)
+    py, dty = _ptr_dtype(y)
+    if dt != dty:
+        raise TypeError("x and y must have the same dtype")
+    _check(lib().moma_matvec_noalloc(h, op, x.shape[0], px, py, dt))
 
 
 def moma_apply_precond(h, x, y):
