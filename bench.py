@@ -41,6 +41,12 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=2, help="steps of the plain FP64 solve (0 = skip)")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="bounded oracle sample (0 = skip)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--serve", action="store_true",
+                    help="serving mode: Poisson request stream through the continuous-batching server")
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-keys", type=int, default=8)
+    ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--lattice", type=int, nargs=3, metavar=("NX", "NY", "B"), default=None,
                     help="override the lattice (profiling of smaller cases; not the benchmark workload)")
     return ap.parse_args()
@@ -207,6 +213,76 @@ def cpu_oracle_sample(spec, blocks, V, seconds):
             "s_per_iteration": t_iter, "iterations_for_1e-10": iters}
 
 
+def run_serving(args):
+    """Serving stream shaped like BASELINE config 5: Poisson arrivals
+    (rate --serve-rate, seed 7) of requests with Nx, Ny ~ U{4..40}, b = 128,
+    1-32 scan-angle RHS.  Blocks come from a pool of --serve-keys lattices
+    (spacing on the 5-point grid 0.3..0.7) generated once on the host, so
+    arrays are built on first use and then served from residency."""
+    import torch
+    import paper_2608_17844_b300 as m
+    from synth import LatticeSpec, offset_blocks, excitation
+    rng = np.random.default_rng(7)
+    pool = []
+    for k in range(args.serve_keys):
+        nx, ny = int(rng.integers(4, 41)), int(rng.integers(4, 41))
+        d = float(rng.choice([0.3, 0.4, 0.5, 0.6, 0.7]))
+        spec = LatticeSpec(nx, ny, 128, d, 0)
+        pool.append((spec, offset_blocks(spec, np.complex64)))
+    reqs = []
+    t = 0.0
+    while t < args.serve_seconds:
+        t += float(rng.exponential(1.0 / args.serve_rate))
+        k = int(rng.integers(len(pool)))
+        nr = int(rng.integers(1, 33))
+        angles = [(float(rng.uniform(0, 60)), float(rng.uniform(0, 90))) for _ in range(nr)]
+        reqs.append((t, k, angles))
+    torch.cuda.set_device(0)
+    s = m.moma_server_create(slots=args.serve_slots)
+    max_outstanding = 64
+    outstanding = []
+    lat, hits, solved, errors = [], 0, 0, 0
+    t0 = time.perf_counter()
+
+    def collect(block):
+        nonlocal hits, solved, errors
+        while outstanding and (block or len(outstanding) >= max_outstanding):
+            tk, bufs = outstanding.pop(0)
+            r = m.moma_server_wait(s, tk, -1.0)
+            lat.append(r["total_ms"])
+            hits += r["resident_hit"]
+            if r["status"] == 0:
+                solved += bufs[0].shape[0]
+            else:
+                errors += 1
+            block = block and bool(outstanding)
+
+    for (ta, k, angles) in reqs:
+        now = time.perf_counter() - t0
+        if ta > now:
+            time.sleep(ta - now)
+        spec, blocks = pool[k]
+        V = excitation(spec, angles)
+        I = np.zeros_like(V)
+        tk = m.moma_server_submit(s, k + 1, blocks, V, I)
+        outstanding.append((tk, (V, I)))
+        collect(False)
+    collect(True)
+    wall = time.perf_counter() - t0
+    stats = m.moma_server_get_stats(s)
+    m.moma_server_destroy(s)
+    lat = np.array(lat)
+    line = {"metric": "serving: solves/s with p50/p99 request latency", "mode": "serve",
+            "value": solved / wall, "unit": "solves/s", "n_gpus": 1, "higher_is_better": True,
+            "offered_req_per_s": len(reqs) / reqs[-1][0], "achieved_req_per_s": len(reqs) / wall,
+            "requests": len(reqs), "errors": errors, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "resident_hit_rate": hits / len(reqs),
+            "slots": args.serve_slots, "server": stats, "data": "synthetic",
+            "config": {"workload": f"Poisson {args.serve_rate}/s, {args.serve_keys} lattice keys Nx,Ny~U{{4..40}}, "
+                                   f"b=128, d on 0.3..0.7 grid, 1-32 RHS", "max_outstanding": max_outstanding}}
+    print(json.dumps(line, default=str), flush=True)
+
+
 def run_reference(args, world, rank):
     """Reference arm: the CPU oracle as it stands, on the host cores."""
     if rank != 0:
@@ -234,6 +310,10 @@ def main():
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.serve:
+        if rank == 0:
+            run_serving(args)
         return
     import torch
     import paper_2608_17844_b300 as m

@@ -190,6 +190,22 @@ moma_status moma_active_impedance(moma_array *a, int nrhs, const void *I, const 
 moma_status moma_profile(moma_array *a, int enable);
 moma_status moma_kernel_stats(moma_array *a, int kernel, long long *launches, double *total_ms);
 
+/* Rebind the array to another CUDA stream (the old stream is synchronised
+ * first).  Lets a pool of workers reuse resident arrays on their streams. */
+moma_status moma_set_stream(moma_array *a, void *cuda_stream);
+
+/* Free the set-up scratch kept after moma_set_blocks (device copy of the
+ * blocks, block-transform intermediate, Gram/summed-area table, FP64
+ * Cholesky factors).  The bins and the inverse factors stay; solves and
+ * products are unaffected; moma_get_precond_block then reports
+ * MOMA_ERR_STATE.  For keeping many arrays resident. */
+moma_status moma_release_setup(moma_array *a);
+
+/* Upper estimate of the device bytes an array needs: stored bins, factors,
+ * workspaces for nrhs right-hand sides and, if with_setup, the set-up
+ * scratch.  0 on invalid sizes.  Used for admission by HBM footprint. */
+size_t moma_estimate_bytes(int nx, int ny, int b, const moma_options *opt, int nrhs, int with_setup);
+
 /* Number of kernel launches issued on the array's stream since creation. */
 long long moma_launch_count(moma_array *a);
 
@@ -198,6 +214,64 @@ size_t moma_device_bytes(const moma_array *a);
 
 void moma_destroy(moma_array *a);
 const char *moma_last_error(void);
+
+/* ------------------------------------------------------------------ serving
+ * Continuous batching of independent solve requests on the current device
+ * (no counterpart in the paper; it serves many array/excitation problems).
+ * A pool of `slots` worker threads, each on its own CUDA stream, takes the
+ * next admissible request whenever it is free, so requests arriving while
+ * others run start as soon as a slot and memory are available and their
+ * GPU work overlaps.  Arrays (stored bins + factored preconditioner) stay
+ * resident between requests under the caller's key; a request is admitted
+ * when moma_estimate_bytes of its array fits the budget, evicting idle
+ * resident arrays least recently used first.  Results equal those of a
+ * stand-alone moma_solve (fixed reduction orders). */
+typedef struct moma_server moma_server;
+
+typedef struct {
+    size_t max_device_bytes; /* budget for resident arrays and workspaces; 0 = 70% of free memory */
+    int slots;               /* concurrent requests (worker threads / streams); 0 = 4 */
+    int precision;           /* moma_precision of the arrays */
+    int restart;             /* GMRES restart; 0 = 50 */
+} moma_server_opts;
+
+typedef struct {
+    unsigned long long key; /* identity of (lattice, blocks): equal keys share a resident array */
+    int nx, ny, b;
+    const void *blocks;     /* [2ny-1][2nx-1][b][b]; read only when the key is not resident */
+    int blocks_dtype;       /* moma_dtype */
+    int nrhs;
+    const void *V;          /* c128 [nrhs][ny][nx][b] */
+    void *I;                /* c128 output, same layout */
+    void *Za, *Gamma;       /* optional c128 [nrhs][ny][nx] port outputs (NULL to skip) */
+    int port_basis;
+    double z0;              /* 0 = 50 ohm */
+    double tol;             /* 0 = 1e-10 */
+} moma_request;             /* all buffers must stay valid until moma_server_wait returns the result */
+
+typedef struct {
+    int status;             /* moma_status of this request */
+    int resident_hit;       /* 1 if the array was resident (no set-up) */
+    double queue_ms, run_ms, total_ms;  /* submit->start, start->done, submit->done (host clock) */
+    moma_solve_info info;
+    char message[256];      /* error text if status != MOMA_OK */
+} moma_result;
+
+typedef struct {
+    unsigned long long submitted, completed, hits, misses, evictions;
+    int resident_arrays, queued;
+    size_t resident_bytes, budget_bytes;
+} moma_server_stats;
+
+moma_status moma_server_create(const moma_server_opts *opt, moma_server **out);
+/* Queue a request; returns immediately with a ticket. */
+moma_status moma_server_submit(moma_server *s, const moma_request *r, unsigned long long *ticket);
+/* Wait for a ticket's result (timeout_s < 0: forever); MOMA_ERR_TIMEOUT if
+ * still running.  Each ticket's result is returned once. */
+moma_status moma_server_wait(moma_server *s, unsigned long long ticket, double timeout_s, moma_result *out);
+moma_status moma_server_get_stats(moma_server *s, moma_server_stats *out);
+/* Drops queued requests, finishes running ones, frees everything. */
+void moma_server_destroy(moma_server *s);
 
 #ifdef __cplusplus
 }

@@ -88,7 +88,11 @@ MOMA_HD void dif_stage(C *col, int ld, const FftPlan &pl, const C *tw, int s, in
     for (int n = 0; n < r; ++n) a[n] = base[(n * Mp + k) * ld];
     butterfly(a, r, tw, M);
     base[k * ld] = a[0];
-    for (int n = 1; n < r; ++n) base[(n * Mp + k) * ld] = cmul(a[n], tw[k * n * G]);
+    if (k == 0) {  // unit twiddles
+      for (int n = 1; n < r; ++n) base[n * Mp * ld] = a[n];
+    } else {
+      for (int n = 1; n < r; ++n) base[(n * Mp + k) * ld] = cmul(a[n], tw[k * n * G]);
+    }
   }
 }
 
@@ -101,7 +105,11 @@ MOMA_HD void dit_stage(C *col, int ld, const FftPlan &pl, const C *tw, int s, in
     C *base = col + (size_t)seg * Ms * ld;
     C a[5];
     a[0] = base[k * ld];
-    for (int n = 1; n < r; ++n) a[n] = cmul(base[(n * Mp + k) * ld], tw[k * n * G]);
+    if (k == 0) {  // unit twiddles
+      for (int n = 1; n < r; ++n) a[n] = base[n * Mp * ld];
+    } else {
+      for (int n = 1; n < r; ++n) a[n] = cmul(base[(n * Mp + k) * ld], tw[k * n * G]);
+    }
     butterfly(a, r, tw, M);
     for (int n = 0; n < r; ++n) base[(n * Mp + k) * ld] = a[n];
   }

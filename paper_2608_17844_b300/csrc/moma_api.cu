@@ -828,6 +828,7 @@ moma_status moma_get_precond_block(moma_array *a, int ex, int ey, void *out) {
   if (!a) { g_last_error = "array is NULL"; return MOMA_ERR_ARG; }
   return guarded([&] {
     if (!a->have_blocks) throw MomaError(MOMA_ERR_STATE, "no blocks");
+    if (!a->S.p) throw MomaError(MOMA_ERR_STATE, "set-up scratch was released");
     if (ex < 0 || ex >= a->nx || ey < 0 || ey >= a->ny || !out) throw MomaError(MOMA_ERR_ARG, "bad element");
     const size_t bytes = (size_t)a->b * a->b * sizeof(double2);
     a->one_blk.ensure(bytes, a->dev_bytes);
@@ -895,6 +896,46 @@ moma_status moma_kernel_stats(moma_array *a, int kernel, long long *launches, do
     if (launches) *launches = a->st_launch[kernel];
     if (total_ms) *total_ms = a->st_ms[kernel];
   });
+}
+
+moma_status moma_set_stream(moma_array *a, void *cuda_stream) {
+  if (!a) { g_last_error = "array is NULL"; return MOMA_ERR_ARG; }
+  return guarded([&] {
+    CK(cudaStreamSynchronize(a->st));
+    a->st = reinterpret_cast<cudaStream_t>(cuda_stream);
+  });
+}
+
+moma_status moma_release_setup(moma_array *a) {
+  if (!a) { g_last_error = "array is NULL"; return MOMA_ERR_ARG; }
+  return guarded([&] {
+    CK(cudaStreamSynchronize(a->st));
+    a->blk.release(a->dev_bytes);
+    a->T.release(a->dev_bytes);
+    a->S.release(a->dev_bytes);
+    a->Lpk.release(a->dev_bytes);
+  });
+}
+
+size_t moma_estimate_bytes(int nx, int ny, int b, const moma_options *opt, int nrhs, int with_setup) {
+  if (nx < 1 || ny < 1 || b < 1 || nrhs < 0) return 0;
+  const int prec = opt ? opt->precision : MOMA_PREC_MIXED;
+  const int m = (opt && opt->restart > 0) ? opt->restart : 50;
+  const size_t Mx = (opt && opt->mx > 0) ? opt->mx : next_smooth(2 * nx - 1);
+  const size_t My = (opt && opt->my > 0) ? opt->my : next_smooth(2 * ny - 1);
+  const size_t B = Mx * My, Bp = B / 2 + 2, ldb = (b % 2) ? b + 1 : b;
+  const size_t nel = (size_t)nx * ny, N = nel * b, nt = (size_t)b * (b + 1) / 2;
+  const size_t nD = (size_t)(2 * nx - 1) * (2 * ny - 1);
+  const size_t c = 16, esz = prec == MOMA_PREC_FP64 ? 16 : 8;
+  size_t bytes = Bp * b * ldb * c + (prec == MOMA_PREC_MIXED ? Bp * b * ldb * 8 : 0);  // stored bins
+  bytes += nel * (nt + 2) * esz;                                                        // inverse factors
+  bytes += B * 16 + nt * 12 + 4096;                                                     // tables
+  const size_t nr = (size_t)nrhs, nch = (N + 1023) / 1024;
+  bytes += nr * N * c * 6 + nr * ny * Mx * b * c + 2 * B * nr * b * c;                 // solve vectors
+  bytes += (size_t)(m + 1) * nr * N * esz + nr * nch * (m + 1) * c + nr * m * (m + 1) * c;  // Krylov
+  bytes += 2 * nr * nel * c;                                                            // ports
+  if (with_setup) bytes += nD * b * b * (c + 8) + (size_t)(2 * ny - 1) * Mx * nt * c + nel * nt * c;
+  return bytes;
 }
 
 long long moma_launch_count(moma_array *a) { return a ? a->launches : 0; }

@@ -31,6 +31,8 @@ EXPORTS = [
     "moma_create_array", "moma_set_blocks", "moma_matvec", "moma_apply_precond", "moma_get_bin",
     "moma_get_precond_block", "moma_solve", "moma_active_impedance", "moma_profile", "moma_kernel_stats",
     "moma_launch_count", "moma_device_bytes", "moma_destroy", "moma_last_error", "moma_matvec_noalloc",
+    "moma_set_stream", "moma_release_setup", "moma_estimate_bytes",
+    "moma_server_create", "moma_server_submit", "moma_server_wait", "moma_server_get_stats", "moma_server_destroy",
 ]
 
 
@@ -57,6 +59,38 @@ class moma_solve_info(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class moma_server_opts(ctypes.Structure):
+    _fields_ = [("max_device_bytes", ctypes.c_size_t), ("slots", ctypes.c_int), ("precision", ctypes.c_int),
+                ("restart", ctypes.c_int)]
+
+
+class moma_request(ctypes.Structure):
+    _fields_ = [("key", ctypes.c_ulonglong), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("b", ctypes.c_int),
+                ("blocks", ctypes.c_void_p), ("blocks_dtype", ctypes.c_int), ("nrhs", ctypes.c_int),
+                ("V", ctypes.c_void_p), ("I", ctypes.c_void_p), ("Za", ctypes.c_void_p), ("Gamma", ctypes.c_void_p),
+                ("port_basis", ctypes.c_int), ("z0", ctypes.c_double), ("tol", ctypes.c_double)]
+
+
+class moma_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("resident_hit", ctypes.c_int), ("queue_ms", ctypes.c_double),
+                ("run_ms", ctypes.c_double), ("total_ms", ctypes.c_double), ("info", moma_solve_info),
+                ("message", ctypes.c_char * 256)]
+
+    def as_dict(self):
+        return {"status": self.status, "resident_hit": self.resident_hit, "queue_ms": self.queue_ms,
+                "run_ms": self.run_ms, "total_ms": self.total_ms, "info": self.info.as_dict(),
+                "message": self.message.decode(errors="replace")}
+
+
+class moma_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_ulonglong), ("completed", ctypes.c_ulonglong), ("hits", ctypes.c_ulonglong),
+                ("misses", ctypes.c_ulonglong), ("evictions", ctypes.c_ulonglong), ("resident_arrays", ctypes.c_int),
+                ("queued", ctypes.c_int), ("resident_bytes", ctypes.c_size_t), ("budget_bytes", ctypes.c_size_t)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 _lib = None
 
 
@@ -74,6 +108,16 @@ def lib():
     L.moma_matvec.argtypes = [vp, i, i, vp, vp, i]
     L.moma_apply_precond.argtypes = [vp, i, vp, vp, i]
     L.moma_matvec_noalloc.argtypes = [vp, i, i, vp, vp, i]
+    L.moma_set_stream.argtypes = [vp, vp]
+    L.moma_release_setup.argtypes = [vp]
+    L.moma_estimate_bytes.argtypes = [i, i, i, ctypes.POINTER(moma_options), i, i]
+    L.moma_estimate_bytes.restype = ctypes.c_size_t
+    L.moma_server_create.argtypes = [ctypes.POINTER(moma_server_opts), ctypes.POINTER(vp)]
+    L.moma_server_submit.argtypes = [vp, ctypes.POINTER(moma_request), ctypes.POINTER(ctypes.c_ulonglong)]
+    L.moma_server_wait.argtypes = [vp, ctypes.c_ulonglong, d, ctypes.POINTER(moma_result)]
+    L.moma_server_get_stats.argtypes = [vp, ctypes.POINTER(moma_server_stats)]
+    L.moma_server_destroy.argtypes = [vp]
+    L.moma_server_destroy.restype = None
     L.moma_get_bin.argtypes = [vp, i, i, i, vp]
     L.moma_get_precond_block.argtypes = [vp, i, i, vp]
     L.moma_solve.argtypes = [vp, i, vp, vp, ctypes.POINTER(moma_solve_opts), ctypes.POINTER(moma_solve_info),
@@ -89,7 +133,8 @@ def lib():
     L.moma_destroy.restype = None
     L.moma_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
-        if name not in ("moma_launch_count", "moma_device_bytes", "moma_destroy", "moma_last_error"):
+        if name not in ("moma_launch_count", "moma_device_bytes", "moma_destroy", "moma_last_error",
+                        "moma_estimate_bytes", "moma_server_destroy"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -234,3 +279,54 @@ def moma_destroy(h):
 
 def moma_last_error():
     return lib().moma_last_error().decode()
+
+
+def moma_set_stream(h, stream):
+    _check(lib().moma_set_stream(h, _stream_handle(stream)))
+
+
+def moma_release_setup(h):
+    _check(lib().moma_release_setup(h))
+
+
+def moma_estimate_bytes(nx, ny, b, nrhs, precision=MOMA_PREC_MIXED, with_setup=True):
+    opt = moma_options(precision, 0, 0, 0)
+    return lib().moma_estimate_bytes(nx, ny, b, ctypes.byref(opt), nrhs, 1 if with_setup else 0)
+
+
+def moma_server_create(slots=4, max_device_bytes=0, precision=MOMA_PREC_MIXED, restart=0):
+    s = ctypes.c_void_p()
+    o = moma_server_opts(max_device_bytes, slots, precision, restart)
+    _check(lib().moma_server_create(ctypes.byref(o), ctypes.byref(s)))
+    return s
+
+
+def moma_server_submit(s, key, blocks, V, I, Za=None, Gamma=None, port_basis=0, z0=50.0, tol=0.0):
+    """Queue a solve; the arrays must stay alive until moma_server_wait returns."""
+    pb, dtb = _ptr_dtype(blocks)
+    pv, _ = _ptr_dtype(V)
+    pi, _ = _ptr_dtype(I)
+    ny, nx, b = V.shape[1], V.shape[2], V.shape[3]
+    r = moma_request(key, nx, ny, b, pb, dtb, V.shape[0], pv, pi,
+                     _ptr_dtype(Za)[0] if Za is not None else None,
+                     _ptr_dtype(Gamma)[0] if Gamma is not None else None, port_basis, z0, tol)
+    t = ctypes.c_ulonglong()
+    _check(lib().moma_server_submit(s, ctypes.byref(r), ctypes.byref(t)))
+    return t.value
+
+
+def moma_server_wait(s, ticket, timeout_s=-1.0):
+    out = moma_result()
+    _check(lib().moma_server_wait(s, ticket, timeout_s, ctypes.byref(out)))
+    return out.as_dict()
+
+
+def moma_server_get_stats(s):
+    out = moma_server_stats()
+    _check(lib().moma_server_get_stats(s, ctypes.byref(out)))
+    return out.as_dict()
+
+
+def moma_server_destroy(s):
+    if s:
+        lib().moma_server_destroy(s)
