@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=2, help="steps of the plain FP64 solve (0 = skip)")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="bounded oracle sample (0 = skip)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--ragged", action="store_true",
+                    help="ragged batch: 24 square lattices 2x2..48x48, b=96, x 3 spacings, one broadside solve each")
     ap.add_argument("--serve", action="store_true",
                     help="serving mode: Poisson request stream through the continuous-batching server")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
@@ -283,6 +285,52 @@ def run_serving(args):
     print(json.dumps(line, default=str), flush=True)
 
 
+def run_ragged(args):
+    """Ragged batch shaped like BASELINE config 4: square lattices 2x2 ..
+    48x48 (step 2), b = 96, spacings 0.3 / 0.5 / 0.7, one broadside solve
+    each (72 problems).  One step = batched set-up (block transform,
+    preconditioner) of all 72 arrays + batched solve + port quantities.
+    Blocks are generated on the GPU (synth.offset_blocks_torch, c64)."""
+    import torch
+    import paper_2608_17844_b300 as m
+    from synth import LatticeSpec, offset_blocks_torch, excitation
+    torch.cuda.set_device(0)
+    specs = [LatticeSpec(n, n, 96, d, 0) for d in (0.3, 0.5, 0.7) for n in range(2, 49, 2)]
+    blocks = [offset_blocks_torch(s, "cuda") for s in specs]
+    Vs = [torch.from_numpy(excitation(s, [(0.0, 0.0)])).cuda() for s in specs]
+    Is = [torch.zeros_like(v) for v in Vs]
+    zas = [torch.zeros(v.shape[:3], dtype=torch.complex128, device="cuda") for v in Vs]
+    hs = [m.moma_create_array(s.nx, s.ny, s.b) for s in specs]
+
+    def step():
+        m.moma_set_blocks_batch(hs, blocks, release_setup=False, workers=8)
+        infos = m.moma_solve_batch(hs, Vs, Is, workers=8)
+        for h, I, V, za in zip(hs, Is, Vs, zas):
+            m.moma_active_impedance(h, I, V, za)
+        return infos
+
+    for _ in range(max(1, args.warmup)):
+        infos = step()
+    torch.cuda.synchronize()
+    steps = max(1, min(args.steps, 5))
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        infos = step()
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / steps
+    centre = {f"{s.nx}x{s.ny}@{s.d}": complex(za[0, s.ny // 2, s.nx // 2].item()) for s, za in zip(specs, zas)}
+    line = {"metric": "ragged batch: solves/s (set-up + solve per problem)", "mode": "ragged",
+            "value": len(specs) / dt, "unit": "solves/s", "ms_per_step": 1000 * dt, "steps": steps,
+            "problems": len(specs), "converged": sum(x["converged"] for x in infos),
+            "inner_iters": [x["inner_iters"] for x in infos],
+            "device_bytes": sum(m.moma_device_bytes(h) for h in hs), "data": "synthetic",
+            "config": {"workload": "2x2..48x48 step 2, b=96, d in {0.3,0.5,0.7}, broadside, c64 blocks"},
+            "centre_Za": {k: f"{v.real:.6f}{v.imag:+.6f}j" for k, v in list(centre.items())[::6]}}
+    for h in hs:
+        m.moma_destroy(h)
+    print(json.dumps(line, default=str), flush=True)
+
+
 def run_reference(args, world, rank):
     """Reference arm: the CPU oracle as it stands, on the host cores."""
     if rank != 0:
@@ -314,6 +362,10 @@ def main():
     if args.serve:
         if rank == 0:
             run_serving(args)
+        return
+    if args.ragged:
+        if rank == 0:
+            run_ragged(args)
         return
     import torch
     import paper_2608_17844_b300 as m
@@ -349,36 +401,46 @@ def main():
     for _ in range(args.warmup):
         step()
     barrier()
-    m.moma_profile(h, True)
-    launches0 = m.moma_launch_count(h)
+
+    def timed_region(profile):
+        """K steps between CUDA events on torch's stream (the library's own
+        streams are ordered into it), barrier + synchronize on both sides."""
+        m.moma_profile(h, profile)
+        launches0 = m.moma_launch_count(h)
+        marks = []
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            e_a = torch.cuda.Event(enable_timing=True)
+            e_b = torch.cuda.Event(enable_timing=True)
+            e_a.record(stream)
+            step()
+            e_b.record(stream)
+            marks.append((e_a, e_b))
+        ev1.record(stream)
+        barrier()
+        total = ev0.elapsed_time(ev1)
+        launches = m.moma_launch_count(h) - launches0
+        stats = {k: m.moma_kernel_stats(h, k) for k in m.KERNEL_IDS} if profile else None
+        m.moma_profile(h, False)
+        return total, [a.elapsed_time(b) for a, b in marks], launches, stats
+
+    # Headline: graphs replayed, no per-kernel events.
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
     clocks.wait_first()
-    step_ms = []
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    barrier()
-    ev0.record(stream)
-    for _ in range(args.steps):
-        e_a = torch.cuda.Event(enable_timing=True)
-        e_b = torch.cuda.Event(enable_timing=True)
-        e_a.record(stream)
-        step()
-        e_b.record(stream)
-        step_ms.append((e_a, e_b))
-    ev1.record(stream)
-    barrier()
+    total_ms, steps_ms, launches, _ = timed_region(False)
     clk = clocks.stop()
-    total_ms = ev0.elapsed_time(ev1)
-    launches = m.moma_launch_count(h) - launches0
-    stats = {k: m.moma_kernel_stats(h, k) for k in m.KERNEL_IDS}
-    m.moma_profile(h, False)
-    steps_ms = [a.elapsed_time(b) for a, b in step_ms]
     if dist is not None:
         t = torch.tensor([total_ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
     value = world * nr * args.steps / (total_ms / 1000.0)
+    # Same steps again with CUDA events around every kernel launch (graphs
+    # off): per-kernel durations for the roofline and the breakdown.
+    prof_total_ms, _, _, stats = timed_region(True)
 
     # Phase breakdown of one step (set-up vs solve), same stream, events.
     e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
@@ -485,6 +547,7 @@ def main():
                        "l2": "inputs larger than L2 (c64 blocks 520 MB; stored bins 269 MB c64 + 537 MB c128)"},
             "step_ms": {"p50": statistics.median(steps_ms), "p99": float(np.percentile(steps_ms, 99)),
                         "min": min(steps_ms), "max": max(steps_ms)},
+            "profiled_ms_per_step": prof_total_ms / args.steps,
             "phases": phases, "roofline": roofline, "kernels": kernel_share, "cpu_baseline": cpu,
             "e2e": e2e, "gpu_launches": launches, "clocks": clk, "fp64_plain": fp64,
             "ports_Za": {k: [f"{z.real:.10f}{z.imag:+.10f}j" for z in v] for k, v in ports.items()},

@@ -73,11 +73,17 @@ typedef enum {
 
 typedef struct moma_array moma_array; /* opaque; owns all device state */
 
+enum {
+    MOMA_FLAG_NO_GRAPHS = 1,   /* launch the inner steps directly instead of replaying CUDA graphs */
+    MOMA_FLAG_NO_AUTOTUNE = 2  /* use the built-in launch-shape heuristics */
+};
+
 typedef struct {
     int precision; /* moma_precision */
     int mx, my;    /* circulant sizes; 0 = smallest 2^a 3^b 5^c >= 2N-1.
                       Any M >= 2N-1 embeds Z exactly (Sec. II-A uses 2N-1). */
     int restart;   /* GMRES restart length m; 0 = 50 */
+    int flags;     /* MOMA_FLAG_* */
 } moma_options;
 
 typedef struct {
@@ -193,6 +199,31 @@ moma_status moma_kernel_stats(moma_array *a, int kernel, long long *launches, do
 /* Rebind the array to another CUDA stream (the old stream is synchronised
  * first).  Lets a pool of workers reuse resident arrays on their streams. */
 moma_status moma_set_stream(moma_array *a, void *cuda_stream);
+
+/* Text summary of the launch shapes the autotuner picked for this array
+ * (empty before the first solve).  Each solve first times candidate shapes
+ * of the bin product (rows per staged tile, pipeline stages) and of every
+ * lattice-FFT pass (threads per line) on its own workspace, once per RHS
+ * count, and keeps the fastest. */
+moma_status moma_tuning_report(const moma_array *a, char *buf, size_t len);
+
+/* The CUDA stream the array currently runs on. */
+void *moma_array_stream(const moma_array *a);
+
+/* Ragged batches (no counterpart in the paper): n independent arrays of
+ * uneven sizes processed concurrently.  `workers` host threads (0 = 8),
+ * each with its own CUDA stream, take the next array; each array is bound
+ * to the worker's stream for the call and returned to its own stream after,
+ * so small problems fill the GPU together.  statuses (optional, [n])
+ * receives each array's status; the return value is the first failure.
+ * moma_set_blocks_batch: blocks[i] / dtypes[i] for arrays[i]; with
+ * release_setup the set-up scratch is freed after each build.
+ * moma_solve_batch: nrhs[i], V[i], I[i] as in moma_solve; infos optional [n]. */
+moma_status moma_set_blocks_batch(int n, moma_array *const *arrays, const void *const *blocks, const int *dtypes,
+                                  int release_setup, int workers, moma_status *statuses);
+moma_status moma_solve_batch(int n, moma_array *const *arrays, const int *nrhs, const void *const *V,
+                             void *const *I, const moma_solve_opts *opts, moma_solve_info *infos, int workers,
+                             moma_status *statuses);
 
 /* Free the set-up scratch kept after moma_set_blocks (device copy of the
  * blocks, block-transform intermediate, Gram/summed-area table, FP64

@@ -28,6 +28,8 @@
 //    streams.
 // All waits are bounded; a timeout sets DEVERR_TIMEOUT and the CTA drains
 // its copies and exits.
+#include <algorithm>
+
 #include "internal.h"
 
 namespace moma {
@@ -335,14 +337,22 @@ static void launch_one(const BinProduct &P, int num_sms, cudaStream_t st, int q0
   if (TR >= 4) TR &= ~3;
   if (TR < 1) TR = 1;
   if (TR > P.b) TR = P.b;
-  const int ntile = (P.b + TR - 1) / TR;
   int NS = 3;
-  auto smem_for = [&](int ns) {
-    return 256 + (size_t)ns * TR * row_bytes + (size_t)4 * NR * P.b * sizeof(C) +
+  auto smem_for = [&](int ns, int tr) {
+    return 256 + (size_t)ns * tr * row_bytes + (size_t)4 * NR * P.b * sizeof(C) +
            (size_t)BP_CONSUMERS * P.b * NR * sizeof(C);
   };
-  while (NS > 2 && smem_for(NS) > 220 * 1024) --NS;
-  const size_t smem = smem_for(NS);
+  // Autotuned shape, if it is valid for this launch.
+  if (P.TR > 0 && P.TR <= 4 * BP_CONSUMERS && P.TR % 4 == 0 && P.NS >= 2 && P.NS <= 6) {
+    const int tr = std::min(P.TR, P.b);
+    if (smem_for(P.NS, tr) <= 220 * 1024) {
+      TR = tr;
+      NS = P.NS;
+    }
+  }
+  const int ntile = (P.b + TR - 1) / TR;
+  while (NS > 2 && smem_for(NS, TR) > 220 * 1024) --NS;
+  const size_t smem = smem_for(NS, TR);
   auto kern = bin_pair_kernel<R, NR, U2, HERM>;
   static int configured = 0;
   if (!configured) {

@@ -193,6 +193,7 @@ static void launch_typed(const AxisPass &p, const FftTables &t, cudaStream_t st)
   int G = std::max(1, std::min(8, M / 16));
   const long long ctas = (long long)((p.ninner + 31) / 32) * p.n1 * p.n2;
   while (G * 2 <= gmax && ctas * G < 24LL * 148) G *= 2;
+  if (p.G > 0) G = std::min(p.G, 32);
   const size_t head = ((size_t)M * sizeof(C) + (size_t)M * sizeof(int) + 15) & ~size_t(15);
   const size_t smem = head + (size_t)M * 32 * sizeof(C);
   static int configured = 0;

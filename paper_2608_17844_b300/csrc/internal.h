@@ -49,6 +49,7 @@ struct AxisPass {
   int refft_keep = 0;      // >0: inverse, keep points < refft_keep, zero the rest, forward again
   int in_c128 = 1, out_c128 = 1;  // element types of in / out
   const int *live = nullptr;       // if set and *live == 0 the pass does nothing
+  int G = 0;                       // threads per line (0 = heuristic; set by the autotuner)
 };
 
 // Launch one axis pass computing in precision R (float or double).
@@ -65,6 +66,7 @@ struct BinProduct {
   int herm = 0;
   unsigned *err = nullptr;
   const int *live = nullptr;  // if set and *live == 0 the product does nothing
+  int TR = 0, NS = 0;         // rows per tile / pipeline stages (0 = heuristic; autotuner)
 };
 template <typename R>
 void launch_bin_product(const BinProduct &p, int num_sms, cudaStream_t st);

@@ -1,7 +1,10 @@
 // C ABI of libmoma: handle management, device memory, and the host-side
 // orchestration of the set-up and solve pipelines (see include/moma.h).
+#include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
+#include <thread>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -119,6 +122,20 @@ struct moma_array {
   unsigned *err = nullptr;
   DevBuf one_blk;
   DevBuf portsb;  // Z_a and Gamma results [2][nr][nel]
+  // CUDA graphs of the inner Arnoldi steps (one per step index j, for the
+  // RHS count g_nr), replayed on an internal capturable stream.
+  bool use_graphs = true;
+  cudaStream_t gs = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  std::vector<cudaGraphExec_t> gexec;
+  int g_nr = -1;
+  long long g_step_launches = 0;
+  // Autotuned launch shapes (0 = built-in heuristic), per RHS count.
+  int tuned_nr = -1;
+  bool no_autotune = false;
+  int tune_bin_tr[2] = {0, 0}, tune_bin_ns[2] = {0, 0};  // [c64, c128]
+  std::vector<std::pair<long long, int>> tune_axis;       // pass signature -> threads per line
+  std::string tune_log;
   const int *live = nullptr;  // operator kernels skip their work while *live == 0
 
   // pinned host mirrors
@@ -302,9 +319,25 @@ AxisPass pass_ix(moma_array *a, int nr, const void *in, void *out, int c128, boo
 
 template <typename R> constexpr int is64() { return sizeof(R) == 8 ? 1 : 0; }
 
+long long axis_sig(const AxisPass &p, int M, int is64v) {
+  long long h = is64v;
+  for (long long v : {(long long)M, (long long)p.ninner, (long long)p.n1 * p.n2, (long long)p.nin,
+                      (long long)p.nout, (long long)p.refft_keep, (long long)p.in_mode, (long long)p.out_mode,
+                      (long long)p.inverse})
+    h = h * 1000003LL + v;
+  return h;
+}
+
+int tuned_G(const moma_array *a, long long sig) {
+  for (auto &kv : a->tune_axis)
+    if (kv.first == sig) return kv.second;
+  return 0;
+}
+
 template <typename R>
 void axis(moma_array *a, AxisPass p, const FftTables &t) {
   p.live = a->live;
+  if (p.G == 0) p.G = tuned_G(a, axis_sig(p, t.plan.M, is64<R>()));
   a->timed(is64<R>() ? PK_FFT128 : PK_FFT64, [&] { launch_axis_pass<R>(p, t, a->st); });
   check_launch(a);
 }
@@ -316,6 +349,8 @@ void binprod(moma_array *a, int nr, const void *x, void *y, int herm) {
   P.pairs = a->pairs.as<int2>();
   P.x = x; P.y = y; P.Bp = a->Bp; P.b = a->b; P.ldb = a->ldb; P.nr = nr; P.herm = herm; P.err = a->err;
   P.live = a->live;
+  P.TR = a->tune_bin_tr[is64<R>()];
+  P.NS = a->tune_bin_ns[is64<R>()];
   a->timed(is64<R>() ? PK_BIN128 : PK_BIN64, [&] { launch_bin_product<R>(P, a->num_sms, a->st); });
   check_launch(a);
 }
@@ -387,8 +422,17 @@ void check_finite(moma_array *a, const void *p, size_t n_real, int is_double) {
   check_launch(a);
 }
 
+void drop_graphs(moma_array *a) {
+  for (auto g : a->gexec)
+    if (g) cudaGraphExecDestroy(g);
+  a->gexec.clear();
+  a->g_nr = -1;
+}
+
 void ensure_ws(moma_array *a, int nr) {
   if (nr <= a->ws_nr) return;
+  drop_graphs(a);
+  a->tuned_nr = -1;
   const size_t c = sizeof(double2);
   const size_t lat = (size_t)nr * a->N;
   const size_t tsz = (size_t)nr * a->ny * a->Mx * a->b;
@@ -524,6 +568,95 @@ void set_blocks_impl(moma_array *a, const void *blocks, int dtype) {
   a->have_blocks = true;
 }
 
+// ----------------------------------------------------------- autotuner --
+// Launch shapes are picked by timing: for the bin product the rows per
+// staged tile and the pipeline depth, for every lattice-FFT pass of the
+// solve the number of threads cooperating on a line.  Candidates run on the
+// solve's own workspace (contents irrelevant, only the timing is used), a
+// warm-up launch and two timed launches each, CUDA events on the array's
+// stream; the fastest wins.  Done once per (array, RHS count) before any
+// graph capture.
+template <typename F>
+float time_launch(moma_array *a, F &&f) {
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  f();
+  CK(cudaEventRecord(e0, a->st));
+  f();
+  f();
+  CK(cudaEventRecord(e1, a->st));
+  CK(cudaEventSynchronize(e1));
+  float ms = 0;
+  CK(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CK(cudaGetLastError());
+  return ms;
+}
+
+template <typename R>
+void autotune_precision(moma_array *a, int nr, int in128) {
+  char buf[256];
+  // Bin product: tile rows x stages.
+  {
+    float best = 1e30f;
+    int btr = 0, bns = 0;
+    for (int tr : {16, 32, 48}) {
+      if (tr > ((a->b + 3) & ~3) && tr != 16) continue;
+      for (int ns : {2, 3, 4}) {
+        BinProduct P;
+        P.Z = is64<R>() ? a->Z128.p : a->Z64.p;
+        P.pairs = a->pairs.as<int2>();
+        P.x = a->bx.p; P.y = a->by.p; P.Bp = a->Bp; P.b = a->b; P.ldb = a->ldb; P.nr = nr; P.err = a->err;
+        P.TR = tr; P.NS = ns;
+        const float ms = time_launch(a, [&] { launch_bin_product<R>(P, a->num_sms, a->st); });
+        if (ms < best) { best = ms; btr = tr; bns = ns; }
+      }
+    }
+    a->tune_bin_tr[is64<R>()] = btr;
+    a->tune_bin_ns[is64<R>()] = bns;
+    snprintf(buf, sizeof(buf), "bin_product<%s> nr=%d: TR=%d NS=%d (%.1f us)\n", is64<R>() ? "c128" : "c64", nr, btr,
+             bns, 1000.0f * best / 2);
+    a->tune_log += buf;
+  }
+  // Lattice FFT passes of the products and the normal operator.
+  const int c = is64<R>();
+  struct Cand { AxisPass p; const FftTables *t; const char *name; };
+  const Cand cands[] = {
+      {pass_fx(a, nr, a->lat_in.p, a->t1.p, in128, c), &a->fx, "Fx"},
+      {pass_fy(a, nr, a->t1.p, a->bx.p, c), &a->fy, "Fy"},
+      {pass_iy(a, nr, a->by.p, a->t1.p, c), &a->fy, "Iy"},
+      {pass_ix(a, nr, a->t1.p, a->t1.p, c, true), &a->fx, "IxMaskFx"},
+      {pass_ix(a, nr, a->t1.p, a->lat_tmp.p, c, false), &a->fx, "Ix"},
+  };
+  for (const Cand &cd : cands) {
+    float best = 1e30f;
+    int bg = 0;
+    for (int G : {1, 2, 4, 8, 16, 32}) {
+      if (G > cd.t->plan.M) continue;
+      AxisPass p = cd.p;
+      p.G = G;
+      const float ms = time_launch(a, [&] { launch_axis_pass<R>(p, *cd.t, a->st); });
+      if (ms < best) { best = ms; bg = G; }
+    }
+    a->tune_axis.push_back({axis_sig(cd.p, cd.t->plan.M, c), bg});
+    snprintf(buf, sizeof(buf), "%s<%s> nr=%d: G=%d (%.1f us)\n", cd.name, c ? "c128" : "c64", nr, bg,
+             1000.0f * best / 2);
+    a->tune_log += buf;
+  }
+}
+
+void autotune(moma_array *a, int nr) {
+  if (a->tuned_nr == nr || a->no_autotune || std::getenv("MOMA_NO_AUTOTUNE")) return;
+  a->tune_axis.clear();
+  a->tune_log.clear();
+  a->tune_bin_tr[0] = a->tune_bin_tr[1] = a->tune_bin_ns[0] = a->tune_bin_ns[1] = 0;
+  if (a->prec == MOMA_PREC_MIXED) autotune_precision<float>(a, nr, 0);
+  autotune_precision<double>(a, nr, 1);
+  a->tuned_nr = nr;
+}
+
 template <typename R>
 void gmres_cycle(moma_array *a, int nr, const std::vector<int> &act, int *inner_iters, double *first_red) {
   using C = typename Cplx<R>::T;
@@ -551,8 +684,10 @@ void gmres_cycle(moma_array *a, int nr, const std::vector<int> &act, int *inner_
       a->poll_ev.push_back(e);
     }
   }
-  int steps = 0;
-  for (int j = 0; j < a->m; ++j) {
+  // One Arnoldi step: the normal operator, the three CGS2 sweeps (the last
+  // one applies the Givens rotation), the scaling of the new basis vector,
+  // and the copy of the active-column count for the host's lagged poll.
+  auto enqueue_step = [&](int j) {
     a->live = c.nact;  // steps queued after convergence cost only their launches
     apply_normal<R>(a, nr, V + (size_t)j * vstride, V + (size_t)(j + 1) * vstride);
     a->live = nullptr;
@@ -566,10 +701,57 @@ void gmres_cycle(moma_array *a, int nr, const std::vector<int> &act, int *inner_
     check_launch(a);
     CK(cudaMemcpyAsync(a->h_nact + j, c.nact, sizeof(int), cudaMemcpyDeviceToHost, a->st));
     CK(cudaEventRecord(a->poll_ev[j], a->st));
+  };
+  // With graphs on, step j is captured once (per RHS count) and replayed.
+  const bool graphs = a->use_graphs && !a->prof && a->st == a->gs && a->gs != nullptr;
+  if (graphs && a->g_nr != nr) {
+    drop_graphs(a);
+    a->gexec.assign(a->m, nullptr);
+    a->g_nr = nr;
+  }
+  int steps = 0;
+  for (int j = 0; j < a->m; ++j) {
+    if (graphs) {
+      if (!a->gexec[j]) {
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(a->st, cudaStreamCaptureModeThreadLocal));
+        const long long l0 = a->launches;
+        try {
+          enqueue_step(j);
+        } catch (...) {
+          cudaStreamEndCapture(a->st, &g);
+          if (g) cudaGraphDestroy(g);
+          throw;
+        }
+        a->g_step_launches = a->launches - l0;
+        a->launches = l0;
+        CK(cudaStreamEndCapture(a->st, &g));
+        cudaGraphExec_t ge = nullptr;
+        const cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
+        cudaGraphDestroy(g);
+        CK(ie);
+        a->gexec[j] = ge;
+      }
+      a->h_nact[j] = -1;  // sentinel, overwritten by the step's copy
+      CK(cudaGraphLaunch(a->gexec[j], a->st));
+      a->launches += a->g_step_launches;
+    } else {
+      a->h_nact[j] = -1;
+      enqueue_step(j);
+    }
     steps = j + 1;
     if (j >= lag) {
-      CK(cudaEventSynchronize(a->poll_ev[j - lag]));
-      if (a->h_nact[j - lag] == 0) break;
+      // Lagged poll of the pinned copy written by step j - lag (bounded).
+      volatile int *hn = a->h_nact;
+      const auto t0 = std::chrono::steady_clock::now();
+      while (hn[j - lag] == -1) {
+        if (cudaStreamQuery(a->st) == cudaSuccess && hn[j - lag] == -1)
+          throw MomaError(MOMA_ERR_CUDA, "poll copy did not arrive");
+        if (std::chrono::steady_clock::now() - t0 > std::chrono::seconds(60))
+          throw MomaError(MOMA_ERR_TIMEOUT, "inner iteration poll timed out");
+        std::this_thread::yield();
+      }
+      if (hn[j - lag] == 0) break;
     }
   }
   CK(cudaStreamSynchronize(a->st));
@@ -601,6 +783,33 @@ void solve_impl(moma_array *a, int nr, const void *Vin, void *Iout, const moma_s
   const bool warm = o && o->warm_start;
   const size_t bytes = (size_t)nr * a->N * sizeof(double2);
   a->ctl.inner_tol = itol;
+
+  // The solve runs on an internal non-blocking stream (capturable into
+  // graphs), ordered after the array's stream on entry and before it on exit.
+  struct StreamSwitch {
+    moma_array *a;
+    cudaStream_t user;
+    bool on = false;
+    StreamSwitch(moma_array *a_) : a(a_), user(a_->st) {
+      if (!a->use_graphs || a->prof) return;
+      if (!a->gs) {
+        CK(cudaStreamCreateWithFlags(&a->gs, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&a->ev_in, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&a->ev_out, cudaEventDisableTiming));
+      }
+      CK(cudaEventRecord(a->ev_in, user));
+      CK(cudaStreamWaitEvent(a->gs, a->ev_in, 0));
+      a->st = a->gs;
+      on = true;
+    }
+    ~StreamSwitch() {
+      if (!on) return;
+      cudaEventRecord(a->ev_out, a->gs);
+      cudaStreamWaitEvent(user, a->ev_out, 0);
+      a->st = user;
+    }
+  } sw(a);
+  autotune(a, nr);
 
   // Inputs into the solver's own buffers.
   CK(cudaMemcpyAsync(a->Vw.p, Vin, bytes, cudaMemcpyDefault, a->st));
@@ -686,6 +895,13 @@ void destroy_impl(moma_array *a) {
   if (a->h_norms) cudaFreeHost(a->h_norms);
   if (a->h_err) cudaFreeHost(a->h_err);
   for (auto e : a->poll_ev) cudaEventDestroy(e);
+  drop_graphs(a);
+  if (a->gs) {
+    cudaStreamSynchronize(a->gs);
+    cudaStreamDestroy(a->gs);
+    cudaEventDestroy(a->ev_in);
+    cudaEventDestroy(a->ev_out);
+  }
   for (auto &p : a->ev_pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
   for (auto e : a->ev_free) cudaEventDestroy(e);
   delete a;
@@ -715,6 +931,8 @@ moma_status moma_create_array(int nx, int ny, int b, const moma_options *opt, vo
     if (b > (prec == MOMA_PREC_FP64 ? 128 : 160)) throw MomaError(MOMA_ERR_ARG, "b too large for this build");
     a->prec = prec;
     a->m = (opt && opt->restart > 0) ? opt->restart : 50;
+    a->use_graphs = !(opt && (opt->flags & MOMA_FLAG_NO_GRAPHS));
+    a->no_autotune = opt && (opt->flags & MOMA_FLAG_NO_AUTOTUNE);
     if (a->m > MOMA_MAX_RESTART) throw MomaError(MOMA_ERR_ARG, "restart too large");
     const int mx = (opt && opt->mx > 0) ? opt->mx : next_smooth(2 * nx - 1);
     const int my = (opt && opt->my > 0) ? opt->my : next_smooth(2 * ny - 1);
@@ -904,6 +1122,14 @@ moma_status moma_set_stream(moma_array *a, void *cuda_stream) {
     CK(cudaStreamSynchronize(a->st));
     a->st = reinterpret_cast<cudaStream_t>(cuda_stream);
   });
+}
+
+void *moma_array_stream(const moma_array *a) { return a ? reinterpret_cast<void *>(a->st) : nullptr; }
+
+moma_status moma_tuning_report(const moma_array *a, char *buf, size_t len) {
+  if (!a || !buf || len == 0) { g_last_error = "bad arguments"; return MOMA_ERR_ARG; }
+  std::snprintf(buf, len, "%s", a->tune_log.c_str());
+  return MOMA_OK;
 }
 
 moma_status moma_release_setup(moma_array *a) {

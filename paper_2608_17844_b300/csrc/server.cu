@@ -320,3 +320,75 @@ void moma_server_destroy(moma_server *s) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------ ragged batches ----
+// Independent problems of uneven sizes (different lattices, frequencies,
+// RHS sets) run concurrently: `workers` host threads, each with its own
+// non-blocking stream, take the next problem index; each array is bound to
+// the worker's stream for its call and handed back to its own stream after.
+namespace {
+
+template <typename F>
+moma_status run_batch(int n, moma_array *const *arrays, int workers, moma_status *statuses, F &&body) {
+  if (n < 0 || (n > 0 && !arrays)) return MOMA_ERR_ARG;
+  if (n == 0) return MOMA_OK;
+  if (workers <= 0) workers = 8;
+  if (workers > n) workers = n;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return MOMA_ERR_CUDA;
+  std::vector<cudaStream_t> streams(workers, nullptr);
+  for (auto &st : streams)
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return MOMA_ERR_CUDA;
+  std::vector<moma_status> stv(n, MOMA_OK);
+  std::mutex mu;
+  int next = 0;
+  std::vector<std::thread> th;
+  for (int w = 0; w < workers; ++w)
+    th.emplace_back([&, w] {
+      cudaSetDevice(dev);
+      for (;;) {
+        int i;
+        {
+          std::lock_guard<std::mutex> lk(mu);
+          if (next >= n) return;
+          i = next++;
+        }
+        moma_array *a = arrays[i];
+        void *own = moma_array_stream(a);
+        moma_status st = moma_set_stream(a, streams[w]);
+        if (st == MOMA_OK) st = body(i, a);
+        const moma_status back = moma_set_stream(a, own);
+        stv[i] = st != MOMA_OK ? st : back;
+      }
+    });
+  for (auto &t : th) t.join();
+  for (auto st : streams) cudaStreamDestroy(st);
+  moma_status first = MOMA_OK;
+  for (int i = 0; i < n; ++i) {
+    if (statuses) statuses[i] = stv[i];
+    if (first == MOMA_OK && stv[i] != MOMA_OK) first = stv[i];
+  }
+  return first;
+}
+
+}  // namespace
+
+extern "C" moma_status moma_set_blocks_batch(int n, moma_array *const *arrays, const void *const *blocks,
+                                             const int *dtypes, int release_setup, int workers,
+                                             moma_status *statuses) {
+  if (n > 0 && (!blocks || !dtypes)) return MOMA_ERR_ARG;
+  return run_batch(n, arrays, workers, statuses, [&](int i, moma_array *a) {
+    moma_status st = moma_set_blocks(a, blocks[i], dtypes[i]);
+    if (st == MOMA_OK && release_setup) st = moma_release_setup(a);
+    return st;
+  });
+}
+
+extern "C" moma_status moma_solve_batch(int n, moma_array *const *arrays, const int *nrhs, const void *const *V,
+                                        void *const *I, const moma_solve_opts *opts, moma_solve_info *infos,
+                                        int workers, moma_status *statuses) {
+  if (n > 0 && (!nrhs || !V || !I)) return MOMA_ERR_ARG;
+  return run_batch(n, arrays, workers, statuses, [&](int i, moma_array *a) {
+    return moma_solve(a, nrhs[i], V[i], I[i], opts, infos ? &infos[i] : nullptr, nullptr);
+  });
+}

@@ -31,7 +31,8 @@ EXPORTS = [
     "moma_create_array", "moma_set_blocks", "moma_matvec", "moma_apply_precond", "moma_get_bin",
     "moma_get_precond_block", "moma_solve", "moma_active_impedance", "moma_profile", "moma_kernel_stats",
     "moma_launch_count", "moma_device_bytes", "moma_destroy", "moma_last_error", "moma_matvec_noalloc",
-    "moma_set_stream", "moma_release_setup", "moma_estimate_bytes",
+    "moma_set_stream", "moma_release_setup", "moma_estimate_bytes", "moma_tuning_report", "moma_array_stream",
+    "moma_set_blocks_batch", "moma_solve_batch",
     "moma_server_create", "moma_server_submit", "moma_server_wait", "moma_server_get_stats", "moma_server_destroy",
 ]
 
@@ -42,8 +43,12 @@ class MomaError(RuntimeError):
         self.status = status
 
 
+MOMA_FLAG_NO_GRAPHS, MOMA_FLAG_NO_AUTOTUNE = 1, 2
+
+
 class moma_options(ctypes.Structure):
-    _fields_ = [("precision", ctypes.c_int), ("mx", ctypes.c_int), ("my", ctypes.c_int), ("restart", ctypes.c_int)]
+    _fields_ = [("precision", ctypes.c_int), ("mx", ctypes.c_int), ("my", ctypes.c_int), ("restart", ctypes.c_int),
+                ("flags", ctypes.c_int)]
 
 
 class moma_solve_opts(ctypes.Structure):
@@ -109,6 +114,14 @@ def lib():
     L.moma_apply_precond.argtypes = [vp, i, vp, vp, i]
     L.moma_matvec_noalloc.argtypes = [vp, i, i, vp, vp, i]
     L.moma_set_stream.argtypes = [vp, vp]
+    L.moma_tuning_report.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
+    L.moma_array_stream.argtypes = [vp]
+    L.moma_array_stream.restype = vp
+    L.moma_set_blocks_batch.argtypes = [i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(i), i, i,
+                                        ctypes.POINTER(i)]
+    L.moma_solve_batch.argtypes = [i, ctypes.POINTER(vp), ctypes.POINTER(i), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                   ctypes.POINTER(moma_solve_opts), ctypes.POINTER(moma_solve_info), i,
+                                   ctypes.POINTER(i)]
     L.moma_release_setup.argtypes = [vp]
     L.moma_estimate_bytes.argtypes = [i, i, i, ctypes.POINTER(moma_options), i, i]
     L.moma_estimate_bytes.restype = ctypes.c_size_t
@@ -134,7 +147,7 @@ def lib():
     L.moma_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
         if name not in ("moma_launch_count", "moma_device_bytes", "moma_destroy", "moma_last_error",
-                        "moma_estimate_bytes", "moma_server_destroy"):
+                        "moma_estimate_bytes", "moma_server_destroy", "moma_array_stream"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -179,9 +192,9 @@ def _stream_handle(stream):
     return getattr(stream, "cuda_stream", stream)
 
 
-def moma_create_array(nx, ny, b, precision=MOMA_PREC_MIXED, mx=0, my=0, restart=0, stream=None):
+def moma_create_array(nx, ny, b, precision=MOMA_PREC_MIXED, mx=0, my=0, restart=0, stream=None, flags=0):
     h = ctypes.c_void_p()
-    opt = moma_options(precision, mx, my, restart)
+    opt = moma_options(precision, mx, my, restart, flags)
     _check(lib().moma_create_array(nx, ny, b, ctypes.byref(opt), _stream_handle(stream), ctypes.byref(h)))
     return h
 
@@ -290,7 +303,7 @@ def moma_release_setup(h):
 
 
 def moma_estimate_bytes(nx, ny, b, nrhs, precision=MOMA_PREC_MIXED, with_setup=True):
-    opt = moma_options(precision, 0, 0, 0)
+    opt = moma_options(precision, 0, 0, 0, 0)
     return lib().moma_estimate_bytes(nx, ny, b, ctypes.byref(opt), nrhs, 1 if with_setup else 0)
 
 
@@ -330,3 +343,43 @@ def moma_server_get_stats(s):
 def moma_server_destroy(s):
     if s:
         lib().moma_server_destroy(s)
+
+
+def moma_tuning_report(h):
+    buf = ctypes.create_string_buffer(8192)
+    _check(lib().moma_tuning_report(h, buf, len(buf)))
+    return buf.value.decode()
+
+
+def moma_array_stream(h):
+    return lib().moma_array_stream(h)
+
+
+def moma_set_blocks_batch(handles, blocks, release_setup=False, workers=0):
+    """Build many arrays concurrently; returns the per-array statuses."""
+    n = len(handles)
+    hs = (ctypes.c_void_p * n)(*[h.value for h in handles])
+    pd = [_ptr_dtype(b) for b in blocks]
+    bp = (ctypes.c_void_p * n)(*[p for p, _ in pd])
+    dt = (ctypes.c_int * n)(*[d for _, d in pd])
+    st = (ctypes.c_int * n)()
+    s = lib().moma_set_blocks_batch(n, hs, bp, dt, 1 if release_setup else 0, workers, st)
+    if s != MOMA_OK:
+        raise MomaError(s, f"batch set_blocks: statuses {list(st)}")
+    return list(st)
+
+
+def moma_solve_batch(handles, Vs, Is, tol=0.0, workers=0):
+    """Solve many independent problems concurrently; returns the infos."""
+    n = len(handles)
+    hs = (ctypes.c_void_p * n)(*[h.value for h in handles])
+    nr = (ctypes.c_int * n)(*[v.shape[0] for v in Vs])
+    vp = (ctypes.c_void_p * n)(*[_ptr_dtype(v)[0] for v in Vs])
+    ip = (ctypes.c_void_p * n)(*[_ptr_dtype(x)[0] for x in Is])
+    infos = (moma_solve_info * n)()
+    st = (ctypes.c_int * n)()
+    opts = moma_solve_opts(tol, 0.0, 0, 0)
+    s = lib().moma_solve_batch(n, hs, nr, vp, ip, ctypes.byref(opts), infos, workers, st)
+    if s != MOMA_OK:
+        raise MomaError(s, f"batch solve: statuses {list(st)}")
+    return [x.as_dict() for x in infos]

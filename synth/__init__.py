@@ -11,6 +11,7 @@ from .lattice import (
     LatticeSpec,
     element_geometry,
     offset_blocks,
+    offset_blocks_torch,
     excitation,
     scan_phase,
     config_c1,
@@ -24,6 +25,7 @@ __all__ = [
     "LatticeSpec",
     "element_geometry",
     "offset_blocks",
+    "offset_blocks_torch",
     "excitation",
     "scan_phase",
     "config_c1",

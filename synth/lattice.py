@@ -83,6 +83,39 @@ def offset_blocks(spec, dtype=np.complex128):
     return out
 
 
+def offset_blocks_torch(spec, device="cuda", dtype=None):
+    """The same offset blocks as offset_blocks(), evaluated with torch on
+    `device` (float64 arithmetic, same formula and geometry draw) -- for
+    workloads whose host generation would be too slow.  Values agree with
+    the numpy version to float64 rounding of the elementary functions.
+    Returns a [2Ny-1][2Nx-1][b][b] tensor (complex64 unless dtype given)."""
+    import torch
+    dtype = dtype or torch.complex64
+    nx, ny, b, d = spec.nx, spec.ny, spec.b, spec.d
+    p, w, alpha = element_geometry(b, d, spec.seed)
+    dev = torch.device(device)
+    p = torch.as_tensor(p, dtype=torch.float64, device=dev)
+    w = torch.as_tensor(w, dtype=torch.float64, device=dev)
+    al = torch.as_tensor(alpha, dtype=torch.float64, device=dev)
+    coef = torch.outer(w, w) * torch.cos(al[:, None] - al[None, :])
+    pij = p[:, None, :] - p[None, :, :]
+    dxs = torch.arange(-(nx - 1), nx, dtype=torch.float64, device=dev) * d
+    out = torch.empty((2 * ny - 1, 2 * nx - 1, b, b), dtype=dtype, device=dev)
+    eye = torch.eye(b, dtype=torch.float64, device=dev)
+    for iy, dy in enumerate(range(-(ny - 1), ny)):
+        rx = dxs[:, None, None] + pij[None, :, :, 0]
+        ry = dy * d + pij[None, :, :, 1]
+        r = torch.clamp(torch.sqrt(rx * rx + ry * ry), min=R_FLOOR)
+        amp = coef[None] / (4.0 * np.pi * r)
+        ph = -K_WAVENUMBER * r
+        re, im = amp * torch.cos(ph), amp * torch.sin(ph)
+        if dy == 0:
+            re[nx - 1] += SELF_LOAD.real * eye
+            im[nx - 1] += SELF_LOAD.imag * eye
+        out[iy] = torch.complex(re, im).to(dtype)
+    return out
+
+
 def scan_phase(nx, ny, d, theta_deg, phi_deg):
     """Progressive port phase a[my][mx] = exp(-j k d sin(theta) (mx cos(phi) + my sin(phi)))."""
     th = np.deg2rad(theta_deg)

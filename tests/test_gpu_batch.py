@@ -1,0 +1,81 @@
+"""Ragged batches, CUDA-graph replay and the autotuner: none of them may
+change a result.  Batched solves of uneven lattices equal stand-alone
+solves bitwise and the dense oracle to the solve tolerance; graph replay
+equals direct launches; the autotuner reports what it picked."""
+import numpy as np
+import pytest
+
+from synth import LatticeSpec, offset_blocks, excitation
+from oracle import dense
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [(1, 1, 5, 0.5), (2, 3, 8, 0.3), (6, 4, 12, 0.7), (5, 5, 9, 0.5), (8, 8, 16, 0.4), (3, 9, 6, 0.6)]
+
+
+def test_ragged_batch_equals_single_solves(moma_lib, cuda):
+    m = moma_lib
+    specs = [LatticeSpec(nx, ny, b, d, 3) for nx, ny, b, d in SIZES]
+    blocks = [offset_blocks(s, np.complex64) for s in specs]
+    Vs = [excitation(s, [(0, 0), (35, 20)][: 1 + i % 2]) for i, s in enumerate(specs)]
+    hs = [m.moma_create_array(s.nx, s.ny, s.b) for s in specs]
+    try:
+        m.moma_set_blocks_batch(hs, blocks, release_setup=True, workers=3)
+        Is = [np.zeros_like(V) for V in Vs]
+        infos = m.moma_solve_batch(hs, Vs, Is, workers=3)
+        assert all(x["converged"] == 1 for x in infos)
+    finally:
+        for h in hs:
+            m.moma_destroy(h)
+    for s, bl, V, I in zip(specs, blocks, Vs, Is):
+        h = m.moma_create_array(s.nx, s.ny, s.b)
+        try:
+            m.moma_set_blocks(h, bl)
+            I1 = np.zeros_like(V)
+            m.moma_solve(h, V, I1)
+        finally:
+            m.moma_destroy(h)
+        assert np.array_equal(I, I1)
+        z = dense.assemble(bl.astype(np.complex128), s.nx, s.ny)
+        assert dense.relative_residual(z, I, V).max() <= 1e-10
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_graph_replay_equals_direct_launches(moma_lib, cuda, prec):
+    m = moma_lib
+    spec = LatticeSpec(7, 6, 10, 0.5, 8)
+    blocks = offset_blocks(spec, np.complex64)
+    V = excitation(spec, [(0, 0), (30, 45), (55, 5)])
+    res = []
+    for flags in (0, m.MOMA_FLAG_NO_GRAPHS):
+        h = m.moma_create_array(spec.nx, spec.ny, spec.b, prec, flags=flags)
+        try:
+            m.moma_set_blocks(h, blocks)
+            for _ in range(2):  # the second solve replays the captured steps
+                I = np.zeros_like(V)
+                m.moma_solve(h, V, I)
+            res.append(I)
+        finally:
+            m.moma_destroy(h)
+    assert np.array_equal(res[0], res[1])
+
+
+def test_autotuner_reports_choices(moma_lib, cuda):
+    m = moma_lib
+    spec = LatticeSpec(6, 6, 16, 0.5, 1)
+    blocks = offset_blocks(spec, np.complex64)
+    V = excitation(spec, [(0, 0)])
+    h = m.moma_create_array(spec.nx, spec.ny, spec.b)
+    h2 = m.moma_create_array(spec.nx, spec.ny, spec.b, flags=m.MOMA_FLAG_NO_AUTOTUNE)
+    try:
+        assert m.moma_tuning_report(h) == ""
+        for x in (h, h2):
+            m.moma_set_blocks(x, blocks)
+            I = np.zeros_like(V)
+            m.moma_solve(x, V, I)
+        rep = m.moma_tuning_report(h)
+        assert "bin_product<c64>" in rep and "IxMaskFx<c64>" in rep and "Fx<c128>" in rep
+        assert m.moma_tuning_report(h2) == ""
+    finally:
+        m.moma_destroy(h)
+        m.moma_destroy(h2)

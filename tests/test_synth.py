@@ -74,3 +74,14 @@ def test_excitation_layout():
     assert np.count_nonzero(v[:, :, :, [0, 1, 3, 4, 5]]) == 0
     ph = np.angle(v[1, 0, 1, 2] / v[1, 0, 0, 2])
     assert np.isclose(ph, -2 * np.pi * 0.5 * np.sin(np.pi / 6))
+
+
+def test_torch_generator_matches_numpy():
+    import torch
+    from synth import offset_blocks_torch
+    spec = LatticeSpec(4, 3, 7, 0.37, 5)
+    a = offset_blocks(spec)
+    t = offset_blocks_torch(spec, "cpu", torch.complex128).numpy()
+    assert np.allclose(t, a, rtol=1e-13, atol=1e-15)
+    c64 = offset_blocks_torch(spec, "cpu").numpy()
+    assert c64.dtype == np.complex64 and np.allclose(c64, a, rtol=1e-6, atol=0)
