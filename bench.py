@@ -498,6 +498,26 @@ def main():
         fp64 = {"value": nr / (ms64 / 1000.0), "unit": "solves/s", "ms_per_step": ms64, "info": inf64,
                 "speedup_mixed_vs_fp64": value / world / (nr / (ms64 / 1000.0))}
 
+    # The paper's PCG solver (Sec. II-C) on the same problem and path.
+    pcg = None
+    if args.fp64_steps > 0:
+        infos_pcg = []
+        for _ in range(2):
+            m.moma_set_blocks(h, blocks_d)
+            infos_pcg.append(m.moma_solve(h, V_d, I_d, solver=m.MOMA_SOLVER_PCG))
+        torch.cuda.synchronize()
+        a_ = torch.cuda.Event(enable_timing=True)
+        b_ = torch.cuda.Event(enable_timing=True)
+        a_.record(stream)
+        for _ in range(args.fp64_steps + 1):
+            m.moma_set_blocks(h, blocks_d)
+            inf_pcg = m.moma_solve(h, V_d, I_d, solver=m.MOMA_SOLVER_PCG)
+            m.moma_active_impedance(h, I_d, V_d, za_d, gam_d)
+        b_.record(stream)
+        torch.cuda.synchronize()
+        ms_pcg = a_.elapsed_time(b_) / (args.fp64_steps + 1)
+        pcg = {"value": nr / (ms_pcg / 1000.0), "unit": "solves/s", "ms_per_step": ms_pcg, "info": inf_pcg}
+
     # End to end through the C ABI with host buffers (pinned), copies inside.
     e2e = None
     if not args.no_e2e:
@@ -549,7 +569,7 @@ def main():
                         "min": min(steps_ms), "max": max(steps_ms)},
             "profiled_ms_per_step": prof_total_ms / args.steps,
             "phases": phases, "roofline": roofline, "kernels": kernel_share, "cpu_baseline": cpu,
-            "e2e": e2e, "gpu_launches": launches, "clocks": clk, "fp64_plain": fp64,
+            "e2e": e2e, "gpu_launches": launches, "clocks": clk, "fp64_plain": fp64, "pcg_mixed": pcg,
             "ports_Za": {k: [f"{z.real:.10f}{z.imag:+.10f}j" for z in v] for k, v in ports.items()},
         }
         print(json.dumps(line, default=str), flush=True)

@@ -86,12 +86,21 @@ typedef struct {
     int flags;     /* MOMA_FLAG_* */
 } moma_options;
 
+typedef enum {
+    MOMA_SOLVER_GMRES = 0, /* restarted GMRES on P^{-1} Z^H Z I = P^{-1} Z^H V (Sec. III-A, "new M1") */
+    MOMA_SOLVER_PCG = 1    /* preconditioned CG on Z^H Z I = Z^H V with preconditioner P (Sec. II-C);
+                              O(1) vectors per RHS */
+} moma_solver;
+
 typedef struct {
     double tol;       /* per-RHS relative true residual ||V - Z I|| / ||V||; 0 = 1e-10 */
-    double inner_tol; /* relative reduction of the inner preconditioned residual per
-                         refinement step; 0 = 1e-5 (mixed) or tol/10 (FP64) */
-    int max_outer;    /* refinement steps (each one GMRES cycle); 0 = 30 */
+    double inner_tol; /* relative reduction of the inner residual per refinement step
+                         (GMRES: preconditioned; PCG: ||Z^H (r - Z d)||); 0 = 1e-5 (mixed)
+                         or tol/10 (FP64) */
+    int max_outer;    /* refinement steps (each one inner solve); 0 = 30 */
     int warm_start;   /* nonzero: I holds an initial guess on entry */
+    int solver;       /* moma_solver */
+    int max_inner;    /* PCG iterations per refinement step; 0 = 500 (GMRES: the restart) */
 } moma_solve_opts;
 
 typedef struct {

@@ -387,3 +387,186 @@ template void launch_to_inner<float>(const double2 *, void *, int, int, const do
 template void launch_to_inner<double>(const double2 *, void *, int, int, const double *, const int *, cudaStream_t);
 
 }  // namespace moma
+
+// ================================================================ PCG =====
+// Preconditioned conjugate gradients on the normal equations
+// Z^H Z d = Z^H r (Sec. II-C): Z^H Z is Hermitian positive definite and P
+// (Eq. 38) is applied as the preconditioner M = P = L L^H, which is the
+// split form P^{-1/2} Z^H Z P^{-H/2} of Sec. III-A in exact arithmetic.
+// Only O(1) vectors per RHS are kept.  Inner products of c64 vectors are
+// accumulated per thread in FP32 and across threads / CTAs in FP64, in a
+// fixed order; the step lengths alpha, beta are FP64 device scalars.
+namespace moma {
+
+// cg_reduce computes out = Re(sum conj(a) b) per RHS; then, by mode:
+//   CG_PQ : alpha = rz / pq       (frozen columns: alpha = 0)
+//   CG_RZ : beta = rz_new / rz, rz = rz_new     (CG_RZ0: rz = rz_new, no beta)
+
+template <typename R>
+__global__ void __launch_bounds__(KT) cg_reduce_kernel(CgCtl c, const typename Cplx<R>::T *a,
+                                                       const typename Cplx<R>::T *b, int N, int mode) {
+  using C = typename Cplx<R>::T;
+  __shared__ C red[8];
+  __shared__ int last;
+  const int q = blockIdx.y, chunk = blockIdx.x, tid = threadIdx.x;
+  if (!c.active[q]) return;
+  const size_t qoff = (size_t)q * N;
+  const int n0 = chunk * KT * KEPT;
+  C acc[1] = {czero<C>()};
+#pragma unroll
+  for (int t = 0; t < KEPT; ++t) {
+    const int n = n0 + tid + KT * t;
+    if (n < N) acc[0] = cfmac(a[qoff + n], b[qoff + n], acc[0]);
+  }
+  block_sum<C, 1>(acc, red);
+  if (tid == 0) c.partial[(size_t)q * gridDim.x + chunk] = (double)acc[0].x;
+  __threadfence();
+  if (tid == 0) last = (atomicAdd(&c.counters[q], 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (tid < 32) {
+    double s = 0;
+    for (int ch = tid; ch < (int)gridDim.x; ch += 32) s += c.partial[(size_t)q * gridDim.x + ch];
+    s = warp_sum(s);
+    if (tid == 0) {
+      if (mode == CG_PQ) {
+        c.alpha[q] = (s > 0.0 && isfinite(s)) ? c.rz[q] / s : 0.0;
+        if (!isfinite(s)) atomicOr(c.err, DEVERR_NONFINITE);
+      } else {
+        if (mode == CG_RZ) c.beta[q] = c.rz[q] != 0.0 ? s / c.rz[q] : 0.0;
+        c.rz[q] = s;
+      }
+      c.counters[q] = 0;
+    }
+  }
+}
+
+// d += alpha p; r -= alpha q; then ||r||^2 -> stop test against tol^2 ||r0||^2
+// (mode 0), or just ||r||^2 into rr0 (mode 1, initialisation).
+template <typename R>
+__global__ void __launch_bounds__(KT) cg_axpy_kernel(CgCtl c, typename Cplx<R>::T *d, const typename Cplx<R>::T *p,
+                                                     typename Cplx<R>::T *r, const typename Cplx<R>::T *qv, int N,
+                                                     int init) {
+  using C = typename Cplx<R>::T;
+  using RT = decltype(C{}.x);
+  __shared__ C red[8];
+  __shared__ int last;
+  const int q = blockIdx.y, chunk = blockIdx.x, tid = threadIdx.x;
+  if (!c.active[q]) return;
+  const size_t qoff = (size_t)q * N;
+  const int n0 = chunk * KT * KEPT;
+  const RT al = init ? (RT)0 : (RT)c.alpha[q];
+  C acc[1] = {czero<C>()};
+#pragma unroll
+  for (int t = 0; t < KEPT; ++t) {
+    const int n = n0 + tid + KT * t;
+    if (n < N) {
+      C rv = r[qoff + n];
+      if (!init) {
+        d[qoff + n] = cadd(d[qoff + n], cscale(p[qoff + n], al));
+        rv = csub(rv, cscale(qv[qoff + n], al));
+        r[qoff + n] = rv;
+      }
+      acc[0].x += rv.x * rv.x + rv.y * rv.y;
+    }
+  }
+  block_sum<C, 1>(acc, red);
+  if (tid == 0) c.partial[(size_t)q * gridDim.x + chunk] = (double)acc[0].x;
+  __threadfence();
+  if (tid == 0) last = (atomicAdd(&c.counters[q], 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (tid < 32) {
+    double s = 0;
+    for (int ch = tid; ch < (int)gridDim.x; ch += 32) s += c.partial[(size_t)q * gridDim.x + ch];
+    s = warp_sum(s);
+    if (tid == 0) {
+      if (init) {
+        c.rr0[q] = s;
+        if (!(s > 0.0) || !isfinite(s)) {  // nothing to solve (or bad input)
+          if (!isfinite(s)) atomicOr(c.err, DEVERR_NONFINITE);
+          c.active[q] = 0;
+          atomicSub(c.nact, 1);
+        }
+      } else {
+        c.rr[q] = s;
+        c.iters[q] += 1;
+        if (!isfinite(s)) {
+          atomicOr(c.err, DEVERR_NONFINITE);
+          c.active[q] = 0;
+          atomicSub(c.nact, 1);
+        } else if (s <= c.tol2 * c.rr0[q]) {
+          c.active[q] = 0;
+          atomicSub(c.nact, 1);
+        }
+      }
+      c.counters[q] = 0;
+    }
+  }
+}
+
+// p = z + beta p (or p = z when init).
+template <typename R>
+__global__ void cg_dir_kernel(CgCtl c, typename Cplx<R>::T *p, const typename Cplx<R>::T *z, int N, int nr,
+                              int init) {
+  using C = typename Cplx<R>::T;
+  using RT = decltype(C{}.x);
+  const size_t total = (size_t)nr * N;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const int q = (int)(idx / N);
+    if (!c.active[q]) continue;
+    p[idx] = init ? z[idx] : cadd(z[idx], cscale(p[idx], (RT)c.beta[q]));
+  }
+}
+
+// I += scale[q] * d (FP64 accumulation of the c64 correction).
+template <typename R>
+__global__ void cg_accum_kernel(const typename Cplx<R>::T *d, int N, int nr, double2 *I, const double *scale) {
+  const size_t total = (size_t)nr * N;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const int q = (int)(idx / N);
+    I[idx] = cadd(I[idx], cscale(cvt<double2>(d[idx]), scale[q]));
+  }
+}
+
+template <typename R>
+void launch_cg_reduce(const CgCtl &c, const void *a, const void *b, int N, int nr, int mode, cudaStream_t st) {
+  using C = typename Cplx<R>::T;
+  dim3 grid(krylov_chunks(N), nr);
+  cg_reduce_kernel<R><<<grid, KT, 0, st>>>(c, reinterpret_cast<const C *>(a), reinterpret_cast<const C *>(b), N,
+                                           mode);
+}
+template <typename R>
+void launch_cg_axpy(const CgCtl &c, void *d, const void *p, void *r, const void *q, int N, int nr, int init,
+                    cudaStream_t st) {
+  using C = typename Cplx<R>::T;
+  dim3 grid(krylov_chunks(N), nr);
+  cg_axpy_kernel<R><<<grid, KT, 0, st>>>(c, reinterpret_cast<C *>(d), reinterpret_cast<const C *>(p),
+                                         reinterpret_cast<C *>(r), reinterpret_cast<const C *>(q), N, init);
+}
+template <typename R>
+void launch_cg_dir(const CgCtl &c, void *p, const void *z, int N, int nr, int init, cudaStream_t st) {
+  using C = typename Cplx<R>::T;
+  cg_dir_kernel<R><<<grid_for((size_t)nr * N), 256, 0, st>>>(c, reinterpret_cast<C *>(p),
+                                                              reinterpret_cast<const C *>(z), N, nr, init);
+}
+template <typename R>
+void launch_cg_accum(const void *d, int N, int nr, double2 *I, const double *scale, cudaStream_t st) {
+  using C = typename Cplx<R>::T;
+  cg_accum_kernel<R><<<grid_for((size_t)nr * N), 256, 0, st>>>(reinterpret_cast<const C *>(d), N, nr, I, scale);
+}
+
+template void launch_cg_reduce<float>(const CgCtl &, const void *, const void *, int, int, int, cudaStream_t);
+template void launch_cg_reduce<double>(const CgCtl &, const void *, const void *, int, int, int, cudaStream_t);
+template void launch_cg_axpy<float>(const CgCtl &, void *, const void *, void *, const void *, int, int, int,
+                                    cudaStream_t);
+template void launch_cg_axpy<double>(const CgCtl &, void *, const void *, void *, const void *, int, int, int,
+                                     cudaStream_t);
+template void launch_cg_dir<float>(const CgCtl &, void *, const void *, int, int, int, cudaStream_t);
+template void launch_cg_dir<double>(const CgCtl &, void *, const void *, int, int, int, cudaStream_t);
+template void launch_cg_accum<float>(const void *, int, int, double2 *, const double *, cudaStream_t);
+template void launch_cg_accum<double>(const void *, int, int, double2 *, const double *, cudaStream_t);
+
+}  // namespace moma

@@ -31,6 +31,29 @@ struct KrylovCtl {
   double2 *y;            // [nr][m]
 };
 
+enum : int { CG_PQ = 0, CG_RZ = 1, CG_RZ0 = 2 };  // modes of launch_cg_reduce
+
+// Per-RHS state of the conjugate-gradient inner solver (device memory).
+struct CgCtl {
+  int *active;        // [nr]
+  int *nact;          // [1]
+  int *iters;         // [nr] iterations taken
+  double *rz, *rr, *rr0, *alpha, *beta;  // [nr]
+  double tol2;        // (relative tolerance)^2 on ||r||^2 / ||r0||^2
+  unsigned *counters; // [nr]
+  double *partial;    // [nr][nchunk]
+  unsigned *err;
+};
+template <typename R>
+void launch_cg_reduce(const CgCtl &c, const void *a, const void *b, int N, int nr, int mode, cudaStream_t st);
+template <typename R>
+void launch_cg_axpy(const CgCtl &c, void *d, const void *p, void *r, const void *q, int N, int nr, int init,
+                    cudaStream_t st);
+template <typename R>
+void launch_cg_dir(const CgCtl &c, void *p, const void *z, int N, int nr, int init, cudaStream_t st);
+template <typename R>
+void launch_cg_accum(const void *d, int N, int nr, double2 *I, const double *scale, cudaStream_t st);
+
 int krylov_chunks(int N);
 template <typename R>
 void launch_cgs(const KrylovCtl &c, void *V, size_t vstride, int N, int nr, int j, int flags, cudaStream_t st);

@@ -115,6 +115,10 @@ struct moma_array {
   DevBuf Iw, Vw, rw, yw;
   DevBuf kbuf;  // Krylov control arrays
   KrylovCtl ctl{};
+  CgCtl cg{};
+  std::vector<cudaGraphExec_t> cg_gexec;  // PCG iteration graphs (ring of poll slots)
+  int cg_g_nr = -1;
+  long long cg_step_launches = 0;
   double *rnorm = nullptr, *vnorm = nullptr, *rpart = nullptr;
   unsigned *rcount = nullptr;
   int *mask = nullptr;
@@ -394,6 +398,18 @@ void apply_normal(moma_array *a, int nr, const void *x, void *y) {
   precond<R>(a, nr, a->lat_tmp.p, y);
 }
 
+// y = Z^H M Z x (the normal matrix, no preconditioner).
+template <typename R>
+void apply_zhz(moma_array *a, int nr, const void *x, void *y) {
+  lattice_to_bins<R>(a, nr, x, is64<R>());
+  binprod<R>(a, nr, a->bx.p, a->by.p, 0);
+  axis<R>(a, pass_iy(a, nr, a->by.p, a->t1.p, is64<R>()), a->fy);
+  axis<R>(a, pass_ix(a, nr, a->t1.p, a->t1.p, is64<R>(), true), a->fx);
+  axis<R>(a, pass_fy(a, nr, a->t1.p, a->bx.p, is64<R>()), a->fy);
+  binprod<R>(a, nr, a->bx.p, a->by.p, 1);
+  bins_to_lattice<R>(a, nr, a->by.p, y);
+}
+
 // y = P^{-1} Z^H x.
 template <typename R>
 void apply_zh_p(moma_array *a, int nr, const void *x, void *y) {
@@ -427,6 +443,10 @@ void drop_graphs(moma_array *a) {
     if (g) cudaGraphExecDestroy(g);
   a->gexec.clear();
   a->g_nr = -1;
+  for (auto g : a->cg_gexec)
+    if (g) cudaGraphExecDestroy(g);
+  a->cg_gexec.clear();
+  a->cg_g_nr = -1;
 }
 
 void ensure_ws(moma_array *a, int nr) {
@@ -443,7 +463,7 @@ void ensure_ws(moma_array *a, int nr) {
   a->bx.ensure(bsz * c, a->dev_bytes);
   a->by.ensure(bsz * c, a->dev_bytes);
   const size_t esz = a->prec == MOMA_PREC_FP64 ? sizeof(double2) : sizeof(float2);
-  a->Vk.ensure((size_t)(a->m + 1) * lat * esz, a->dev_bytes);
+  a->Vk.ensure((size_t)std::max(a->m + 1, 5) * lat * esz, a->dev_bytes);
   a->Iw.ensure(lat * c, a->dev_bytes);
   a->Vw.ensure(lat * c, a->dev_bytes);
   a->rw.ensure(lat * c, a->dev_bytes);
@@ -461,6 +481,9 @@ void ensure_ws(moma_array *a, int nr) {
   const size_t o_g = take((size_t)nr * (m + 1) * c), o_y = take((size_t)nr * m * c);
   const size_t o_rn = take(nr * sizeof(double)), o_vn = take(nr * sizeof(double));
   const size_t o_rp = take((size_t)nr * nch * sizeof(double)), o_mask = take(nr * sizeof(int));
+  const size_t o_cg_act = take(nr * sizeof(int)), o_cg_nact = take(sizeof(int)), o_cg_it = take(nr * sizeof(int));
+  const size_t o_cg_s = take((size_t)5 * nr * sizeof(double)), o_cg_cnt = take(nr * sizeof(unsigned));
+  const size_t o_cg_part = take((size_t)nr * nch * sizeof(double));
   a->kbuf.ensure(off, a->dev_bytes);
   unsigned char *base = a->kbuf.as<unsigned char>();
   CK(cudaMemset(base, 0, off));
@@ -488,6 +511,15 @@ void ensure_ws(moma_array *a, int nr) {
   a->rpart = reinterpret_cast<double *>(base + o_rp);
   a->rcount = k.counters + nr;
   a->mask = reinterpret_cast<int *>(base + o_mask);
+  CgCtl &g = a->cg;
+  g.active = reinterpret_cast<int *>(base + o_cg_act);
+  g.nact = reinterpret_cast<int *>(base + o_cg_nact);
+  g.iters = reinterpret_cast<int *>(base + o_cg_it);
+  double *cs5 = reinterpret_cast<double *>(base + o_cg_s);
+  g.rz = cs5; g.rr = cs5 + nr; g.rr0 = cs5 + 2 * nr; g.alpha = cs5 + 3 * nr; g.beta = cs5 + 4 * nr;
+  g.counters = reinterpret_cast<unsigned *>(base + o_cg_cnt);
+  g.partial = reinterpret_cast<double *>(base + o_cg_part);
+  g.err = a->err;
   if (a->h_norms) cudaFreeHost(a->h_norms);
   CK(cudaMallocHost(&a->h_norms, (size_t)3 * nr * sizeof(double) + 64));
   a->ws_nr = nr;
@@ -774,6 +806,123 @@ void gmres_cycle(moma_array *a, int nr, const std::vector<int> &act, int *inner_
   check_launch(a);
 }
 
+// Inner PCG solve of Z^H Z d = Z^H r~ with preconditioner P (Sec. II-C,
+// Sec. III-A), then I += ||r|| d.  Vectors (c64 in MIXED): d, r, p, q, z in
+// the first five Krylov slots.  Iterations are graph-captured per slot of a
+// 16-entry ring of poll copies and replayed.
+template <typename R>
+void pcg_cycle(moma_array *a, int nr, const std::vector<int> &act, int max_inner, int *inner_iters,
+               double *first_red) {
+  using C = typename Cplx<R>::T;
+  const size_t vs = (size_t)nr * a->N;
+  C *base = a->Vk.as<C>();
+  C *d = base, *r = base + vs, *p = base + 2 * vs, *q = base + 3 * vs, *z = base + 4 * vs;
+  CgCtl c = a->cg;
+  c.tol2 = a->ctl.inner_tol * a->ctl.inner_tol;
+  int nact = 0;
+  for (int k = 0; k < nr; ++k) nact += act[k] ? 1 : 0;
+  a->h_nact[MOMA_MAX_RESTART + 4] = nact;
+  CK(cudaMemcpyAsync(c.active, a->mask, nr * sizeof(int), cudaMemcpyDeviceToDevice, a->st));
+  CK(cudaMemcpyAsync(c.nact, a->h_nact + MOMA_MAX_RESTART + 4, sizeof(int), cudaMemcpyHostToDevice, a->st));
+  CK(cudaMemsetAsync(c.iters, 0, nr * sizeof(int), a->st));
+  CK(cudaMemsetAsync(d, 0, vs * sizeof(C), a->st));
+  // r = Z^H r~ (right-hand side of the normal equations), ||r0||, z = P^{-1} r, p = z.
+  apply_z<R>(a, nr, a->lat_in.p, r, 1);
+  a->timed(PK_KRYLOV, [&] { launch_cg_axpy<R>(c, d, p, r, q, a->N, nr, 1, a->st); });
+  check_launch(a);
+  precond<R>(a, nr, r, z);
+  a->timed(PK_KRYLOV, [&] { launch_cg_reduce<R>(c, r, z, a->N, nr, CG_RZ0, a->st); });
+  check_launch(a);
+  a->timed(PK_KRYLOV, [&] { launch_cg_dir<R>(c, p, z, a->N, nr, 1, a->st); });
+  check_launch(a);
+
+  constexpr int RING = 16;
+  auto enqueue_iter = [&](int slot) {
+    a->live = c.nact;
+    apply_zhz<R>(a, nr, p, q);
+    a->timed(PK_KRYLOV, [&] { launch_cg_reduce<R>(c, p, q, a->N, nr, CG_PQ, a->st); });
+    check_launch(a);
+    a->timed(PK_KRYLOV, [&] { launch_cg_axpy<R>(c, d, p, r, q, a->N, nr, 0, a->st); });
+    check_launch(a);
+    precond<R>(a, nr, r, z);
+    a->live = nullptr;
+    a->timed(PK_KRYLOV, [&] { launch_cg_reduce<R>(c, r, z, a->N, nr, CG_RZ, a->st); });
+    check_launch(a);
+    a->timed(PK_KRYLOV, [&] { launch_cg_dir<R>(c, p, z, a->N, nr, 0, a->st); });
+    check_launch(a);
+    CK(cudaMemcpyAsync(a->h_nact + slot, c.nact, sizeof(int), cudaMemcpyDeviceToHost, a->st));
+  };
+  const bool graphs = a->use_graphs && !a->prof && a->st == a->gs && a->gs != nullptr;
+  if (graphs && a->cg_g_nr != nr) {
+    for (auto g : a->cg_gexec)
+      if (g) cudaGraphExecDestroy(g);
+    a->cg_gexec.assign(RING, nullptr);
+    a->cg_g_nr = nr;
+  }
+  const int lag = 2;
+  int it = 0;
+  for (; it < max_inner; ++it) {
+    const int slot = it % RING;
+    a->h_nact[slot] = -1;
+    if (graphs) {
+      if (!a->cg_gexec[slot]) {
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(a->st, cudaStreamCaptureModeThreadLocal));
+        const long long l0 = a->launches;
+        try {
+          enqueue_iter(slot);
+        } catch (...) {
+          cudaStreamEndCapture(a->st, &g);
+          if (g) cudaGraphDestroy(g);
+          throw;
+        }
+        a->cg_step_launches = a->launches - l0;
+        a->launches = l0;
+        CK(cudaStreamEndCapture(a->st, &g));
+        cudaGraphExec_t ge = nullptr;
+        const cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
+        cudaGraphDestroy(g);
+        CK(ie);
+        a->cg_gexec[slot] = ge;
+      }
+      CK(cudaGraphLaunch(a->cg_gexec[slot], a->st));
+      a->launches += a->cg_step_launches;
+    } else {
+      enqueue_iter(slot);
+    }
+    if (it >= lag) {
+      volatile int *hn = a->h_nact;
+      const int ps = (it - lag) % RING;
+      const auto t0 = std::chrono::steady_clock::now();
+      while (hn[ps] == -1) {
+        if (cudaStreamQuery(a->st) == cudaSuccess && hn[ps] == -1)
+          throw MomaError(MOMA_ERR_CUDA, "poll copy did not arrive");
+        if (std::chrono::steady_clock::now() - t0 > std::chrono::seconds(60))
+          throw MomaError(MOMA_ERR_TIMEOUT, "inner iteration poll timed out");
+        std::this_thread::yield();
+      }
+      if (hn[ps] == 0) break;
+    }
+  }
+  CK(cudaStreamSynchronize(a->st));
+  std::vector<int> its(nr);
+  CK(cudaMemcpy(its.data(), c.iters, nr * sizeof(int), cudaMemcpyDeviceToHost));
+  int mx = 0;
+  for (int k = 0; k < nr; ++k) mx = std::max(mx, its[k]);
+  *inner_iters += mx;
+  if (first_red) {
+    std::vector<double> rr(nr), rr0(nr);
+    CK(cudaMemcpy(rr.data(), c.rr, nr * sizeof(double), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(rr0.data(), c.rr0, nr * sizeof(double), cudaMemcpyDeviceToHost));
+    double m2 = 0;
+    for (int k = 0; k < nr; ++k)
+      if (act[k] && rr0[k] > 0) m2 = std::max(m2, std::sqrt(rr[k] / rr0[k]));
+    *first_red = m2;
+  }
+  a->timed(PK_KRYLOV, [&] { launch_cg_accum<R>(d, a->N, nr, a->Iw.as<double2>(), a->rnorm, a->st); });
+  check_launch(a);
+}
+
 template <typename R>
 void solve_impl(moma_array *a, int nr, const void *Vin, void *Iout, const moma_solve_opts *o, moma_solve_info *info,
                 double *relres) {
@@ -851,7 +1000,10 @@ void solve_impl(moma_array *a, int nr, const void *Vin, void *Iout, const moma_s
     CK(cudaMemcpyAsync(a->mask, mask.data(), nr * sizeof(int), cudaMemcpyHostToDevice, a->st));
     a->timed(PK_MISC, [&] { launch_to_inner<R>(a->rw.as<double2>(), a->lat_in.p, a->N, nr, a->rnorm, a->mask, a->st); });
     check_launch(a);
-    gmres_cycle<R>(a, nr, mask, &inner, outer == 0 ? &first_red : nullptr);
+    if (o && o->solver == MOMA_SOLVER_PCG)
+      pcg_cycle<R>(a, nr, mask, (o->max_inner > 0) ? o->max_inner : 500, &inner, outer == 0 ? &first_red : nullptr);
+    else
+      gmres_cycle<R>(a, nr, mask, &inner, outer == 0 ? &first_red : nullptr);
     sync_and_check(a);
     ++outer;
   }

@@ -51,9 +51,12 @@ class moma_options(ctypes.Structure):
                 ("flags", ctypes.c_int)]
 
 
+MOMA_SOLVER_GMRES, MOMA_SOLVER_PCG = 0, 1
+
+
 class moma_solve_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int),
-                ("warm_start", ctypes.c_int)]
+                ("warm_start", ctypes.c_int), ("solver", ctypes.c_int), ("max_inner", ctypes.c_int)]
 
 
 class moma_solve_info(ctypes.Structure):
@@ -237,14 +240,15 @@ def moma_get_precond_block(h, ex, ey, out):
     _check(lib().moma_get_precond_block(h, ex, ey, p))
 
 
-def moma_solve(h, V, I, tol=0.0, inner_tol=0.0, max_outer=0, warm_start=False, rel_residual=None):
+def moma_solve(h, V, I, tol=0.0, inner_tol=0.0, max_outer=0, warm_start=False, rel_residual=None, solver=0,
+               max_inner=0):
     """Returns the moma_solve_info as a dict; raises MomaError on failure
     (the exception carries .info for MOMA_ERR_NOT_CONVERGED)."""
     pv, dv = _ptr_dtype(V)
     pi, di = _ptr_dtype(I)
     if dv != MOMA_C128 or di != MOMA_C128:
         raise TypeError("V and I are complex128")
-    opts = moma_solve_opts(tol, inner_tol, max_outer, 1 if warm_start else 0)
+    opts = moma_solve_opts(tol, inner_tol, max_outer, 1 if warm_start else 0, solver, max_inner)
     info = moma_solve_info()
     rr = None
     if rel_residual is not None:
@@ -369,7 +373,7 @@ def moma_set_blocks_batch(handles, blocks, release_setup=False, workers=0):
     return list(st)
 
 
-def moma_solve_batch(handles, Vs, Is, tol=0.0, workers=0):
+def moma_solve_batch(handles, Vs, Is, tol=0.0, workers=0, solver=0):
     """Solve many independent problems concurrently; returns the infos."""
     n = len(handles)
     hs = (ctypes.c_void_p * n)(*[h.value for h in handles])
@@ -378,7 +382,7 @@ def moma_solve_batch(handles, Vs, Is, tol=0.0, workers=0):
     ip = (ctypes.c_void_p * n)(*[_ptr_dtype(x)[0] for x in Is])
     infos = (moma_solve_info * n)()
     st = (ctypes.c_int * n)()
-    opts = moma_solve_opts(tol, 0.0, 0, 0)
+    opts = moma_solve_opts(tol, 0.0, 0, 0, solver, 0)
     s = lib().moma_solve_batch(n, hs, nr, vp, ip, ctypes.byref(opts), infos, workers, st)
     if s != MOMA_OK:
         raise MomaError(s, f"batch solve: statuses {list(st)}")

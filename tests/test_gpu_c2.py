@@ -25,13 +25,13 @@ def c2():
     return spec, blocks64, excitation(spec, angles)
 
 
-def _solve(m, spec, blocks64, V, prec):
+def _solve(m, spec, blocks64, V, prec, solver=0):
     h = m.moma_create_array(spec.nx, spec.ny, spec.b, prec)
     try:
         m.moma_set_blocks(h, blocks64)
         I = np.zeros_like(V)
         rr = np.zeros(V.shape[0])
-        info = m.moma_solve(h, V, I, rel_residual=rr)
+        info = m.moma_solve(h, V, I, rel_residual=rr, solver=solver)
         za = np.zeros(V.shape[:3], np.complex128)
         gam = np.zeros_like(za)
         m.moma_active_impedance(h, I, V, za, gam)
@@ -63,3 +63,15 @@ def test_c2_plain_fp64_reaches_tolerance(moma_lib, cuda, c2):
     I, za, gam, info, rr = _solve(moma_lib, spec, blocks64, V, 0)
     print("C2 fp64: info", info)
     assert info["converged"] == 1 and rr.max() <= 1e-10
+
+
+def test_c2_pcg_certified(moma_lib, cuda, c2):
+    """The paper's PCG solver on the full-size problem: residual certified
+    by the oracle's direct offset sum."""
+    spec, blocks64, V = c2
+    I, za, gam, info, rr = _solve(moma_lib, spec, blocks64, V, 1, solver=1)
+    assert info["converged"] == 1 and rr.max() <= 1e-10
+    res = V - mbt.matvec(blocks64.astype(np.complex128), spec.nx, spec.ny, I)
+    cert = np.linalg.norm(res.reshape(2, -1), axis=1) / np.linalg.norm(V.reshape(2, -1), axis=1)
+    print("C2 pcg: info", info, "certified residual", cert)
+    assert cert.max() <= 1e-10

@@ -312,3 +312,28 @@ def test_solves_are_deterministic(moma_lib, cuda):
             m.moma_destroy(h)
     for o in outs[1:]:
         assert np.array_equal(o, outs[0])
+
+
+PCG_CASES = [(1, 1, 3, 0.5), (2, 1, 1, 0.5), (3, 2, 4, 0.3), (4, 4, 32, 0.5), (5, 3, 7, 0.7), (6, 6, 33, 0.4)]
+
+
+@pytest.mark.parametrize("nx,ny,b,d", PCG_CASES)
+@pytest.mark.parametrize("prec", [FP64, MIXED])
+def test_pcg_solve_matches_dense_lu(moma_lib, cuda, nx, ny, b, d, prec):
+    """The paper's PCG form (Sec. II-C): CG on Z^H Z with preconditioner P,
+    inside the same FP64 refinement, reaches the plain solution."""
+    m = moma_lib
+    spec, blocks, h = make(m, nx, ny, b, prec, d=d)
+    try:
+        V = excitation(spec, [(0, 0), (45, 0), (30, 60)])
+        I = np.zeros_like(V)
+        rr = np.zeros(V.shape[0])
+        info = m.moma_solve(h, V, I, rel_residual=rr, solver=m.MOMA_SOLVER_PCG)
+        assert info["converged"] == 1 and rr.max() <= 1e-10
+        za = np.zeros(V.shape[:3], np.complex128)
+        gam = np.zeros_like(za)
+        m.moma_active_impedance(h, I, V, za, gam)
+        _check_solution(spec, blocks, V, I, za, gam)
+        RAW_ERRORS[f"pcg_first_inner_reduction {nx}x{ny}x{b} prec={prec}"] = info["first_inner_reduction"]
+    finally:
+        m.moma_destroy(h)
