@@ -192,6 +192,17 @@ moma_status moma_solve(moma_array *a, int nrhs, const void *V, void *I,
 moma_status moma_active_impedance(moma_array *a, int nrhs, const void *I, const void *V,
                                   int port_basis, double z0, void *Za, void *Gamma);
 
+/* Passive port impedance matrix Z_p (Eq. 18): for every element port j
+ * (basis port_basis), solve Z I = e_j (unit voltage on port j, zero on the
+ * others) with the array's solver, in chunks of `chunk` RHS (0 = 64), and
+ * gather column j of the port admittance Y_p (the port currents); then
+ * Z_p = Y_p^{-1} by FP64 Gauss-Jordan elimination with partial pivoting.
+ * Zp, Yp: c128 [Nel][Nel] row-major (element index e = mx + Nx*my), host or
+ * device; either may be NULL.  Z_p is symmetric for a reciprocal Z.  With
+ * Z_p, Eq. 17 gives Z_a for any port-current excitation. */
+moma_status moma_port_impedance(moma_array *a, int port_basis, int chunk, const moma_solve_opts *opts, void *Zp,
+                                void *Yp);
+
 /* Per-kernel timing over the calls made since moma_profile(a, 1), measured
  * with CUDA events recorded on the array's stream around each launch of a
  * kernel family.  kernel: 0 = c64 bin product, 1 = c128 bin product,

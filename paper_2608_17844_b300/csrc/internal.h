@@ -89,6 +89,13 @@ template <typename R>
 void launch_precond_apply(const void *X, size_t x_stride, int nel, int b, int nr, const void *x, void *y,
                           unsigned *err, const int *live, cudaStream_t st);
 
+// ------------------------------------------------------- port matrix ----
+void launch_unit_ports(double2 *V, int nel, int b, int pb, int j0, int nq, cudaStream_t st);
+void launch_gather_ports(const double2 *I, int nel, int b, int pb, int j0, int nq, double2 *Y, cudaStream_t st);
+// In-place inverse of the n x n row-major complex matrix A (FP64
+// Gauss-Jordan, partial pivoting); perm [n], colk [n] scratch.
+void launch_invert(double2 *A, int n, int *perm, double2 *colk, unsigned *err, cudaStream_t st);
+
 // ------------------------------------------------------------- Krylov ----
 struct ArnoldiCtl;  // device-side control block (krylov.cu)
 }  // namespace moma

@@ -126,6 +126,7 @@ struct moma_array {
   unsigned *err = nullptr;
   DevBuf one_blk;
   DevBuf portsb;  // Z_a and Gamma results [2][nr][nel]
+  DevBuf zp_V, zp_I, zp_Y, zp_tmp;  // port-matrix solves
   // CUDA graphs of the inner Arnoldi steps (one per step index j, for the
   // RHS count g_nr), replayed on an internal capturable stream.
   bool use_graphs = true;
@@ -1041,7 +1042,7 @@ template <typename F> moma_status guarded(F &&f) {
 void destroy_impl(moma_array *a) {
   DevBuf *bufs[] = {&a->tabs, &a->pairs, &a->slot_of, &a->bin_slot, &a->tri, &a->tri_in, &a->Z128, &a->Z64, &a->Xinv, &a->blk, &a->T, &a->S,
                     &a->Lpk, &a->lat_in, &a->lat_tmp, &a->t1, &a->bx, &a->by, &a->Vk, &a->Iw, &a->Vw,
-                    &a->rw, &a->yw, &a->kbuf, &a->errbuf, &a->one_blk, &a->portsb};
+                    &a->rw, &a->yw, &a->kbuf, &a->errbuf, &a->one_blk, &a->portsb, &a->zp_V, &a->zp_I, &a->zp_Y, &a->zp_tmp};
   for (DevBuf *b : bufs) b->release(a->dev_bytes);
   if (a->h_nact) cudaFreeHost(a->h_nact);
   if (a->h_norms) cudaFreeHost(a->h_norms);
@@ -1244,6 +1245,45 @@ moma_status moma_active_impedance(moma_array *a, int nrhs, const void *I, const 
     check_launch(a);
     copy_out(a, Za, za, (size_t)nrhs * a->nel * sizeof(double2));
     if (Gamma) copy_out(a, Gamma, ga, (size_t)nrhs * a->nel * sizeof(double2));
+    sync_and_check(a);
+  });
+}
+
+moma_status moma_port_impedance(moma_array *a, int port_basis, int chunk, const moma_solve_opts *opts, void *Zp,
+                                void *Yp) {
+  if (!a) { g_last_error = "array is NULL"; return MOMA_ERR_ARG; }
+  return guarded([&] {
+    if (!a->have_blocks) throw MomaError(MOMA_ERR_STATE, "set_blocks must precede moma_port_impedance");
+    if (port_basis < 0 || port_basis >= a->b) throw MomaError(MOMA_ERR_ARG, "port_basis out of range");
+    if (!Zp && !Yp) throw MomaError(MOMA_ERR_ARG, "Zp and Yp are both NULL");
+    const int n = a->nel;
+    if (chunk <= 0) chunk = 64;
+    if (chunk > n) chunk = n;
+    const size_t vbytes = (size_t)chunk * a->N * sizeof(double2);
+    a->zp_V.ensure(vbytes, a->dev_bytes);
+    a->zp_I.ensure(vbytes, a->dev_bytes);
+    a->zp_Y.ensure((size_t)n * n * sizeof(double2), a->dev_bytes);
+    a->zp_tmp.ensure((size_t)n * (sizeof(double2) + sizeof(int)) + 256, a->dev_bytes);
+    double2 *Y = a->zp_Y.as<double2>();
+    for (int j0 = 0; j0 < n; j0 += chunk) {
+      const int nq = std::min(chunk, n - j0);
+      launch_unit_ports(a->zp_V.as<double2>(), n, a->b, port_basis, j0, nq, a->st);
+      check_launch(a);
+      CK(cudaMemsetAsync(a->zp_I.p, 0, (size_t)nq * a->N * sizeof(double2), a->st));
+      moma_solve_info info{};
+      const moma_status s = moma_solve(a, nq, a->zp_V.p, a->zp_I.p, opts, &info, nullptr);
+      if (s != MOMA_OK) throw MomaError(s, std::string("port solve: ") + moma_last_error());
+      launch_gather_ports(a->zp_I.as<double2>(), n, a->b, port_basis, j0, nq, Y, a->st);
+      check_launch(a);
+    }
+    if (Yp) copy_out(a, Yp, Y, (size_t)n * n * sizeof(double2));
+    if (Zp) {
+      double2 *colk = a->zp_tmp.as<double2>();
+      int *perm = reinterpret_cast<int *>(a->zp_tmp.as<unsigned char>() + (size_t)n * sizeof(double2));
+      launch_invert(Y, n, perm, colk, a->err, a->st);
+      check_launch(a);
+      copy_out(a, Zp, Y, (size_t)n * n * sizeof(double2));
+    }
     sync_and_check(a);
   });
 }

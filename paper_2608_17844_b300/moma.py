@@ -32,7 +32,7 @@ EXPORTS = [
     "moma_get_precond_block", "moma_solve", "moma_active_impedance", "moma_profile", "moma_kernel_stats",
     "moma_launch_count", "moma_device_bytes", "moma_destroy", "moma_last_error", "moma_matvec_noalloc",
     "moma_set_stream", "moma_release_setup", "moma_estimate_bytes", "moma_tuning_report", "moma_array_stream",
-    "moma_set_blocks_batch", "moma_solve_batch",
+    "moma_set_blocks_batch", "moma_solve_batch", "moma_port_impedance",
     "moma_server_create", "moma_server_submit", "moma_server_wait", "moma_server_get_stats", "moma_server_destroy",
 ]
 
@@ -117,6 +117,7 @@ def lib():
     L.moma_apply_precond.argtypes = [vp, i, vp, vp, i]
     L.moma_matvec_noalloc.argtypes = [vp, i, i, vp, vp, i]
     L.moma_set_stream.argtypes = [vp, vp]
+    L.moma_port_impedance.argtypes = [vp, i, i, ctypes.POINTER(moma_solve_opts), vp, vp]
     L.moma_tuning_report.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
     L.moma_array_stream.argtypes = [vp]
     L.moma_array_stream.restype = vp
@@ -387,3 +388,11 @@ def moma_solve_batch(handles, Vs, Is, tol=0.0, workers=0, solver=0):
     if s != MOMA_OK:
         raise MomaError(s, f"batch solve: statuses {list(st)}")
     return [x.as_dict() for x in infos]
+
+
+def moma_port_impedance(h, Zp=None, Yp=None, port_basis=0, chunk=0, solver=0, tol=0.0):
+    """Passive port impedance matrix (and/or port admittance) [Nel][Nel]."""
+    opts = moma_solve_opts(tol, 0.0, 0, 0, solver, 0)
+    pz = _ptr_dtype(Zp)[0] if Zp is not None else None
+    py = _ptr_dtype(Yp)[0] if Yp is not None else None
+    _check(lib().moma_port_impedance(h, port_basis, chunk, ctypes.byref(opts), pz, py))
