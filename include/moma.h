@@ -74,9 +74,18 @@ typedef enum {
 typedef struct moma_array moma_array; /* opaque; owns all device state */
 
 enum {
-    MOMA_FLAG_NO_GRAPHS = 1,   /* launch the inner steps directly instead of replaying CUDA graphs */
-    MOMA_FLAG_NO_AUTOTUNE = 2  /* use the built-in launch-shape heuristics */
+    MOMA_FLAG_NO_GRAPHS = 1,     /* launch the inner steps directly instead of replaying CUDA graphs */
+    MOMA_FLAG_NO_AUTOTUNE = 2,   /* use the built-in launch-shape heuristics */
+    MOMA_FLAG_NO_TENSOR = 4,     /* c64 bin products on the CUDA cores at every RHS count */
+    MOMA_FLAG_TENSOR_ALWAYS = 8  /* c64 bin products on the tensor cores from one RHS up
+                                    (default: from 16 RHS; MIXED arrays, 128 <= b <= 256, b even) */
 };
+/* The tensor-core bin product (MIXED arrays): every circulant bin's block
+ * Zhat_k (Eq. 3) is kept whole as a pair of TF32 values (hi + lo) and
+ * multiplied with the RHS block by tcgen05 MMAs (3xTF32: hi*hi + hi*lo +
+ * lo*hi, FP32 accumulation), y_k = Zhat_k x_k, or conj(Zhat_{-k}) x_k for
+ * Z^H.  The split bins (4 B*b*b*2 bytes) are built on the first call with
+ * enough RHS after moma_set_blocks and kept until the next one. */
 
 typedef struct {
     int precision; /* moma_precision */
@@ -210,7 +219,7 @@ moma_status moma_port_impedance(moma_array *a, int port_basis, int chunk, const 
  * transform (set-up), 5 = c128 lattice FFT passes, 6 = offset Gram
  * products, 7 = summed-area table, 8 = box sums + Cholesky, 9 = inverse
  * factors, 10 = Arnoldi/Givens/update kernels, 11 = residual and
- * conversion kernels.  Writes the number of
+ * conversion kernels, 12 = tensor-core c64 bin product.  Writes the number of
  * timed launches and their total milliseconds.  moma_profile(a, 0) stops
  * timing; either call resets the counters. */
 moma_status moma_profile(moma_array *a, int enable);

@@ -1,5 +1,6 @@
 // Host-side declarations shared by the translation units of libmoma.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -70,6 +71,30 @@ struct BinProduct {
 };
 template <typename R>
 void launch_bin_product(const BinProduct &p, int num_sms, cudaStream_t st);
+
+// Tensor-core bin product (tcgen05, 3xTF32) for many right-hand sides.
+// Every bin k holds its full block A_k = Zhat_k as split TF32 pairs
+// (hi, lo: [B][b][2b] floats each, interleaved complex rows); the adjoint
+// product reads the partner bin -k and conjugates.
+struct TcBins {
+  bool ready = false;
+  int b = 0, B = 0;
+  float *Ahi = nullptr, *Alo = nullptr;
+  const int *partner = nullptr;  // [B] index of -k
+  CUtensorMap map_hi{}, map_lo{};
+};
+struct TcProduct {
+  const void *x = nullptr;  // bins [B][nr][b] c64
+  void *y = nullptr;        // bins [B][nr][b] c64
+  int nr = 0, herm = 0;
+  unsigned *err = nullptr;
+  const int *live = nullptr;
+};
+bool tc_supported(int b);
+size_t tc_bytes(int B, int b);
+void tc_build(TcBins &tc, const void *Z64, int b, int ldb, const int2 *bin_slot, const int *partner, int B,
+              float *Ahi, float *Alo, cudaStream_t st);
+void launch_tc_product(const TcBins &tc, const TcProduct &P, int num_sms, cudaStream_t st);
 
 // ------------------------------------------------------ preconditioner ----
 // G_D = Z_D^H Z_D for every offset, output FP64 [nD][b][b].

@@ -84,7 +84,7 @@ __global__ void nonfinite_kernel(const void *p, size_t n_real, int is_double, un
 
 enum {
   PK_BIN64 = 0, PK_BIN128 = 1, PK_PREC = 2, PK_FFT64 = 3, PK_BLOCKFFT = 4, PK_FFT128 = 5,
-  PK_GRAM = 6, PK_SAT = 7, PK_CHOL = 8, PK_TRINV = 9, PK_KRYLOV = 10, PK_MISC = 11, PK_N = 12
+  PK_GRAM = 6, PK_SAT = 7, PK_CHOL = 8, PK_TRINV = 9, PK_KRYLOV = 10, PK_MISC = 11, PK_BINTC = 12, PK_N = 13
 };
 
 }  // namespace
@@ -104,6 +104,12 @@ struct moma_array {
   DevBuf bin_slot, tri, tri_in;  // symmetric block-transform tables
   DevBuf Z128, Z64;  // pair storage [Bp][b][ldb]
   DevBuf Xinv;       // inverse factors, packed row-major, inner precision
+  // Tensor-core bin product (inner precision c64, many RHS): split full
+  // bins and the partner table; built on first use after set_blocks.
+  DevBuf tcA, partner;
+  TcBins tc;
+  bool no_tensor = false;
+  int tc_min_nr = 16;
   size_t x_stride = 0;
   bool have_blocks = false;
 
@@ -249,6 +255,12 @@ void build_tables(moma_array *a) {
       }
     }
   a->Bp = (int)pr.size();
+  std::vector<int> part(a->B);
+  for (int ky = 0; ky < a->My; ++ky)
+    for (int kx = 0; kx < a->Mx; ++kx)
+      part[ky * a->Mx + kx] = ((a->My - ky) % a->My) * a->Mx + ((a->Mx - kx) % a->Mx);
+  a->partner.ensure(part.size() * sizeof(int), a->dev_bytes);
+  CK(cudaMemcpy(a->partner.p, part.data(), part.size() * sizeof(int), cudaMemcpyHostToDevice));
   a->pairs.ensure(pr.size() * sizeof(int2), a->dev_bytes);
   a->slot_of.ensure(slot.size() * sizeof(int), a->dev_bytes);
   CK(cudaMemcpy(a->pairs.p, pr.data(), pr.size() * sizeof(int2), cudaMemcpyHostToDevice));
@@ -349,6 +361,13 @@ void axis(moma_array *a, AxisPass p, const FftTables &t) {
 
 template <typename R>
 void binprod(moma_array *a, int nr, const void *x, void *y, int herm) {
+  if (!is64<R>() && a->tc.ready && nr >= a->tc_min_nr) {
+    TcProduct T;
+    T.x = x; T.y = y; T.nr = nr; T.herm = herm; T.err = a->err; T.live = a->live;
+    a->timed(PK_BINTC, [&] { launch_tc_product(a->tc, T, a->num_sms, a->st); });
+    check_launch(a);
+    return;
+  }
   BinProduct P;
   P.Z = is64<R>() ? a->Z128.p : a->Z64.p;
   P.pairs = a->pairs.as<int2>();
@@ -528,6 +547,25 @@ void ensure_ws(moma_array *a, int nr) {
 
 // Stage a caller buffer on the device: returns a device pointer (the
 // caller's own if it is device memory, else `tmp` after a copy).
+// Split full bins for the tensor-core product, once per set_blocks, when a
+// call brings enough right-hand sides to use it.
+void ensure_tc(moma_array *a, int nr) {
+  if (a->tc.ready || a->no_tensor || a->prec != MOMA_PREC_MIXED || nr < a->tc_min_nr || !tc_supported(a->b)) return;
+  drop_graphs(a);
+  const size_t half = tc_bytes(a->B, a->b) / 2;
+  a->tcA.ensure(2 * half, a->dev_bytes);
+  float *hi = a->tcA.as<float>();
+  float *lo = reinterpret_cast<float *>(a->tcA.as<unsigned char>() + half);
+  try {
+    a->timed(PK_BLOCKFFT, [&] {
+      tc_build(a->tc, a->Z64.p, a->b, a->ldb, a->bin_slot.as<int2>(), a->partner.as<int>(), a->B, hi, lo, a->st);
+    });
+  } catch (const std::runtime_error &e) {
+    throw MomaError(MOMA_ERR_CUDA, e.what());
+  }
+  check_launch(a);
+}
+
 const void *stage_in(moma_array *a, const void *src, size_t bytes, DevBuf &tmp) {
   if (is_device_ptr(src)) return src;
   tmp.ensure(bytes, a->dev_bytes);
@@ -567,6 +605,7 @@ void set_blocks_impl(moma_array *a, const void *blocks, int dtype) {
   const size_t esz = dtype == MOMA_C128 ? sizeof(double2) : sizeof(float2);
   const void *blk = stage_in(a, blocks, (size_t)nD * bb * esz, a->blk);
   a->have_blocks = false;
+  a->tc.ready = false;
   check_finite(a, blk, (size_t)nD * bb * 2, dtype == MOMA_C128);
   sync_and_check(a);
 
@@ -1086,6 +1125,8 @@ moma_status moma_create_array(int nx, int ny, int b, const moma_options *opt, vo
     a->m = (opt && opt->restart > 0) ? opt->restart : 50;
     a->use_graphs = !(opt && (opt->flags & MOMA_FLAG_NO_GRAPHS));
     a->no_autotune = opt && (opt->flags & MOMA_FLAG_NO_AUTOTUNE);
+    a->no_tensor = opt && (opt->flags & MOMA_FLAG_NO_TENSOR);
+    if (opt && (opt->flags & MOMA_FLAG_TENSOR_ALWAYS)) a->tc_min_nr = 1;
     if (a->m > MOMA_MAX_RESTART) throw MomaError(MOMA_ERR_ARG, "restart too large");
     const int mx = (opt && opt->mx > 0) ? opt->mx : next_smooth(2 * nx - 1);
     const int my = (opt && opt->my > 0) ? opt->my : next_smooth(2 * ny - 1);
@@ -1132,6 +1173,7 @@ moma_status moma_matvec(moma_array *a, int op, int nrhs, const void *x, void *y,
       throw MomaError(MOMA_ERR_ARG, "the normal operator runs in the array's inner precision");
     if (nrhs == 0) return;
     ensure_ws(a, nrhs);
+    ensure_tc(a, nrhs);
     const size_t bytes = (size_t)nrhs * a->N * (d64 ? sizeof(double2) : sizeof(float2));
     CK(cudaMemcpyAsync(a->Vw.p, x, bytes, cudaMemcpyDefault, a->st));
     if (d64) {
@@ -1156,6 +1198,7 @@ moma_status moma_apply_precond(moma_array *a, int nrhs, const void *x, void *y, 
     if (nrhs < 0 || (nrhs > 0 && (!x || !y))) throw MomaError(MOMA_ERR_ARG, "bad nrhs or NULL buffer");
     if (nrhs == 0) return;
     ensure_ws(a, nrhs);
+    ensure_tc(a, nrhs);
     const size_t bytes = (size_t)nrhs * a->N * (d64 ? sizeof(double2) : sizeof(float2));
     CK(cudaMemcpyAsync(a->Vw.p, x, bytes, cudaMemcpyDefault, a->st));
     if (d64) precond<double>(a, nrhs, a->Vw.p, a->yw.p);
@@ -1222,6 +1265,7 @@ moma_status moma_solve(moma_array *a, int nrhs, const void *V, void *I, const mo
       return;
     }
     ensure_ws(a, nrhs);
+    ensure_tc(a, nrhs);
     if (a->prec == MOMA_PREC_FP64) solve_impl<double>(a, nrhs, V, I, opts, info, rel_residual);
     else solve_impl<float>(a, nrhs, V, I, opts, info, rel_residual);
   });

@@ -1,0 +1,120 @@
+"""GPU parity of the tensor-core (tcgen05, 3xTF32) bin product against the
+oracle: Z x and Z^H x through the whole lattice-FFT path with the tensor
+path forced (several RHS tile widths, ragged RHS tails, b not a multiple of
+the 128-row MMA tile or of the 16-value K chunk), the normal operator, and
+full solves that take the tensor path by default (>= 16 RHS).
+
+Tolerance: the c64 products must stay within FP32-level error of the FP64
+oracle (3xTF32 keeps ~22 significant bits per operand): <= 2e-5 relative;
+the raw errors are printed.  Solves must still meet the 1e-10 residual and
+the 1e-8 active-impedance bars.
+"""
+import numpy as np
+import pytest
+
+from synth import LatticeSpec, offset_blocks, excitation
+from oracle import dense, mbt, ports
+
+pytestmark = pytest.mark.gpu
+
+MIXED = 1
+
+
+def relerr(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def rand_vec(nr, spec, seed=1):
+    rng = np.random.default_rng(seed)
+    v = rng.standard_normal((nr, spec.ny, spec.nx, spec.b)) + 1j * rng.standard_normal((nr, spec.ny, spec.nx, spec.b))
+    return v.astype(np.complex64)
+
+
+@pytest.mark.parametrize("nx,ny,b,nr", [
+    (3, 2, 128, 20),   # 32-wide RHS tile, ragged
+    (2, 2, 136, 5),    # 8-wide tile, b past one M tile, partial K chunk
+    (4, 3, 160, 40),   # 64-wide tile, two M tiles
+    (2, 3, 144, 70),   # two 64-wide RHS tiles
+    (1, 1, 128, 16),   # single element, 16-wide tile
+])
+def test_tensor_products_match_oracle(moma_lib, cuda, nx, ny, b, nr):
+    m = moma_lib
+    spec = LatticeSpec(nx, ny, b, 0.5, 2)
+    blocks = offset_blocks(spec, np.complex64)
+    b128 = blocks.astype(np.complex128)
+    x = rand_vec(nr, spec)
+    ref_z = mbt.matvec(b128, nx, ny, x.astype(np.complex128))
+    ref_h = mbt.matvec_h(b128, nx, ny, x.astype(np.complex128))
+    out = {}
+    for name, flags in (("tensor", m.MOMA_FLAG_TENSOR_ALWAYS), ("cuda", m.MOMA_FLAG_NO_TENSOR)):
+        h = m.moma_create_array(nx, ny, b, MIXED, flags=flags)
+        try:
+            m.moma_set_blocks(h, blocks)
+            m.moma_profile(h, 1)
+            yz = np.zeros_like(x)
+            yh = np.zeros_like(x)
+            m.moma_matvec(h, m.MOMA_OP_Z, x, yz)
+            m.moma_matvec(h, m.MOMA_OP_ZH, x, yh)
+            n_tc = m.moma_kernel_stats(h, "bin_tc")[0]
+            m.moma_profile(h, 0)
+        finally:
+            m.moma_destroy(h)
+        out[name] = (yz, yh, n_tc)
+    yz, yh, n_tc = out["tensor"]
+    assert n_tc == 2 and out["cuda"][2] == 0
+    ez, eh = relerr(yz, ref_z), relerr(yh, ref_h)
+    cz, ch = relerr(out["cuda"][0], ref_z), relerr(out["cuda"][1], ref_h)
+    print(f"tensor {nx}x{ny}x{b} nr={nr}: Z err {ez:.3g} (cuda cores {cz:.3g}), Z^H err {eh:.3g} (cuda cores {ch:.3g})")
+    assert ez <= 2e-5 and eh <= 2e-5
+    # Element-wise: every output entry, not only the norm.
+    scale = np.abs(ref_z).max()
+    assert np.abs(yz - ref_z).max() <= 1e-4 * scale
+
+
+def test_tensor_normal_operator(moma_lib, cuda):
+    m = moma_lib
+    spec = LatticeSpec(3, 3, 128, 0.5, 4)
+    blocks = offset_blocks(spec, np.complex64)
+    x = rand_vec(24, spec, seed=5)
+    ys = []
+    for flags in (m.MOMA_FLAG_TENSOR_ALWAYS, m.MOMA_FLAG_NO_TENSOR):
+        h = m.moma_create_array(3, 3, 128, MIXED, flags=flags)
+        try:
+            m.moma_set_blocks(h, blocks)
+            y = np.zeros_like(x)
+            m.moma_matvec(h, m.MOMA_OP_NORMAL, x, y)
+            ys.append(y)
+        finally:
+            m.moma_destroy(h)
+    e = relerr(ys[0], ys[1])
+    print("normal operator tensor vs cuda cores:", e)
+    assert e <= 5e-5
+
+
+def test_solve_takes_tensor_path_and_matches_dense(moma_lib, cuda):
+    m = moma_lib
+    spec = LatticeSpec(4, 3, 128, 0.5, 1)
+    blocks = offset_blocks(spec, np.complex64)
+    b128 = blocks.astype(np.complex128)
+    angles = [(th, ph) for th in (0.0, 20.0, 40.0, 60.0) for ph in (0.0, 30.0, 60.0, 90.0)]
+    V = excitation(spec, angles)
+    h = m.moma_create_array(spec.nx, spec.ny, spec.b, MIXED)
+    try:
+        m.moma_set_blocks(h, blocks)
+        m.moma_profile(h, 1)
+        I = np.zeros_like(V)
+        rr = np.zeros(len(angles))
+        info = m.moma_solve(h, V, I, rel_residual=rr)
+        n_tc = m.moma_kernel_stats(h, "bin_tc")[0]
+        m.moma_profile(h, 0)
+        za = np.zeros(V.shape[:3], np.complex128)
+        m.moma_active_impedance(h, I, V, za)
+    finally:
+        m.moma_destroy(h)
+    print("tensor-path solve:", info, "bin_tc launches", n_tc)
+    assert n_tc > 0
+    assert info["converged"] == 1 and rr.max() <= 1e-10
+    z = dense.assemble(b128, spec.nx, spec.ny)
+    i_ref = dense.solve(z, V)
+    za_ref = ports.active_impedance(i_ref, V)
+    assert relerr(za, za_ref) <= 1e-8
