@@ -80,12 +80,14 @@ enum {
     MOMA_FLAG_TENSOR_ALWAYS = 8  /* c64 bin products on the tensor cores from one RHS up
                                     (default: from 16 RHS; MIXED arrays, 128 <= b <= 256, b even) */
 };
-/* The tensor-core bin product (MIXED arrays): every circulant bin's block
+/* The tensor-core products (MIXED arrays): every circulant bin's block
  * Zhat_k (Eq. 3) is kept whole as a pair of TF32 values (hi + lo) and
  * multiplied with the RHS block by tcgen05 MMAs (3xTF32: hi*hi + hi*lo +
  * lo*hi, FP32 accumulation), y_k = Zhat_k x_k, or conj(Zhat_{-k}) x_k for
- * Z^H.  The split bins (4 B*b*b*2 bytes) are built on the first call with
- * enough RHS after moma_set_blocks and kept until the next one. */
+ * Z^H; the block preconditioner is applied the same way as X_e^H (X_e x_e)
+ * with X_e = L_e^{-1} kept whole.  The split matrices (16 b^2 (B + 2 Nel)
+ * bytes) are built on the first call with enough RHS after moma_set_blocks
+ * and kept until the next one. */
 
 typedef struct {
     int precision; /* moma_precision */
@@ -125,7 +127,7 @@ typedef struct {
  * cuda_stream: a cudaStream_t (NULL = legacy default stream).
  * Allocates the device store for the transformed bins (c128, plus c64 in
  * MIXED mode), the factored preconditioner and the workspaces.
- * Errors: MOMA_ERR_ARG (nx, ny, b < 1, bad options), MOMA_ERR_OOM. */
+ * Errors: MOMA_ERR_ARG (nx, ny, b < 1, b > 256, bad options), MOMA_ERR_OOM. */
 moma_status moma_create_array(int nx, int ny, int b, const moma_options *opt,
                               void *cuda_stream, moma_array **out);
 
@@ -219,7 +221,8 @@ moma_status moma_port_impedance(moma_array *a, int port_basis, int chunk, const 
  * transform (set-up), 5 = c128 lattice FFT passes, 6 = offset Gram
  * products, 7 = summed-area table, 8 = box sums + Cholesky, 9 = inverse
  * factors, 10 = Arnoldi/Givens/update kernels, 11 = residual and
- * conversion kernels, 12 = tensor-core c64 bin product.  Writes the number of
+ * conversion kernels, 12 = tensor-core c64 bin product, 13 = tensor-core
+ * preconditioner apply.  Writes the number of
  * timed launches and their total milliseconds.  moma_profile(a, 0) stops
  * timing; either call resets the counters. */
 moma_status moma_profile(moma_array *a, int enable);

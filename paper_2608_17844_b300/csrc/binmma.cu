@@ -16,8 +16,13 @@
 // exact TF32 values; the accumulator receives hi*hi + hi*lo + lo*hi in FP32
 // (tcgen05.mma kind::tf32, FP32 accumulate), which keeps the product close
 // to FP32 accuracy (relative error ~1e-6 instead of TF32's ~1e-3).  The
-// A splits are made once per array (tc_split_kernel); B' is built and split
-// in shared memory per K chunk.
+// A splits are made once per array (tc_split_*_kernel); B' is built and
+// split in shared memory per K chunk.
+//
+// The same kernel applies the block preconditioner for many RHS: the
+// items are then the lattice elements, A = X_e = L_e^{-1} and A = X_e^H
+// (each kept whole, zeros included), and the two products run back to
+// back (y = X^H (X x)).
 //
 // Kernel layout (persistent, one CTA per SM):
 //   warp 0     TMA producer: A_hi / A_lo K-chunks (128 rows x 128 B, 128B
@@ -382,7 +387,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // A_hi / A_lo of every bin from the pair storage: bin k reads its stored
 // block directly (mode 0, 2) or transposed (mode 1).  Output row i of bin k
 // is interleaved complex (2b floats) in both arrays.
-__global__ void tc_split_kernel(const float2 *Z, int b, int ldb, const int2 *bin_slot, int B, float *Ahi, float *Alo) {
+MOMA_DEV void put_split(float *hi, float *lo, size_t o, float2 v) {
+  float2 h, l;
+  h.x = tf32_hi(v.x);
+  h.y = tf32_hi(v.y);
+  l.x = tf32_trunc(v.x - h.x);
+  l.y = tf32_trunc(v.y - h.y);
+  reinterpret_cast<float2 *>(hi)[o] = h;
+  reinterpret_cast<float2 *>(lo)[o] = l;
+}
+
+__global__ void tc_split_bins_kernel(const float2 *Z, int b, int ldb, const int2 *bin_slot, float *Ahi, float *Alo) {
   __shared__ float2 tile[32][33];
   const int k = blockIdx.z;
   const int2 bs = bin_slot[k];
@@ -401,14 +416,40 @@ __global__ void tc_split_kernel(const float2 *Z, int b, int ldb, const int2 *bin
     const int i = i0 + r, j = j0 + tx;
     if (i >= b || j >= b) continue;
     const float2 v = bs.y == 1 ? tile[tx][r] : Zs[(size_t)i * ldb + j];
-    float2 hi, lo;
-    hi.x = tf32_hi(v.x);
-    hi.y = tf32_hi(v.y);
-    lo.x = tf32_trunc(v.x - hi.x);
-    lo.y = tf32_trunc(v.y - hi.y);
-    const size_t o = ((size_t)k * b + i) * b + j;
-    reinterpret_cast<float2 *>(Ahi)[o] = hi;
-    reinterpret_cast<float2 *>(Alo)[o] = lo;
+    put_split(Ahi, Alo, ((size_t)k * b + i) * b + j, v);
+  }
+}
+
+// Full X_e = L_e^{-1} (zero above the diagonal) from the packed column-major
+// inverse factor: X(i, k) sits at colbase(k) - k + i for i >= k.  Tiles of
+// 32 x 32 are staged so that the packed columns are read contiguously.
+__global__ void tc_split_x_kernel(const float2 *X, size_t x_stride, int b, float *hi, float *lo) {
+  __shared__ float2 tile[32][33];
+  const int e = blockIdx.z;
+  const float2 *Xe = X + (size_t)e * x_stride;
+  const int i0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int r = ty; r < 32; r += 8) {
+    const int k = k0 + r, i = i0 + tx;  // tile[r][tx] = X(i, k)
+    float2 v = make_float2(0.f, 0.f);
+    if (i < b && k < b && i >= k) v = Xe[(size_t)k * b - (size_t)k * (k - 1) / 2 + (i - k)];
+    tile[r][tx] = v;
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int i = i0 + r, k = k0 + tx;
+    if (i < b && k < b) put_split(hi, lo, ((size_t)e * b + i) * b + k, tile[tx][r]);
+  }
+}
+// Full X_e^H: X^H(i, k) = conj(X(k, i)), nonzero for k >= i; row i of X^H
+// is column i of X, contiguous in the packed layout.
+__global__ void tc_split_xh_kernel(const float2 *X, size_t x_stride, int b, float *hi, float *lo) {
+  const int e = blockIdx.y, i = blockIdx.x;
+  const float2 *col = X + (size_t)e * x_stride + (size_t)i * b - (size_t)i * (i - 1) / 2 - i;  // col[k] = X(k, i)
+  for (int k = threadIdx.x; k < b; k += blockDim.x) {
+    float2 v = make_float2(0.f, 0.f);
+    if (k >= i) v = make_float2(col[k].x, -col[k].y);
+    put_split(hi, lo, ((size_t)e * b + i) * b + k, v);
   }
 }
 
@@ -425,6 +466,26 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
+// Tensor maps over hi / lo viewed as [T][b][2b] floats; boxes of 128 rows x
+// 32 floats (128 B, 128-byte swizzle).  Rows past b read as zeros.
+void encode_maps(TcMats &m) {
+  auto fn = encode_fn();
+  if (!fn) throw std::runtime_error("cuTensorMapEncodeTiled is not available");
+  const int b = m.b;
+  const cuuint64_t dims[3] = {(cuuint64_t)(2 * b), (cuuint64_t)b, (cuuint64_t)m.T};
+  const cuuint64_t strides[2] = {(cuuint64_t)(2 * b) * sizeof(float), (cuuint64_t)(2 * b) * b * sizeof(float)};
+  const cuuint32_t box[3] = {TC_KC, TC_M, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  float *bases[2] = {m.hi, m.lo};
+  CUtensorMap *maps[2] = {&m.map_hi, &m.map_lo};
+  for (int h = 0; h < 2; ++h) {
+    const CUresult r = fn(maps[h], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, bases[h], dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) throw std::runtime_error("cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+  }
+}
+
 template <int NRT>
 size_t smem_bytes(int nmt, int NS) {
   const size_t stage = (size_t)nmt * 2 * TC_ATILE + 2 * (size_t)(2 * NRT) * 128;
@@ -432,14 +493,14 @@ size_t smem_bytes(int nmt, int NS) {
 }
 
 template <int NRT>
-void launch_nrt(const TcBins &tc, const TcProduct &P, int num_sms, cudaStream_t st) {
-  const int b = tc.b;
+void launch_nrt(const TcMats &m, const TcProduct &P, int num_sms, cudaStream_t st) {
+  const int b = m.b;
   MmaArgs a{};
   a.x = static_cast<const float2 *>(P.x);
   a.y = static_cast<float2 *>(P.y);
-  a.x_ts = (long long)P.nr * b; a.x_rs = b; a.y_ts = (long long)P.nr * b; a.y_rs = b;
-  a.amap = P.herm ? tc.partner : nullptr;
-  a.T = tc.B; a.b = b; a.nr = P.nr; a.conj = P.herm;
+  a.x_ts = P.x_ts; a.x_rs = P.x_rs; a.y_ts = P.y_ts; a.y_rs = P.y_rs;
+  a.amap = P.amap;
+  a.T = m.T; a.b = b; a.nr = P.nr; a.conj = P.conj;
   a.nmt = (b + TC_M - 1) / TC_M;
   a.nkc = (2 * b + TC_KC - 1) / TC_KC;
   a.nrtiles = (P.nr + NRT - 1) / NRT;
@@ -464,46 +525,36 @@ void launch_nrt(const TcBins &tc, const TcProduct &P, int num_sms, cudaStream_t 
   }
   const int units = a.T * a.nrtiles;
   const int grid = std::min(units, num_sms);
-  kern<<<grid, TC_THREADS, smem, st>>>(tc.map_hi, tc.map_lo, a);
+  kern<<<grid, TC_THREADS, smem, st>>>(m.map_hi, m.map_lo, a);
 }
 
 }  // namespace
 
 bool tc_supported(int b) { return b >= 128 && b <= 256 && b % 2 == 0; }
 
-size_t tc_bytes(int B, int b) { return 2 * (size_t)B * b * 2 * b * sizeof(float); }
+size_t tc_bytes(int T, int b) { return 2 * (size_t)T * b * 2 * b * sizeof(float); }
 
-void tc_build(TcBins &tc, const void *Z64, int b, int ldb, const int2 *bin_slot, const int *partner, int B,
-              float *Ahi, float *Alo, cudaStream_t st) {
-  tc.b = b;
-  tc.B = B;
-  tc.Ahi = Ahi;
-  tc.Alo = Alo;
-  tc.partner = partner;
-  dim3 grid((b + 31) / 32, (b + 31) / 32, B), block(32, 8);
-  tc_split_kernel<<<grid, block, 0, st>>>(static_cast<const float2 *>(Z64), b, ldb, bin_slot, B, Ahi, Alo);
-  auto fn = encode_fn();
-  if (!fn) throw std::runtime_error("cuTensorMapEncodeTiled is not available");
-  const cuuint64_t dims[3] = {(cuuint64_t)(2 * b), (cuuint64_t)b, (cuuint64_t)B};
-  const cuuint64_t strides[2] = {(cuuint64_t)(2 * b) * sizeof(float), (cuuint64_t)(2 * b) * b * sizeof(float)};
-  const cuuint32_t box[3] = {TC_KC, TC_M, 1};
-  const cuuint32_t estr[3] = {1, 1, 1};
-  float *bases[2] = {Ahi, Alo};
-  CUtensorMap *maps[2] = {&tc.map_hi, &tc.map_lo};
-  for (int h = 0; h < 2; ++h) {
-    const CUresult r = fn(maps[h], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, bases[h], dims, strides, box, estr,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) throw std::runtime_error("cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
-  }
-  tc.ready = true;
+void tc_split_bins(TcMats &m, const void *Z64, int ldb, const int2 *bin_slot, cudaStream_t st) {
+  const int b = m.b;
+  dim3 grid((b + 31) / 32, (b + 31) / 32, m.T), block(32, 8);
+  tc_split_bins_kernel<<<grid, block, 0, st>>>(static_cast<const float2 *>(Z64), b, ldb, bin_slot, m.hi, m.lo);
+  encode_maps(m);
 }
 
-void launch_tc_product(const TcBins &tc, const TcProduct &P, int num_sms, cudaStream_t st) {
-  if (P.nr > 32) launch_nrt<64>(tc, P, num_sms, st);
-  else if (P.nr > 16) launch_nrt<32>(tc, P, num_sms, st);
-  else if (P.nr > 8) launch_nrt<16>(tc, P, num_sms, st);
-  else launch_nrt<8>(tc, P, num_sms, st);
+void tc_split_factor(TcMats &X, TcMats &XH, const void *Xpk, size_t x_stride, cudaStream_t st) {
+  const int b = X.b;
+  dim3 grid((b + 31) / 32, (b + 31) / 32, X.T), block(32, 8);
+  tc_split_x_kernel<<<grid, block, 0, st>>>(static_cast<const float2 *>(Xpk), x_stride, b, X.hi, X.lo);
+  tc_split_xh_kernel<<<dim3(b, XH.T), 128, 0, st>>>(static_cast<const float2 *>(Xpk), x_stride, b, XH.hi, XH.lo);
+  encode_maps(X);
+  encode_maps(XH);
+}
+
+void launch_tc_product(const TcMats &m, const TcProduct &P, int num_sms, cudaStream_t st) {
+  if (P.nr > 32) launch_nrt<64>(m, P, num_sms, st);
+  else if (P.nr > 16) launch_nrt<32>(m, P, num_sms, st);
+  else if (P.nr > 8) launch_nrt<16>(m, P, num_sms, st);
+  else launch_nrt<8>(m, P, num_sms, st);
 }
 
 }  // namespace moma

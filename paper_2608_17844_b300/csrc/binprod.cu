@@ -350,8 +350,9 @@ static void launch_one(const BinProduct &P, int num_sms, cudaStream_t st, int q0
       NS = P.NS;
     }
   }
-  const int ntile = (P.b + TR - 1) / TR;
   while (NS > 2 && smem_for(NS, TR) > 220 * 1024) --NS;
+  while (TR > 4 && smem_for(NS, TR) > 220 * 1024) TR -= 4;  // wide blocks (b > 160)
+  const int ntile = (P.b + TR - 1) / TR;
   const size_t smem = smem_for(NS, TR);
   auto kern = bin_pair_kernel<R, NR, U2, HERM>;
   static int configured = 0;

@@ -72,29 +72,32 @@ struct BinProduct {
 template <typename R>
 void launch_bin_product(const BinProduct &p, int num_sms, cudaStream_t st);
 
-// Tensor-core bin product (tcgen05, 3xTF32) for many right-hand sides.
-// Every bin k holds its full block A_k = Zhat_k as split TF32 pairs
-// (hi, lo: [B][b][2b] floats each, interleaved complex rows); the adjoint
-// product reads the partner bin -k and conjugates.
-struct TcBins {
-  bool ready = false;
-  int b = 0, B = 0;
-  float *Ahi = nullptr, *Alo = nullptr;
-  const int *partner = nullptr;  // [B] index of -k
+// Tensor-core products (tcgen05, 3xTF32) for many right-hand sides.  A
+// TcMats holds T complex b x b matrices, each split into exact TF32 pairs
+// (hi, lo: [T][b][2b] floats, interleaved complex rows), with TMA maps.
+struct TcMats {
+  int b = 0, T = 0;
+  float *hi = nullptr, *lo = nullptr;
   CUtensorMap map_hi{}, map_lo{};
 };
+// y_t[j] = op(A_{amap(t)}) x_t[j] for items t < T, RHS j < nr; op = conj
+// if conj.  x_t[j][k] at x + t*x_ts + j*x_rs + k (complex64), same for y.
 struct TcProduct {
-  const void *x = nullptr;  // bins [B][nr][b] c64
-  void *y = nullptr;        // bins [B][nr][b] c64
-  int nr = 0, herm = 0;
+  const void *x = nullptr;
+  void *y = nullptr;
+  long long x_ts = 0, x_rs = 0, y_ts = 0, y_rs = 0;
+  int nr = 0, conj = 0;
+  const int *amap = nullptr;  // nullptr = identity
   unsigned *err = nullptr;
   const int *live = nullptr;
 };
 bool tc_supported(int b);
-size_t tc_bytes(int B, int b);
-void tc_build(TcBins &tc, const void *Z64, int b, int ldb, const int2 *bin_slot, const int *partner, int B,
-              float *Ahi, float *Alo, cudaStream_t st);
-void launch_tc_product(const TcBins &tc, const TcProduct &P, int num_sms, cudaStream_t st);
+size_t tc_bytes(int T, int b);  // hi + lo
+// Every bin's full block from the pair storage (transposed for the partner).
+void tc_split_bins(TcMats &m, const void *Z64, int ldb, const int2 *bin_slot, cudaStream_t st);
+// X_e and X_e^H from the packed inverse factors (c64).
+void tc_split_factor(TcMats &X, TcMats &XH, const void *Xpk, size_t x_stride, cudaStream_t st);
+void launch_tc_product(const TcMats &m, const TcProduct &P, int num_sms, cudaStream_t st);
 
 // ------------------------------------------------------ preconditioner ----
 // G_D = Z_D^H Z_D for every offset, output FP64 [nD][b][b].

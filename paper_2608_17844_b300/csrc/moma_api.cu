@@ -84,7 +84,7 @@ __global__ void nonfinite_kernel(const void *p, size_t n_real, int is_double, un
 
 enum {
   PK_BIN64 = 0, PK_BIN128 = 1, PK_PREC = 2, PK_FFT64 = 3, PK_BLOCKFFT = 4, PK_FFT128 = 5,
-  PK_GRAM = 6, PK_SAT = 7, PK_CHOL = 8, PK_TRINV = 9, PK_KRYLOV = 10, PK_MISC = 11, PK_BINTC = 12, PK_N = 13
+  PK_GRAM = 6, PK_SAT = 7, PK_CHOL = 8, PK_TRINV = 9, PK_KRYLOV = 10, PK_MISC = 11, PK_BINTC = 12, PK_PRECTC = 13, PK_N = 14
 };
 
 }  // namespace
@@ -104,10 +104,12 @@ struct moma_array {
   DevBuf bin_slot, tri, tri_in;  // symmetric block-transform tables
   DevBuf Z128, Z64;  // pair storage [Bp][b][ldb]
   DevBuf Xinv;       // inverse factors, packed row-major, inner precision
-  // Tensor-core bin product (inner precision c64, many RHS): split full
-  // bins and the partner table; built on first use after set_blocks.
-  DevBuf tcA, partner;
-  TcBins tc;
+  // Tensor-core products (inner precision c64, many RHS): split full bins,
+  // the partner table, split X_e and X_e^H; built on first use after
+  // set_blocks.
+  DevBuf tcA, tcP, partner;
+  TcMats tcZ, tcX, tcXH;
+  bool tc_ready = false;
   bool no_tensor = false;
   int tc_min_nr = 16;
   size_t x_stride = 0;
@@ -361,10 +363,13 @@ void axis(moma_array *a, AxisPass p, const FftTables &t) {
 
 template <typename R>
 void binprod(moma_array *a, int nr, const void *x, void *y, int herm) {
-  if (!is64<R>() && a->tc.ready && nr >= a->tc_min_nr) {
+  if (!is64<R>() && a->tc_ready && nr >= a->tc_min_nr) {
+    // Bins [B][nr][b]; Z^H reads the partner bin, conjugated (Eq. 6).
     TcProduct T;
-    T.x = x; T.y = y; T.nr = nr; T.herm = herm; T.err = a->err; T.live = a->live;
-    a->timed(PK_BINTC, [&] { launch_tc_product(a->tc, T, a->num_sms, a->st); });
+    T.x = x; T.y = y; T.nr = nr; T.conj = herm; T.amap = herm ? a->partner.as<int>() : nullptr;
+    T.x_ts = T.y_ts = (long long)nr * a->b; T.x_rs = T.y_rs = a->b;
+    T.err = a->err; T.live = a->live;
+    a->timed(PK_BINTC, [&] { launch_tc_product(a->tcZ, T, a->num_sms, a->st); });
     check_launch(a);
     return;
   }
@@ -381,6 +386,20 @@ void binprod(moma_array *a, int nr, const void *x, void *y, int herm) {
 
 template <typename R>
 void precond(moma_array *a, int nr, const void *x, void *y) {
+  if (!is64<R>() && a->tc_ready && nr >= a->tc_min_nr) {
+    // Lattice vectors [nr][nel][b]: item e, RHS j at (j*nel + e)*b.  t = X x
+    // goes to the FFT scratch (free here), then y = X^H t.
+    TcProduct T;
+    T.nr = nr; T.err = a->err; T.live = a->live;
+    T.x_ts = T.y_ts = a->b; T.x_rs = T.y_rs = a->N;
+    T.x = x; T.y = a->t1.p;
+    a->timed(PK_PRECTC, [&] { launch_tc_product(a->tcX, T, a->num_sms, a->st); });
+    check_launch(a);
+    T.x = a->t1.p; T.y = y;
+    a->timed(PK_PRECTC, [&] { launch_tc_product(a->tcXH, T, a->num_sms, a->st); });
+    check_launch(a);
+    return;
+  }
   a->timed(PK_PREC, [&] { launch_precond_apply<R>(a->Xinv.p, a->x_stride, a->nel, a->b, nr, x, y, a->err, a->live, a->st); });
   check_launch(a);
 }
@@ -547,23 +566,33 @@ void ensure_ws(moma_array *a, int nr) {
 
 // Stage a caller buffer on the device: returns a device pointer (the
 // caller's own if it is device memory, else `tmp` after a copy).
-// Split full bins for the tensor-core product, once per set_blocks, when a
-// call brings enough right-hand sides to use it.
+// Split full bins and inverse factors for the tensor-core products, once
+// per set_blocks, when a call brings enough right-hand sides to use them.
 void ensure_tc(moma_array *a, int nr) {
-  if (a->tc.ready || a->no_tensor || a->prec != MOMA_PREC_MIXED || nr < a->tc_min_nr || !tc_supported(a->b)) return;
+  if (a->tc_ready || a->no_tensor || a->prec != MOMA_PREC_MIXED || nr < a->tc_min_nr || !tc_supported(a->b)) return;
   drop_graphs(a);
-  const size_t half = tc_bytes(a->B, a->b) / 2;
-  a->tcA.ensure(2 * half, a->dev_bytes);
-  float *hi = a->tcA.as<float>();
-  float *lo = reinterpret_cast<float *>(a->tcA.as<unsigned char>() + half);
+  const int b = a->b;
+  const size_t zb = tc_bytes(a->B, b), xb = tc_bytes(a->nel, b);
+  a->tcA.ensure(zb, a->dev_bytes);
+  a->tcP.ensure(2 * xb, a->dev_bytes);
+  unsigned char *pz = a->tcA.as<unsigned char>(), *px = a->tcP.as<unsigned char>();
+  a->tcZ = TcMats{};
+  a->tcZ.b = b; a->tcZ.T = a->B;
+  a->tcZ.hi = reinterpret_cast<float *>(pz); a->tcZ.lo = reinterpret_cast<float *>(pz + zb / 2);
+  a->tcX = TcMats{};
+  a->tcX.b = b; a->tcX.T = a->nel;
+  a->tcX.hi = reinterpret_cast<float *>(px); a->tcX.lo = reinterpret_cast<float *>(px + xb / 2);
+  a->tcXH = a->tcX;
+  a->tcXH.hi = reinterpret_cast<float *>(px + xb); a->tcXH.lo = reinterpret_cast<float *>(px + xb + xb / 2);
   try {
-    a->timed(PK_BLOCKFFT, [&] {
-      tc_build(a->tc, a->Z64.p, a->b, a->ldb, a->bin_slot.as<int2>(), a->partner.as<int>(), a->B, hi, lo, a->st);
-    });
+    a->timed(PK_BLOCKFFT, [&] { tc_split_bins(a->tcZ, a->Z64.p, a->ldb, a->bin_slot.as<int2>(), a->st); });
+    check_launch(a);
+    a->timed(PK_TRINV, [&] { tc_split_factor(a->tcX, a->tcXH, a->Xinv.p, a->x_stride, a->st); });
+    check_launch(a);
   } catch (const std::runtime_error &e) {
     throw MomaError(MOMA_ERR_CUDA, e.what());
   }
-  check_launch(a);
+  a->tc_ready = true;
 }
 
 const void *stage_in(moma_array *a, const void *src, size_t bytes, DevBuf &tmp) {
@@ -605,7 +634,7 @@ void set_blocks_impl(moma_array *a, const void *blocks, int dtype) {
   const size_t esz = dtype == MOMA_C128 ? sizeof(double2) : sizeof(float2);
   const void *blk = stage_in(a, blocks, (size_t)nD * bb * esz, a->blk);
   a->have_blocks = false;
-  a->tc.ready = false;
+  a->tc_ready = false;
   check_finite(a, blk, (size_t)nD * bb * 2, dtype == MOMA_C128);
   sync_and_check(a);
 
@@ -1118,9 +1147,9 @@ moma_status moma_create_array(int nx, int ny, int b, const moma_options *opt, vo
     a->st = reinterpret_cast<cudaStream_t>(cuda_stream);
     const int prec = opt ? opt->precision : MOMA_PREC_MIXED;
     if (prec != MOMA_PREC_FP64 && prec != MOMA_PREC_MIXED) throw MomaError(MOMA_ERR_ARG, "bad precision");
-    // The factored preconditioner block of one element is staged whole in
-    // shared memory (packed triangle): b <= 128 in FP64, b <= 160 in c64.
-    if (b > (prec == MOMA_PREC_FP64 ? 128 : 160)) throw MomaError(MOMA_ERR_ARG, "b too large for this build");
+    // Preconditioner blocks up to 256 x 256 (the box Cholesky's (i, k) table
+    // and the bin product's per-warp column sums must fit in shared memory).
+    if (b > 256) throw MomaError(MOMA_ERR_ARG, "b too large for this build (b <= 256)");
     a->prec = prec;
     a->m = (opt && opt->restart > 0) ? opt->restart : 50;
     a->use_graphs = !(opt && (opt->flags & MOMA_FLAG_NO_GRAPHS));
@@ -1397,6 +1426,10 @@ size_t moma_estimate_bytes(int nx, int ny, int b, const moma_options *opt, int n
   bytes += (size_t)(m + 1) * nr * N * esz + nr * nch * (m + 1) * c + nr * m * (m + 1) * c;  // Krylov
   bytes += 2 * nr * nel * c;                                                            // ports
   if (with_setup) bytes += nD * b * b * (c + 8) + (size_t)(2 * ny - 1) * Mx * nt * c + nel * nt * c;
+  const bool tensor = !(opt && (opt->flags & MOMA_FLAG_NO_TENSOR));
+  const int tmin = (opt && (opt->flags & MOMA_FLAG_TENSOR_ALWAYS)) ? 1 : 16;
+  if (prec == MOMA_PREC_MIXED && tensor && nrhs >= tmin && tc_supported(b))
+    bytes += tc_bytes((int)B, b) + 2 * tc_bytes((int)nel, b);  // split bins and factors
   return bytes;
 }
 

@@ -239,23 +239,27 @@ void launch_box_one(const double2 *S, int nx, int ny, int b, int ex, int ey, dou
 // X = L^{-1}, one column per warp: column k solves L x = e_k by forward
 // substitution in axpy form -- at step m the lane holding row m finishes
 // x_m = x_m / L_mm, broadcasts it, and every lane updates its rows i > m
-// with column m of L (contiguous in the packed column-major layout, staged
-// in shared memory in precision R).  x lives in registers (lane owns rows
-// lane + 32u).  X is written packed column-major, so the column store is
-// coalesced.
-template <typename R, int U>
+// with column m of L (contiguous in the packed column-major layout).  L is
+// staged in shared memory in precision R when it fits (b <= 160 in c64,
+// b <= 128 in c128); larger blocks read their columns from global memory
+// (FP64, L2-resident while the CTA works on them).  x lives in registers
+// (lane owns rows lane + 32u).  X is written packed column-major, so the
+// column store is coalesced.
+template <typename R, int U, bool L_IN_SMEM>
 __global__ void __launch_bounds__(256) tri_inverse_kernel(const double2 *__restrict__ Lpk, int b,
                                                           typename Cplx<R>::T *X, size_t x_stride) {
   using C = typename Cplx<R>::T;
   extern __shared__ __align__(16) unsigned char smraw[];
-  C *L = reinterpret_cast<C *>(smraw);
+  C *Ls = reinterpret_cast<C *>(smraw);
   const int e = blockIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const size_t npk = (size_t)b * (b + 1) / 2;
   const double2 *Le = Lpk + (size_t)e * npk;
   C *Xe = X + (size_t)e * x_stride;
-  for (size_t q = threadIdx.x; q < npk; q += blockDim.x) L[q] = cvt<C>(Le[q]);
+  if (L_IN_SMEM)
+    for (size_t q = threadIdx.x; q < npk; q += blockDim.x) Ls[q] = cvt<C>(Le[q]);
   for (size_t q = npk + threadIdx.x; q < x_stride; q += blockDim.x) Xe[q] = czero<C>();  // pad
   __syncthreads();
+  auto Lat = [&](size_t q) -> C { return L_IN_SMEM ? Ls[q] : cvt<C>(__ldg(Le + q)); };
   for (int k = w; k < b; k += nw) {
     C x[U];
 #pragma unroll
@@ -266,15 +270,15 @@ __global__ void __launch_bounds__(256) tri_inverse_kernel(const double2 *__restr
         const int m = 32 * u0 + lm;
         if (m >= b) break;
         if (m < k) continue;
-        const C *Lc = L + colbase(m, b) - m;  // Lc[i] = L(i, m)
-        if (lane == lm) x[u0] = cscale(x[u0], (R)1 / Lc[m].x);
+        const size_t cb = (size_t)colbase(m, b) - m;  // L(i, m) at cb + i
+        if (lane == lm) x[u0] = cscale(x[u0], (R)1 / Lat(cb + m).x);
         C xm;
         xm.x = __shfl_sync(0xffffffffu, x[u0].x, lm);
         xm.y = __shfl_sync(0xffffffffu, x[u0].y, lm);
 #pragma unroll
         for (int u = u0; u < U; ++u) {
           const int i = lane + 32 * u;
-          if (i > m && i < b) x[u] = csub(x[u], cmul(Lc[i], xm));
+          if (i > m && i < b) x[u] = csub(x[u], cmul(Lat(cb + i), xm));
         }
       }
     }
@@ -291,29 +295,35 @@ template <typename R>
 void launch_tri_inverse(const double2 *Lpk, int nel, int b, void *X, size_t x_stride, cudaStream_t st) {
   using C = typename Cplx<R>::T;
   const size_t bytes = (size_t)b * (b + 1) / 2 * sizeof(C);
+  const bool in_smem = bytes <= 200 * 1024;
   const int U = (b + 31) / 32;
   auto go = [&](auto kern) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-    kern<<<nel, 256, bytes, st>>>(Lpk, b, reinterpret_cast<C *>(X), x_stride);
+    kern<<<nel, 256, in_smem ? bytes : 0, st>>>(Lpk, b, reinterpret_cast<C *>(X), x_stride);
   };
-  if (U <= 1) go(tri_inverse_kernel<R, 1>);
-  else if (U <= 2) go(tri_inverse_kernel<R, 2>);
-  else if (U <= 4) go(tri_inverse_kernel<R, 4>);
-  else go(tri_inverse_kernel<R, 8>);
+  if (in_smem) {
+    if (U <= 1) go(tri_inverse_kernel<R, 1, true>);
+    else if (U <= 2) go(tri_inverse_kernel<R, 2, true>);
+    else if (U <= 4) go(tri_inverse_kernel<R, 4, true>);
+    else go(tri_inverse_kernel<R, 8, true>);
+  } else {
+    go(tri_inverse_kernel<R, 8, false>);
+  }
 }
 template void launch_tri_inverse<float>(const double2 *, int, int, void *, size_t, cudaStream_t);
 template void launch_tri_inverse<double>(const double2 *, int, int, void *, size_t, cudaStream_t);
 
 // ------------------------------------------------------------ apply ------
 // y_e = X_e^H (X_e x_e), X_e = L_e^{-1} packed column-major.  One CTA per
-// element; X_e arrives in shared memory with one bulk copy.
+// element; X_e arrives in shared memory with one bulk copy when it fits
+// (otherwise its columns are read from global memory).
 //  Phase 1, t = X x: warps own columns k, lanes own rows i >= k and
 //    accumulate X(i,k) x_k in registers; partial t is reduced across warps.
 //  Phase 2, z = X^H t: warps own columns k, lanes own rows i >= k, and
 //    z_k = sum_i conj(X(i,k)) t_i is a warp reduction.
 constexpr int PA_THREADS = 256, PA_WARPS = 8;
 
-template <typename R, int NR, int U>
+template <typename R, int NR, int U, bool X_IN_SMEM>
 __global__ void __launch_bounds__(PA_THREADS) precond_apply_kernel(const typename Cplx<R>::T *__restrict__ X,
                                                                    size_t x_stride, int nel, int b, int nr,
                                                                    const typename Cplx<R>::T *__restrict__ x,
@@ -322,30 +332,32 @@ __global__ void __launch_bounds__(PA_THREADS) precond_apply_kernel(const typenam
   using C = typename Cplx<R>::T;
   extern __shared__ __align__(128) unsigned char smraw[];
   uint64_t *bar = reinterpret_cast<uint64_t *>(smraw);
-  C *Xs = reinterpret_cast<C *>(smraw + 128);
-  C *xs = Xs + x_stride;              // [b][NR]
+  C *xs = reinterpret_cast<C *>(smraw + 128) + (X_IN_SMEM ? x_stride : 0);  // [b][NR]
+  const C *Xs = X_IN_SMEM ? reinterpret_cast<const C *>(smraw + 128) : X + (size_t)blockIdx.x * x_stride;
   C *ts = xs + (size_t)b * NR;        // [b][NR]
   C *tp = ts + (size_t)b * NR;        // [PA_WARPS][b][NR]
   const int e = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   if (live && *live == 0) return;
-  if (tid == 0) {
-    mbar_init(bar, 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
-  if (tid == 0) {
-    const uint32_t bytes = (uint32_t)(x_stride * sizeof(C));
-    fence_proxy_async();
-    mbar_expect_tx(bar, bytes);
-    bulk_g2s(Xs, X + (size_t)e * x_stride, bytes, bar);
-  }
-  const bool ok = mbar_wait_bounded(bar, 0, 2000000000ull);
-  if (__syncthreads_or(!ok)) {
+  if (X_IN_SMEM) {
     if (tid == 0) {
-      atomicOr(err, DEVERR_TIMEOUT);
-      mbar_wait_bounded(bar, 0, 2000000000ull);
+      mbar_init(bar, 1);
+      fence_mbar_init();
     }
-    return;
+    __syncthreads();
+    if (tid == 0) {
+      const uint32_t bytes = (uint32_t)(x_stride * sizeof(C));
+      fence_proxy_async();
+      mbar_expect_tx(bar, bytes);
+      bulk_g2s(const_cast<C *>(Xs), X + (size_t)e * x_stride, bytes, bar);
+    }
+    const bool ok = mbar_wait_bounded(bar, 0, 2000000000ull);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        atomicOr(err, DEVERR_TIMEOUT);
+        mbar_wait_bounded(bar, 0, 2000000000ull);
+      }
+      return;
+    }
   }
 
   for (int q0 = 0; q0 < nr; q0 += NR) {
@@ -416,13 +428,18 @@ template <typename R, int NR, int U>
 static void apply_launch(const void *X, size_t x_stride, int nel, int b, int nr, const void *x, void *y,
                          unsigned *err, const int *live, cudaStream_t st) {
   using C = typename Cplx<R>::T;
-  const size_t smem = 128 + x_stride * sizeof(C) + (size_t)(2 + PA_WARPS) * b * NR * sizeof(C);
+  const size_t vec = (size_t)(2 + PA_WARPS) * b * NR * sizeof(C);
+  const bool in_smem = 128 + x_stride * sizeof(C) + vec <= 220 * 1024;
+  const size_t smem = 128 + (in_smem ? x_stride * sizeof(C) : 0) + vec;
   static int configured = 0;
   if (!configured) {
-    cudaFuncSetAttribute(precond_apply_kernel<R, NR, U>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    cudaFuncSetAttribute(precond_apply_kernel<R, NR, U, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    cudaFuncSetAttribute(precond_apply_kernel<R, NR, U, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         220 * 1024);
     configured = 1;
   }
-  precond_apply_kernel<R, NR, U><<<nel, PA_THREADS, smem, st>>>(
+  auto kern = in_smem ? precond_apply_kernel<R, NR, U, true> : precond_apply_kernel<R, NR, U, false>;
+  kern<<<nel, PA_THREADS, smem, st>>>(
       reinterpret_cast<const C *>(X), x_stride, nel, b, nr, reinterpret_cast<const C *>(x),
       reinterpret_cast<C *>(y), err, live);
 }

@@ -25,7 +25,7 @@ MOMA_PREC_FP64, MOMA_PREC_MIXED = 0, 1
 MOMA_OP_Z, MOMA_OP_ZH, MOMA_OP_NORMAL = 0, 1, 2
 KERNEL_IDS = {"bin_c64": 0, "bin_c128": 1, "precond": 2, "fft_c64": 3, "block_fft": 4, "fft_c128": 5,
               "gram": 6, "sat": 7, "cholesky": 8, "tri_inverse": 9, "krylov": 10, "misc": 11,
-              "bin_tc": 12}
+              "bin_tc": 12, "precond_tc": 13}
 
 # Every symbol include/moma.h declares, for the export check.
 EXPORTS = [

@@ -118,3 +118,57 @@ def test_solve_takes_tensor_path_and_matches_dense(moma_lib, cuda):
     i_ref = dense.solve(z, V)
     za_ref = ports.active_impedance(i_ref, V)
     assert relerr(za, za_ref) <= 1e-8
+
+
+@pytest.mark.parametrize("nx,ny,b,nr", [(3, 2, 128, 20), (2, 2, 160, 33), (2, 1, 256, 16)])
+def test_tensor_preconditioner_apply(moma_lib, cuda, nx, ny, b, nr):
+    """y = P^{-1} x through X_e^H X_e on the tensor cores vs the oracle's
+    direct block solve (Eq. 37 blocks, Cholesky)."""
+    m = moma_lib
+    spec = LatticeSpec(nx, ny, b, 0.5, 3)
+    blocks = offset_blocks(spec, np.complex64)
+    x = rand_vec(nr, spec, seed=7)
+    ref = mbt.precond_solve(mbt.precond_blocks(blocks.astype(np.complex128), nx, ny), x.astype(np.complex128))
+    ys = {}
+    for name, flags in (("tensor", m.MOMA_FLAG_TENSOR_ALWAYS), ("cuda", m.MOMA_FLAG_NO_TENSOR)):
+        h = m.moma_create_array(nx, ny, b, MIXED, flags=flags)
+        try:
+            m.moma_set_blocks(h, blocks)
+            m.moma_profile(h, 1)
+            y = np.zeros_like(x)
+            m.moma_apply_precond(h, x, y)
+            n_tc = m.moma_kernel_stats(h, "precond_tc")[0]
+            m.moma_profile(h, 0)
+        finally:
+            m.moma_destroy(h)
+        ys[name] = (y, n_tc)
+    et, ec = relerr(ys["tensor"][0], ref), relerr(ys["cuda"][0], ref)
+    print(f"precond {nx}x{ny}x{b} nr={nr}: tensor err {et:.3g}, cuda cores err {ec:.3g}")
+    assert ys["tensor"][1] == 2 and ys["cuda"][1] == 0
+    assert et <= 1e-4 and ec <= 1e-4
+
+
+@pytest.mark.parametrize("prec,nr", [(MIXED, 16), (MIXED, 2), (0, 2)])
+def test_wide_blocks_b256_solve_matches_dense(moma_lib, cuda, prec, nr):
+    """b = 256 (preconditioner factors read from global memory): mixed with
+    the tensor path (16 RHS), mixed on the CUDA cores (2 RHS), plain FP64."""
+    m = moma_lib
+    spec = LatticeSpec(3, 2, 256, 0.5, 5)
+    blocks = offset_blocks(spec, np.complex64 if prec == MIXED else np.complex128)
+    b128 = blocks.astype(np.complex128)
+    angles = [(th, ph) for th in (0.0, 15.0, 30.0, 45.0) for ph in (0.0, 30.0, 60.0, 90.0)][:nr]
+    V = excitation(spec, angles)
+    h = m.moma_create_array(spec.nx, spec.ny, spec.b, prec)
+    try:
+        m.moma_set_blocks(h, blocks)
+        I = np.zeros_like(V)
+        rr = np.zeros(nr)
+        info = m.moma_solve(h, V, I, rel_residual=rr)
+        za = np.zeros(V.shape[:3], np.complex128)
+        m.moma_active_impedance(h, I, V, za)
+    finally:
+        m.moma_destroy(h)
+    print(f"b=256 prec={prec} nr={nr}:", info)
+    assert info["converged"] == 1 and rr.max() <= 1e-10
+    i_ref = dense.solve(dense.assemble(b128, spec.nx, spec.ny), V)
+    assert relerr(za, ports.active_impedance(i_ref, V)) <= 1e-8
