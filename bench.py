@@ -43,12 +43,16 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ragged", action="store_true",
                     help="ragged batch: 24 square lattices 2x2..48x48, b=96, x 3 spacings, one broadside solve each")
+    ap.add_argument("--scan", action="store_true",
+                    help="scan workload: 24x24, b=256, 64 scan-angle RHS at spacings 0.3/0.5/0.7 (tensor cores)")
     ap.add_argument("--serve", action="store_true",
                     help="serving mode: Poisson request stream through the continuous-batching server")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-keys", type=int, default=8)
     ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--nrhs", type=int, default=0,
+                    help="profiling: this many scan-angle RHS instead of the workload's two")
     ap.add_argument("--lattice", type=int, nargs=3, metavar=("NX", "NY", "B"), default=None,
                     help="override the lattice (profiling of smaller cases; not the benchmark workload)")
     return ap.parse_args()
@@ -122,11 +126,13 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def make_inputs(lattice=None):
-    from synth import config_c2, offset_blocks, excitation, LatticeSpec
+def make_inputs(lattice=None, nrhs=0):
+    from synth import config_c2, offset_blocks, excitation, LatticeSpec, config_c3_angles
     spec, angles = config_c2()
     if lattice:
         spec = LatticeSpec(lattice[0], lattice[1], lattice[2], spec.d, spec.seed)
+    if nrhs:
+        angles = (config_c3_angles() * (nrhs // 64 + 1))[:nrhs]
     blocks = offset_blocks(spec, np.complex64)
     V = excitation(spec, angles)
     return spec, blocks, V
@@ -331,6 +337,94 @@ def run_ragged(args):
     print(json.dumps(line, default=str), flush=True)
 
 
+def tf32_peak():
+    """Dense TF32 tensor peak: the measured bf16 burst peak times the nominal
+    tf32/bf16 ratio (1.1 / 2.25 PFLOP/s)."""
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+        return json.load(f)["bf16_tflops"] * 1.1 / 2.25, "of measured (bf16 burst x nominal tf32/bf16)"
+
+
+def run_scan(args):
+    """Scan workload: 24 x 24 lattice, b = 256 (N = 147456), 64 RHS per
+    array (8 x 8 grid of scan angles, theta in [0, 60], phi in [0, 90)) at
+    three element spacings (0.3, 0.5, 0.7 wavelengths: three arrays, c64
+    blocks generated on the GPU).  One step = set-up of the three arrays +
+    three 64-RHS solves (bin products and preconditioner on the tensor
+    cores) + port quantities.  value = RHS solved per second."""
+    import torch
+    import paper_2608_17844_b300 as m
+    from synth import LatticeSpec, offset_blocks_torch, excitation, config_c3_angles
+    torch.cuda.set_device(0)
+    angles = config_c3_angles()
+    specs = [LatticeSpec(24, 24, 256, d, 0) for d in (0.3, 0.5, 0.7)]
+    blocks = [offset_blocks_torch(s, "cuda") for s in specs]
+    Vs = [torch.from_numpy(excitation(s, angles)).cuda() for s in specs]
+    Is = [torch.zeros_like(v) for v in Vs]
+    zas = [torch.zeros(v.shape[:3], dtype=torch.complex128, device="cuda") for v in Vs]
+    hs = [m.moma_create_array(s.nx, s.ny, s.b) for s in specs]
+    nr = len(angles)
+
+    def step():
+        m.moma_set_blocks_batch(hs, blocks, release_setup=False, workers=3)
+        infos = m.moma_solve_batch(hs, Vs, Is, workers=3)
+        for h, I, V, za in zip(hs, Is, Vs, zas):
+            m.moma_active_impedance(h, I, V, za)
+        return infos
+
+    for _ in range(max(1, args.warmup)):
+        infos = step()
+    torch.cuda.synchronize()
+    steps = max(1, min(args.steps, 5))
+    clk = ClockSampler(0)
+    clk.start()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        infos = step()
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / steps
+    clocks = clk.stop()
+    # One profiled step, arrays one after another, for the per-kernel split.
+    for h in hs:
+        m.moma_profile(h, 1)
+    for h, b, V, I in zip(hs, blocks, Vs, Is):
+        m.moma_set_blocks(h, b)
+        m.moma_solve(h, V, I)
+    torch.cuda.synchronize()
+    fam = {}
+    for name in m.KERNEL_IDS:
+        n = sum(m.moma_kernel_stats(h, name)[0] for h in hs)
+        ms = sum(m.moma_kernel_stats(h, name)[1] for h in hs)
+        if n:
+            fam[name] = {"launches": n, "ms": round(ms, 3)}
+    for h in hs:
+        m.moma_profile(h, 0)
+    spec = specs[0]
+    B = 48 * 48
+    flops_launch = 8.0 * B * spec.b * spec.b * nr  # complex b x b by b x nr per bin
+    tc = fam.get("bin_tc", {"launches": 0, "ms": 0.0})
+    peak, peak_src = tf32_peak()
+    achieved = flops_launch / (tc["ms"] / tc["launches"] * 1e-3) / 1e12 if tc["launches"] else None
+    line = {"metric": "scan workload: RHS solved/s (set-up + solve, 3 spacings x 64 RHS)", "mode": "scan",
+            "value": len(specs) * nr / dt, "unit": "solves/s", "ms_per_step": 1000 * dt, "steps": steps,
+            "converged": sum(x["converged"] for x in infos),
+            "max_rel_residual": max(x["max_rel_residual"] for x in infos),
+            "inner_iters": [x["inner_iters"] for x in infos], "outer_iters": [x["outer_iters"] for x in infos],
+            "device_bytes": sum(m.moma_device_bytes(h) for h in hs), "data": "synthetic", "dtype": "c64+c128",
+            "config": {"workload": "24x24 lattice, b=256 (N=147456), 64 RHS (8x8 scan grid), d in {0.3,0.5,0.7}, "
+                                   "c64 blocks, GMRES(50) + FP64 refinement to 1e-10"},
+            "kernels_profiled_step": fam,
+            "roofline": {"kernel": "bin_mma_kernel (tcgen05 kind::tf32, 3xTF32)", "bound": "tensor",
+                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak if achieved else None,
+                         "issued_frac": 3 * achieved / peak if achieved else None,
+                         "flops_per_launch": flops_launch, "peak_source": peak_src},
+            "clocks": clocks,
+            "centre_Za_broadside": {f"d={s.d}": f"{complex(za[0, 12, 12].item()):.6f}" for s, za in zip(specs, zas)}}
+    for h in hs:
+        m.moma_destroy(h)
+    print(json.dumps(line, default=str), flush=True)
+
+
 def run_reference(args, world, rank):
     """Reference arm: the CPU oracle as it stands, on the host cores."""
     if rank != 0:
@@ -367,6 +461,10 @@ def main():
         if rank == 0:
             run_ragged(args)
         return
+    if args.scan:
+        if rank == 0:
+            run_scan(args)
+        return
     import torch
     import paper_2608_17844_b300 as m
 
@@ -381,7 +479,7 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    spec, blocks, V = make_inputs(args.lattice)
+    spec, blocks, V = make_inputs(args.lattice, args.nrhs)
     nr = V.shape[0]
     stream = torch.cuda.current_stream()
     blocks_d = torch.from_numpy(blocks).cuda()
@@ -562,7 +660,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c64 (FP32) inner + f64 refinement",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD if not args.lattice else f"profiling lattice {args.lattice}",
+            "config": {"workload": WORKLOAD if not (args.lattice or args.nrhs)
+                       else f"profiling lattice {args.lattice or 'C2'}, {nr} RHS",
                        "rhs_per_step": nr * world, "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (c64 blocks 520 MB; stored bins 269 MB c64 + 537 MB c128)"},
             "step_ms": {"p50": statistics.median(steps_ms), "p99": float(np.percentile(steps_ms, 99)),

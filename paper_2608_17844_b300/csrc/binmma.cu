@@ -181,15 +181,17 @@ MOMA_DEV bool warp_aborted(volatile int *abort_flag) {
 
 template <int NRT>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    bin_mma_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo, MmaArgs P) {
+    bin_mma_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo,
+                   const __grid_constant__ CUtensorMap map_x, MmaArgs P) {
   if (P.live && *P.live == 0) return;
   constexpr int NP = 2 * NRT;           // MMA N
   constexpr int BTILE = NP * 128;       // bytes of one B' tile
+  constexpr int XTILE = NRT * 128;      // bytes of one raw RHS chunk (NRT rows x 32 floats)
   constexpr int LW = NRT < 32 ? NRT : 32;  // accumulator columns per tcgen05.ld
   extern __shared__ unsigned char smem_raw[];
   unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int NS = P.NS, nmt = P.nmt, nkc = P.nkc;
-  const int stage_bytes = nmt * 2 * TC_ATILE + 2 * BTILE;
+  const int stage_bytes = nmt * 2 * TC_ATILE + 2 * BTILE + XTILE;
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)NS * stage_bytes);
   uint64_t *fullA = bars, *fullB = bars + NS, *empty = bars + 2 * NS;
   uint64_t *accf = bars + 3 * NS, *acce = accf + 2, *drain = acce + 2;
@@ -229,22 +231,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (lane == 0) {
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_hi)) : "memory");
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_lo)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_x)) : "memory");
       int g = 0;
       int issued_in[8];
       for (int s = 0; s < 8; ++s) issued_in[s] = -1;
       for (int u = blockIdx.x; u < units && !*abort_flag; u += gridDim.x) {
-        const int t = u / P.nrtiles;
+        const int t = u / P.nrtiles, j0 = (u % P.nrtiles) * NRT;
         const int ai = P.amap ? P.amap[t] : t;
         for (int kc = 0; kc < nkc; ++kc, ++g) {
           const int s = g % NS;
           const uint32_t ph = (uint32_t)(g / NS) & 1u;
           if (!wait_or_abort(&empty[s], ph ^ 1u, abort_flag, P.err)) break;
           unsigned char *st = smem + (size_t)s * stage_bytes;
-          mbar_expect_tx(&fullA[s], (uint32_t)(nmt * 2 * TC_ATILE));
+          mbar_expect_tx(&fullA[s], (uint32_t)(nmt * 2 * TC_ATILE + XTILE));
           for (int mt = 0; mt < nmt; ++mt) {
             tma_load_3d(st + (size_t)(2 * mt) * TC_ATILE, &map_hi, kc * TC_KC, mt * TC_M, ai, &fullA[s]);
             tma_load_3d(st + (size_t)(2 * mt + 1) * TC_ATILE, &map_lo, kc * TC_KC, mt * TC_M, ai, &fullA[s]);
           }
+          // Raw RHS chunk: rows j0 .. j0+NRT-1 (past nr read as zeros).
+          tma_load_3d(st + (size_t)nmt * 2 * TC_ATILE + 2 * BTILE, &map_x, kc * TC_KC, t, j0, &fullA[s]);
           issued_in[s] = g;
         }
       }
@@ -297,34 +302,30 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   } else if (warp < 6) {
     // ------------------------------------------------ B' construction --
     const int bt = threadIdx.x - 64;
-    const int b = P.b;
     const float sgn = P.conj ? 1.0f : -1.0f;  // sign of the Im x term in the real rows
     int g = 0;
     for (int u = blockIdx.x; u < units && !warp_aborted(abort_flag); u += gridDim.x) {
-      const int t = u / P.nrtiles, j0 = (u % P.nrtiles) * NRT;
-      const float2 *xt = P.x + (size_t)t * P.x_ts;
       bool ok = true;
       for (int kc = 0; kc < nkc; ++kc, ++g) {
         const int s = g % NS;
         const uint32_t ph = (uint32_t)(g / NS) & 1u;
-        if (!warp_wait(&empty[s], ph ^ 1u, abort_flag, P.err)) {
+        // The stage's copies (issued after the stage was freed) have landed.
+        if (!warp_wait(&fullA[s], ph, abort_flag, P.err)) {
           ok = false;
           break;
         }
         unsigned char *bhi = smem + (size_t)s * stage_bytes + (size_t)nmt * 2 * TC_ATILE;
         unsigned char *blo = bhi + BTILE;
-        for (int idx = bt; idx < NRT * 8; idx += 128) {
+        const float4 *xr = reinterpret_cast<const float4 *>(blo + BTILE);  // [NRT][8] float4
+#pragma unroll
+        for (int it = 0; it < NRT * 8 / 128 + (NRT * 8 % 128 ? 1 : 0); ++it) {
+          const int idx = bt + it * 128;
+          if (idx >= NRT * 8) break;
           const int j = idx >> 3, c = idx & 7;
-          const int k0 = kc * 16 + 2 * c;
-          float2 v0 = make_float2(0.f, 0.f), v1 = make_float2(0.f, 0.f);
-          if (j0 + j < P.nr) {
-            const float2 *row = xt + (size_t)(j0 + j) * P.x_rs;
-            if (k0 < b) v0 = row[k0];
-            if (k0 + 1 < b) v1 = row[k0 + 1];
-          }
+          const float4 v = xr[idx];  // x[j][k0], x[j][k0 + 1] with k0 = 16 kc + 2 c
           // Real-part row j and imaginary-part row NRT + j (see header).
-          const float re[4] = {v0.x, sgn * v0.y, v1.x, sgn * v1.y};
-          const float im[4] = {v0.y, -sgn * v0.x, v1.y, -sgn * v1.x};
+          const float re[4] = {v.x, sgn * v.y, v.z, sgn * v.w};
+          const float im[4] = {v.y, -sgn * v.x, v.w, -sgn * v.z};
           float4 rh, rl, ih, il;
           float *prh = &rh.x, *prl = &rl.x, *pih = &ih.x, *pil = &il.x;
 #pragma unroll
@@ -488,7 +489,7 @@ void encode_maps(TcMats &m) {
 
 template <int NRT>
 size_t smem_bytes(int nmt, int NS) {
-  const size_t stage = (size_t)nmt * 2 * TC_ATILE + 2 * (size_t)(2 * NRT) * 128;
+  const size_t stage = (size_t)nmt * 2 * TC_ATILE + 2 * (size_t)(2 * NRT) * 128 + (size_t)NRT * 128;
   return 1024 + NS * stage + (3 * NS + 5) * sizeof(uint64_t) + 16;
 }
 
@@ -523,9 +524,24 @@ void launch_nrt(const TcMats &m, const TcProduct &P, int num_sms, cudaStream_t s
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     configured = true;
   }
+  // RHS chunks by TMA: x viewed as floats [nr][T][2b] with the given item
+  // and row strides; boxes of 32 floats x 1 item x NRT rows, no swizzle.
+  CUtensorMap map_x;
+  {
+    auto fn = encode_fn();
+    if (!fn) throw std::runtime_error("cuTensorMapEncodeTiled is not available");
+    const cuuint64_t dims[3] = {(cuuint64_t)(2 * b), (cuuint64_t)m.T, (cuuint64_t)P.nr};
+    const cuuint64_t strides[2] = {(cuuint64_t)P.x_ts * 8, (cuuint64_t)P.x_rs * 8};
+    const cuuint32_t box[3] = {TC_KC, 1, (cuuint32_t)NRT};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = fn(&map_x, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(P.x), dims, strides, box,
+                          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) throw std::runtime_error("cuTensorMapEncodeTiled (x) failed: " + std::to_string((int)r));
+  }
   const int units = a.T * a.nrtiles;
   const int grid = std::min(units, num_sms);
-  kern<<<grid, TC_THREADS, smem, st>>>(m.map_hi, m.map_lo, a);
+  kern<<<grid, TC_THREADS, smem, st>>>(m.map_hi, m.map_lo, map_x, a);
 }
 
 }  // namespace
