@@ -19,13 +19,21 @@ III-A: the preconditioned normal equations have the same solution):
                   GMRES on the ORIGINAL system Z I = V with a block-Jacobi
                   preconditioner and the direct offset-sum product (no FFT,
                   so no algorithm in common with the CUDA path).
+* predictors.py -- the error predictors of Sec. II-E: xi (Eq. 20), the
+                  border bound (Eq. 23), xi_Z (Eqs. 24-25), the column
+                  coupling C_n (Eqs. 28-30), S <-> Z (Eq. 31) and xi_S
+                  (Eq. 36).
 
 Pins (tests/test_oracle_*.py): brute-force inversion, exact reciprocity and
 Toeplitz invariants of the assembly, per-entry recomputation from the
 lattice geometry, closed forms for 1x1 and two-element arrays, the Hermitian
 commutation theorem (Eq. 6) and circulant-embedding identity (Eq. 3), equal
 spectra of the two preconditioned forms (Sec. III-A), agreement of the two
-active-impedance routes, and dense-vs-iterative agreement.
+active-impedance routes, dense-vs-iterative agreement, and for the
+predictors: the 1x1 reflection coefficient and uncoupled / matched special
+cases of S <-> Z, Fourier coefficients of exp(a e^{j psi}) (a^n / n!), exact
+recovery of trigonometric polynomials, the theta substitution, hand-counted
+border sets, and the border bound holding when a lattice grows.
 Parity is pinned for every function here; none is "parity unpinned".
 """
-from . import dense, mbt, ports, iterative  # noqa: F401
+from . import dense, mbt, ports, iterative, predictors  # noqa: F401

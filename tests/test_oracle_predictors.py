@@ -1,0 +1,113 @@
+"""Pins of the predictor oracle (oracle/predictors.py) against closed forms,
+special cases and the paper's own inequality -- nothing here re-types the
+function under test."""
+import numpy as np
+import pytest
+from scipy.special import factorial
+
+from synth import LatticeSpec, offset_blocks, excitation
+from oracle import dense, ports, predictors as pr
+
+
+def test_xi_definition_eq20():
+    za = 54.1 + 29.9j
+    assert abs(pr.xi(za * (1 + 0.013 - 0.002j), za) - (0.013 - 0.002j)) < 1e-15
+
+
+def test_s_of_single_port_is_reflection_coefficient():
+    """1x1: S = (Z - Z0)/(Z + Z0), Eq. 19's reflection coefficient."""
+    for z in (50.0 + 0j, 73.1 + 42.5j, 12.0 - 80.0j):
+        s = pr.s_from_z(np.array([[z]]), 50.0)
+        assert abs(s[0, 0] - ports.reflection(z, 50.0)) < 1e-15
+        assert abs(pr.z_from_s(s, 50.0)[0, 0] - z) < 1e-12
+
+
+def test_s_to_z_special_cases_and_round_trip():
+    n = 7
+    # Matched ports (S = 0) give Z_p = Z0 I.
+    assert np.allclose(pr.z_from_s(np.zeros((n, n)), 50.0), 50.0 * np.eye(n), atol=1e-13)
+    # Uncoupled ports: diagonal S from diagonal Z, entry by entry Eq. 19.
+    zd = np.diag(np.linspace(20, 90, n) + 1j * np.linspace(-30, 30, n))
+    sd = pr.s_from_z(zd, 50.0)
+    assert np.allclose(np.diag(sd), ports.reflection(np.diag(zd), 50.0), atol=1e-15)
+    assert np.abs(sd - np.diag(np.diag(sd))).max() < 1e-15
+    # A reciprocal Z_p from a solved lattice: S symmetric, and back to Z_p.
+    spec = LatticeSpec(3, 2, 5, 0.5, 1)
+    z = dense.assemble(offset_blocks(spec), 3, 2)
+    zp = ports.port_impedance_matrix(z, 3, 2, 5)
+    s = pr.s_from_z(zp, 50.0)
+    assert np.abs(s - s.T).max() < 1e-12
+    assert np.abs(pr.z_from_s(s, 50.0) - zp).max() < 1e-10 * np.abs(zp).max()
+
+
+def test_column_coupling_closed_form_and_sign():
+    """Gamma(psi) = exp(a e^{j psi}) = sum_{n>=0} a^n e^{j n psi} / n!, so
+    C_n = a^n / n! for n >= 0 and 0 for n < 0 (pins the e^{-j n psi} kernel)."""
+    a = 0.7
+    q = 64
+    psi = pr.psi_samples(q)
+    c = pr.column_coupling(np.exp(a * np.exp(1j * psi)), 6)
+    n = np.arange(-6, 7)
+    expect = np.where(n >= 0, a ** np.abs(n) / factorial(np.abs(n)), 0.0)
+    assert np.abs(c - expect).max() < 1e-15
+
+
+def test_column_coupling_recovers_trig_polynomial():
+    rng = np.random.default_rng(3)
+    coef = rng.standard_normal(11) + 1j * rng.standard_normal(11)  # n = -5..5
+    q = 16
+    psi = pr.psi_samples(q)
+    gamma = sum(coef[k] * np.exp(1j * (k - 5) * psi) for k in range(11))
+    assert np.abs(pr.column_coupling(gamma, 5) - coef).max() < 1e-13
+
+
+def test_theta_form_is_the_substitution():
+    """Eq. 30 with kd = pi (d = lambda/2): sampling Gamma^(theta) at
+    theta = asin(psi / kd) equals sampling Gamma(psi)."""
+    kd = np.pi
+    g_psi = lambda p: 0.2 * np.exp(1j * p) - 0.05 * np.exp(-2j * p) + 0.1
+    c1 = pr.column_coupling(g_psi(pr.psi_samples(32)), 4)
+    c2 = pr.column_coupling_theta(lambda t: g_psi(kd * np.sin(t)), 4, 32, kd)
+    assert np.abs(c1 - c2).max() < 1e-14
+    assert abs(c1[4 + 1] - 0.2) < 1e-14 and abs(c1[4 - 2] + 0.05) < 1e-14
+
+
+def test_border_set_and_closest_element():
+    assert len(pr.border_elements(6, 4)) == 2 * 6 + 2 * 4 - 4
+    assert len(pr.border_elements(5, 1)) == 5
+    # 5x5: centre (2,2); the four edge midpoints are at distance 2; the one on
+    # the centre's row with the smaller index is (0, 2) -> 10.
+    assert pr.closest_border_element(5, 5) == 10
+    # 6x4: centre (3,2); (3,3) on the top row is at distance 1 -> 21.
+    assert pr.closest_border_element(6, 4) == 21
+    assert pr.centre_index(6, 4) == 15
+
+
+def test_border_bound_holds_when_growing_the_array():
+    """Eq. 23: growing the array from (N-2)x(N-2) to NxN changes the centre
+    element's broadside Z_a by at most sum_{n in E_B} |Z_p,cn|."""
+    for n in (3, 5):
+        za = []
+        for m in (n - 2, n):
+            spec = LatticeSpec(m, m, 6, 0.5, 2)
+            z = dense.assemble(offset_blocks(spec), m, m)
+            v = excitation(spec, [(0.0, 0.0)])
+            i = dense.solve(z, v)
+            za.append(ports.active_impedance(i, v)[0, m // 2, m // 2])
+            zp = ports.port_impedance_matrix(z, m, m, 6)
+        bound = pr.border_bound(zp, n, n)
+        assert abs(za[1] - za[0]) <= bound
+        assert pr.xi_z(zp, n, n) <= pr.xi_z_max(zp, n, n) + 1e-15
+
+
+def test_s_ideal_structure_and_xi_s_limit():
+    kd = np.pi
+    s = pr.s_ideal(5, 4, 0.1 + 0.05j, -0.2 + 0.1j, kd)
+    assert np.abs(s - s.T).max() == 0
+    assert np.allclose(np.diag(s), 0.1 + 0.05j)
+    c = pr.centre_index(5, 4)
+    assert s[c, c + 1] == -0.2 + 0.1j                      # nearest neighbour: s1 itself
+    assert abs(abs(s[0, 3]) * 9 - abs(-0.2 + 0.1j)) < 1e-15  # distance 3: |s1| / 9
+    # Without coupling S_ideal is diagonal, Z is diagonal and xi_S vanishes.
+    assert pr.xi_s(5, 5, 0.1, 0.0, kd) == 0.0
+    assert 0 < pr.xi_s(5, 5, 0.1, 0.05, kd) < 1
