@@ -214,6 +214,49 @@ moma_status moma_active_impedance(moma_array *a, int nrhs, const void *I, const 
 moma_status moma_port_impedance(moma_array *a, int port_basis, int chunk, const moma_solve_opts *opts, void *Zp,
                                 void *Yp);
 
+/* ---- Error predictors (Sec. II-E, after Eq. 19) -------------------------
+ * Element index e = mx + Nx*my; the centre c = (Nx/2, Ny/2) (integer
+ * division); the border set E_B = the outermost ring of the lattice; "the
+ * border element closest to c" = smallest Euclidean lattice distance, ties
+ * to the element on the centre's row, then the smallest index. */
+
+/* Column coupling C_n (Eq. 28; Eq. 30 is the same integral over scan angle
+ * with psi = k d sin(theta)): solves the row-phase excitations
+ * V_q[my][mx][port_basis] = exp(j mx psi_q) (Eq. 29), psi_q = -pi + 2 pi q / nq,
+ * q < nq, with the array's solver (opts as moma_solve), takes the centre
+ * element's active reflection coefficient Gamma_q (Eq. 19, reference z0) and
+ * returns C[n + nmax] = (1/nq) sum_q Gamma_q exp(-j n psi_q) for
+ * n = -nmax..nmax (trapezoidal rule; exact for trigonometric polynomials of
+ * degree < nq).  C: c128 [2 nmax + 1]; gamma (nullable): c128 [nq]; host or
+ * device.  Errors: MOMA_ERR_STATE before set_blocks, MOMA_ERR_ARG, solver
+ * errors. */
+moma_status moma_column_coupling(moma_array *a, int port_basis, int nq, int nmax, double z0,
+                                 const moma_solve_opts *opts, void *C, void *gamma);
+
+/* Eq. 31: Zp = z0 (I + S)(I - S)^{-1} for an n x n c128 row-major S (host or
+ * device; Zp likewise), FP64 on the device (Gauss-Jordan inverse of I - S).
+ * Allocates and frees its own scratch.  MOMA_ERR_NONFINITE if I - S is
+ * singular. */
+moma_status moma_s_to_z(const void *S, int n, double z0, void *Zp, void *cuda_stream);
+
+/* The idealised scattering matrix behind xi_S (Eq. 36): S[i][i] = s_cc;
+ * S[i][j] = s1 dist^-2 exp(-j kd (dist - 1)) with dist the Euclidean
+ * distance of elements i, j in units of the spacing d and kd = k d.  S: c128
+ * [Nel][Nel], host or device. */
+moma_status moma_s_ideal(int nx, int ny, double s_cc_re, double s_cc_im, double s1_re, double s1_im, double kd,
+                         void *S, void *cuda_stream);
+
+/* From Zp (c128 [Nel][Nel], host or device): out[0] = xi_Z predictor
+ * |Zp[c][j]| / |Zp[c][c]| with j the border element closest to c (Eq. 25);
+ * out[1] = max over j in E_B of |Zp[c][j]| / |Zp[c][c]| (Eq. 24);
+ * out[2] = sum over n in E_B of |Zp[c][n]| (the border bound, Eq. 23). */
+moma_status moma_xi_z(const void *Zp, int nx, int ny, double *out);
+
+/* Eq. 36: xi_S = |Z[c][j]| / |Z[c][c]| for Z = z0 (I + S_ideal)(I - S_ideal)^{-1}
+ * (moma_s_ideal, moma_s_to_z), j the border element closest to c. */
+moma_status moma_xi_s(int nx, int ny, double s_cc_re, double s_cc_im, double s1_re, double s1_im, double kd,
+                      double z0, double *xi_s);
+
 /* Per-kernel timing over the calls made since moma_profile(a, 1), measured
  * with CUDA events recorded on the array's stream around each launch of a
  * kernel family.  kernel: 0 = c64 bin product, 1 = c128 bin product,

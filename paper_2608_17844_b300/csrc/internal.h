@@ -124,6 +124,13 @@ void launch_gather_ports(const double2 *I, int nel, int b, int pb, int j0, int n
 // Gauss-Jordan, partial pivoting); perm [n], colk [n] scratch.
 void launch_invert(double2 *A, int n, int *perm, double2 *colk, unsigned *err, cudaStream_t st);
 
+// ---------------------------------------------------------- predictors ----
+void launch_row_phase(double2 *V, int nx, int nel, int b, int pb, int q0, int nq, int Q, cudaStream_t st);
+void launch_column_coupling(const double2 *gamma, int Q, int nmax, double2 *C, cudaStream_t st);
+void launch_s_ideal(double2 *S, int nx, int ny, double2 s_cc, double2 s1, double kd, cudaStream_t st);
+// Z = z0 (I + S)(I - S)^{-1}; work holds n*n + n double2 and n ints.
+void launch_z_from_s(const double2 *S, int n, double z0, double2 *Z, double2 *work, unsigned *err, cudaStream_t st);
+
 // ------------------------------------------------------------- Krylov ----
 struct ArnoldiCtl;  // device-side control block (krylov.cu)
 }  // namespace moma

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <memory>
 #include <thread>
 #include <cstring>
 #include <mutex>
@@ -1358,6 +1359,166 @@ moma_status moma_port_impedance(moma_array *a, int port_basis, int chunk, const 
       copy_out(a, Zp, Y, (size_t)n * n * sizeof(double2));
     }
     sync_and_check(a);
+  });
+}
+
+// ------------------------------------------------------------ predictors --
+namespace {
+int centre_of(int nx, int ny) { return nx / 2 + nx * (ny / 2); }
+// Border element (outermost ring) closest to the centre; ties: on the
+// centre's row first, then the smallest index.
+int closest_border(int nx, int ny) {
+  const int cx = nx / 2, cy = ny / 2;
+  long best_d = -1;
+  int best_row = 2, best_e = -1;
+  for (int my = 0; my < ny; ++my)
+    for (int mx = 0; mx < nx; ++mx) {
+      if (!(mx == 0 || mx == nx - 1 || my == 0 || my == ny - 1)) continue;
+      const long d = (long)(mx - cx) * (mx - cx) + (long)(my - cy) * (my - cy);
+      const int row = my == cy ? 0 : 1, e = mx + nx * my;
+      if (best_e < 0 || d < best_d || (d == best_d && (row < best_row || (row == best_row && e < best_e)))) {
+        best_d = d;
+        best_row = row;
+        best_e = e;
+      }
+    }
+  return best_e;
+}
+double cabs2(double2 v) { return std::sqrt(v.x * v.x + v.y * v.y); }
+// Row c of an n x n c128 matrix (host or device) into host memory.
+std::vector<double2> matrix_row(const void *M, int n, int c) {
+  std::vector<double2> row(n);
+  const double2 *src = static_cast<const double2 *>(M) + (size_t)c * n;
+  CK(cudaMemcpy(row.data(), src, (size_t)n * sizeof(double2), cudaMemcpyDefault));
+  return row;
+}
+struct ScratchDev {
+  void *p = nullptr;
+  explicit ScratchDev(size_t bytes) {
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      throw MomaError(MOMA_ERR_OOM, "device allocation failed");
+    }
+  }
+  ~ScratchDev() {
+    if (p) cudaFree(p);
+  }
+};
+// Z = z0 (I + S)(I - S)^{-1} on the device for S host or device.
+void z_from_s_impl(const void *S, int n, double z0, void *Zp, cudaStream_t st) {
+  const size_t mat = (size_t)n * n * sizeof(double2);
+  ScratchDev buf(3 * mat + (size_t)n * (sizeof(double2) + sizeof(int)) + 256);
+  double2 *Sd = static_cast<double2 *>(buf.p), *Zd = Sd + (size_t)n * n, *work = Zd + (size_t)n * n;
+  unsigned *err = reinterpret_cast<unsigned *>(reinterpret_cast<unsigned char *>(buf.p) + 3 * mat +
+                                               (size_t)n * (sizeof(double2) + sizeof(int)));
+  CK(cudaMemsetAsync(err, 0, sizeof(unsigned), st));
+  CK(cudaMemcpyAsync(Sd, S, mat, cudaMemcpyDefault, st));
+  launch_z_from_s(Sd, n, z0, Zd, work, err, st);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(Zp, Zd, mat, cudaMemcpyDefault, st));
+  unsigned h = 0;
+  CK(cudaMemcpyAsync(&h, err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (h) throw MomaError(MOMA_ERR_NONFINITE, "I - S is singular (zero pivot)");
+}
+}  // namespace
+
+moma_status moma_column_coupling(moma_array *a, int port_basis, int nq, int nmax, double z0,
+                                 const moma_solve_opts *opts, void *C, void *gamma) {
+  if (!a) { g_last_error = "array is NULL"; return MOMA_ERR_ARG; }
+  return guarded([&] {
+    if (!a->have_blocks) throw MomaError(MOMA_ERR_STATE, "set_blocks must precede moma_column_coupling");
+    if (port_basis < 0 || port_basis >= a->b) throw MomaError(MOMA_ERR_ARG, "port_basis out of range");
+    if (nq < 1 || nmax < 0 || !C) throw MomaError(MOMA_ERR_ARG, "need nq >= 1, nmax >= 0 and C");
+    const int chunk = std::min(nq, 64), nel = a->nel, c = centre_of(a->nx, a->ny);
+    const size_t vbytes = (size_t)chunk * a->N * sizeof(double2);
+    a->zp_V.ensure(vbytes, a->dev_bytes);
+    a->zp_I.ensure(vbytes, a->dev_bytes);
+    a->portsb.ensure((size_t)2 * chunk * nel * sizeof(double2), a->dev_bytes);
+    a->zp_tmp.ensure((size_t)(nq + 2 * nmax + 1) * sizeof(double2) + 256, a->dev_bytes);
+    double2 *gam_d = a->zp_tmp.as<double2>(), *C_d = gam_d + nq;
+    double2 *za = a->portsb.as<double2>(), *ga = za + (size_t)chunk * nel;
+    for (int q0 = 0; q0 < nq; q0 += chunk) {
+      const int nqc = std::min(chunk, nq - q0);
+      launch_row_phase(a->zp_V.as<double2>(), a->nx, nel, a->b, port_basis, q0, nqc, nq, a->st);
+      check_launch(a);
+      moma_solve_info info{};
+      const moma_status s = moma_solve(a, nqc, a->zp_V.p, a->zp_I.p, opts, &info, nullptr);
+      if (s != MOMA_OK) throw MomaError(s, std::string("phase-sweep solve: ") + moma_last_error());
+      launch_ports(a->zp_I.as<double2>(), a->zp_V.as<double2>(), nel, a->b, nqc, port_basis, z0, za, ga, a->err,
+                   a->st);
+      check_launch(a);
+      CK(cudaMemcpy2DAsync(gam_d + q0, sizeof(double2), ga + c, (size_t)nel * sizeof(double2), sizeof(double2), nqc,
+                           cudaMemcpyDeviceToDevice, a->st));
+    }
+    launch_column_coupling(gam_d, nq, nmax, C_d, a->st);
+    check_launch(a);
+    copy_out(a, C, C_d, (size_t)(2 * nmax + 1) * sizeof(double2));
+    if (gamma) copy_out(a, gamma, gam_d, (size_t)nq * sizeof(double2));
+    sync_and_check(a);
+  });
+}
+
+moma_status moma_s_to_z(const void *S, int n, double z0, void *Zp, void *cuda_stream) {
+  return guarded([&] {
+    if (!S || !Zp || n < 1) throw MomaError(MOMA_ERR_ARG, "need S, Zp and n >= 1");
+    z_from_s_impl(S, n, z0, Zp, reinterpret_cast<cudaStream_t>(cuda_stream));
+  });
+}
+
+moma_status moma_s_ideal(int nx, int ny, double s_cc_re, double s_cc_im, double s1_re, double s1_im, double kd,
+                         void *S, void *cuda_stream) {
+  return guarded([&] {
+    if (nx < 1 || ny < 1 || !S) throw MomaError(MOMA_ERR_ARG, "need nx, ny >= 1 and S");
+    const int n = nx * ny;
+    const size_t mat = (size_t)n * n * sizeof(double2);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+    double2 *dst = static_cast<double2 *>(S);
+    std::unique_ptr<ScratchDev> tmp;
+    if (!is_device_ptr(S)) {
+      tmp.reset(new ScratchDev(mat));
+      dst = static_cast<double2 *>(tmp->p);
+    }
+    launch_s_ideal(dst, nx, ny, make_double2(s_cc_re, s_cc_im), make_double2(s1_re, s1_im), kd, st);
+    CK(cudaGetLastError());
+    if (tmp) CK(cudaMemcpyAsync(S, dst, mat, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+  });
+}
+
+moma_status moma_xi_z(const void *Zp, int nx, int ny, double *out) {
+  return guarded([&] {
+    if (!Zp || !out || nx < 1 || ny < 1) throw MomaError(MOMA_ERR_ARG, "need Zp, out and nx, ny >= 1");
+    const int n = nx * ny, c = centre_of(nx, ny);
+    const std::vector<double2> row = matrix_row(Zp, n, c);
+    const double zcc = cabs2(row[c]);
+    double bound = 0, mx = 0;
+    for (int my = 0; my < ny; ++my)
+      for (int mxi = 0; mxi < nx; ++mxi) {
+        if (!(mxi == 0 || mxi == nx - 1 || my == 0 || my == ny - 1)) continue;
+        const double v = cabs2(row[mxi + nx * my]);
+        bound += v;
+        mx = std::max(mx, v);
+      }
+    out[0] = cabs2(row[closest_border(nx, ny)]) / zcc;  // Eq. 25
+    out[1] = mx / zcc;                                   // Eq. 24
+    out[2] = bound;                                      // Eq. 23
+  });
+}
+
+moma_status moma_xi_s(int nx, int ny, double s_cc_re, double s_cc_im, double s1_re, double s1_im, double kd,
+                      double z0, double *xi_s) {
+  return guarded([&] {
+    if (nx < 1 || ny < 1 || !xi_s) throw MomaError(MOMA_ERR_ARG, "need nx, ny >= 1 and xi_s");
+    const int n = nx * ny, c = centre_of(nx, ny);
+    const size_t mat = (size_t)n * n * sizeof(double2);
+    ScratchDev buf(2 * mat);
+    double2 *S = static_cast<double2 *>(buf.p), *Z = S + (size_t)n * n;
+    launch_s_ideal(S, nx, ny, make_double2(s_cc_re, s_cc_im), make_double2(s1_re, s1_im), kd, nullptr);
+    CK(cudaGetLastError());
+    z_from_s_impl(S, n, z0, Z, nullptr);
+    const std::vector<double2> row = matrix_row(Z, n, c);
+    *xi_s = cabs2(row[closest_border(nx, ny)]) / cabs2(row[c]);  // Eq. 36
   });
 }
 

@@ -34,6 +34,7 @@ EXPORTS = [
     "moma_launch_count", "moma_device_bytes", "moma_destroy", "moma_last_error", "moma_matvec_noalloc",
     "moma_set_stream", "moma_release_setup", "moma_estimate_bytes", "moma_tuning_report", "moma_array_stream",
     "moma_set_blocks_batch", "moma_solve_batch", "moma_port_impedance",
+    "moma_column_coupling", "moma_s_to_z", "moma_s_ideal", "moma_xi_z", "moma_xi_s",
     "moma_server_create", "moma_server_submit", "moma_server_wait", "moma_server_get_stats", "moma_server_destroy",
 ]
 
@@ -119,6 +120,12 @@ def lib():
     L.moma_matvec_noalloc.argtypes = [vp, i, i, vp, vp, i]
     L.moma_set_stream.argtypes = [vp, vp]
     L.moma_port_impedance.argtypes = [vp, i, i, ctypes.POINTER(moma_solve_opts), vp, vp]
+    d = ctypes.c_double
+    L.moma_column_coupling.argtypes = [vp, i, i, i, d, ctypes.POINTER(moma_solve_opts), vp, vp]
+    L.moma_s_to_z.argtypes = [vp, i, d, vp, vp]
+    L.moma_s_ideal.argtypes = [i, i, d, d, d, d, d, vp, vp]
+    L.moma_xi_z.argtypes = [vp, i, i, ctypes.POINTER(ctypes.c_double)]
+    L.moma_xi_s.argtypes = [i, i, d, d, d, d, d, d, ctypes.POINTER(ctypes.c_double)]
     L.moma_tuning_report.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
     L.moma_array_stream.argtypes = [vp]
     L.moma_array_stream.restype = vp
@@ -397,3 +404,32 @@ def moma_port_impedance(h, Zp=None, Yp=None, port_basis=0, chunk=0, solver=0, to
     pz = _ptr_dtype(Zp)[0] if Zp is not None else None
     py = _ptr_dtype(Yp)[0] if Yp is not None else None
     _check(lib().moma_port_impedance(h, port_basis, chunk, ctypes.byref(opts), pz, py))
+
+
+def moma_column_coupling(h, nq, nmax, C, gamma=None, port_basis=0, z0=50.0, solver=0, tol=0.0):
+    """Column coupling C_n, n = -nmax..nmax, from an nq-sample phase sweep."""
+    opts = moma_solve_opts(tol, 0.0, 0, 0, solver, 0)
+    pg = _ptr_dtype(gamma)[0] if gamma is not None else None
+    _check(lib().moma_column_coupling(h, port_basis, nq, nmax, z0, ctypes.byref(opts), _ptr_dtype(C)[0], pg))
+
+
+def moma_s_to_z(S, Zp, z0=50.0, stream=None):
+    _check(lib().moma_s_to_z(_ptr_dtype(S)[0], S.shape[0], z0, _ptr_dtype(Zp)[0], _stream_handle(stream)))
+
+
+def moma_s_ideal(nx, ny, s_cc, s1, kd, S, stream=None):
+    _check(lib().moma_s_ideal(nx, ny, s_cc.real, s_cc.imag, s1.real, s1.imag, kd, _ptr_dtype(S)[0],
+                              _stream_handle(stream)))
+
+
+def moma_xi_z(Zp, nx, ny):
+    """(xi_Z predictor (Eq. 25), xi_Z max (Eq. 24), border bound (Eq. 23))."""
+    out = (ctypes.c_double * 3)()
+    _check(lib().moma_xi_z(_ptr_dtype(Zp)[0], nx, ny, out))
+    return tuple(out)
+
+
+def moma_xi_s(nx, ny, s_cc, s1, kd, z0=50.0):
+    out = ctypes.c_double()
+    _check(lib().moma_xi_s(nx, ny, s_cc.real, s_cc.imag, s1.real, s1.imag, kd, z0, ctypes.byref(out)))
+    return out.value
