@@ -137,8 +137,16 @@ moma_status moma_create_array(int nx, int ny, int b, const moma_options *opt,
  * of P = blockdiag(Z^H Z) by summed-area box sums of the offset Gram
  * products Z_D^H Z_D (Eq. 37); their Cholesky factors P_e = L_e L_e^H
  * (Sec. III-A) and the inverse factors used to apply P^{-1}.
- * blocks: [2Ny-1][2Nx-1][b][b] of dtype (moma_dtype), host or device.
- * Errors: MOMA_ERR_NONFINITE (NaN/Inf in blocks), MOMA_ERR_NOT_PD. */
+ * blocks: [2Ny-1][2Nx-1][b][b] of dtype (moma_dtype), offset (dx, dy) at
+ * index (dy + Ny - 1, dx + Nx - 1), host or device.  The library assumes
+ * reciprocity, Z_{-D} = Z_D^T (Sec. II-D: the MoM matrix is symmetric).
+ * From host memory only the offsets with dy >= 0 are read (Ny (2Nx - 1)
+ * blocks, copied in chunks that overlap the transform and the Gram
+ * products); the rows dy < 0 are completed on the device as transposes.
+ * A device buffer is read whole and must stay valid for the call only.
+ * In MIXED arrays the c128-class bins used by the refinement residual are
+ * computed and stored as double-FP32 pairs (~48 significant bits).
+ * Errors: MOMA_ERR_NONFINITE (NaN/Inf in the blocks read), MOMA_ERR_NOT_PD. */
 moma_status moma_set_blocks(moma_array *a, const void *blocks, int dtype);
 
 /* Apply an operator to nrhs vectors x -> y (layout [nrhs][Ny][Nx][b]).

@@ -29,6 +29,7 @@
 // All waits are bounded; a timeout sets DEVERR_TIMEOUT and the CTA drains
 // its copies and exits.
 #include <algorithm>
+#include <type_traits>
 
 #include "internal.h"
 
@@ -70,12 +71,12 @@ MOMA_DEV void halving_reduce(T (&v)[NV], int lane) {
         if (i < h) {
           const T send = up ? v[i] : v[i + h];
           const T keep = up ? v[i + h] : v[i];
-          v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+          v[i] = keep + shfl_xor(send, o);
         }
       }
       n = h;
     } else {
-      v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+      v[0] += shfl_xor(v[0], o);
     }
   }
 }
@@ -97,6 +98,10 @@ MOMA_DEV void load_pair(const float2 *p, float2 (&z)[2]) {
   const float4 v = *reinterpret_cast<const float4 *>(p);
   z[0] = make_float2(v.x, v.y);
   z[1] = make_float2(v.z, v.w);
+}
+MOMA_DEV void load_pair(const dfl2 *p, dfl2 (&z)[2]) {
+  z[0] = p[0];
+  z[1] = p[1];
 }
 MOMA_DEV void load_pair(const double2 *p, double2 (&z)[2]) {
   z[0] = p[0];
@@ -385,9 +390,12 @@ void launch_bin_product(const BinProduct &P, int num_sms, cudaStream_t st) {
   // RHS are processed in chunks of up to NRMAX columns (the kernel masks
   // columns past nr); each chunk streams the bins once.
   constexpr int NRMAX = sizeof(R) == 4 ? 4 : 2;
-  for (int q0 = 0; q0 < P.nr; q0 += NRMAX) {
+  // Double-FP32 accumulators of wide blocks (b > 128) take one RHS per
+  // chunk so that they stay in registers.
+  const int nrmax = (std::is_same<R, dfl>::value && P.b > 128) ? 1 : NRMAX;
+  for (int q0 = 0; q0 < P.nr; q0 += nrmax) {
     const int left = P.nr - q0;
-    if (left == 1) launch_nr<R, 1>(P, num_sms, st, q0);
+    if (left == 1 || nrmax == 1) launch_nr<R, 1>(P, num_sms, st, q0);
     else if (left == 2) launch_nr<R, 2>(P, num_sms, st, q0);
     else launch_nr<R, NRMAX>(P, num_sms, st, q0);
   }
@@ -395,5 +403,6 @@ void launch_bin_product(const BinProduct &P, int num_sms, cudaStream_t st) {
 
 template void launch_bin_product<float>(const BinProduct &, int, cudaStream_t);
 template void launch_bin_product<double>(const BinProduct &, int, cudaStream_t);
+template void launch_bin_product<dfl>(const BinProduct &, int, cudaStream_t);
 
 }  // namespace moma

@@ -8,12 +8,78 @@
 #define MOMA_DEV __device__ __forceinline__
 #define MOMA_HD __host__ __device__ __forceinline__
 
+// ---- double-FP32 ("dfl") arithmetic -------------------------------------
+// A value hi + lo of two floats with |lo| <= ulp(hi) / 2: about 48
+// significant bits (relative rounding ~2^-47), carried on the FP32 pipes.
+// B300 runs FP64 at ~1/58 of its FP32 rate, so the FP64-bound stages of
+// the mixed path (block-bin transform, residual bin product and FFTs)
+// compute in dfl.  Built from error-free transformations: Knuth's
+// two-sum, Dekker's fast two-sum (|a| >= |b|) and the FMA two-product;
+// every step uses the _rn intrinsics so that the compiler cannot contract
+// or reassociate them.  Addition is the "sloppy" variant (one two-sum on
+// the high parts), whose error is bounded by ~2^-46 (|a| + |b|): enough for
+// sums of products and FFT butterflies, whose error analysis is normwise.
+struct dfl {
+  float hi, lo;
+  dfl() = default;
+  MOMA_HD constexpr dfl(float h, float l) : hi(h), lo(l) {}
+  MOMA_HD constexpr dfl(float v) : hi(v), lo(0.0f) {}
+  MOMA_HD dfl(double v) : hi((float)v), lo((float)(v - (double)(float)v)) {}
+  MOMA_HD dfl(int v) : dfl((double)v) {}
+  MOMA_HD explicit operator double() const { return (double)hi + (double)lo; }
+};
+struct __align__(16) dfl2 {
+  dfl x, y;
+};
+
+#ifdef __CUDACC__
+MOMA_DEV dfl df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bp = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+  return dfl(s, e);
+}
+MOMA_DEV dfl df_fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return dfl(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+MOMA_DEV dfl operator+(dfl a, dfl b) {
+  const dfl s = df_two_sum(a.hi, b.hi);
+  return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+MOMA_DEV dfl operator-(dfl a) { return dfl(-a.hi, -a.lo); }
+MOMA_DEV dfl operator-(dfl a, dfl b) { return a + (-b); }
+MOMA_DEV dfl operator*(dfl a, dfl b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+  return df_fast_two_sum(p, e);
+}
+// c + a*b with one renormalisation.
+MOMA_DEV dfl fma(dfl a, dfl b, dfl c) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+  const dfl s = df_two_sum(c.hi, p);
+  return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(e, c.lo)));
+}
+MOMA_DEV dfl operator/(dfl a, dfl b) {
+  const float q1 = __fdiv_rn(a.hi, b.hi);
+  const dfl r = a - b * dfl(q1, 0.0f);
+  return df_fast_two_sum(q1, __fdiv_rn(r.hi, b.hi));
+}
+MOMA_DEV dfl &operator+=(dfl &a, dfl b) { return a = a + b; }
+MOMA_DEV dfl &operator*=(dfl &a, dfl b) { return a = a * b; }
+#endif
+
 template <typename R> struct Cplx;
 template <> struct Cplx<float> { using T = float2; };
 template <> struct Cplx<double> { using T = double2; };
+template <> struct Cplx<dfl> { using T = dfl2; };
 
 MOMA_HD float2 mk(float a, float b) { return make_float2(a, b); }
 MOMA_HD double2 mk(double a, double b) { return make_double2(a, b); }
+MOMA_HD dfl2 mk(dfl a, dfl b) { dfl2 r; r.x = a; r.y = b; return r; }
 
 template <typename C> MOMA_HD C cadd(C a, C b) { C r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
 template <typename C> MOMA_HD C csub(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
@@ -57,10 +123,18 @@ MOMA_HD float2 to_c(float2 v, float2*) { return v; }
 MOMA_HD float2 to_c(double2 v, float2*) { return make_float2((float)v.x, (float)v.y); }
 MOMA_HD double2 to_c(float2 v, double2*) { return make_double2(v.x, v.y); }
 MOMA_HD double2 to_c(double2 v, double2*) { return v; }
+MOMA_HD dfl2 to_c(float2 v, dfl2*) { dfl2 r; r.x = dfl(v.x); r.y = dfl(v.y); return r; }
+MOMA_HD dfl2 to_c(double2 v, dfl2*) { dfl2 r; r.x = dfl(v.x); r.y = dfl(v.y); return r; }
+MOMA_HD dfl2 to_c(dfl2 v, dfl2*) { return v; }
+MOMA_HD float2 to_c(dfl2 v, float2*) { return make_float2(v.x.hi + v.x.lo, v.y.hi + v.y.lo); }
+MOMA_HD double2 to_c(dfl2 v, double2*) { return make_double2((double)v.x, (double)v.y); }
 template <typename Cout, typename Cin> MOMA_HD Cout cvt(Cin v) { return to_c(v, (Cout*)nullptr); }
 
 MOMA_DEV float shfl_xor(float v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
 MOMA_DEV double shfl_xor(double v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+MOMA_DEV dfl shfl_xor(dfl v, int m) {
+  return dfl(__shfl_xor_sync(0xffffffffu, v.hi, m), __shfl_xor_sync(0xffffffffu, v.lo, m));
+}
 
 template <typename C> MOMA_DEV C warp_sum(C v) {
 #pragma unroll

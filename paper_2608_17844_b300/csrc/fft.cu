@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <stdexcept>
+#include <type_traits>
 
 #include "internal.h"
 
@@ -194,6 +195,13 @@ static void launch_typed(const AxisPass &p, const FftTables &t, cudaStream_t st)
   const long long ctas = (long long)((p.ninner + 31) / 32) * p.n1 * p.n2;
   while (G * 2 <= gmax && ctas * G < 24LL * 148) G *= 2;
   if (p.G > 0) G = std::min(p.G, 32);
+  // Never more threads than the compiled kernel's registers allow.
+  static int max_threads = 0;
+  if (!max_threads) {
+    cudaFuncAttributes attr{};
+    max_threads = cudaFuncGetAttributes(&attr, axis_kernel<R, Cin, Cout>) == cudaSuccess ? attr.maxThreadsPerBlock : 256;
+  }
+  while (G > 1 && 32 * G > max_threads) G >>= 1;
   const size_t head = ((size_t)M * sizeof(C) + (size_t)M * sizeof(int) + 15) & ~size_t(15);
   const size_t smem = head + (size_t)M * 32 * sizeof(C);
   static int configured = 0;
@@ -204,20 +212,36 @@ static void launch_typed(const AxisPass &p, const FftTables &t, cudaStream_t st)
   dim3 grid((p.ninner + 31) / 32, p.n1 * p.n2);
   AxisKernelArgs a{p, t.plan};
   const C *tw = nullptr;
-  if constexpr (sizeof(R) == 8) tw = t.tw64; else tw = t.tw32;
+  if constexpr (std::is_same<R, double>::value) tw = t.tw64;
+  else if constexpr (std::is_same<R, dfl>::value) tw = t.twdf;
+  else tw = t.tw32;
   axis_kernel<R, Cin, Cout><<<grid, 32 * G, smem, st>>>(a, tw, t.pos);
 }
 
+// Element types of the pass's input / output: 0 = c64, 1 = c128, 2 = dfl2.
 template <typename R>
 void launch_axis_pass(const AxisPass &p, const FftTables &t, cudaStream_t st) {
   if (p.ninner <= 0 || p.n1 * p.n2 <= 0) return;
-  if (p.in_c128 && p.out_c128) launch_typed<R, double2, double2>(p, t, st);
-  else if (p.in_c128) launch_typed<R, double2, float2>(p, t, st);
-  else if (p.out_c128) launch_typed<R, float2, double2>(p, t, st);
-  else launch_typed<R, float2, float2>(p, t, st);
+  const int io = p.in_c128 * 3 + p.out_c128;
+  if constexpr (std::is_same<R, dfl>::value) {
+    switch (io) {
+      case 0 * 3 + 2: launch_typed<R, float2, dfl2>(p, t, st); break;
+      case 1 * 3 + 2: launch_typed<R, double2, dfl2>(p, t, st); break;
+      case 2 * 3 + 2: launch_typed<R, dfl2, dfl2>(p, t, st); break;
+      case 2 * 3 + 1: launch_typed<R, dfl2, double2>(p, t, st); break;
+      default: throw std::runtime_error("axis pass: unsupported element types for dfl");
+    }
+  } else {
+    if (p.in_c128 > 1 || p.out_c128 > 1) throw std::runtime_error("axis pass: dfl2 storage needs dfl arithmetic");
+    if (p.in_c128 && p.out_c128) launch_typed<R, double2, double2>(p, t, st);
+    else if (p.in_c128) launch_typed<R, double2, float2>(p, t, st);
+    else if (p.out_c128) launch_typed<R, float2, double2>(p, t, st);
+    else launch_typed<R, float2, float2>(p, t, st);
+  }
 }
 
 template void launch_axis_pass<float>(const AxisPass &, const FftTables &, cudaStream_t);
 template void launch_axis_pass<double>(const AxisPass &, const FftTables &, cudaStream_t);
+template void launch_axis_pass<dfl>(const AxisPass &, const FftTables &, cudaStream_t);
 
 }  // namespace moma

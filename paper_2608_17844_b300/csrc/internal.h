@@ -18,6 +18,7 @@ struct FftTables {
   FftPlan plan;
   double2 *tw64 = nullptr;  // [M]
   float2 *tw32 = nullptr;   // [M]
+  dfl2 *twdf = nullptr;     // [M] twiddles as double-FP32 pairs
   int *pos = nullptr;       // [M]
 };
 
@@ -48,7 +49,7 @@ struct AxisPass {
   const int2 *tri = nullptr;          // out_mode 2: inner j -> block entry (i, j), i <= j
   int inverse = 0;         // conj(DFT(conj x)) / M
   int refft_keep = 0;      // >0: inverse, keep points < refft_keep, zero the rest, forward again
-  int in_c128 = 1, out_c128 = 1;  // element types of in / out
+  int in_c128 = 1, out_c128 = 1;  // element types of in / out: 0 c64, 1 c128, 2 dfl2
   const int *live = nullptr;       // if set and *live == 0 the pass does nothing
   int G = 0;                       // threads per line (0 = heuristic; set by the autotuner)
 };

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <memory>
+#include <type_traits>
 #include <thread>
 #include <cstring>
 #include <mutex>
@@ -77,10 +78,27 @@ struct DevBuf {
 __global__ void nonfinite_kernel(const void *p, size_t n_real, int is_double, unsigned *err) {
   bool bad = false;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n_real; i += (size_t)gridDim.x * blockDim.x) {
-    const double v = is_double ? reinterpret_cast<const double *>(p)[i] : (double)reinterpret_cast<const float *>(p)[i];
-    if (!isfinite(v)) bad = true;
+    if (is_double ? !isfinite(reinterpret_cast<const double *>(p)[i]) : !isfinite(reinterpret_cast<const float *>(p)[i]))
+      bad = true;
   }
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(err, DEVERR_NONFINITE);
+}
+
+// Reciprocity completion of the staged blocks (Sec. II-D: Z_{-D} = Z_D^T):
+// rows (dy index) m in [m0, m1) receive Z[m][ix] = Z[2Ny-2-m][2Nx-2-ix]^T.
+template <typename C>
+__global__ void reciprocal_fill_kernel(C *Z, int ndy, int ndx, int b, int m0) {
+  __shared__ C tile[32][33];
+  const int blk = blockIdx.z, m = m0 + blk / ndx, ix = blk % ndx;
+  const size_t bb = (size_t)b * b;
+  const C *src = Z + ((size_t)(ndy - 1 - m) * ndx + (ndx - 1 - ix)) * bb;
+  C *dst = Z + ((size_t)m * ndx + ix) * bb;
+  const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32, tx = threadIdx.x, ty = threadIdx.y;
+  for (int r = ty; r < 32; r += 8)  // tile[r][tx] = src[j0 + r][i0 + tx]
+    if (j0 + r < b && i0 + tx < b) tile[r][tx] = src[(size_t)(j0 + r) * b + i0 + tx];
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8)  // dst[i0 + r][j0 + tx] = src[j0 + tx][i0 + r]
+    if (i0 + r < b && j0 + tx < b) dst[(size_t)(i0 + r) * b + j0 + tx] = tile[tx][r];
 }
 
 enum {
@@ -118,6 +136,8 @@ struct moma_array {
 
   // set-up workspace
   DevBuf blk, T, S, Lpk;
+  cudaStream_t cs = nullptr;  // host-to-device copies of the blocks
+  cudaEvent_t ev_cs0 = nullptr, ev_chunk[8] = {};
   // solve workspace
   int ws_nr = 0;
   DevBuf lat_in, lat_tmp, t1, bx, by, Vk;
@@ -218,7 +238,7 @@ void build_tables(moma_array *a) {
   auto px = digit_reversal(a->fx.plan), py = digit_reversal(a->fy.plan);
   const int Ms[2] = {a->Mx, a->My};
   size_t bytes = 0;
-  for (int M : Ms) bytes += (size_t)M * (sizeof(double2) + sizeof(float2) + sizeof(int)) + 256;
+  for (int M : Ms) bytes += (size_t)M * (sizeof(double2) + sizeof(float2) + sizeof(dfl2) + sizeof(int)) + 256;
   a->tabs.ensure(bytes, a->dev_bytes);
   std::vector<unsigned char> host(bytes, 0);
   size_t off = 0;
@@ -232,6 +252,10 @@ void build_tables(moma_array *a) {
     float2 *t32 = reinterpret_cast<float2 *>(host.data() + off);
     tt[d]->tw32 = reinterpret_cast<float2 *>(a->tabs.as<unsigned char>() + off);
     off += (size_t)M * sizeof(float2);
+    off = (off + 15) & ~size_t(15);
+    dfl2 *tdf = reinterpret_cast<dfl2 *>(host.data() + off);
+    tt[d]->twdf = reinterpret_cast<dfl2 *>(a->tabs.as<unsigned char>() + off);
+    off += (size_t)M * sizeof(dfl2);
     int *ps = reinterpret_cast<int *>(host.data() + off);
     tt[d]->pos = reinterpret_cast<int *>(a->tabs.as<unsigned char>() + off);
     off += (size_t)M * sizeof(int);
@@ -240,6 +264,8 @@ void build_tables(moma_array *a) {
       const double ang = -2.0 * M_PI * (double)t / (double)M;
       t64[t] = make_double2(std::cos(ang), std::sin(ang));
       t32[t] = make_float2((float)t64[t].x, (float)t64[t].y);
+      tdf[t].x = dfl(t64[t].x);
+      tdf[t].y = dfl(t64[t].y);
       ps[t] = (*pp[d])[t];
     }
   }
@@ -323,7 +349,7 @@ AxisPass pass_iy(moma_array *a, int nr, const void *in, void *out, int c128) {
   p.in_c128 = p.out_c128 = c128;
   return p;
 }
-AxisPass pass_ix(moma_array *a, int nr, const void *in, void *out, int c128, bool mask_refft) {
+AxisPass pass_ix(moma_array *a, int nr, const void *in, void *out, int c128, bool mask_refft, int out_code = -1) {
   AxisPass p;
   p.in = in; p.out = out; p.n1 = nr; p.n2 = a->ny; p.ninner = a->b; p.inverse = 1;
   p.in_s1 = (long long)a->ny * a->Mx * a->b; p.in_s2 = (long long)a->Mx * a->b; p.in_sm = a->b; p.nin = a->Mx;
@@ -333,11 +359,19 @@ AxisPass pass_ix(moma_array *a, int nr, const void *in, void *out, int c128, boo
   } else {
     p.out_s1 = (long long)a->ny * a->nx * a->b; p.out_s2 = (long long)a->nx * a->b; p.out_sm = a->b; p.nout = a->nx;
   }
-  p.in_c128 = p.out_c128 = c128;
+  p.in_c128 = c128;
+  p.out_c128 = out_code < 0 ? c128 : out_code;
   return p;
 }
 
 template <typename R> constexpr int is64() { return sizeof(R) == 8 ? 1 : 0; }
+// Storage code of the element type an R computation keeps between passes
+// (0 = c64, 1 = c128, 2 = double-FP32 pairs) and of its lattice vectors
+// (the double-FP32 path reads and writes c128 lattice vectors).
+template <typename R> constexpr int st_code() {
+  return std::is_same<R, float>::value ? 0 : (std::is_same<R, double>::value ? 1 : 2);
+}
+template <typename R> constexpr int lat_code() { return std::is_same<R, float>::value ? 0 : 1; }
 
 long long axis_sig(const AxisPass &p, int M, int is64v) {
   long long h = is64v;
@@ -357,7 +391,7 @@ int tuned_G(const moma_array *a, long long sig) {
 template <typename R>
 void axis(moma_array *a, AxisPass p, const FftTables &t) {
   p.live = a->live;
-  if (p.G == 0) p.G = tuned_G(a, axis_sig(p, t.plan.M, is64<R>()));
+  if (p.G == 0) p.G = tuned_G(a, axis_sig(p, t.plan.M, st_code<R>()));
   a->timed(is64<R>() ? PK_FFT128 : PK_FFT64, [&] { launch_axis_pass<R>(p, t, a->st); });
   check_launch(a);
 }
@@ -408,19 +442,19 @@ void precond(moma_array *a, int nr, const void *x, void *y) {
 // lattice -> bins (Fx then Fy); in may be c128 when R is double.
 template <typename R>
 void lattice_to_bins(moma_array *a, int nr, const void *in, int in128) {
-  axis<R>(a, pass_fx(a, nr, in, a->t1.p, in128, is64<R>()), a->fx);
-  axis<R>(a, pass_fy(a, nr, a->t1.p, a->bx.p, is64<R>()), a->fy);
+  axis<R>(a, pass_fx(a, nr, in, a->t1.p, in128, st_code<R>()), a->fx);
+  axis<R>(a, pass_fy(a, nr, a->t1.p, a->bx.p, st_code<R>()), a->fy);
 }
 template <typename R>
 void bins_to_lattice(moma_array *a, int nr, const void *bins, void *out) {
-  axis<R>(a, pass_iy(a, nr, bins, a->t1.p, is64<R>()), a->fy);
-  axis<R>(a, pass_ix(a, nr, a->t1.p, out, is64<R>(), false), a->fx);
+  axis<R>(a, pass_iy(a, nr, bins, a->t1.p, st_code<R>()), a->fy);
+  axis<R>(a, pass_ix(a, nr, a->t1.p, out, st_code<R>(), false, lat_code<R>()), a->fx);
 }
 
 // y = Z x (herm = 0) or Z^H x (herm = 1), lattice in/out in precision R.
 template <typename R>
 void apply_z(moma_array *a, int nr, const void *x, void *y, int herm) {
-  lattice_to_bins<R>(a, nr, x, is64<R>());
+  lattice_to_bins<R>(a, nr, x, lat_code<R>());
   binprod<R>(a, nr, a->bx.p, a->by.p, herm);
   bins_to_lattice<R>(a, nr, a->by.p, y);
 }
@@ -607,12 +641,20 @@ void copy_out(moma_array *a, void *dst, const void *src, size_t bytes) {
   CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, a->st));
 }
 
+// Gram products G_D = Z_D^H Z_D of offsets [d0, d0 + nd) into S.
 template <typename R>
-void build_preconditioner(moma_array *a, const void *blk, int blk128) {
-  const int nD = (2 * a->nx - 1) * (2 * a->ny - 1), bb = a->b * a->b;
-  a->S.ensure((size_t)nD * bb * sizeof(double2), a->dev_bytes);
-  a->timed(PK_GRAM, [&] { launch_gram<R>(blk, blk128, nD, a->b, a->S.as<double2>(), a->st); });
+void gram_chunk(moma_array *a, const void *blk, int blk128, int d0, int nd) {
+  const size_t bb = (size_t)a->b * a->b, esz = blk128 ? sizeof(double2) : sizeof(float2);
+  const void *src = static_cast<const unsigned char *>(blk) + (size_t)d0 * bb * esz;
+  a->timed(PK_GRAM, [&] { launch_gram<R>(src, blk128, nd, a->b, a->S.as<double2>() + (size_t)d0 * bb, a->st); });
   check_launch(a);
+}
+
+// Summed-area table, box sums + Cholesky, inverse factors (after every
+// offset's Gram product is in S).
+template <typename R>
+void finish_preconditioner(moma_array *a) {
+  const int bb = a->b * a->b;
   a->timed(PK_SAT, [&] { launch_sat(a->S.as<double2>(), 2 * a->ny - 1, 2 * a->nx - 1, bb, a->st); });
   check_launch(a);
   const size_t npk = (size_t)a->b * (a->b + 1) / 2;
@@ -631,41 +673,110 @@ void build_preconditioner(moma_array *a, const void *blk, int blk128) {
 void set_blocks_impl(moma_array *a, const void *blocks, int dtype) {
   if (dtype != MOMA_C128 && dtype != MOMA_C64) throw MomaError(MOMA_ERR_ARG, "blocks dtype must be MOMA_C128 or MOMA_C64");
   if (!blocks) throw MomaError(MOMA_ERR_ARG, "blocks is NULL");
-  const int nD = (2 * a->nx - 1) * (2 * a->ny - 1), bb = a->b * a->b;
+  const int ndy = 2 * a->ny - 1, ndx = 2 * a->nx - 1, nD = ndx * ndy, bb = a->b * a->b;
   const size_t esz = dtype == MOMA_C128 ? sizeof(double2) : sizeof(float2);
-  const void *blk = stage_in(a, blocks, (size_t)nD * bb * esz, a->blk);
+  const size_t row_bytes = (size_t)ndx * bb * esz;  // one dy row of offsets
   a->have_blocks = false;
   a->tc_ready = false;
-  check_finite(a, blk, (size_t)nD * bb * 2, dtype == MOMA_C128);
-  sync_and_check(a);
 
-  // Transformed first column of the circulant embedding (Eqs. 3, 11), FP64.
+  // Transformed first column of the circulant embedding (Eqs. 3, 11).
   // Reciprocity (Z_{-D} = Z_D^T) makes Zhat_{-k} = Zhat_k^T, so only the
   // b(b+1)/2 entries i <= j are transformed; the y pass scatters each bin's
   // values into the stored block of its pair (transposed for the partner).
+  // FP64 in the plain path; double-FP32 pairs (c128-class bins stored as
+  // dfl2) in the mixed path, where B300's FP64 rate would bound it.
+  const bool df = a->prec == MOMA_PREC_MIXED;
   const int nt = a->b * (a->b + 1) / 2;
-  a->T.ensure((size_t)(2 * a->ny - 1) * a->Mx * nt * sizeof(double2), a->dev_bytes);
+  a->T.ensure((size_t)ndy * a->Mx * nt * sizeof(double2), a->dev_bytes);
+  a->S.ensure((size_t)nD * bb * sizeof(double2), a->dev_bytes);
+
+  // Blocks in host memory: only the rows dy >= 0 cross the bus (the rows
+  // dy < 0 are their transposes by reciprocity and are completed on the
+  // device), in chunks of rows on a copy stream; each chunk's finiteness
+  // check, completion, x-pass of the block transform and Gram products start
+  // as soon as it has landed, overlapping the next copy.  Blocks already on
+  // the device are read whole.
+  const bool host = !is_device_ptr(blocks);
+  const unsigned char *blk = static_cast<const unsigned char *>(blocks);
+  const int yh = a->ny - 1;  // row index of dy = 0
+  int nchunk = 1, r0 = 0;
+  if (host) {
+    a->blk.ensure((size_t)ndy * row_bytes, a->dev_bytes);
+    blk = a->blk.as<unsigned char>();
+    r0 = yh;
+    nchunk = std::min(ndy - yh, 8);
+    if (!a->cs) {
+      CK(cudaStreamCreateWithFlags(&a->cs, cudaStreamNonBlocking));
+      CK(cudaEventCreateWithFlags(&a->ev_cs0, cudaEventDisableTiming));
+      for (auto &e : a->ev_chunk) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    CK(cudaEventRecord(a->ev_cs0, a->st));  // earlier work on the staging buffer is done
+    CK(cudaStreamWaitEvent(a->cs, a->ev_cs0, 0));
+  }
   AxisPass px;
-  px.in = blk; px.out = a->T.p; px.n1 = 2 * a->ny - 1; px.n2 = 1; px.ninner = nt;
-  px.in_s1 = (long long)(2 * a->nx - 1) * bb; px.in_sm = bb; px.nin = 2 * a->nx - 1; px.in_mode = 1;
+  px.n2 = 1; px.ninner = nt;
+  px.in_s1 = (long long)ndx * bb; px.in_sm = bb; px.nin = ndx; px.in_mode = 1;
   px.inner_in_map = a->tri_in.as<int>();
   px.out_s1 = (long long)a->Mx * nt; px.out_sm = nt; px.nout = a->Mx;
-  px.in_c128 = dtype == MOMA_C128; px.out_c128 = 1;
-  a->timed(PK_BLOCKFFT, [&] { launch_axis_pass<double>(px, a->fx, a->st); });
-  check_launch(a);
+  px.in_c128 = dtype == MOMA_C128; px.out_c128 = df ? 2 : 1;
+  auto rows_work = [&](int y0, int y1) {  // transform x-pass + Gram of rows [y0, y1)
+    if (y1 <= y0) return;
+    px.in = blk + (size_t)y0 * row_bytes; px.n1 = y1 - y0;
+    px.out = a->T.as<double2>() + (size_t)y0 * a->Mx * nt;
+    a->timed(PK_BLOCKFFT, [&] {
+      if (df) launch_axis_pass<dfl>(px, a->fx, a->st);
+      else launch_axis_pass<double>(px, a->fx, a->st);
+    });
+    check_launch(a);
+    // Gram products of these offsets (Eq. 37 precomputation).
+    if (a->prec == MOMA_PREC_FP64) gram_chunk<double>(a, blk, dtype == MOMA_C128, y0 * ndx, (y1 - y0) * ndx);
+    else gram_chunk<float>(a, blk, dtype == MOMA_C128, y0 * ndx, (y1 - y0) * ndx);
+  };
+  const int nrows = ndy - r0;
+  for (int c = 0; c < nchunk; ++c) {
+    const int y0 = r0 + (int)((long long)nrows * c / nchunk), y1 = r0 + (int)((long long)nrows * (c + 1) / nchunk);
+    if (y1 <= y0) continue;
+    unsigned char *dst = const_cast<unsigned char *>(blk) + (size_t)y0 * row_bytes;
+    if (host) {
+      CK(cudaMemcpyAsync(dst, static_cast<const unsigned char *>(blocks) + (size_t)y0 * row_bytes,
+                         (size_t)(y1 - y0) * row_bytes, cudaMemcpyHostToDevice, a->cs));
+      CK(cudaEventRecord(a->ev_chunk[c], a->cs));
+      CK(cudaStreamWaitEvent(a->st, a->ev_chunk[c], 0));
+    }
+    check_finite(a, dst, (size_t)(y1 - y0) * ndx * bb * 2, dtype == MOMA_C128);
+    rows_work(y0, y1);
+    if (host) {
+      // Mirror rows of [y0, y1) below dy = 0: [2Ny-1-y1, 2Ny-1-y0) within [0, yh).
+      const int m0 = std::max(0, ndy - y1), m1 = std::min(yh, ndy - y0);
+      if (m1 > m0) {
+        dim3 grid((a->b + 31) / 32, (a->b + 31) / 32, (m1 - m0) * ndx), block(32, 8);
+        if (dtype == MOMA_C128)
+          reciprocal_fill_kernel<double2><<<grid, block, 0, a->st>>>(a->blk.as<double2>(), ndy, ndx, a->b, m0);
+        else
+          reciprocal_fill_kernel<float2><<<grid, block, 0, a->st>>>(a->blk.as<float2>(), ndy, ndx, a->b, m0);
+        check_launch(a);
+        rows_work(m0, m1);
+      }
+    }
+  }
+  // Non-finite input: report before anything is marked usable.
+  sync_and_check(a);
   AxisPass py;
   py.in = a->T.p; py.out = a->Z128.p; py.out2 = a->prec == MOMA_PREC_MIXED ? a->Z64.p : nullptr;
   py.n1 = a->Mx; py.n2 = 1; py.ninner = nt;
   py.in_s1 = nt; py.in_sm = (long long)a->Mx * nt; py.nin = 2 * a->ny - 1; py.in_mode = 1;
   py.out_mode = 2; py.bin_slot = a->bin_slot.as<int2>(); py.tri = a->tri.as<int2>(); py.slot_mul = a->Mx;
   py.out_sm = (long long)a->b * a->ldb; py.remap_ld = a->ldb; py.nout = a->My;
-  py.in_c128 = 1; py.out_c128 = 1;
-  a->timed(PK_BLOCKFFT, [&] { launch_axis_pass<double>(py, a->fy, a->st); });
+  py.in_c128 = df ? 2 : 1; py.out_c128 = df ? 2 : 1;
+  a->timed(PK_BLOCKFFT, [&] {
+    if (df) launch_axis_pass<dfl>(py, a->fy, a->st);
+    else launch_axis_pass<double>(py, a->fy, a->st);
+  });
   check_launch(a);
 
   // Preconditioner (Eq. 37) and its factorisation (Sec. III-A).
-  if (a->prec == MOMA_PREC_FP64) build_preconditioner<double>(a, blk, dtype == MOMA_C128);
-  else build_preconditioner<float>(a, blk, dtype == MOMA_C128);
+  if (a->prec == MOMA_PREC_FP64) finish_preconditioner<double>(a);
+  else finish_preconditioner<float>(a);
   sync_and_check(a);
   a->have_blocks = true;
 }
@@ -718,19 +829,20 @@ void autotune_precision(moma_array *a, int nr, int in128) {
     }
     a->tune_bin_tr[is64<R>()] = btr;
     a->tune_bin_ns[is64<R>()] = bns;
-    snprintf(buf, sizeof(buf), "bin_product<%s> nr=%d: TR=%d NS=%d (%.1f us)\n", is64<R>() ? "c128" : "c64", nr, btr,
+    snprintf(buf, sizeof(buf), "bin_product<%s> nr=%d: TR=%d NS=%d (%.1f us)\n",
+             st_code<R>() == 2 ? "dfl" : (is64<R>() ? "c128" : "c64"), nr, btr,
              bns, 1000.0f * best / 2);
     a->tune_log += buf;
   }
   // Lattice FFT passes of the products and the normal operator.
-  const int c = is64<R>();
+  const int c = st_code<R>();
   struct Cand { AxisPass p; const FftTables *t; const char *name; };
   const Cand cands[] = {
       {pass_fx(a, nr, a->lat_in.p, a->t1.p, in128, c), &a->fx, "Fx"},
       {pass_fy(a, nr, a->t1.p, a->bx.p, c), &a->fy, "Fy"},
       {pass_iy(a, nr, a->by.p, a->t1.p, c), &a->fy, "Iy"},
       {pass_ix(a, nr, a->t1.p, a->t1.p, c, true), &a->fx, "IxMaskFx"},
-      {pass_ix(a, nr, a->t1.p, a->lat_tmp.p, c, false), &a->fx, "Ix"},
+      {pass_ix(a, nr, a->t1.p, a->lat_tmp.p, c, false, lat_code<R>()), &a->fx, "Ix"},
   };
   for (const Cand &cd : cands) {
     float best = 1e30f;
@@ -743,7 +855,7 @@ void autotune_precision(moma_array *a, int nr, int in128) {
       if (ms < best) { best = ms; bg = G; }
     }
     a->tune_axis.push_back({axis_sig(cd.p, cd.t->plan.M, c), bg});
-    snprintf(buf, sizeof(buf), "%s<%s> nr=%d: G=%d (%.1f us)\n", cd.name, c ? "c128" : "c64", nr, bg,
+    snprintf(buf, sizeof(buf), "%s<%s> nr=%d: G=%d (%.1f us)\n", cd.name, c == 2 ? "dfl" : (c ? "c128" : "c64"), nr, bg,
              1000.0f * best / 2);
     a->tune_log += buf;
   }
@@ -755,7 +867,9 @@ void autotune(moma_array *a, int nr) {
   a->tune_log.clear();
   a->tune_bin_tr[0] = a->tune_bin_tr[1] = a->tune_bin_ns[0] = a->tune_bin_ns[1] = 0;
   if (a->prec == MOMA_PREC_MIXED) autotune_precision<float>(a, nr, 0);
-  autotune_precision<double>(a, nr, 1);
+  // The FP64-class residual runs in double-FP32 pairs in the mixed path.
+  if (a->prec == MOMA_PREC_MIXED) autotune_precision<dfl>(a, nr, 1);
+  else autotune_precision<double>(a, nr, 1);
   a->tuned_nr = nr;
 }
 
@@ -996,6 +1110,9 @@ void pcg_cycle(moma_array *a, int nr, const std::vector<int> &act, int max_inner
 template <typename R>
 void solve_impl(moma_array *a, int nr, const void *Vin, void *Iout, const moma_solve_opts *o, moma_solve_info *info,
                 double *relres) {
+  // Arithmetic of the refinement residual V - Z I: FP64 in the plain path,
+  // double-FP32 pairs (~48 bits) in the mixed path.
+  using H = typename std::conditional<std::is_same<R, float>::value, dfl, double>::type;
   const double tol = (o && o->tol > 0) ? o->tol : 1e-10;
   const double itol = (o && o->inner_tol > 0) ? o->inner_tol : (is64<R>() ? tol * 0.1 : 1e-5);
   const int max_outer = (o && o->max_outer > 0) ? o->max_outer : 30;
@@ -1050,7 +1167,7 @@ void solve_impl(moma_array *a, int nr, const void *Vin, void *Iout, const moma_s
     if (outer == 0 && !warm) {
       a->timed(PK_MISC, [&] { launch_resid(a->Vw.as<double2>(), nullptr, a->rw.as<double2>(), a->N, nr, a->rpart, a->rcount, a->rnorm, a->st); });
     } else {
-      apply_z<double>(a, nr, a->Iw.p, a->yw.p, 0);
+      apply_z<H>(a, nr, a->Iw.p, a->yw.p, 0);
       a->timed(PK_MISC, [&] { launch_resid(a->Vw.as<double2>(), a->yw.as<double2>(), a->rw.as<double2>(), a->N, nr, a->rpart, a->rcount,
                    a->rnorm, a->st); });
     }
@@ -1111,8 +1228,15 @@ template <typename F> moma_status guarded(F &&f) {
 void destroy_impl(moma_array *a) {
   DevBuf *bufs[] = {&a->tabs, &a->pairs, &a->slot_of, &a->bin_slot, &a->tri, &a->tri_in, &a->Z128, &a->Z64, &a->Xinv, &a->blk, &a->T, &a->S,
                     &a->Lpk, &a->lat_in, &a->lat_tmp, &a->t1, &a->bx, &a->by, &a->Vk, &a->Iw, &a->Vw,
-                    &a->rw, &a->yw, &a->kbuf, &a->errbuf, &a->one_blk, &a->portsb, &a->zp_V, &a->zp_I, &a->zp_Y, &a->zp_tmp};
+                    &a->rw, &a->yw, &a->kbuf, &a->errbuf, &a->one_blk, &a->portsb, &a->zp_V, &a->zp_I, &a->zp_Y, &a->zp_tmp,
+                    &a->tcA, &a->tcP, &a->partner};
   for (DevBuf *b : bufs) b->release(a->dev_bytes);
+  if (a->cs) {
+    cudaStreamSynchronize(a->cs);
+    cudaStreamDestroy(a->cs);
+    cudaEventDestroy(a->ev_cs0);
+    for (auto e : a->ev_chunk) cudaEventDestroy(e);
+  }
   if (a->h_nact) cudaFreeHost(a->h_nact);
   if (a->h_norms) cudaFreeHost(a->h_norms);
   if (a->h_err) cudaFreeHost(a->h_err);
@@ -1208,6 +1332,7 @@ moma_status moma_matvec(moma_array *a, int op, int nrhs, const void *x, void *y,
     CK(cudaMemcpyAsync(a->Vw.p, x, bytes, cudaMemcpyDefault, a->st));
     if (d64) {
       if (op == MOMA_OP_NORMAL) apply_normal<double>(a, nrhs, a->Vw.p, a->yw.p);
+      else if (a->prec == MOMA_PREC_MIXED) apply_z<dfl>(a, nrhs, a->Vw.p, a->yw.p, op == MOMA_OP_ZH);
       else apply_z<double>(a, nrhs, a->Vw.p, a->yw.p, op == MOMA_OP_ZH);
     } else {
       if (op == MOMA_OP_NORMAL) apply_normal<float>(a, nrhs, a->Vw.p, a->yw.p);
@@ -1258,10 +1383,20 @@ moma_status moma_get_bin(moma_array *a, int kx, int ky, int dtype, void *out) {
     CK(cudaMemcpy(blk.data(), (const unsigned char *)src + (size_t)s * b * ldb * esz, blk.size(),
                   cudaMemcpyDeviceToHost));
     const bool transpose = k != canon;
+    // In the mixed path the c128-class bins are stored as double-FP32 pairs.
+    const bool from_df = dtype == MOMA_C128 && a->prec == MOMA_PREC_MIXED;
     for (int i = 0; i < b; ++i)
       for (int j = 0; j < b; ++j) {
         const int si = transpose ? j : i, sj = transpose ? i : j;
-        std::memcpy(&res[((size_t)i * b + j) * esz], &blk[((size_t)si * ldb + sj) * esz], esz);
+        const unsigned char *e = &blk[((size_t)si * ldb + sj) * esz];
+        if (from_df) {
+          dfl2 v;
+          std::memcpy(&v, e, sizeof(v));
+          const double2 d = make_double2((double)v.x, (double)v.y);
+          std::memcpy(&res[((size_t)i * b + j) * esz], &d, esz);
+        } else {
+          std::memcpy(&res[((size_t)i * b + j) * esz], e, esz);
+        }
       }
     if (is_device_ptr(out)) CK(cudaMemcpy(out, res.data(), res.size(), cudaMemcpyHostToDevice));
     else std::memcpy(out, res.data(), res.size());
@@ -1641,20 +1776,20 @@ void noalloc_product(moma_array *a, int nr, const void *x, void *y, int herm, un
   unsigned char *t1 = scratch;
   unsigned char *bx = t1 + align256((size_t)nr * a->ny * a->Mx * a->b * esz);
   unsigned char *by = bx + align256((size_t)a->B * nr * a->b * esz);
-  const int c = is64<R>();
-  launch_axis_pass<R>(pass_fx(a, nr, x, t1, c, c), a->fx, a->st);
+  const int c = st_code<R>(), lc = lat_code<R>();
+  launch_axis_pass<R>(pass_fx(a, nr, x, t1, lc, c), a->fx, a->st);
   check_launch(a);
   launch_axis_pass<R>(pass_fy(a, nr, t1, bx, c), a->fy, a->st);
   check_launch(a);
   BinProduct P;
-  P.Z = c ? a->Z128.p : a->Z64.p;
+  P.Z = is64<R>() ? a->Z128.p : a->Z64.p;
   P.pairs = a->pairs.as<int2>();
   P.x = bx; P.y = by; P.Bp = a->Bp; P.b = a->b; P.ldb = a->ldb; P.nr = nr; P.herm = herm; P.err = a->err;
   launch_bin_product<R>(P, a->num_sms, a->st);
   check_launch(a);
   launch_axis_pass<R>(pass_iy(a, nr, by, t1, c), a->fy, a->st);
   check_launch(a);
-  launch_axis_pass<R>(pass_ix(a, nr, t1, y, c, false), a->fx, a->st);
+  launch_axis_pass<R>(pass_ix(a, nr, t1, y, c, false, lc), a->fx, a->st);
   check_launch(a);
 }
 
@@ -1681,7 +1816,8 @@ extern "C" moma_status moma_matvec_noalloc(moma_array *a, int op, int nrhs, cons
     int dev = 0;
     CK(cudaGetDevice(&dev));
     unsigned char *scratch = static_cast<unsigned char *>(noalloc_scratch(dev));
-    if (d64) noalloc_product<double>(a, nrhs, x, y, op == MOMA_OP_ZH, scratch);
+    if (d64 && a->prec == MOMA_PREC_MIXED) noalloc_product<dfl>(a, nrhs, x, y, op == MOMA_OP_ZH, scratch);
+    else if (d64) noalloc_product<double>(a, nrhs, x, y, op == MOMA_OP_ZH, scratch);
     else noalloc_product<float>(a, nrhs, x, y, op == MOMA_OP_ZH, scratch);
     sync_and_check(a);
   });

@@ -74,7 +74,8 @@ def test_autotuner_reports_choices(moma_lib, cuda):
             I = np.zeros_like(V)
             m.moma_solve(x, V, I)
         rep = m.moma_tuning_report(h)
-        assert "bin_product<c64>" in rep and "IxMaskFx<c64>" in rep and "Fx<c128>" in rep
+        # inner passes in c64, the refinement residual's in double-FP32 pairs
+        assert "bin_product<c64>" in rep and "IxMaskFx<c64>" in rep and "Fx<dfl>" in rep and "bin_product<dfl>" in rep
         assert m.moma_tuning_report(h2) == ""
     finally:
         m.moma_destroy(h)

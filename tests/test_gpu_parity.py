@@ -337,3 +337,31 @@ def test_pcg_solve_matches_dense_lu(moma_lib, cuda, nx, ny, b, d, prec):
         RAW_ERRORS[f"pcg_first_inner_reduction {nx}x{ny}x{b} prec={prec}"] = info["first_inner_reduction"]
     finally:
         m.moma_destroy(h)
+
+
+@pytest.mark.parametrize("nx,ny,b,prec", [(5, 4, 12, MIXED), (3, 1, 8, FP64), (4, 2, 6, MIXED), (6, 7, 5, FP64)])
+def test_host_blocks_read_only_upper_rows(moma_lib, cuda, nx, ny, b, prec):
+    """From host memory only the offsets with dy >= 0 are read; the rows
+    dy < 0 are completed by reciprocity.  Overwriting them with unrelated
+    finite values changes nothing, and host and device inputs agree."""
+    m = moma_lib
+    import torch
+    spec = LatticeSpec(nx, ny, b, 0.5, 6)
+    dt = np.complex128 if prec == FP64 else np.complex64
+    blocks = offset_blocks(spec, dt)
+    junk = blocks.copy()
+    rng = np.random.default_rng(9)
+    junk[:ny - 1] = (rng.standard_normal(junk[:ny - 1].shape) + 1j * rng.standard_normal(junk[:ny - 1].shape)).astype(dt)
+    V = excitation(spec, [(0.0, 0.0), (30.0, 20.0)])
+    out = []
+    for src in (blocks, junk, torch.from_numpy(blocks).cuda()):
+        h = m.moma_create_array(nx, ny, b, prec)
+        try:
+            m.moma_set_blocks(h, src)
+            I = np.zeros_like(V)
+            m.moma_solve(h, V, I)
+            out.append(I)
+        finally:
+            m.moma_destroy(h)
+    assert np.array_equal(out[0], out[1])
+    assert np.array_equal(out[0], out[2])
