@@ -641,8 +641,11 @@ def main():
             t = torch.tensor([dt], device="cuda")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             dt = float(t.item())
+        # Host blocks: the library copies the offsets with dy >= 0 (Ny of the
+        # 2Ny-1 rows; the rest follow from reciprocity); V goes in twice
+        # (solve, port quantities) and I once.
         e2e = {"value": world * nr * args.steps / dt, "unit": "solves/s",
-               "h2d_bytes_per_step": int(blocks.nbytes + 2 * V.nbytes + V.nbytes),
+               "h2d_bytes_per_step": int(blocks.nbytes // (2 * spec.ny - 1) * spec.ny + 2 * V.nbytes + V.nbytes),
                "d2h_bytes_per_step": int(V.nbytes + 2 * hz.numel() * 16)}
 
     za = za_d.cpu().numpy()

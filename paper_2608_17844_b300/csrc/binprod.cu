@@ -108,8 +108,10 @@ MOMA_DEV void load_pair(const double2 *p, double2 (&z)[2]) {
   z[1] = p[1];
 }
 
-template <typename R, int NR, int U2, bool HERM>
-__global__ void __launch_bounds__(BP_THREADS, 1) bin_pair_kernel(BinKernelArgs A) {
+// MINB = CTAs per SM the register budget is sized for (2: smaller tiles,
+// twice the warps in flight to hide shared-memory and FMA latency).
+template <typename R, int NR, int U2, bool HERM, int MINB>
+__global__ void __launch_bounds__(BP_THREADS, MINB) bin_pair_kernel(BinKernelArgs A) {
   using C = typename Cplx<R>::T;
   extern __shared__ __align__(128) unsigned char sm[];
   const BinProduct &P = A.P;
@@ -252,7 +254,12 @@ __global__ void __launch_bounds__(BP_THREADS, 1) bin_pair_kernel(BinKernelArgs A
     const C *tile = stage0 + (size_t)s * stage_elems;
     const int r0 = t * TR, rows = ok ? min(TR, b - r0) : 0;
     constexpr int NV = BP_ROWS * NR * 2;
-    for (int g = w * BP_ROWS; g < rows; g += BP_CONSUMERS * BP_ROWS) {
+    // Row group j (rows 4j .. 4j+3 of the block) belongs to warp j mod 12
+    // whatever the tile height, so every warp accumulates the same rows in
+    // the same order for any tuned shape: results are bitwise independent
+    // of TR, NS and CTAs per SM (tiles start on multiples of 4 rows).
+    const int gfirst = ((w - r0 / BP_ROWS) % BP_CONSUMERS + BP_CONSUMERS) % BP_CONSUMERS;
+    for (int g = gfirst * BP_ROWS; g < rows; g += BP_CONSUMERS * BP_ROWS) {
       R part[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) part[v] = (R)0;
@@ -335,6 +342,15 @@ template <typename R, int NR, int U2, bool HERM>
 static void launch_one(const BinProduct &P, int num_sms, cudaStream_t st, int q0) {
   using C = typename Cplx<R>::T;
   const int row_bytes = P.ldb * (int)sizeof(C);
+  auto smem_for = [&](int ns, int tr) {
+    return 256 + (size_t)ns * tr * row_bytes + (size_t)4 * NR * P.b * sizeof(C) +
+           (size_t)BP_CONSUMERS * P.b * NR * sizeof(C);
+  };
+  // Two CTAs per SM (smaller tiles, 72-register budget) only where the
+  // per-lane state is small: c64, at most two RHS per chunk and b <= 128.
+  constexpr bool two_ok = sizeof(R) == 4 && NR <= 2 && U2 <= 2;
+  const int occ = (two_ok && P.occ == 2) ? 2 : 1;
+  const size_t cap = occ == 2 ? 110 * 1024 : 220 * 1024;
   // Tiles of whole rows, at most 48 KB and at most one 4-row group per
   // consumer warp; 3 stages (fewer if shared memory runs out).
   int TR = 49152 / row_bytes;
@@ -343,31 +359,39 @@ static void launch_one(const BinProduct &P, int num_sms, cudaStream_t st, int q0
   if (TR < 1) TR = 1;
   if (TR > P.b) TR = P.b;
   int NS = 3;
-  auto smem_for = [&](int ns, int tr) {
-    return 256 + (size_t)ns * tr * row_bytes + (size_t)4 * NR * P.b * sizeof(C) +
-           (size_t)BP_CONSUMERS * P.b * NR * sizeof(C);
-  };
   // Autotuned shape, if it is valid for this launch.
   if (P.TR > 0 && P.TR <= 4 * BP_CONSUMERS && P.TR % 4 == 0 && P.NS >= 2 && P.NS <= 6) {
     const int tr = std::min(P.TR, P.b);
-    if (smem_for(P.NS, tr) <= 220 * 1024) {
+    if (smem_for(P.NS, tr) <= cap) {
       TR = tr;
       NS = P.NS;
     }
   }
-  while (NS > 2 && smem_for(NS, TR) > 220 * 1024) --NS;
-  while (TR > 4 && smem_for(NS, TR) > 220 * 1024) TR -= 4;  // wide blocks (b > 160)
+  while (NS > 2 && smem_for(NS, TR) > cap) --NS;
+  while (TR > 4 && smem_for(NS, TR) > cap) TR -= 4;  // wide blocks (b > 160) or two CTAs per SM
   const int ntile = (P.b + TR - 1) / TR;
   const size_t smem = smem_for(NS, TR);
-  auto kern = bin_pair_kernel<R, NR, U2, HERM>;
+  int grid = num_sms * occ;
+  if (grid > P.Bp) grid = P.Bp;
+  BinKernelArgs a{P, TR, ntile, NS, q0};
+  if constexpr (two_ok) {
+    if (occ == 2) {
+      auto kern = bin_pair_kernel<R, NR, U2, HERM, 2>;
+      static int configured2 = 0;
+      if (!configured2) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 112 * 1024);
+        configured2 = 1;
+      }
+      kern<<<grid, BP_THREADS, smem, st>>>(a);
+      return;
+    }
+  }
+  auto kern = bin_pair_kernel<R, NR, U2, HERM, 1>;
   static int configured = 0;
   if (!configured) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     configured = 1;
   }
-  int grid = num_sms;
-  if (grid > P.Bp) grid = P.Bp;
-  BinKernelArgs a{P, TR, ntile, NS, q0};
   kern<<<grid, BP_THREADS, smem, st>>>(a);
 }
 

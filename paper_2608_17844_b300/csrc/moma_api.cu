@@ -167,7 +167,7 @@ struct moma_array {
   // Autotuned launch shapes (0 = built-in heuristic), per RHS count.
   int tuned_nr = -1;
   bool no_autotune = false;
-  int tune_bin_tr[2] = {0, 0}, tune_bin_ns[2] = {0, 0};  // [c64, c128]
+  int tune_bin_tr[2] = {0, 0}, tune_bin_ns[2] = {0, 0}, tune_bin_occ[2] = {1, 1};  // [c64, c128]
   std::vector<std::pair<long long, int>> tune_axis;       // pass signature -> threads per line
   std::string tune_log;
   const int *live = nullptr;  // operator kernels skip their work while *live == 0
@@ -415,6 +415,7 @@ void binprod(moma_array *a, int nr, const void *x, void *y, int herm) {
   P.live = a->live;
   P.TR = a->tune_bin_tr[is64<R>()];
   P.NS = a->tune_bin_ns[is64<R>()];
+  P.occ = a->tune_bin_occ[is64<R>()];
   a->timed(is64<R>() ? PK_BIN128 : PK_BIN64, [&] { launch_bin_product<R>(P, a->num_sms, a->st); });
   check_launch(a);
 }
@@ -814,24 +815,28 @@ void autotune_precision(moma_array *a, int nr, int in128) {
   // Bin product: tile rows x stages.
   {
     float best = 1e30f;
-    int btr = 0, bns = 0;
-    for (int tr : {16, 32, 48}) {
-      if (tr > ((a->b + 3) & ~3) && tr != 16) continue;
-      for (int ns : {2, 3, 4}) {
-        BinProduct P;
-        P.Z = is64<R>() ? a->Z128.p : a->Z64.p;
-        P.pairs = a->pairs.as<int2>();
-        P.x = a->bx.p; P.y = a->by.p; P.Bp = a->Bp; P.b = a->b; P.ldb = a->ldb; P.nr = nr; P.err = a->err;
-        P.TR = tr; P.NS = ns;
-        const float ms = time_launch(a, [&] { launch_bin_product<R>(P, a->num_sms, a->st); });
-        if (ms < best) { best = ms; btr = tr; bns = ns; }
+    int btr = 0, bns = 0, bocc = 1;
+    for (int occ : {1, 2}) {
+      if (occ == 2 && (is64<R>() || nr > 2 || a->b > 128)) continue;  // the two-CTA variant's domain
+      for (int tr : {8, 16, 24, 32, 48}) {
+        if (tr > ((a->b + 3) & ~3) && tr != 16) continue;
+        if (occ == 1 && tr < 16) continue;
+        for (int ns : {2, 3, 4}) {
+          BinProduct P;
+          P.Z = is64<R>() ? a->Z128.p : a->Z64.p;
+          P.pairs = a->pairs.as<int2>();
+          P.x = a->bx.p; P.y = a->by.p; P.Bp = a->Bp; P.b = a->b; P.ldb = a->ldb; P.nr = nr; P.err = a->err;
+          P.TR = tr; P.NS = ns; P.occ = occ;
+          const float ms = time_launch(a, [&] { launch_bin_product<R>(P, a->num_sms, a->st); });
+          if (ms < best) { best = ms; btr = tr; bns = ns; bocc = occ; }
+        }
       }
     }
     a->tune_bin_tr[is64<R>()] = btr;
     a->tune_bin_ns[is64<R>()] = bns;
-    snprintf(buf, sizeof(buf), "bin_product<%s> nr=%d: TR=%d NS=%d (%.1f us)\n",
-             st_code<R>() == 2 ? "dfl" : (is64<R>() ? "c128" : "c64"), nr, btr,
-             bns, 1000.0f * best / 2);
+    a->tune_bin_occ[is64<R>()] = bocc;
+    snprintf(buf, sizeof(buf), "bin_product<%s> nr=%d: TR=%d NS=%d CTAs/SM=%d (%.1f us)\n",
+             st_code<R>() == 2 ? "dfl" : (is64<R>() ? "c128" : "c64"), nr, btr, bns, bocc, 1000.0f * best / 2);
     a->tune_log += buf;
   }
   // Lattice FFT passes of the products and the normal operator.
@@ -866,6 +871,7 @@ void autotune(moma_array *a, int nr) {
   a->tune_axis.clear();
   a->tune_log.clear();
   a->tune_bin_tr[0] = a->tune_bin_tr[1] = a->tune_bin_ns[0] = a->tune_bin_ns[1] = 0;
+  a->tune_bin_occ[0] = a->tune_bin_occ[1] = 1;
   if (a->prec == MOMA_PREC_MIXED) autotune_precision<float>(a, nr, 0);
   // The FP64-class residual runs in double-FP32 pairs in the mixed path.
   if (a->prec == MOMA_PREC_MIXED) autotune_precision<dfl>(a, nr, 1);

@@ -250,43 +250,65 @@ __global__ void __launch_bounds__(256) tri_inverse_kernel(const double2 *__restr
                                                           typename Cplx<R>::T *X, size_t x_stride) {
   using C = typename Cplx<R>::T;
   extern __shared__ __align__(16) unsigned char smraw[];
-  C *Ls = reinterpret_cast<C *>(smraw);
+  R *inv_d = reinterpret_cast<R *>(smraw);  // [b] 1 / L(m, m)
+  C *Ls = reinterpret_cast<C *>(smraw + (((size_t)b * sizeof(R) + 15) & ~size_t(15)));
   const int e = blockIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const size_t npk = (size_t)b * (b + 1) / 2;
   const double2 *Le = Lpk + (size_t)e * npk;
   C *Xe = X + (size_t)e * x_stride;
   if (L_IN_SMEM)
     for (size_t q = threadIdx.x; q < npk; q += blockDim.x) Ls[q] = cvt<C>(Le[q]);
+  for (int m = threadIdx.x; m < b; m += blockDim.x) inv_d[m] = (R)(1.0 / Le[(size_t)colbase(m, b)].x);
   for (size_t q = npk + threadIdx.x; q < x_stride; q += blockDim.x) Xe[q] = czero<C>();  // pad
   __syncthreads();
   auto Lat = [&](size_t q) -> C { return L_IN_SMEM ? Ls[q] : cvt<C>(__ldg(Le + q)); };
-  for (int k = w; k < b; k += nw) {
-    C x[U];
+  // Two columns per warp at a time (k and k + nw), interleaved so that
+  // their independent substitution chains overlap.
+  for (int k1 = w; k1 < b; k1 += 2 * nw) {
+    const int k2 = k1 + nw;
+    const bool has2 = k2 < b;
+    C x1[U], x2[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) x[u] = (lane + 32 * u == k) ? mk((R)1, (R)0) : czero<C>();
+    for (int u = 0; u < U; ++u) {
+      x1[u] = (lane + 32 * u == k1) ? mk((R)1, (R)0) : czero<C>();
+      x2[u] = (has2 && lane + 32 * u == k2) ? mk((R)1, (R)0) : czero<C>();
+    }
 #pragma unroll
     for (int u0 = 0; u0 < U; ++u0) {
       for (int lm = 0; lm < 32; ++lm) {
         const int m = 32 * u0 + lm;
         if (m >= b) break;
-        if (m < k) continue;
+        if (m < k1) continue;
         const size_t cb = (size_t)colbase(m, b) - m;  // L(i, m) at cb + i
-        if (lane == lm) x[u0] = cscale(x[u0], (R)1 / Lat(cb + m).x);
-        C xm;
-        xm.x = __shfl_sync(0xffffffffu, x[u0].x, lm);
-        xm.y = __shfl_sync(0xffffffffu, x[u0].y, lm);
+        const R idm = inv_d[m];
+        if (lane == lm) {
+          x1[u0] = cscale(x1[u0], idm);
+          x2[u0] = cscale(x2[u0], idm);
+        }
+        C xm1, xm2;
+        xm1.x = __shfl_sync(0xffffffffu, x1[u0].x, lm);
+        xm1.y = __shfl_sync(0xffffffffu, x1[u0].y, lm);
+        xm2.x = __shfl_sync(0xffffffffu, x2[u0].x, lm);
+        xm2.y = __shfl_sync(0xffffffffu, x2[u0].y, lm);
+        const bool use2 = has2 && m >= k2;
 #pragma unroll
         for (int u = u0; u < U; ++u) {
           const int i = lane + 32 * u;
-          if (i > m && i < b) x[u] = csub(x[u], cmul(Lat(cb + i), xm));
+          if (i > m && i < b) {
+            const C l = Lat(cb + i);
+            x1[u] = csub(x1[u], cmul(l, xm1));
+            if (use2) x2[u] = csub(x2[u], cmul(l, xm2));
+          }
         }
       }
     }
-    C *Xc = Xe + colbase(k, b) - k;  // Xc[i] = X(i, k)
+    C *Xc1 = Xe + colbase(k1, b) - k1;  // Xc[i] = X(i, k)
+    C *Xc2 = Xe + (has2 ? colbase(k2, b) - k2 : 0);
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int i = lane + 32 * u;
-      if (i >= k && i < b) Xc[i] = x[u];
+      if (i >= k1 && i < b) Xc1[i] = x1[u];
+      if (has2 && i >= k2 && i < b) Xc2[i] = x2[u];
     }
   }
 }
@@ -294,12 +316,13 @@ __global__ void __launch_bounds__(256) tri_inverse_kernel(const double2 *__restr
 template <typename R>
 void launch_tri_inverse(const double2 *Lpk, int nel, int b, void *X, size_t x_stride, cudaStream_t st) {
   using C = typename Cplx<R>::T;
+  const size_t head = ((size_t)b * sizeof(R) + 15) & ~size_t(15);
   const size_t bytes = (size_t)b * (b + 1) / 2 * sizeof(C);
-  const bool in_smem = bytes <= 200 * 1024;
+  const bool in_smem = head + bytes <= 200 * 1024;
   const int U = (b + 31) / 32;
   auto go = [&](auto kern) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-    kern<<<nel, 256, in_smem ? bytes : 0, st>>>(Lpk, b, reinterpret_cast<C *>(X), x_stride);
+    kern<<<nel, 256, head + (in_smem ? bytes : 0), st>>>(Lpk, b, reinterpret_cast<C *>(X), x_stride);
   };
   if (in_smem) {
     if (U <= 1) go(tri_inverse_kernel<R, 1, true>);
@@ -400,25 +423,42 @@ __global__ void __launch_bounds__(PA_THREADS) precond_apply_kernel(const typenam
       ts[idx] = v;
     }
     __syncthreads();
-    for (int k = w; k < b; k += PA_WARPS) {
-      const C *col = Xs + colbase(k, b) - k;
-      C p[NR];
+    // Phase 2, z = X^H t: lanes own outputs k, warps own rows i (strided
+    // so that the triangle is shared evenly); z_k = sum_{i >= k}
+    // conj(X(i,k)) t_i accumulates in registers, partial sums of the warps
+    // are added through shared memory (no per-column warp reductions).
 #pragma unroll
-      for (int qq = 0; qq < NR; ++qq) p[qq] = czero<C>();
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int qq = 0; qq < NR; ++qq) acc[u][qq] = czero<C>();
+    for (int i = w; i < b; i += PA_WARPS) {
+      C ti[NR];
+#pragma unroll
+      for (int qq = 0; qq < NR; ++qq) ti[qq] = ts[i * NR + qq];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const int i = lane + 32 * u;
-        if (i >= k && i < b) {
-          const C xv = col[i];
+        const int k = lane + 32 * u;
+        if (k <= i) {
+          const C xv = Xs[colbase(k, b) - k + i];  // X(i, k)
 #pragma unroll
-          for (int qq = 0; qq < NR; ++qq) p[qq] = cfmac(xv, ts[i * NR + qq], p[qq]);
+          for (int qq = 0; qq < NR; ++qq) acc[u][qq] = cfmac(xv, ti[qq], acc[u][qq]);
         }
       }
+    }
+    __syncthreads();  // every warp has finished reading ts / tp of phase 1
 #pragma unroll
-      for (int qq = 0; qq < NR; ++qq) {
-        const C v = warp_sum(p[qq]);
-        if (lane == 0 && q0 + qq < nr) y[((size_t)(q0 + qq) * nel + e) * b + k] = v;
-      }
+    for (int u = 0; u < U; ++u) {
+      const int k = lane + 32 * u;
+      if (k < b)
+#pragma unroll
+        for (int qq = 0; qq < NR; ++qq) tp[((size_t)w * b + k) * NR + qq] = acc[u][qq];
+    }
+    __syncthreads();
+    for (int idx = tid; idx < b * NR; idx += PA_THREADS) {
+      C v = czero<C>();
+      for (int ww = 0; ww < PA_WARPS; ++ww) v = cadd(v, tp[(size_t)ww * b * NR + idx]);
+      const int k = idx / NR, qq = idx % NR;
+      if (q0 + qq < nr) y[((size_t)(q0 + qq) * nel + e) * b + k] = v;
     }
     __syncthreads();
   }

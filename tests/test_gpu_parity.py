@@ -254,7 +254,7 @@ def test_error_statuses(moma_lib, cuda):
             m.moma_solve(h, V, I)
         assert e.value.status == 2  # MOMA_ERR_STATE: no blocks yet
         bad = offset_blocks(spec)
-        bad[1, 2, 0, 1] = np.nan
+        bad[3, 2, 0, 1] = np.nan  # a row the host ingest reads (dy >= 0)
         with pytest.raises(m.MomaError) as e:
             m.moma_set_blocks(h, bad)
         assert e.value.status == 8  # MOMA_ERR_NONFINITE

@@ -79,7 +79,7 @@ def test_server_reports_per_request_errors(moma_lib, cuda):
     m = moma_lib
     spec = LatticeSpec(3, 3, 4, 0.5, 0)
     bad = offset_blocks(spec, np.complex64)
-    bad[0, 0, 0, 0] = np.nan
+    bad[-1, 0, 0, 0] = np.nan  # a row the host ingest reads (dy >= 0)
     V = excitation(spec, [(0, 0)])
     I = np.zeros_like(V)
     s = m.moma_server_create(slots=2)
