@@ -76,7 +76,8 @@ typedef struct moma_array moma_array; /* opaque; owns all device state */
 enum {
     MOMA_FLAG_NO_GRAPHS = 1,     /* launch the inner steps directly instead of replaying CUDA graphs */
     MOMA_FLAG_NO_AUTOTUNE = 2,   /* use the built-in launch-shape heuristics */
-    MOMA_FLAG_NO_TENSOR = 4,     /* c64 bin products on the CUDA cores at every RHS count */
+    MOMA_FLAG_NO_TENSOR = 4,     /* no tensor-core path: c64 bin products, preconditioner apply
+                                    and (set-up) Gram products on the CUDA cores */
     MOMA_FLAG_TENSOR_ALWAYS = 8  /* c64 bin products on the tensor cores from one RHS up
                                     (default: from 16 RHS; MIXED arrays, 128 <= b <= 256, b even) */
 };
@@ -145,7 +146,10 @@ moma_status moma_create_array(int nx, int ny, int b, const moma_options *opt,
  * products); the rows dy < 0 are completed on the device as transposes.
  * A device buffer is read whole and must stay valid for the call only.
  * In MIXED arrays the c128-class bins used by the refinement residual are
- * computed and stored as double-FP32 pairs (~48 significant bits).
+ * computed and stored as double-FP32 pairs (~48 significant bits), the
+ * Cholesky factorisation runs in the same arithmetic (FP64 output), and for
+ * c64 blocks with 128 <= b <= 256 the Gram products run on the tensor cores
+ * (3xTF32); the plain FP64 path is FP64 throughout.
  * Errors: MOMA_ERR_NONFINITE (NaN/Inf in the blocks read), MOMA_ERR_NOT_PD. */
 moma_status moma_set_blocks(moma_array *a, const void *blocks, int dtype);
 

@@ -421,6 +421,12 @@ __global__ void tc_split_bins_kernel(const float2 *Z, int b, int ldb, const int2
   }
 }
 
+// Elementwise split of T whole c64 b x b matrices (row-major) into hi / lo.
+__global__ void tc_split_plain_kernel(const float2 *Z, size_t n, float *hi, float *lo) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    put_split(hi, lo, i, Z[i]);
+}
+
 // Full X_e = L_e^{-1} (zero above the diagonal) from the packed column-major
 // inverse factor: X(i, k) sits at colbase(k) - k + i for i >= k.  Tiles of
 // 32 x 32 are staged so that the packed columns are read contiguously.
@@ -554,6 +560,14 @@ void tc_split_bins(TcMats &m, const void *Z64, int ldb, const int2 *bin_slot, cu
   const int b = m.b;
   dim3 grid((b + 31) / 32, (b + 31) / 32, m.T), block(32, 8);
   tc_split_bins_kernel<<<grid, block, 0, st>>>(static_cast<const float2 *>(Z64), b, ldb, bin_slot, m.hi, m.lo);
+  encode_maps(m);
+}
+
+void tc_split_plain(TcMats &m, const void *Z64, cudaStream_t st) {
+  const size_t n = (size_t)m.T * m.b * m.b;
+  size_t g = (n + 255) / 256;
+  if (g > 16384) g = 16384;
+  tc_split_plain_kernel<<<(int)g, 256, 0, st>>>(static_cast<const float2 *>(Z64), n, m.hi, m.lo);
   encode_maps(m);
 }
 

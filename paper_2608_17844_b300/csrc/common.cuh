@@ -68,6 +68,15 @@ MOMA_DEV dfl operator/(dfl a, dfl b) {
   const dfl r = a - b * dfl(q1, 0.0f);
   return df_fast_two_sum(q1, __fdiv_rn(r.hi, b.hi));
 }
+// Square root: one Newton correction of the float root, s + (a - s^2) / 2s.
+MOMA_DEV dfl dsqrt(dfl a) {
+  const float s = sqrtf(a.hi);
+  if (!(s > 0.0f)) return dfl(s, 0.0f);
+  const float p = __fmul_rn(s, s);
+  const float e = __fmaf_rn(s, s, -p);  // s*s = p + e exactly
+  const float r = __fadd_rn(__fsub_rn(__fsub_rn(a.hi, p), e), a.lo);
+  return df_fast_two_sum(s, __fdiv_rn(r, __fmul_rn(2.0f, s)));
+}
 MOMA_DEV dfl &operator+=(dfl &a, dfl b) { return a = a + b; }
 MOMA_DEV dfl &operator*=(dfl &a, dfl b) { return a = a * b; }
 #endif

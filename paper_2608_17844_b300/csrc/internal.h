@@ -97,6 +97,8 @@ bool tc_supported(int b);
 size_t tc_bytes(int T, int b);  // hi + lo
 // Every bin's full block from the pair storage (transposed for the partner).
 void tc_split_bins(TcMats &m, const void *Z64, int ldb, const int2 *bin_slot, cudaStream_t st);
+// T whole row-major c64 matrices (e.g. offset blocks), split elementwise.
+void tc_split_plain(TcMats &m, const void *Z64, cudaStream_t st);
 // X_e and X_e^H from the packed inverse factors (c64).
 void tc_split_factor(TcMats &X, TcMats &XH, const void *Xpk, size_t x_stride, cudaStream_t st);
 void launch_tc_product(const TcMats &m, const TcProduct &P, int num_sms, cudaStream_t st);
@@ -107,8 +109,13 @@ template <typename R>
 void launch_gram(const void *blocks, int blocks_c128, int nD, int b, double2 *G, cudaStream_t st);
 // In-place 2D inclusive prefix sum over the (2Ny-1) x (2Nx-1) offset grid.
 void launch_sat(double2 *S, int ndy, int ndx, int bb, cudaStream_t st);
+// The same from Y (c64, [nD][b][b]) with Y_{-D} = conj(G_D) (the tensor-core
+// Gram products of the reflected offsets): S = prefix sums of conj(Y_{-D}).
+void launch_sat_from_reflected(const float2 *Y, double2 *S, int ndy, int ndx, int bb, cudaStream_t st);
 // Box sums + Cholesky: L_e (packed lower, column-major, FP64) for each element.
-void launch_box_cholesky(const double2 *S, int nx, int ny, int b, double2 *Lpk, unsigned *err, cudaStream_t st);
+// df: factor in double-FP32 arithmetic (output still FP64).
+void launch_box_cholesky(const double2 *S, int nx, int ny, int b, double2 *Lpk, unsigned *err, bool df,
+                         cudaStream_t st);
 // Full P_e (b x b, FP64) of one element from the summed-area table.
 void launch_box_one(const double2 *S, int nx, int ny, int b, int ex, int ey, double2 *out, cudaStream_t st);
 // Inverse factor X_e = L_e^{-1}, packed row-major lower, in precision R.

@@ -137,6 +137,8 @@ struct moma_array {
   // set-up workspace
   DevBuf blk, T, S, Lpk;
   cudaStream_t cs = nullptr;  // host-to-device copies of the blocks
+  DevBuf gramA, gramY;        // tensor-core Gram products: split blocks, reflected products
+  bool tgram = false;         // this set-up's Gram products ran on the tensor cores
   cudaEvent_t ev_cs0 = nullptr, ev_chunk[8] = {};
   // solve workspace
   int ws_nr = 0;
@@ -656,11 +658,17 @@ void gram_chunk(moma_array *a, const void *blk, int blk128, int d0, int nd) {
 template <typename R>
 void finish_preconditioner(moma_array *a) {
   const int bb = a->b * a->b;
-  a->timed(PK_SAT, [&] { launch_sat(a->S.as<double2>(), 2 * a->ny - 1, 2 * a->nx - 1, bb, a->st); });
+  a->timed(PK_SAT, [&] {
+    if (a->tgram)
+      launch_sat_from_reflected(a->gramY.as<float2>(), a->S.as<double2>(), 2 * a->ny - 1, 2 * a->nx - 1, bb, a->st);
+    else
+      launch_sat(a->S.as<double2>(), 2 * a->ny - 1, 2 * a->nx - 1, bb, a->st);
+  });
   check_launch(a);
   const size_t npk = (size_t)a->b * (a->b + 1) / 2;
   a->Lpk.ensure((size_t)a->nel * npk * sizeof(double2), a->dev_bytes);
-  a->timed(PK_CHOL, [&] { launch_box_cholesky(a->S.as<double2>(), a->nx, a->ny, a->b, a->Lpk.as<double2>(), a->err, a->st); });
+  a->timed(PK_CHOL, [&] { launch_box_cholesky(a->S.as<double2>(), a->nx, a->ny, a->b, a->Lpk.as<double2>(), a->err,
+                                                      a->prec == MOMA_PREC_MIXED, a->st); });
   check_launch(a);
   using C = typename Cplx<R>::T;
   size_t xs = npk;
@@ -730,10 +738,44 @@ void set_blocks_impl(moma_array *a, const void *blocks, int dtype) {
     });
     check_launch(a);
     // Gram products of these offsets (Eq. 37 precomputation).
-    if (a->prec == MOMA_PREC_FP64) gram_chunk<double>(a, blk, dtype == MOMA_C128, y0 * ndx, (y1 - y0) * ndx);
-    else gram_chunk<float>(a, blk, dtype == MOMA_C128, y0 * ndx, (y1 - y0) * ndx);
+    const int d0 = y0 * ndx, nd = (y1 - y0) * ndx;
+    if (a->tgram) {
+      // Tensor cores: item D with A = Z_D (conjugated) and RHS rows Z_D[j]
+      // gives y_D[j][i] = sum_k conj(Z_D[i][k]) Z_D[j][k], which by
+      // reciprocity is G_{-D}[i][j]; the summed-area pass reads it back
+      // reflected and conjugated.
+      TcMats mA;
+      mA.b = a->b; mA.T = nd;
+      mA.hi = a->gramA.as<float>() + (size_t)d0 * a->b * 2 * a->b;
+      mA.lo = mA.hi + (size_t)nD * a->b * 2 * a->b;
+      const float2 *zb = reinterpret_cast<const float2 *>(blk) + (size_t)d0 * bb;
+      TcProduct P;
+      P.x = zb; P.y = a->gramY.as<float2>() + (size_t)d0 * bb;
+      P.x_ts = P.y_ts = bb; P.x_rs = P.y_rs = a->b; P.nr = a->b; P.conj = 1; P.err = a->err;
+      a->timed(PK_GRAM, [&] {
+        try {
+          tc_split_plain(mA, zb, a->st);
+          check_launch(a);
+          launch_tc_product(mA, P, a->num_sms, a->st);
+        } catch (const std::runtime_error &e) {
+          throw MomaError(MOMA_ERR_CUDA, e.what());
+        }
+      });
+      check_launch(a);
+    } else if (a->prec == MOMA_PREC_FP64) {
+      gram_chunk<double>(a, blk, dtype == MOMA_C128, d0, nd);
+    } else {
+      gram_chunk<float>(a, blk, dtype == MOMA_C128, d0, nd);
+    }
   };
   const int nrows = ndy - r0;
+  // Gram products on the tensor cores (3xTF32) for c64 blocks in the mixed
+  // path when the block size suits the MMA kernel.
+  a->tgram = df && dtype == MOMA_C64 && !a->no_tensor && tc_supported(a->b);
+  if (a->tgram) {
+    a->gramA.ensure(tc_bytes(nD, a->b), a->dev_bytes);
+    a->gramY.ensure((size_t)nD * bb * sizeof(float2), a->dev_bytes);
+  }
   for (int c = 0; c < nchunk; ++c) {
     const int y0 = r0 + (int)((long long)nrows * c / nchunk), y1 = r0 + (int)((long long)nrows * (c + 1) / nchunk);
     if (y1 <= y0) continue;
@@ -1235,7 +1277,7 @@ void destroy_impl(moma_array *a) {
   DevBuf *bufs[] = {&a->tabs, &a->pairs, &a->slot_of, &a->bin_slot, &a->tri, &a->tri_in, &a->Z128, &a->Z64, &a->Xinv, &a->blk, &a->T, &a->S,
                     &a->Lpk, &a->lat_in, &a->lat_tmp, &a->t1, &a->bx, &a->by, &a->Vk, &a->Iw, &a->Vw,
                     &a->rw, &a->yw, &a->kbuf, &a->errbuf, &a->one_blk, &a->portsb, &a->zp_V, &a->zp_I, &a->zp_Y, &a->zp_tmp,
-                    &a->tcA, &a->tcP, &a->partner};
+                    &a->tcA, &a->tcP, &a->partner, &a->gramA, &a->gramY};
   for (DevBuf *b : bufs) b->release(a->dev_bytes);
   if (a->cs) {
     cudaStreamSynchronize(a->cs);
@@ -1704,6 +1746,8 @@ moma_status moma_release_setup(moma_array *a) {
   return guarded([&] {
     CK(cudaStreamSynchronize(a->st));
     a->blk.release(a->dev_bytes);
+    a->gramA.release(a->dev_bytes);
+    a->gramY.release(a->dev_bytes);
     a->T.release(a->dev_bytes);
     a->S.release(a->dev_bytes);
     a->Lpk.release(a->dev_bytes);
@@ -1728,6 +1772,8 @@ size_t moma_estimate_bytes(int nx, int ny, int b, const moma_options *opt, int n
   bytes += (size_t)(m + 1) * nr * N * esz + nr * nch * (m + 1) * c + nr * m * (m + 1) * c;  // Krylov
   bytes += 2 * nr * nel * c;                                                            // ports
   if (with_setup) bytes += nD * b * b * (c + 8) + (size_t)(2 * ny - 1) * Mx * nt * c + nel * nt * c;
+  const bool tens_setup = prec == MOMA_PREC_MIXED && !(opt && (opt->flags & MOMA_FLAG_NO_TENSOR)) && tc_supported(b);
+  if (with_setup && tens_setup) bytes += tc_bytes((int)nD, b) + nD * b * b * 8;  // tensor-core Gram scratch
   const bool tensor = !(opt && (opt->flags & MOMA_FLAG_NO_TENSOR));
   const int tmin = (opt && (opt->flags & MOMA_FLAG_TENSOR_ALWAYS)) ? 1 : 16;
   if (prec == MOMA_PREC_MIXED && tensor && nrhs >= tmin && tc_supported(b))

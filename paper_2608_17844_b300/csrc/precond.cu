@@ -98,6 +98,27 @@ __global__ void sat_y_kernel(double2 *S, int ndy, int ndx, int bb) {
     col[(size_t)y * ndx * bb] = run;
   }
 }
+// x pass from the reflected tensor-core Gram products:
+// S[y][x][e] = sum_{x' <= x} conj(Y[ndy-1-y][ndx-1-x'][e]).
+__global__ void sat_x_reflected_kernel(const float2 *Y, double2 *S, int ndy, int ndx, int bb) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= bb) return;
+  const int y = blockIdx.y;
+  const float2 *src = Y + (size_t)(ndy - 1 - y) * ndx * bb + e;
+  double2 *row = S + (size_t)y * ndx * bb + e;
+  double2 run = make_double2(0, 0);
+  for (int x = 0; x < ndx; ++x) {
+    const float2 g = src[(size_t)(ndx - 1 - x) * bb];
+    run.x += (double)g.x;
+    run.y -= (double)g.y;
+    row[(size_t)x * bb] = run;
+  }
+}
+void launch_sat_from_reflected(const float2 *Y, double2 *S, int ndy, int ndx, int bb, cudaStream_t st) {
+  sat_x_reflected_kernel<<<dim3((bb + 255) / 256, ndy), 256, 0, st>>>(Y, S, ndy, ndx, bb);
+  sat_y_kernel<<<dim3((bb + 255) / 256, ndx), 256, 0, st>>>(S, ndy, ndx, bb);
+}
+
 void launch_sat(double2 *S, int ndy, int ndx, int bb, cudaStream_t st) {
   sat_x_kernel<<<dim3((bb + 255) / 256, ndy), 256, 0, st>>>(S, ndx, bb);
   sat_y_kernel<<<dim3((bb + 255) / 256, ndx), 256, 0, st>>>(S, ndy, ndx, bb);
@@ -133,14 +154,24 @@ constexpr int CH_NB = 8;
 
 MOMA_HD int colbase(int k, int b) { return k * b - k * (k - 1) / 2; }  // start of column k (packed)
 
-template <bool IN_SMEM>
+// Arithmetic R: double (plain path) or dfl, double-FP32 pairs of ~48 bits
+// (mixed path, where B300's FP64 rate would bound the factorisation; the
+// factor only has to be an accurate preconditioner, and it is stored FP64).
+MOMA_DEV double real_part(double2 v) { return v.x; }
+MOMA_DEV double real_part(dfl2 v) { return (double)v.x; }
+MOMA_DEV double rsqrt_root(double d, double *l) { *l = sqrt(d); return 1.0 / *l; }
+MOMA_DEV dfl rsqrt_root(dfl d, dfl *l) { *l = dsqrt(d); return dfl(1.0f) / *l; }
+
+template <bool IN_SMEM, typename R>
 __global__ void __launch_bounds__(512) box_cholesky_kernel(const double2 *__restrict__ S, int nx, int ny, int b,
                                                            double2 *__restrict__ Lpk, unsigned *err) {
+  using C = typename Cplx<R>::T;
+  static_assert(sizeof(C) == sizeof(double2), "the factor is stored in place of its FP64 output");
   extern __shared__ __align__(16) unsigned char smraw[];
   const int e = blockIdx.x, ex = e % nx, ey = e / nx;
   const int npk = b * (b + 1) / 2;
-  double2 *A = IN_SMEM ? reinterpret_cast<double2 *>(smraw) : Lpk + (size_t)e * npk;
-  short2 *tab = reinterpret_cast<short2 *>(smraw + (IN_SMEM ? (size_t)npk * sizeof(double2) : 0));
+  C *A = IN_SMEM ? reinterpret_cast<C *>(smraw) : reinterpret_cast<C *>(Lpk + (size_t)e * npk);
+  short2 *tab = reinterpret_cast<short2 *>(smraw + (IN_SMEM ? (size_t)npk * sizeof(C) : 0));
   const int ndx = 2 * nx - 1, bb = b * b;
   const int x0 = nx - 1 - ex, x1 = 2 * nx - 2 - ex, y0 = ny - 1 - ey, y1 = 2 * ny - 2 - ey;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
@@ -152,7 +183,7 @@ __global__ void __launch_bounds__(512) box_cholesky_kernel(const double2 *__rest
     while ((i + 1) * (i + 2) / 2 <= t) ++i;
     const int k = t - i * (i + 1) / 2;
     const int q = colbase(k, b) + i - k;
-    A[q] = box_entry(S, ndx, bb, x0, x1, y0, y1, i * b + k);
+    A[q] = cvt<C>(box_entry(S, ndx, bb, x0, x1, y0, y1, i * b + k));
     tab[q] = make_short2((short)i, (short)k);
   }
   __syncthreads();
@@ -161,19 +192,20 @@ __global__ void __launch_bounds__(512) box_cholesky_kernel(const double2 *__rest
     const int je = min(jb + CH_NB, b);
     // Panel: columns jb .. je-1, unblocked.
     for (int j = jb; j < je; ++j) {
-      double2 *cj = A + colbase(j, b) - j;  // cj[i] = A(i, j), i >= j
-      const double d = cj[j].x;
+      C *cj = A + colbase(j, b) - j;  // cj[i] = A(i, j), i >= j
+      const double d = real_part(cj[j]);
       if (!(d > 0.0) || !isfinite(d)) {  // uniform: every thread reads the same value
         if (tid == 0) atomicOr(err, DEVERR_NOT_PD);
         return;
       }
-      const double l = sqrt(d), inv_l = 1.0 / l;
+      R l;
+      const R inv_l = rsqrt_root(cj[j].x, &l);
       __syncthreads();  // everyone has read d before the column is overwritten
-      for (int i = j + tid; i < b; i += blockDim.x) cj[i] = (i == j) ? make_double2(l, 0.0) : cscale(cj[i], inv_l);
+      for (int i = j + tid; i < b; i += blockDim.x) cj[i] = (i == j) ? mk(l, (R)0) : cscale(cj[i], inv_l);
       __syncthreads();
       for (int k = j + 1 + w; k < je; k += nw) {
-        double2 *ck = A + colbase(k, b) - k;
-        const double2 lkj = cj[k];
+        C *ck = A + colbase(k, b) - k;
+        const C lkj = cj[k];
         for (int i = k + lane; i < b; i += 32) ck[i] = cfms_conj(cj[i], lkj, ck[i]);
       }
       __syncthreads();
@@ -190,7 +222,7 @@ __global__ void __launch_bounds__(512) box_cholesky_kernel(const double2 *__rest
       const int t2 = t + nthr;
       const bool two = t2 < npk;
       const short2 ik0 = tab[t], ik1 = two ? tab[t2] : ik0;
-      double2 a0 = A[t], a1 = two ? A[t2] : a0;
+      C a0 = A[t], a1 = two ? A[t2] : a0;
 #pragma unroll
       for (int p = 0; p < CH_NB; ++p) {
         if (p < np) {
@@ -203,25 +235,35 @@ __global__ void __launch_bounds__(512) box_cholesky_kernel(const double2 *__rest
     }
     __syncthreads();
   }
-  if (IN_SMEM) {
-    double2 *dst = Lpk + (size_t)e * npk;
-    for (int q = tid; q < npk; q += blockDim.x) dst[q] = A[q];
+  // FP64 output (in place for the global-memory variant: each thread
+  // converts the entries it reads).
+  double2 *dst = Lpk + (size_t)e * npk;
+  for (int q = tid; q < npk; q += blockDim.x) {
+    const C v = A[q];
+    dst[q] = cvt<double2>(v);
   }
 }
 
-void launch_box_cholesky(const double2 *S, int nx, int ny, int b, double2 *Lpk, unsigned *err, cudaStream_t st) {
+template <typename R>
+static void launch_chol_typed(const double2 *S, int nx, int ny, int b, double2 *Lpk, unsigned *err, cudaStream_t st) {
   // Shared memory: the packed triangle (if it fits) and the (i, k) table.
   const size_t npk = (size_t)b * (b + 1) / 2;
   const size_t matb = npk * sizeof(double2), tabb = npk * sizeof(short2);
   const int nel = nx * ny;
   static int configured = 0;
   if (!configured) {
-    cudaFuncSetAttribute(box_cholesky_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
-    cudaFuncSetAttribute(box_cholesky_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+    cudaFuncSetAttribute(box_cholesky_kernel<true, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+    cudaFuncSetAttribute(box_cholesky_kernel<false, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
     configured = 1;
   }
-  if (matb + tabb <= 200 * 1024) box_cholesky_kernel<true><<<nel, 512, matb + tabb, st>>>(S, nx, ny, b, Lpk, err);
-  else box_cholesky_kernel<false><<<nel, 512, tabb, st>>>(S, nx, ny, b, Lpk, err);
+  if (matb + tabb <= 200 * 1024) box_cholesky_kernel<true, R><<<nel, 512, matb + tabb, st>>>(S, nx, ny, b, Lpk, err);
+  else box_cholesky_kernel<false, R><<<nel, 512, tabb, st>>>(S, nx, ny, b, Lpk, err);
+}
+
+void launch_box_cholesky(const double2 *S, int nx, int ny, int b, double2 *Lpk, unsigned *err, bool df,
+                         cudaStream_t st) {
+  if (df) launch_chol_typed<dfl>(S, nx, ny, b, Lpk, err, st);
+  else launch_chol_typed<double>(S, nx, ny, b, Lpk, err, st);
 }
 
 // Full P_e of one element (debug / inspection).

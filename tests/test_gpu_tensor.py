@@ -172,3 +172,36 @@ def test_wide_blocks_b256_solve_matches_dense(moma_lib, cuda, prec, nr):
     assert info["converged"] == 1 and rr.max() <= 1e-10
     i_ref = dense.solve(dense.assemble(b128, spec.nx, spec.ny), V)
     assert relerr(za, ports.active_impedance(i_ref, V)) <= 1e-8
+
+
+@pytest.mark.parametrize("nx,ny,b", [(3, 2, 128), (2, 2, 160)])
+def test_tensor_gram_preconditioner_blocks(moma_lib, cuda, nx, ny, b):
+    """Set-up Gram products on the tensor cores (c64 blocks, mixed path):
+    every P_e (Eq. 37) against the oracle's direct sum, and against the
+    CUDA-core Gram products (MOMA_FLAG_NO_TENSOR).  3xTF32 products carry
+    ~2e-6 relative error, so the bar is 2e-5 of the block's largest entry."""
+    m = moma_lib
+    spec = LatticeSpec(nx, ny, b, 0.5, 8)
+    blocks = offset_blocks(spec, np.complex64)
+    P = mbt.precond_blocks(blocks.astype(np.complex128), nx, ny)
+    got = {}
+    for name, flags in (("tensor", 0), ("cuda", m.MOMA_FLAG_NO_TENSOR)):
+        h = m.moma_create_array(nx, ny, b, MIXED, flags=flags)
+        try:
+            m.moma_set_blocks(h, blocks)
+            out = np.zeros((ny, nx, b, b), np.complex128)
+            for ey in range(ny):
+                for ex in range(nx):
+                    blk = np.zeros((b, b), np.complex128)
+                    m.moma_get_precond_block(h, ex, ey, blk)
+                    out[ey, ex] = blk
+            got[name] = out
+        finally:
+            m.moma_destroy(h)
+    for name, out in got.items():
+        err = max(np.abs(out[ey, ex] - P[ey, ex]).max() / np.abs(P[ey, ex]).max()
+                  for ey in range(ny) for ex in range(nx))
+        print(f"P_e {nx}x{ny}x{b} ({name} Gram): max rel err {err:.3g}")
+        assert err <= 2e-5
+    # Hermitian to the last bit is not required, but the factor must exist:
+    # both arrays factorised (set_blocks raised no MOMA_ERR_NOT_PD).
