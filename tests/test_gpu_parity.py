@@ -63,15 +63,17 @@ def test_bins_match_circulant_definition(moma_lib, cuda, nx, ny, b):
         scale = np.abs(ref).max()
         out = np.zeros((b, b), np.complex128)
         out64 = np.zeros((b, b), np.complex64)
-        worst64 = 0.0
+        worst64 = worst128 = 0.0
         for ky in range(My):
             for kx in range(Mx):
                 m.moma_get_bin(h, kx, ky, out)
                 assert np.abs(out - ref[ky, kx]).max() <= 1e-12 * scale
+                worst128 = max(worst128, np.abs(out - ref[ky, kx]).max() / scale)
                 m.moma_get_bin(h, kx, ky, out64)
                 worst64 = max(worst64, np.abs(out64 - ref[ky, kx]).max() / scale)
         assert worst64 < 1e-6
         RAW_ERRORS[f"bins_c64 {nx}x{ny}x{b}"] = worst64
+        RAW_ERRORS[f"bins_dfl {nx}x{ny}x{b}"] = worst128  # c128-class bins of a MIXED array (double-FP32)
     finally:
         m.moma_destroy(h)
 
@@ -100,6 +102,7 @@ def test_matvec_fp64_and_c64(moma_lib, cuda, nx, ny, b, op):
         y = np.zeros_like(x)
         m.moma_matvec(h, op, x, y)
         assert relerr(y, ref) < 1e-12
+        RAW_ERRORS[f"matvec{'H' if op else ''}_dfl {nx}x{ny}x{b}"] = relerr(y, ref)
         assert np.abs(y - ref).max() <= 1e-11 * np.abs(ref).max()
         x32 = x.astype(np.complex64)
         y32 = np.zeros_like(x32)
