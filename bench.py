@@ -45,6 +45,8 @@ def parse():
                     help="ragged batch: 24 square lattices 2x2..48x48, b=96, x 3 spacings, one broadside solve each")
     ap.add_argument("--scan", action="store_true",
                     help="scan workload: 24x24, b=256, 64 scan-angle RHS at spacings 0.3/0.5/0.7 (tensor cores)")
+    ap.add_argument("--predictors", action="store_true",
+                    help="all-port Z_p (16x16, b=128) + xi_Z, column coupling (32x32, b=128, 64 phase samples), xi_S")
     ap.add_argument("--serve", action="store_true",
                     help="serving mode: Poisson request stream through the continuous-batching server")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
@@ -425,6 +427,60 @@ def run_scan(args):
     print(json.dumps(line, default=str), flush=True)
 
 
+def run_predictors(args):
+    """Analysis workloads on top of the solver (Sec. II-E): the all-port
+    passive impedance matrix Z_p of a 16 x 16 lattice (b = 128, 256 unit
+    port excitations in RHS chunks of 64 on the tensor-core path, FP64
+    Gauss-Jordan inverse) with the xi_Z family; the column coupling C_n of
+    the 32 x 32 lattice from 64 row-phase samples; xi_S from S_ideal for the
+    32 x 32 lattice.  Timed with CUDA events / host clock, after one warm-up."""
+    import torch
+    import paper_2608_17844_b300 as m
+    from synth import LatticeSpec, offset_blocks_torch
+    torch.cuda.set_device(0)
+    out = {"metric": "analysis: all-port Z_p, column coupling, xi_S", "mode": "predictors", "data": "synthetic"}
+    # Z_p
+    spec = LatticeSpec(16, 16, 128, 0.5, 0)
+    blocks = offset_blocks_torch(spec, "cuda")
+    h = m.moma_create_array(spec.nx, spec.ny, spec.b)
+    m.moma_set_blocks(h, blocks)
+    n = spec.n_el
+    zp = torch.zeros((n, n), dtype=torch.complex128, device="cuda")
+    m.moma_port_impedance(h, zp, chunk=64)  # warm-up (builds the tensor-core store)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    m.moma_port_impedance(h, zp, chunk=64)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    zpn = zp.cpu().numpy()
+    xz, xmax, bound = m.moma_xi_z(zpn, spec.nx, spec.ny)
+    out["zp"] = {"lattice": "16x16, b=128", "ports": n, "seconds": dt, "ports_per_s": n / dt,
+                 "symmetry_rel": float(np.linalg.norm(zpn - zpn.T) / np.linalg.norm(zpn)),
+                 "xi_z": xz, "xi_z_max": xmax, "border_bound_ohm": bound}
+    m.moma_destroy(h)
+    # column coupling
+    spec = LatticeSpec(32, 32, 128, 0.5, 0)
+    blocks = offset_blocks_torch(spec, "cuda")
+    h = m.moma_create_array(spec.nx, spec.ny, spec.b)
+    m.moma_set_blocks(h, blocks)
+    C = torch.zeros(2 * 10 + 1, dtype=torch.complex128, device="cuda")
+    g = torch.zeros(64, dtype=torch.complex128, device="cuda")
+    m.moma_column_coupling(h, 64, 10, C, g)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    m.moma_column_coupling(h, 64, 10, C, g)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    c = C.cpu().numpy()
+    out["column_coupling"] = {"lattice": "32x32, b=128", "samples": 64, "seconds": dt,
+                              "abs_C_n": {str(k - 10): float(abs(c[k])) for k in range(10, 21)}}
+    m.moma_destroy(h)
+    t0 = time.perf_counter()
+    xs = m.moma_xi_s(32, 32, 0.1 + 0.05j, -0.15 + 0.07j, np.pi, 50.0)
+    out["xi_s"] = {"lattice": "32x32", "value": xs, "seconds": time.perf_counter() - t0}
+    print(json.dumps(out, default=str), flush=True)
+
+
 def run_reference(args, world, rank):
     """Reference arm: the CPU oracle as it stands, on the host cores."""
     if rank != 0:
@@ -464,6 +520,10 @@ def main():
     if args.scan:
         if rank == 0:
             run_scan(args)
+        return
+    if args.predictors:
+        if rank == 0:
+            run_predictors(args)
         return
     import torch
     import paper_2608_17844_b300 as m

@@ -226,6 +226,19 @@ moma_status moma_active_impedance(moma_array *a, int nrhs, const void *I, const 
 moma_status moma_port_impedance(moma_array *a, int port_basis, int chunk, const moma_solve_opts *opts, void *Zp,
                                 void *Yp);
 
+/* Array margin (Eq. 1): Z = [Z_A, Z_B^T; Z_B, Z_C] with Z_A the MBT element
+ * part (moma_set_blocks), Z_B [nm][N] the margin-element coupling and Z_C
+ * [nm][nm] the margin part (row-major, dtype moma_dtype, host or device;
+ * copied).  Afterwards every vector of this array (V, I of moma_solve,
+ * moma_matvec, moma_apply_precond, the port calls) is [nrhs][N + nm]: the
+ * lattice unknowns in the usual order, then the nm margin unknowns.  The
+ * preconditioner gains the margin block P_C = conj(Z_B) Z_B^T + Z_C^H Z_C
+ * (Eq. 38; P_A stays the block diagonal of Z_A^H Z_A), factored in FP64.
+ * nm = 0 removes the margin.  0 <= nm <= 1024.  Not supported by
+ * moma_matvec_noalloc.  Errors: MOMA_ERR_ARG, MOMA_ERR_NONFINITE,
+ * MOMA_ERR_NOT_PD (P_C). */
+moma_status moma_set_margin(moma_array *a, int nm, const void *ZB, const void *ZC, int dtype);
+
 /* ---- Error predictors (Sec. II-E, after Eq. 19) -------------------------
  * Element index e = mx + Nx*my; the centre c = (Nx/2, Ny/2) (integer
  * division); the border set E_B = the outermost ring of the lattice; "the

@@ -34,6 +34,23 @@ def assemble(blocks, nx, ny):
     return z
 
 
+def assemble_with_margin(blocks, nx, ny, zb, zc):
+    """Z = [Z_A, Z_B^T; Z_B, Z_C] (Eq. 1): the MBT element part from the
+    offset blocks, the margin coupling Z_B (nm x N) below it and its
+    transpose to the right (the MoM matrix is symmetric, Sec. II-D), the
+    margin part Z_C in the corner.  Unknown order: lattice, then margin."""
+    za = assemble(blocks, nx, ny)
+    zb = np.asarray(zb, dtype=np.complex128)
+    zc = np.asarray(zc, dtype=np.complex128)
+    n, nm = za.shape[0], zc.shape[0]
+    z = np.zeros((n + nm, n + nm), dtype=np.complex128)
+    z[:n, :n] = za
+    z[:n, n:] = zb.T
+    z[n:, :n] = zb
+    z[n:, n:] = zc
+    return z
+
+
 def solve(z, v):
     """Solve Z I = V for every RHS column by LU (LAPACK getrf/getrs).
 

@@ -104,3 +104,24 @@ def circulant_bins(blocks, nx, ny, mx, my):
         for dx in range(-(nx - 1), nx):
             col[dy % my, dx % mx] = _blk(blocks, nx, ny, dx, dy)
     return np.fft.fft2(col, axes=(0, 1))
+
+
+def precond_margin(zb, zc):
+    """Margin block of the preconditioner (the matrix P_C of Eq. 38):
+    P_C = conj(Z_B) Z_B^T + Z_C^H Z_C, the margin-margin block of Z^H Z."""
+    zb = np.asarray(zb, dtype=np.complex128)
+    zc = np.asarray(zc, dtype=np.complex128)
+    return zb.conj() @ zb.T + zc.conj().T @ zc
+
+
+def precond_solve_margin(p, pc, x, n):
+    """blockdiag(P_A, P_C)^{-1} x (Eq. 38) for vectors [nrhs][N + nm]: the
+    lattice part by the element blocks p [Ny][Nx][b][b], the margin part by
+    P_C."""
+    ny, nx, b, _ = p.shape
+    x = np.asarray(x, dtype=np.complex128)
+    y = np.empty_like(x)
+    y[:, :n] = precond_solve(p, x[:, :n].reshape(-1, ny, nx, b)).reshape(x.shape[0], n)
+    y[:, n:] = np.linalg.solve(pc, x[:, n:].T).T
+    return y
+

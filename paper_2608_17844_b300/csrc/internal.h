@@ -121,20 +121,35 @@ void launch_box_one(const double2 *S, int nx, int ny, int b, int ex, int ey, dou
 // Inverse factor X_e = L_e^{-1}, packed row-major lower, in precision R.
 template <typename R>
 void launch_tri_inverse(const double2 *Lpk, int nel, int b, void *X, size_t x_stride, cudaStream_t st);
-// y_e = X_e^H X_e x_e for each element.
+// y_e = X_e^H X_e x_e for each element; vectors: RHS q, element e, basis k at
+// q * vstride + voff + e * b + k (vstride <= 0: nel * b).
 template <typename R>
 void launch_precond_apply(const void *X, size_t x_stride, int nel, int b, int nr, const void *x, void *y,
-                          unsigned *err, const int *live, cudaStream_t st);
+                          unsigned *err, const int *live, long long vstride, long long voff, cudaStream_t st);
+
+// -------------------------------------------------------------- margin ----
+// y += margin terms of Z (herm = 0) or Z^H (herm = 1) for vectors
+// [lattice N | margin nm] with per-RHS stride ldv; Z_B [nm][N], Z_C [nm][nm].
+template <typename R>
+void launch_margin_apply(const void *ZB, const void *ZC, int nm, int N, long long ldv, int nr, int herm,
+                         const void *x, void *y, cudaStream_t st);
+// P_C = conj(Z_B) Z_B^T + Z_C^H Z_C (FP64, full nm x nm in P) and its
+// Cholesky factor (packed lower column-major in Lpk); nm <= 1024.
+void launch_margin_precond_build(const double2 *ZB, const double2 *ZC, int nm, int N, double2 *P, double2 *Lpk,
+                                 unsigned *err, cudaStream_t st);
 
 // ------------------------------------------------------- port matrix ----
-void launch_unit_ports(double2 *V, int nel, int b, int pb, int j0, int nq, cudaStream_t st);
-void launch_gather_ports(const double2 *I, int nel, int b, int pb, int j0, int nq, double2 *Y, cudaStream_t st);
+// ldv: per-RHS vector stride (lattice unknowns first, then any margin).
+void launch_unit_ports(double2 *V, int nel, int b, int pb, int j0, int nq, long long ldv, cudaStream_t st);
+void launch_gather_ports(const double2 *I, int nel, int b, int pb, int j0, int nq, double2 *Y, long long ldv,
+                         cudaStream_t st);
 // In-place inverse of the n x n row-major complex matrix A (FP64
 // Gauss-Jordan, partial pivoting); perm [n], colk [n] scratch.
 void launch_invert(double2 *A, int n, int *perm, double2 *colk, unsigned *err, cudaStream_t st);
 
 // ---------------------------------------------------------- predictors ----
-void launch_row_phase(double2 *V, int nx, int nel, int b, int pb, int q0, int nq, int Q, cudaStream_t st);
+void launch_row_phase(double2 *V, int nx, int nel, int b, int pb, int q0, int nq, int Q, long long ldv,
+                      cudaStream_t st);
 void launch_column_coupling(const double2 *gamma, int Q, int nmax, double2 *C, cudaStream_t st);
 void launch_s_ideal(double2 *S, int nx, int ny, double2 s_cc, double2 s1, double kd, cudaStream_t st);
 // Z = z0 (I + S)(I - S)^{-1}; work holds n*n + n double2 and n ints.

@@ -311,11 +311,12 @@ __global__ void to_inner_kernel(const double2 *src, typename Cplx<R>::T *dst, in
 
 // Port quantities (Eqs. 16-19).
 __global__ void ports_kernel(const double2 *I, const double2 *V, int nel, int b, int nr, int pb, double z0,
-                             double2 *Za, double2 *Gam, unsigned *err) {
+                             double2 *Za, double2 *Gam, unsigned *err, long long ldv) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= nel * nr) return;
-  const double2 ip = I[(size_t)idx * b + pb];
-  const double2 vp = V[(size_t)idx * b + pb];
+  const size_t at = (size_t)(idx / nel) * ldv + (size_t)(idx % nel) * b + pb;  // RHS q, element e
+  const double2 ip = I[at];
+  const double2 vp = V[at];
   const double den = ip.x * ip.x + ip.y * ip.y;
   double2 za;
   if (den == 0.0 || !isfinite(den)) {
@@ -371,8 +372,8 @@ void launch_to_inner(const double2 *src, void *dst, int N, int nr, const double 
                                                                  nr, rnorm, mask);
 }
 void launch_ports(const double2 *I, const double2 *V, int nel, int b, int nr, int pb, double z0, double2 *Za,
-                  double2 *Gam, unsigned *err, cudaStream_t st) {
-  ports_kernel<<<(nel * nr + 255) / 256, 256, 0, st>>>(I, V, nel, b, nr, pb, z0, Za, Gam, err);
+                  double2 *Gam, unsigned *err, long long ldv, cudaStream_t st) {
+  ports_kernel<<<(nel * nr + 255) / 256, 256, 0, st>>>(I, V, nel, b, nr, pb, z0, Za, Gam, err, ldv);
 }
 
 template void launch_cgs<float>(const KrylovCtl &, void *, size_t, int, int, int, int, cudaStream_t);

@@ -68,7 +68,8 @@ void launch_resid(const double2 *V, const double2 *y, double2 *r, int N, int nr,
 template <typename R>
 void launch_to_inner(const double2 *src, void *dst, int N, int nr, const double *rnorm, const int *mask,
                      cudaStream_t st);
+// ldv: per-RHS vector stride (lattice unknowns first, then any margin).
 void launch_ports(const double2 *I, const double2 *V, int nel, int b, int nr, int pb, double z0, double2 *Za,
-                  double2 *Gam, unsigned *err, cudaStream_t st);
+                  double2 *Gam, unsigned *err, long long ldv, cudaStream_t st);
 
 }  // namespace moma

@@ -84,6 +84,22 @@ __global__ void nonfinite_kernel(const void *p, size_t n_real, int is_double, un
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(err, DEVERR_NONFINITE);
 }
 
+// Element-type conversion c64 / c128 (n complex values).
+__global__ void convert_kernel(const void *src, int src128, void *dst, int dst128, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    double2 v = src128 ? reinterpret_cast<const double2 *>(src)[i]
+                       : cvt<double2>(reinterpret_cast<const float2 *>(src)[i]);
+    if (dst128) reinterpret_cast<double2 *>(dst)[i] = v;
+    else reinterpret_cast<float2 *>(dst)[i] = cvt<float2>(v);
+  }
+}
+void launch_convert(const void *src, int src128, void *dst, int dst128, size_t n, cudaStream_t st) {
+  size_t g = (n + 255) / 256;
+  if (g > 8192) g = 8192;
+  if (g < 1) g = 1;
+  convert_kernel<<<(int)g, 256, 0, st>>>(src, src128, dst, dst128, n);
+}
+
 // Reciprocity completion of the staged blocks (Sec. II-D: Z_{-D} = Z_D^T):
 // rows (dy index) m in [m0, m1) receive Z[m][ix] = Z[2Ny-2-m][2Nx-2-ix]^T.
 template <typename C>
@@ -110,6 +126,13 @@ enum {
 
 struct moma_array {
   int nx = 0, ny = 0, b = 0, nel = 0, N = 0;
+  // Array margin (Z = [Z_A, Z_B^T; Z_B, Z_C]): nm margin unknowns after the
+  // N lattice unknowns of every vector; ldv = N + nm is the per-RHS stride.
+  int nm = 0;
+  long long ldv = 0;
+  DevBuf mZB128, mZC128, mZB64, mZC64;  // Z_B [nm][N], Z_C [nm][nm] (FP64; c64 in MIXED)
+  DevBuf mP, mL, mX;                    // P_C, its packed Cholesky factor, X_C = L_C^{-1} (inner precision)
+  size_t mx_stride = 0;
   int Mx = 0, My = 0, B = 0, Bp = 0, ldb = 0;
   int prec = MOMA_PREC_MIXED, m = 50;
   cudaStream_t st = nullptr;
@@ -142,7 +165,7 @@ struct moma_array {
   cudaEvent_t ev_cs0 = nullptr, ev_chunk[8] = {};
   // solve workspace
   int ws_nr = 0;
-  DevBuf lat_in, lat_tmp, t1, bx, by, Vk;
+  DevBuf lat_in, lat_tmp, lat_u, t1, bx, by, Vk;
   DevBuf Iw, Vw, rw, yw;
   DevBuf kbuf;  // Krylov control arrays
   KrylovCtl ctl{};
@@ -330,7 +353,7 @@ void build_tables(moma_array *a) {
 AxisPass pass_fx(moma_array *a, int nr, const void *in, void *out, int in128, int out128) {
   AxisPass p;
   p.in = in; p.out = out; p.n1 = nr; p.n2 = a->ny; p.ninner = a->b;
-  p.in_s1 = (long long)a->ny * a->nx * a->b; p.in_s2 = (long long)a->nx * a->b; p.in_sm = a->b; p.nin = a->nx;
+  p.in_s1 = a->ldv; p.in_s2 = (long long)a->nx * a->b; p.in_sm = a->b; p.nin = a->nx;
   p.out_s1 = (long long)a->ny * a->Mx * a->b; p.out_s2 = (long long)a->Mx * a->b; p.out_sm = a->b; p.nout = a->Mx;
   p.in_c128 = in128; p.out_c128 = out128;
   return p;
@@ -359,7 +382,7 @@ AxisPass pass_ix(moma_array *a, int nr, const void *in, void *out, int c128, boo
     p.refft_keep = a->nx;
     p.out_s1 = p.in_s1; p.out_s2 = p.in_s2; p.out_sm = p.in_sm; p.nout = a->Mx;
   } else {
-    p.out_s1 = (long long)a->ny * a->nx * a->b; p.out_s2 = (long long)a->nx * a->b; p.out_sm = a->b; p.nout = a->nx;
+    p.out_s1 = a->ldv; p.out_s2 = (long long)a->nx * a->b; p.out_sm = a->b; p.nout = a->nx;
   }
   p.in_c128 = c128;
   p.out_c128 = out_code < 0 ? c128 : out_code;
@@ -422,6 +445,29 @@ void binprod(moma_array *a, int nr, const void *x, void *y, int herm) {
   check_launch(a);
 }
 
+// Margin part of P^{-1} (Eq. 38): X_C^H X_C on the margin entries.
+template <typename R>
+void precond_margin(moma_array *a, int nr, const void *x, void *y) {
+  if (a->nm <= 0) return;
+  a->timed(PK_PREC, [&] {
+    launch_precond_apply<R>(a->mX.p, a->mx_stride, 1, a->nm, nr, x, y, a->err, a->live, a->ldv, a->N, a->st);
+  });
+  check_launch(a);
+}
+// Margin terms of Z or Z^H added to y (whose lattice part holds Z_A x or
+// Z_A^H x); margin arithmetic follows the lattice vectors' storage.
+template <typename R>
+void margin_terms(moma_array *a, int nr, const void *x, void *y, int herm) {
+  if (a->nm <= 0) return;
+  a->timed(PK_MISC, [&] {
+    if (std::is_same<R, float>::value)
+      launch_margin_apply<float>(a->mZB64.p, a->mZC64.p, a->nm, a->N, a->ldv, nr, herm, x, y, a->st);
+    else
+      launch_margin_apply<double>(a->mZB128.p, a->mZC128.p, a->nm, a->N, a->ldv, nr, herm, x, y, a->st);
+  });
+  check_launch(a);
+}
+
 template <typename R>
 void precond(moma_array *a, int nr, const void *x, void *y) {
   if (!is64<R>() && a->tc_ready && nr >= a->tc_min_nr) {
@@ -429,17 +475,21 @@ void precond(moma_array *a, int nr, const void *x, void *y) {
     // goes to the FFT scratch (free here), then y = X^H t.
     TcProduct T;
     T.nr = nr; T.err = a->err; T.live = a->live;
-    T.x_ts = T.y_ts = a->b; T.x_rs = T.y_rs = a->N;
+    T.x_ts = T.y_ts = a->b; T.x_rs = T.y_rs = a->ldv;
     T.x = x; T.y = a->t1.p;
     a->timed(PK_PRECTC, [&] { launch_tc_product(a->tcX, T, a->num_sms, a->st); });
     check_launch(a);
     T.x = a->t1.p; T.y = y;
     a->timed(PK_PRECTC, [&] { launch_tc_product(a->tcXH, T, a->num_sms, a->st); });
     check_launch(a);
+    precond_margin<R>(a, nr, x, y);
     return;
   }
-  a->timed(PK_PREC, [&] { launch_precond_apply<R>(a->Xinv.p, a->x_stride, a->nel, a->b, nr, x, y, a->err, a->live, a->st); });
+  a->timed(PK_PREC, [&] {
+    launch_precond_apply<R>(a->Xinv.p, a->x_stride, a->nel, a->b, nr, x, y, a->err, a->live, a->ldv, 0, a->st);
+  });
   check_launch(a);
+  precond_margin<R>(a, nr, x, y);
 }
 
 // lattice -> bins (Fx then Fy); in may be c128 when R is double.
@@ -460,11 +510,18 @@ void apply_z(moma_array *a, int nr, const void *x, void *y, int herm) {
   lattice_to_bins<R>(a, nr, x, lat_code<R>());
   binprod<R>(a, nr, a->bx.p, a->by.p, herm);
   bins_to_lattice<R>(a, nr, a->by.p, y);
+  margin_terms<R>(a, nr, x, y, herm);
 }
 
 // y = P^{-1} Z^H M Z x, M the restriction to the lattice (mask between legs).
 template <typename R>
 void apply_normal(moma_array *a, int nr, const void *x, void *y) {
+  if (a->nm > 0) {  // with a margin the mask pass cannot stay in the bins
+    apply_z<R>(a, nr, x, a->lat_u.p, 0);
+    apply_z<R>(a, nr, a->lat_u.p, a->lat_tmp.p, 1);
+    precond<R>(a, nr, a->lat_tmp.p, y);
+    return;
+  }
   lattice_to_bins<R>(a, nr, x, is64<R>());
   binprod<R>(a, nr, a->bx.p, a->by.p, 0);
   axis<R>(a, pass_iy(a, nr, a->by.p, a->t1.p, is64<R>()), a->fy);
@@ -478,6 +535,11 @@ void apply_normal(moma_array *a, int nr, const void *x, void *y) {
 // y = Z^H M Z x (the normal matrix, no preconditioner).
 template <typename R>
 void apply_zhz(moma_array *a, int nr, const void *x, void *y) {
+  if (a->nm > 0) {
+    apply_z<R>(a, nr, x, a->lat_u.p, 0);
+    apply_z<R>(a, nr, a->lat_u.p, y, 1);
+    return;
+  }
   lattice_to_bins<R>(a, nr, x, is64<R>());
   binprod<R>(a, nr, a->bx.p, a->by.p, 0);
   axis<R>(a, pass_iy(a, nr, a->by.p, a->t1.p, is64<R>()), a->fy);
@@ -531,11 +593,12 @@ void ensure_ws(moma_array *a, int nr) {
   drop_graphs(a);
   a->tuned_nr = -1;
   const size_t c = sizeof(double2);
-  const size_t lat = (size_t)nr * a->N;
+  const size_t lat = (size_t)nr * a->ldv;
   const size_t tsz = (size_t)nr * a->ny * a->Mx * a->b;
   const size_t bsz = (size_t)a->B * nr * a->b;
   a->lat_in.ensure(lat * c, a->dev_bytes);
   a->lat_tmp.ensure(lat * c, a->dev_bytes);
+  if (a->nm > 0) a->lat_u.ensure(lat * c, a->dev_bytes);
   a->t1.ensure(tsz * c, a->dev_bytes);
   a->bx.ensure(bsz * c, a->dev_bytes);
   a->by.ensure(bsz * c, a->dev_bytes);
@@ -546,7 +609,7 @@ void ensure_ws(moma_array *a, int nr) {
   a->rw.ensure(lat * c, a->dev_bytes);
   a->yw.ensure(lat * c, a->dev_bytes);
   // Krylov control arrays
-  const int m = a->m, nch = krylov_chunks(a->N);
+  const int m = a->m, nch = krylov_chunks((int)a->ldv);
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off = (off + bytes + 255) & ~size_t(255); return o; };
   const size_t o_active = take(nr * sizeof(int)), o_kq = take(nr * sizeof(int)), o_nact = take(sizeof(int));
@@ -924,7 +987,7 @@ void autotune(moma_array *a, int nr) {
 template <typename R>
 void gmres_cycle(moma_array *a, int nr, const std::vector<int> &act, int *inner_iters, double *first_red) {
   using C = typename Cplx<R>::T;
-  const size_t vstride = (size_t)nr * a->N;
+  const size_t vstride = (size_t)nr * a->ldv;
   C *V = a->Vk.as<C>();
   KrylovCtl c = a->ctl;
   // Inner right-hand side P^{-1} Z^H r~ into slot 0; its norm starts the cycle.
@@ -935,9 +998,9 @@ void gmres_cycle(moma_array *a, int nr, const std::vector<int> &act, int *inner_
   CK(cudaMemcpyAsync(c.active, a->mask, nr * sizeof(int), cudaMemcpyDeviceToDevice, a->st));
   CK(cudaMemsetAsync(c.kq, 0, nr * sizeof(int), a->st));
   CK(cudaMemcpyAsync(c.nact, a->h_nact + MOMA_MAX_RESTART + 4, sizeof(int), cudaMemcpyHostToDevice, a->st));
-  a->timed(PK_KRYLOV, [&] { launch_cgs<R>(c, V, vstride, a->N, nr, -1, KF_NORM | KF_INIT, a->st); });
+  a->timed(PK_KRYLOV, [&] { launch_cgs<R>(c, V, vstride, (int)a->ldv, nr, -1, KF_NORM | KF_INIT, a->st); });
   check_launch(a);
-  a->timed(PK_KRYLOV, [&] { launch_scale<R>(c, V, vstride, a->N, nr, a->st); });
+  a->timed(PK_KRYLOV, [&] { launch_scale<R>(c, V, vstride, (int)a->ldv, nr, a->st); });
   check_launch(a);
 
   const int lag = 2;
@@ -955,13 +1018,13 @@ void gmres_cycle(moma_array *a, int nr, const std::vector<int> &act, int *inner_
     a->live = c.nact;  // steps queued after convergence cost only their launches
     apply_normal<R>(a, nr, V + (size_t)j * vstride, V + (size_t)(j + 1) * vstride);
     a->live = nullptr;
-    a->timed(PK_KRYLOV, [&] { launch_cgs<R>(c, V, vstride, a->N, nr, j, KF_DOTS, a->st); });
+    a->timed(PK_KRYLOV, [&] { launch_cgs<R>(c, V, vstride, (int)a->ldv, nr, j, KF_DOTS, a->st); });
     check_launch(a);
-    a->timed(PK_KRYLOV, [&] { launch_cgs<R>(c, V, vstride, a->N, nr, j, KF_UPDATE | KF_DOTS | KF_ACCUM, a->st); });
+    a->timed(PK_KRYLOV, [&] { launch_cgs<R>(c, V, vstride, (int)a->ldv, nr, j, KF_UPDATE | KF_DOTS | KF_ACCUM, a->st); });
     check_launch(a);
-    a->timed(PK_KRYLOV, [&] { launch_cgs<R>(c, V, vstride, a->N, nr, j, KF_UPDATE | KF_NORM, a->st); });
+    a->timed(PK_KRYLOV, [&] { launch_cgs<R>(c, V, vstride, (int)a->ldv, nr, j, KF_UPDATE | KF_NORM, a->st); });
     check_launch(a);
-    a->timed(PK_KRYLOV, [&] { launch_scale<R>(c, V + (size_t)(j + 1) * vstride, vstride, a->N, nr, a->st); });
+    a->timed(PK_KRYLOV, [&] { launch_scale<R>(c, V + (size_t)(j + 1) * vstride, vstride, (int)a->ldv, nr, a->st); });
     check_launch(a);
     CK(cudaMemcpyAsync(a->h_nact + j, c.nact, sizeof(int), cudaMemcpyDeviceToHost, a->st));
     CK(cudaEventRecord(a->poll_ev[j], a->st));
@@ -1034,7 +1097,7 @@ void gmres_cycle(moma_array *a, int nr, const std::vector<int> &act, int *inner_
   }
   a->timed(PK_KRYLOV, [&] { launch_backsolve(c, nr, a->st); });
   check_launch(a);
-  a->timed(PK_KRYLOV, [&] { launch_lincomb<R>(c, V, vstride, a->N, nr, a->Iw.as<double2>(), a->rnorm, a->st); });
+  a->timed(PK_KRYLOV, [&] { launch_lincomb<R>(c, V, vstride, (int)a->ldv, nr, a->Iw.as<double2>(), a->rnorm, a->st); });
   check_launch(a);
 }
 
@@ -1046,7 +1109,7 @@ template <typename R>
 void pcg_cycle(moma_array *a, int nr, const std::vector<int> &act, int max_inner, int *inner_iters,
                double *first_red) {
   using C = typename Cplx<R>::T;
-  const size_t vs = (size_t)nr * a->N;
+  const size_t vs = (size_t)nr * a->ldv;
   C *base = a->Vk.as<C>();
   C *d = base, *r = base + vs, *p = base + 2 * vs, *q = base + 3 * vs, *z = base + 4 * vs;
   CgCtl c = a->cg;
@@ -1060,27 +1123,27 @@ void pcg_cycle(moma_array *a, int nr, const std::vector<int> &act, int max_inner
   CK(cudaMemsetAsync(d, 0, vs * sizeof(C), a->st));
   // r = Z^H r~ (right-hand side of the normal equations), ||r0||, z = P^{-1} r, p = z.
   apply_z<R>(a, nr, a->lat_in.p, r, 1);
-  a->timed(PK_KRYLOV, [&] { launch_cg_axpy<R>(c, d, p, r, q, a->N, nr, 1, a->st); });
+  a->timed(PK_KRYLOV, [&] { launch_cg_axpy<R>(c, d, p, r, q, (int)a->ldv, nr, 1, a->st); });
   check_launch(a);
   precond<R>(a, nr, r, z);
-  a->timed(PK_KRYLOV, [&] { launch_cg_reduce<R>(c, r, z, a->N, nr, CG_RZ0, a->st); });
+  a->timed(PK_KRYLOV, [&] { launch_cg_reduce<R>(c, r, z, (int)a->ldv, nr, CG_RZ0, a->st); });
   check_launch(a);
-  a->timed(PK_KRYLOV, [&] { launch_cg_dir<R>(c, p, z, a->N, nr, 1, a->st); });
+  a->timed(PK_KRYLOV, [&] { launch_cg_dir<R>(c, p, z, (int)a->ldv, nr, 1, a->st); });
   check_launch(a);
 
   constexpr int RING = 16;
   auto enqueue_iter = [&](int slot) {
     a->live = c.nact;
     apply_zhz<R>(a, nr, p, q);
-    a->timed(PK_KRYLOV, [&] { launch_cg_reduce<R>(c, p, q, a->N, nr, CG_PQ, a->st); });
+    a->timed(PK_KRYLOV, [&] { launch_cg_reduce<R>(c, p, q, (int)a->ldv, nr, CG_PQ, a->st); });
     check_launch(a);
-    a->timed(PK_KRYLOV, [&] { launch_cg_axpy<R>(c, d, p, r, q, a->N, nr, 0, a->st); });
+    a->timed(PK_KRYLOV, [&] { launch_cg_axpy<R>(c, d, p, r, q, (int)a->ldv, nr, 0, a->st); });
     check_launch(a);
     precond<R>(a, nr, r, z);
     a->live = nullptr;
-    a->timed(PK_KRYLOV, [&] { launch_cg_reduce<R>(c, r, z, a->N, nr, CG_RZ, a->st); });
+    a->timed(PK_KRYLOV, [&] { launch_cg_reduce<R>(c, r, z, (int)a->ldv, nr, CG_RZ, a->st); });
     check_launch(a);
-    a->timed(PK_KRYLOV, [&] { launch_cg_dir<R>(c, p, z, a->N, nr, 0, a->st); });
+    a->timed(PK_KRYLOV, [&] { launch_cg_dir<R>(c, p, z, (int)a->ldv, nr, 0, a->st); });
     check_launch(a);
     CK(cudaMemcpyAsync(a->h_nact + slot, c.nact, sizeof(int), cudaMemcpyDeviceToHost, a->st));
   };
@@ -1151,7 +1214,7 @@ void pcg_cycle(moma_array *a, int nr, const std::vector<int> &act, int max_inner
       if (act[k] && rr0[k] > 0) m2 = std::max(m2, std::sqrt(rr[k] / rr0[k]));
     *first_red = m2;
   }
-  a->timed(PK_KRYLOV, [&] { launch_cg_accum<R>(d, a->N, nr, a->Iw.as<double2>(), a->rnorm, a->st); });
+  a->timed(PK_KRYLOV, [&] { launch_cg_accum<R>(d, (int)a->ldv, nr, a->Iw.as<double2>(), a->rnorm, a->st); });
   check_launch(a);
 }
 
@@ -1165,7 +1228,7 @@ void solve_impl(moma_array *a, int nr, const void *Vin, void *Iout, const moma_s
   const double itol = (o && o->inner_tol > 0) ? o->inner_tol : (is64<R>() ? tol * 0.1 : 1e-5);
   const int max_outer = (o && o->max_outer > 0) ? o->max_outer : 30;
   const bool warm = o && o->warm_start;
-  const size_t bytes = (size_t)nr * a->N * sizeof(double2);
+  const size_t bytes = (size_t)nr * a->ldv * sizeof(double2);
   a->ctl.inner_tol = itol;
 
   // The solve runs on an internal non-blocking stream (capturable into
@@ -1199,8 +1262,8 @@ void solve_impl(moma_array *a, int nr, const void *Vin, void *Iout, const moma_s
   CK(cudaMemcpyAsync(a->Vw.p, Vin, bytes, cudaMemcpyDefault, a->st));
   if (warm) CK(cudaMemcpyAsync(a->Iw.p, Iout, bytes, cudaMemcpyDefault, a->st));
   else CK(cudaMemsetAsync(a->Iw.p, 0, bytes, a->st));
-  check_finite(a, a->Vw.p, (size_t)nr * a->N * 2, 1);
-  a->timed(PK_MISC, [&] { launch_resid(a->Vw.as<double2>(), nullptr, nullptr, a->N, nr, a->rpart, a->rcount, a->vnorm, a->st); });
+  check_finite(a, a->Vw.p, (size_t)nr * a->ldv * 2, 1);
+  a->timed(PK_MISC, [&] { launch_resid(a->Vw.as<double2>(), nullptr, nullptr, (int)a->ldv, nr, a->rpart, a->rcount, a->vnorm, a->st); });
   check_launch(a);
   sync_and_check(a);
 
@@ -1213,10 +1276,10 @@ void solve_impl(moma_array *a, int nr, const void *Vin, void *Iout, const moma_s
   for (;;) {
     // True residual r = V - Z I in FP64 (c128 bins); I = 0 needs no product.
     if (outer == 0 && !warm) {
-      a->timed(PK_MISC, [&] { launch_resid(a->Vw.as<double2>(), nullptr, a->rw.as<double2>(), a->N, nr, a->rpart, a->rcount, a->rnorm, a->st); });
+      a->timed(PK_MISC, [&] { launch_resid(a->Vw.as<double2>(), nullptr, a->rw.as<double2>(), (int)a->ldv, nr, a->rpart, a->rcount, a->rnorm, a->st); });
     } else {
       apply_z<H>(a, nr, a->Iw.p, a->yw.p, 0);
-      a->timed(PK_MISC, [&] { launch_resid(a->Vw.as<double2>(), a->yw.as<double2>(), a->rw.as<double2>(), a->N, nr, a->rpart, a->rcount,
+      a->timed(PK_MISC, [&] { launch_resid(a->Vw.as<double2>(), a->yw.as<double2>(), a->rw.as<double2>(), (int)a->ldv, nr, a->rpart, a->rcount,
                    a->rnorm, a->st); });
     }
     check_launch(a);
@@ -1233,7 +1296,7 @@ void solve_impl(moma_array *a, int nr, const void *Vin, void *Iout, const moma_s
     if (nact == 0) { converged = true; break; }
     if (outer >= max_outer) break;
     CK(cudaMemcpyAsync(a->mask, mask.data(), nr * sizeof(int), cudaMemcpyHostToDevice, a->st));
-    a->timed(PK_MISC, [&] { launch_to_inner<R>(a->rw.as<double2>(), a->lat_in.p, a->N, nr, a->rnorm, a->mask, a->st); });
+    a->timed(PK_MISC, [&] { launch_to_inner<R>(a->rw.as<double2>(), a->lat_in.p, (int)a->ldv, nr, a->rnorm, a->mask, a->st); });
     check_launch(a);
     if (o && o->solver == MOMA_SOLVER_PCG)
       pcg_cycle<R>(a, nr, mask, (o->max_inner > 0) ? o->max_inner : 500, &inner, outer == 0 ? &first_red : nullptr);
@@ -1277,7 +1340,8 @@ void destroy_impl(moma_array *a) {
   DevBuf *bufs[] = {&a->tabs, &a->pairs, &a->slot_of, &a->bin_slot, &a->tri, &a->tri_in, &a->Z128, &a->Z64, &a->Xinv, &a->blk, &a->T, &a->S,
                     &a->Lpk, &a->lat_in, &a->lat_tmp, &a->t1, &a->bx, &a->by, &a->Vk, &a->Iw, &a->Vw,
                     &a->rw, &a->yw, &a->kbuf, &a->errbuf, &a->one_blk, &a->portsb, &a->zp_V, &a->zp_I, &a->zp_Y, &a->zp_tmp,
-                    &a->tcA, &a->tcP, &a->partner, &a->gramA, &a->gramY};
+                    &a->tcA, &a->tcP, &a->partner, &a->gramA, &a->gramY, &a->lat_u, &a->mZB128,
+                    &a->mZC128, &a->mZB64, &a->mZC64, &a->mP, &a->mL, &a->mX};
   for (DevBuf *b : bufs) b->release(a->dev_bytes);
   if (a->cs) {
     cudaStreamSynchronize(a->cs);
@@ -1317,6 +1381,7 @@ moma_status moma_create_array(int nx, int ny, int b, const moma_options *opt, vo
     if ((long long)nx * ny * b > (1ll << 31) / 4) throw MomaError(MOMA_ERR_ARG, "lattice too large");
     a = new moma_array();
     a->nx = nx; a->ny = ny; a->b = b; a->nel = nx * ny; a->N = nx * ny * b;
+    a->ldv = a->N;
     a->st = reinterpret_cast<cudaStream_t>(cuda_stream);
     const int prec = opt ? opt->precision : MOMA_PREC_MIXED;
     if (prec != MOMA_PREC_FP64 && prec != MOMA_PREC_MIXED) throw MomaError(MOMA_ERR_ARG, "bad precision");
@@ -1376,7 +1441,7 @@ moma_status moma_matvec(moma_array *a, int op, int nrhs, const void *x, void *y,
     if (nrhs == 0) return;
     ensure_ws(a, nrhs);
     ensure_tc(a, nrhs);
-    const size_t bytes = (size_t)nrhs * a->N * (d64 ? sizeof(double2) : sizeof(float2));
+    const size_t bytes = (size_t)nrhs * a->ldv * (d64 ? sizeof(double2) : sizeof(float2));
     CK(cudaMemcpyAsync(a->Vw.p, x, bytes, cudaMemcpyDefault, a->st));
     if (d64) {
       if (op == MOMA_OP_NORMAL) apply_normal<double>(a, nrhs, a->Vw.p, a->yw.p);
@@ -1402,7 +1467,7 @@ moma_status moma_apply_precond(moma_array *a, int nrhs, const void *x, void *y, 
     if (nrhs == 0) return;
     ensure_ws(a, nrhs);
     ensure_tc(a, nrhs);
-    const size_t bytes = (size_t)nrhs * a->N * (d64 ? sizeof(double2) : sizeof(float2));
+    const size_t bytes = (size_t)nrhs * a->ldv * (d64 ? sizeof(double2) : sizeof(float2));
     CK(cudaMemcpyAsync(a->Vw.p, x, bytes, cudaMemcpyDefault, a->st));
     if (d64) precond<double>(a, nrhs, a->Vw.p, a->yw.p);
     else precond<float>(a, nrhs, a->Vw.p, a->yw.p);
@@ -1492,13 +1557,14 @@ moma_status moma_active_impedance(moma_array *a, int nrhs, const void *I, const 
     if (port_basis < 0 || port_basis >= a->b) throw MomaError(MOMA_ERR_ARG, "port_basis out of range");
     if (nrhs == 0) return;
     ensure_ws(a, nrhs);
-    const size_t bytes = (size_t)nrhs * a->N * sizeof(double2);
+    const size_t bytes = (size_t)nrhs * a->ldv * sizeof(double2);
     CK(cudaMemcpyAsync(a->rw.p, I, bytes, cudaMemcpyDefault, a->st));
     CK(cudaMemcpyAsync(a->Vw.p, V, bytes, cudaMemcpyDefault, a->st));
     a->portsb.ensure((size_t)2 * nrhs * a->nel * sizeof(double2), a->dev_bytes);
     double2 *za = a->portsb.as<double2>();
     double2 *ga = Gamma ? za + (size_t)nrhs * a->nel : nullptr;
-    launch_ports(a->rw.as<double2>(), a->Vw.as<double2>(), a->nel, a->b, nrhs, port_basis, z0, za, ga, a->err, a->st);
+    launch_ports(a->rw.as<double2>(), a->Vw.as<double2>(), a->nel, a->b, nrhs, port_basis, z0, za, ga, a->err, a->ldv,
+                 a->st);
     check_launch(a);
     copy_out(a, Za, za, (size_t)nrhs * a->nel * sizeof(double2));
     if (Gamma) copy_out(a, Gamma, ga, (size_t)nrhs * a->nel * sizeof(double2));
@@ -1516,7 +1582,7 @@ moma_status moma_port_impedance(moma_array *a, int port_basis, int chunk, const 
     const int n = a->nel;
     if (chunk <= 0) chunk = 64;
     if (chunk > n) chunk = n;
-    const size_t vbytes = (size_t)chunk * a->N * sizeof(double2);
+    const size_t vbytes = (size_t)chunk * a->ldv * sizeof(double2);
     a->zp_V.ensure(vbytes, a->dev_bytes);
     a->zp_I.ensure(vbytes, a->dev_bytes);
     a->zp_Y.ensure((size_t)n * n * sizeof(double2), a->dev_bytes);
@@ -1524,13 +1590,13 @@ moma_status moma_port_impedance(moma_array *a, int port_basis, int chunk, const 
     double2 *Y = a->zp_Y.as<double2>();
     for (int j0 = 0; j0 < n; j0 += chunk) {
       const int nq = std::min(chunk, n - j0);
-      launch_unit_ports(a->zp_V.as<double2>(), n, a->b, port_basis, j0, nq, a->st);
+      launch_unit_ports(a->zp_V.as<double2>(), n, a->b, port_basis, j0, nq, a->ldv, a->st);
       check_launch(a);
-      CK(cudaMemsetAsync(a->zp_I.p, 0, (size_t)nq * a->N * sizeof(double2), a->st));
+      CK(cudaMemsetAsync(a->zp_I.p, 0, (size_t)nq * a->ldv * sizeof(double2), a->st));
       moma_solve_info info{};
       const moma_status s = moma_solve(a, nq, a->zp_V.p, a->zp_I.p, opts, &info, nullptr);
       if (s != MOMA_OK) throw MomaError(s, std::string("port solve: ") + moma_last_error());
-      launch_gather_ports(a->zp_I.as<double2>(), n, a->b, port_basis, j0, nq, Y, a->st);
+      launch_gather_ports(a->zp_I.as<double2>(), n, a->b, port_basis, j0, nq, Y, a->ldv, a->st);
       check_launch(a);
     }
     if (Yp) copy_out(a, Yp, Y, (size_t)n * n * sizeof(double2));
@@ -1614,7 +1680,7 @@ moma_status moma_column_coupling(moma_array *a, int port_basis, int nq, int nmax
     if (port_basis < 0 || port_basis >= a->b) throw MomaError(MOMA_ERR_ARG, "port_basis out of range");
     if (nq < 1 || nmax < 0 || !C) throw MomaError(MOMA_ERR_ARG, "need nq >= 1, nmax >= 0 and C");
     const int chunk = std::min(nq, 64), nel = a->nel, c = centre_of(a->nx, a->ny);
-    const size_t vbytes = (size_t)chunk * a->N * sizeof(double2);
+    const size_t vbytes = (size_t)chunk * a->ldv * sizeof(double2);
     a->zp_V.ensure(vbytes, a->dev_bytes);
     a->zp_I.ensure(vbytes, a->dev_bytes);
     a->portsb.ensure((size_t)2 * chunk * nel * sizeof(double2), a->dev_bytes);
@@ -1623,13 +1689,13 @@ moma_status moma_column_coupling(moma_array *a, int port_basis, int nq, int nmax
     double2 *za = a->portsb.as<double2>(), *ga = za + (size_t)chunk * nel;
     for (int q0 = 0; q0 < nq; q0 += chunk) {
       const int nqc = std::min(chunk, nq - q0);
-      launch_row_phase(a->zp_V.as<double2>(), a->nx, nel, a->b, port_basis, q0, nqc, nq, a->st);
+      launch_row_phase(a->zp_V.as<double2>(), a->nx, nel, a->b, port_basis, q0, nqc, nq, a->ldv, a->st);
       check_launch(a);
       moma_solve_info info{};
       const moma_status s = moma_solve(a, nqc, a->zp_V.p, a->zp_I.p, opts, &info, nullptr);
       if (s != MOMA_OK) throw MomaError(s, std::string("phase-sweep solve: ") + moma_last_error());
       launch_ports(a->zp_I.as<double2>(), a->zp_V.as<double2>(), nel, a->b, nqc, port_basis, z0, za, ga, a->err,
-                   a->st);
+                   a->ldv, a->st);
       check_launch(a);
       CK(cudaMemcpy2DAsync(gam_d + q0, sizeof(double2), ga + c, (size_t)nel * sizeof(double2), sizeof(double2), nqc,
                            cudaMemcpyDeviceToDevice, a->st));
@@ -1702,6 +1768,59 @@ moma_status moma_xi_s(int nx, int ny, double s_cc_re, double s_cc_im, double s1_
     z_from_s_impl(S, n, z0, Z, nullptr);
     const std::vector<double2> row = matrix_row(Z, n, c);
     *xi_s = cabs2(row[closest_border(nx, ny)]) / cabs2(row[c]);  // Eq. 36
+  });
+}
+
+moma_status moma_set_margin(moma_array *a, int nm, const void *ZB, const void *ZC, int dtype) {
+  if (!a) { g_last_error = "array is NULL"; return MOMA_ERR_ARG; }
+  return guarded([&] {
+    if (nm < 0 || nm > 1024) throw MomaError(MOMA_ERR_ARG, "nm must be in 0..1024");
+    if (nm > 0 && (!ZB || !ZC)) throw MomaError(MOMA_ERR_ARG, "ZB and ZC are required");
+    if (dtype != MOMA_C128 && dtype != MOMA_C64) throw MomaError(MOMA_ERR_ARG, "bad dtype");
+    CK(cudaStreamSynchronize(a->st));
+    drop_graphs(a);
+    a->ws_nr = 0;  // vector length changes: workspaces are re-sized on the next call
+    a->tuned_nr = -1;
+    a->nm = nm;
+    a->ldv = (long long)a->N + nm;
+    if (nm == 0) return;
+    const size_t nb = (size_t)nm * a->N, nc = (size_t)nm * nm;
+    const size_t esz = dtype == MOMA_C128 ? sizeof(double2) : sizeof(float2);
+    DevBuf tmpB, tmpC;
+    size_t scratch = 0;
+    const void *zb = stage_in(a, ZB, nb * esz, tmpB), *zc = stage_in(a, ZC, nc * esz, tmpC);
+    (void)scratch;
+    check_finite(a, zb, nb * 2, dtype == MOMA_C128);
+    check_finite(a, zc, nc * 2, dtype == MOMA_C128);
+    sync_and_check(a);
+    a->mZB128.ensure(nb * sizeof(double2), a->dev_bytes);
+    a->mZC128.ensure(nc * sizeof(double2), a->dev_bytes);
+    launch_convert(zb, dtype == MOMA_C128, a->mZB128.p, 1, nb, a->st);
+    launch_convert(zc, dtype == MOMA_C128, a->mZC128.p, 1, nc, a->st);
+    if (a->prec == MOMA_PREC_MIXED) {
+      a->mZB64.ensure(nb * sizeof(float2), a->dev_bytes);
+      a->mZC64.ensure(nc * sizeof(float2), a->dev_bytes);
+      launch_convert(zb, dtype == MOMA_C128, a->mZB64.p, 0, nb, a->st);
+      launch_convert(zc, dtype == MOMA_C128, a->mZC64.p, 0, nc, a->st);
+    }
+    // Margin block of the preconditioner (Eq. 38), factored in FP64.
+    a->mP.ensure(nc * sizeof(double2), a->dev_bytes);
+    const size_t npk = (size_t)nm * (nm + 1) / 2;
+    a->mL.ensure(npk * sizeof(double2), a->dev_bytes);
+    launch_margin_precond_build(a->mZB128.as<double2>(), a->mZC128.as<double2>(), nm, a->N, a->mP.as<double2>(),
+                                a->mL.as<double2>(), a->err, a->st);
+    check_launch(a);
+    const size_t csz = a->prec == MOMA_PREC_FP64 ? sizeof(double2) : sizeof(float2);
+    size_t xs = npk;
+    while ((xs * csz) % 16) ++xs;
+    a->mx_stride = xs;
+    a->mX.ensure(xs * csz, a->dev_bytes);
+    if (a->prec == MOMA_PREC_FP64) launch_tri_inverse<double>(a->mL.as<double2>(), 1, nm, a->mX.p, xs, a->st);
+    else launch_tri_inverse<float>(a->mL.as<double2>(), 1, nm, a->mX.p, xs, a->st);
+    check_launch(a);
+    sync_and_check(a);
+    tmpB.release(a->dev_bytes);
+    tmpC.release(a->dev_bytes);
   });
 }
 
@@ -1853,6 +1972,7 @@ extern "C" moma_status moma_matvec_noalloc(moma_array *a, int op, int nrhs, cons
     if (!a->have_blocks) throw MomaError(MOMA_ERR_STATE, "set_blocks must precede matvec");
     if (op != MOMA_OP_Z && op != MOMA_OP_ZH) throw MomaError(MOMA_ERR_ARG, "op must be MOMA_OP_Z or MOMA_OP_ZH");
     if (dtype != MOMA_C128 && dtype != MOMA_C64) throw MomaError(MOMA_ERR_ARG, "bad dtype");
+    if (a->nm > 0) throw MomaError(MOMA_ERR_ARG, "the allocation-free product has no margin terms");
     const bool d64 = dtype == MOMA_C128;
     if (!d64 && a->prec != MOMA_PREC_MIXED) throw MomaError(MOMA_ERR_ARG, "c64 operators need a MIXED array");
     if (nrhs < 0) throw MomaError(MOMA_ERR_ARG, "nrhs < 0");

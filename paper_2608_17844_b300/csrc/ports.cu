@@ -8,23 +8,25 @@
 
 namespace moma {
 
-// V[q][e*b + pb] = (e == j0 + q), zero elsewhere; q < nq.
-__global__ void unit_ports_kernel(double2 *V, int nel, int b, int pb, int j0, int nq) {
-  const size_t N = (size_t)nel * b, total = (size_t)nq * N;
+// V[q][e*b + pb] = (e == j0 + q), zero elsewhere (margin entries too); q < nq,
+// per-RHS stride ldv.
+__global__ void unit_ports_kernel(double2 *V, int nel, int b, int pb, int j0, int nq, long long ldv) {
+  const size_t N = (size_t)ldv, total = (size_t)nq * N, NA = (size_t)nel * b;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
     const int q = (int)(idx / N);
     const size_t n = idx % N;
-    const bool on = (n % b) == (size_t)pb && (int)(n / b) == j0 + q;
+    const bool on = n < NA && (n % b) == (size_t)pb && (int)(n / b) == j0 + q;
     V[idx] = make_double2(on ? 1.0 : 0.0, 0.0);
   }
 }
 
 // Y[i][j0 + q] = I[q][i*b + pb]  (Y row-major n x n).
-__global__ void gather_ports_kernel(const double2 *I, int nel, int b, int pb, int j0, int nq, double2 *Y) {
+__global__ void gather_ports_kernel(const double2 *I, int nel, int b, int pb, int j0, int nq, double2 *Y,
+                                    long long ldv) {
   const int total = nel * nq;
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
     const int q = idx / nel, i = idx % nel;
-    Y[(size_t)i * nel + j0 + q] = I[((size_t)q * nel + i) * b + pb];
+    Y[(size_t)i * nel + j0 + q] = I[(size_t)q * ldv + (size_t)i * b + pb];
   }
 }
 
@@ -106,15 +108,16 @@ __global__ void gj_unpermute_kernel(double2 *A, int n, const int *perm) {
   }
 }
 
-void launch_unit_ports(double2 *V, int nel, int b, int pb, int j0, int nq, cudaStream_t st) {
-  size_t total = (size_t)nq * nel * b, g = (total + 255) / 256;
+void launch_unit_ports(double2 *V, int nel, int b, int pb, int j0, int nq, long long ldv, cudaStream_t st) {
+  size_t total = (size_t)nq * ldv, g = (total + 255) / 256;
   if (g > 4096) g = 4096;
-  unit_ports_kernel<<<(int)g, 256, 0, st>>>(V, nel, b, pb, j0, nq);
+  unit_ports_kernel<<<(int)g, 256, 0, st>>>(V, nel, b, pb, j0, nq, ldv);
 }
-void launch_gather_ports(const double2 *I, int nel, int b, int pb, int j0, int nq, double2 *Y, cudaStream_t st) {
+void launch_gather_ports(const double2 *I, int nel, int b, int pb, int j0, int nq, double2 *Y, long long ldv,
+                         cudaStream_t st) {
   int total = nel * nq, g = (total + 255) / 256;
   if (g > 4096) g = 4096;
-  gather_ports_kernel<<<g, 256, 0, st>>>(I, nel, b, pb, j0, nq, Y);
+  gather_ports_kernel<<<g, 256, 0, st>>>(I, nel, b, pb, j0, nq, Y, ldv);
 }
 void launch_invert(double2 *A, int n, int *perm, double2 *colk, unsigned *err, cudaStream_t st) {
   for (int k = 0; k < n; ++k) {

@@ -393,7 +393,8 @@ __global__ void __launch_bounds__(PA_THREADS) precond_apply_kernel(const typenam
                                                                    size_t x_stride, int nel, int b, int nr,
                                                                    const typename Cplx<R>::T *__restrict__ x,
                                                                    typename Cplx<R>::T *__restrict__ y,
-                                                                   unsigned *err, const int *live) {
+                                                                   unsigned *err, const int *live,
+                                                                   long long vstride, long long voff) {
   using C = typename Cplx<R>::T;
   extern __shared__ __align__(128) unsigned char smraw[];
   uint64_t *bar = reinterpret_cast<uint64_t *>(smraw);
@@ -428,7 +429,7 @@ __global__ void __launch_bounds__(PA_THREADS) precond_apply_kernel(const typenam
   for (int q0 = 0; q0 < nr; q0 += NR) {
     for (int idx = tid; idx < b * NR; idx += PA_THREADS) {
       const int k = idx / NR, q = q0 + idx % NR;
-      xs[idx] = q < nr ? x[((size_t)q * nel + e) * b + k] : czero<C>();
+      xs[idx] = q < nr ? x[(size_t)q * vstride + voff + (size_t)e * b + k] : czero<C>();
     }
     __syncthreads();
     C acc[U][NR];
@@ -500,7 +501,7 @@ __global__ void __launch_bounds__(PA_THREADS) precond_apply_kernel(const typenam
       C v = czero<C>();
       for (int ww = 0; ww < PA_WARPS; ++ww) v = cadd(v, tp[(size_t)ww * b * NR + idx]);
       const int k = idx / NR, qq = idx % NR;
-      if (q0 + qq < nr) y[((size_t)(q0 + qq) * nel + e) * b + k] = v;
+      if (q0 + qq < nr) y[(size_t)(q0 + qq) * vstride + voff + (size_t)e * b + k] = v;
     }
     __syncthreads();
   }
@@ -508,7 +509,7 @@ __global__ void __launch_bounds__(PA_THREADS) precond_apply_kernel(const typenam
 
 template <typename R, int NR, int U>
 static void apply_launch(const void *X, size_t x_stride, int nel, int b, int nr, const void *x, void *y,
-                         unsigned *err, const int *live, cudaStream_t st) {
+                         unsigned *err, const int *live, long long vstride, long long voff, cudaStream_t st) {
   using C = typename Cplx<R>::T;
   const size_t vec = (size_t)(2 + PA_WARPS) * b * NR * sizeof(C);
   const bool in_smem = 128 + x_stride * sizeof(C) + vec <= 220 * 1024;
@@ -523,28 +524,29 @@ static void apply_launch(const void *X, size_t x_stride, int nel, int b, int nr,
   auto kern = in_smem ? precond_apply_kernel<R, NR, U, true> : precond_apply_kernel<R, NR, U, false>;
   kern<<<nel, PA_THREADS, smem, st>>>(
       reinterpret_cast<const C *>(X), x_stride, nel, b, nr, reinterpret_cast<const C *>(x),
-      reinterpret_cast<C *>(y), err, live);
+      reinterpret_cast<C *>(y), err, live, vstride, voff);
 }
 
 template <typename R, int NR>
 static void apply_u(const void *X, size_t xs, int nel, int b, int nr, const void *x, void *y, unsigned *err,
-                    const int *live, cudaStream_t st) {
+                    const int *live, long long vs, long long vo, cudaStream_t st) {
   const int U = (b + 31) / 32;
-  if (U <= 1) apply_launch<R, NR, 1>(X, xs, nel, b, nr, x, y, err, live, st);
-  else if (U <= 2) apply_launch<R, NR, 2>(X, xs, nel, b, nr, x, y, err, live, st);
-  else if (U <= 4) apply_launch<R, NR, 4>(X, xs, nel, b, nr, x, y, err, live, st);
-  else apply_launch<R, NR, 8>(X, xs, nel, b, nr, x, y, err, live, st);
+  if (U <= 1) apply_launch<R, NR, 1>(X, xs, nel, b, nr, x, y, err, live, vs, vo, st);
+  else if (U <= 2) apply_launch<R, NR, 2>(X, xs, nel, b, nr, x, y, err, live, vs, vo, st);
+  else if (U <= 4) apply_launch<R, NR, 4>(X, xs, nel, b, nr, x, y, err, live, vs, vo, st);
+  else apply_launch<R, NR, 8>(X, xs, nel, b, nr, x, y, err, live, vs, vo, st);
 }
 
 template <typename R>
 void launch_precond_apply(const void *X, size_t x_stride, int nel, int b, int nr, const void *x, void *y,
-                          unsigned *err, const int *live, cudaStream_t st) {
-  if (nr == 1) apply_u<R, 1>(X, x_stride, nel, b, nr, x, y, err, live, st);
-  else apply_u<R, 2>(X, x_stride, nel, b, nr, x, y, err, live, st);
+                          unsigned *err, const int *live, long long vstride, long long voff, cudaStream_t st) {
+  if (vstride <= 0) vstride = (long long)nel * b;
+  if (nr == 1) apply_u<R, 1>(X, x_stride, nel, b, nr, x, y, err, live, vstride, voff, st);
+  else apply_u<R, 2>(X, x_stride, nel, b, nr, x, y, err, live, vstride, voff, st);
 }
 template void launch_precond_apply<float>(const void *, size_t, int, int, int, const void *, void *, unsigned *,
-                                          const int *, cudaStream_t);
+                                          const int *, long long, long long, cudaStream_t);
 template void launch_precond_apply<double>(const void *, size_t, int, int, int, const void *, void *, unsigned *,
-                                           const int *, cudaStream_t);
+                                           const int *, long long, long long, cudaStream_t);
 
 }  // namespace moma

@@ -22,13 +22,13 @@
 namespace moma {
 
 // V[q][e*b + pb] = exp(j mx psi_{q0+q}), zero on the other bases.
-__global__ void row_phase_kernel(double2 *V, int nx, int nel, int b, int pb, int q0, int nq, int Q) {
-  const size_t N = (size_t)nel * b, total = (size_t)nq * N;
+__global__ void row_phase_kernel(double2 *V, int nx, int nel, int b, int pb, int q0, int nq, int Q, long long ldv) {
+  const size_t N = (size_t)ldv, total = (size_t)nq * N, NA = (size_t)nel * b;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
     const int q = (int)(idx / N);
     const size_t n = idx % N;
     double2 v = make_double2(0.0, 0.0);
-    if ((int)(n % b) == pb) {
+    if (n < NA && (int)(n % b) == pb) {
       const int mx = (int)(n / b) % nx;
       // psi = -pi + 2 pi k / Q, k = q0 + q; mx psi = pi (2 mx k / Q - mx).
       const long long k = q0 + q;
@@ -110,8 +110,9 @@ static int grid_for(size_t total) {
   return (int)(g > 8192 ? 8192 : (g < 1 ? 1 : g));
 }
 
-void launch_row_phase(double2 *V, int nx, int nel, int b, int pb, int q0, int nq, int Q, cudaStream_t st) {
-  row_phase_kernel<<<grid_for((size_t)nq * nel * b), 256, 0, st>>>(V, nx, nel, b, pb, q0, nq, Q);
+void launch_row_phase(double2 *V, int nx, int nel, int b, int pb, int q0, int nq, int Q, long long ldv,
+                      cudaStream_t st) {
+  row_phase_kernel<<<grid_for((size_t)nq * ldv), 256, 0, st>>>(V, nx, nel, b, pb, q0, nq, Q, ldv);
 }
 void launch_column_coupling(const double2 *gamma, int Q, int nmax, double2 *C, cudaStream_t st) {
   column_coupling_kernel<<<(2 * nmax + 1 + 127) / 128, 128, 0, st>>>(gamma, Q, nmax, C);

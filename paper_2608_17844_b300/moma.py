@@ -34,7 +34,7 @@ EXPORTS = [
     "moma_launch_count", "moma_device_bytes", "moma_destroy", "moma_last_error", "moma_matvec_noalloc",
     "moma_set_stream", "moma_release_setup", "moma_estimate_bytes", "moma_tuning_report", "moma_array_stream",
     "moma_set_blocks_batch", "moma_solve_batch", "moma_port_impedance",
-    "moma_column_coupling", "moma_s_to_z", "moma_s_ideal", "moma_xi_z", "moma_xi_s",
+    "moma_column_coupling", "moma_s_to_z", "moma_s_ideal", "moma_xi_z", "moma_xi_s", "moma_set_margin",
     "moma_server_create", "moma_server_submit", "moma_server_wait", "moma_server_get_stats", "moma_server_destroy",
 ]
 
@@ -123,6 +123,7 @@ def lib():
     d = ctypes.c_double
     L.moma_column_coupling.argtypes = [vp, i, i, i, d, ctypes.POINTER(moma_solve_opts), vp, vp]
     L.moma_s_to_z.argtypes = [vp, i, d, vp, vp]
+    L.moma_set_margin.argtypes = [vp, i, vp, vp, i]
     L.moma_s_ideal.argtypes = [i, i, d, d, d, d, d, vp, vp]
     L.moma_xi_z.argtypes = [vp, i, i, ctypes.POINTER(ctypes.c_double)]
     L.moma_xi_s.argtypes = [i, i, d, d, d, d, d, d, ctypes.POINTER(ctypes.c_double)]
@@ -433,3 +434,15 @@ def moma_xi_s(nx, ny, s_cc, s1, kd, z0=50.0):
     out = ctypes.c_double()
     _check(lib().moma_xi_s(nx, ny, s_cc.real, s_cc.imag, s1.real, s1.imag, kd, z0, ctypes.byref(out)))
     return out.value
+
+
+def moma_set_margin(h, ZB, ZC):
+    """Margin blocks Z_B [nm][N], Z_C [nm][nm] (same dtype); ZB=None removes the margin."""
+    if ZB is None:
+        _check(lib().moma_set_margin(h, 0, None, None, MOMA_C128))
+        return
+    pb, db = _ptr_dtype(ZB)
+    pc, dc = _ptr_dtype(ZC)
+    if db != dc:
+        raise TypeError("ZB and ZC must have the same dtype")
+    _check(lib().moma_set_margin(h, ZB.shape[0], pb, pc, db))

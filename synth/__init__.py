@@ -12,6 +12,8 @@ from .lattice import (
     element_geometry,
     offset_blocks,
     offset_blocks_torch,
+    margin_geometry,
+    margin_blocks,
     excitation,
     scan_phase,
     config_c1,
@@ -26,6 +28,8 @@ __all__ = [
     "element_geometry",
     "offset_blocks",
     "offset_blocks_torch",
+    "margin_geometry",
+    "margin_blocks",
     "excitation",
     "scan_phase",
     "config_c1",

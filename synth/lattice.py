@@ -116,6 +116,48 @@ def offset_blocks_torch(spec, device="cuda", dtype=None):
     return out
 
 
+def margin_geometry(spec, bm=2):
+    """Basis positions, weights and orientations of a synthetic array margin:
+    bm basis functions in every cell of the ring around the lattice (cells
+    (mx, my), -1 <= mx <= Nx, -1 <= my <= Ny, on the ring's boundary), drawn
+    from seed + 1.  Returns (pos [nm, 2], w [nm], alpha [nm])."""
+    nx, ny, d = spec.nx, spec.ny, spec.d
+    u, w1, a1 = element_geometry(bm, d, spec.seed + 1)
+    cells = [(mx, my) for my in range(-1, ny + 1) for mx in range(-1, nx + 1)
+             if mx in (-1, nx) or my in (-1, ny)]
+    pos = np.array([[mx * d + u[i, 0], my * d + u[i, 1]] for (mx, my) in cells for i in range(bm)])
+    w = np.tile(w1, len(cells))
+    alpha = np.tile(a1, len(cells))
+    return pos, w, alpha
+
+
+def margin_blocks(spec, bm=2, dtype=np.complex128):
+    """Margin blocks of the reciprocal synthetic MoM matrix Z = [Z_A, Z_B^T;
+    Z_B, Z_C] (Sec. II-A's margin partition): Z_B [nm][N] couples margin
+    basis m to lattice unknown e*b + i, Z_C [nm][nm] the margin bases among
+    themselves, both with the lattice kernel w w' cos(alpha - alpha')
+    e^{-jkr} / (4 pi r) (r floored at 0.01) and 50+30j ohm self-loading on
+    Z_C's diagonal."""
+    nx, ny, b, d = spec.nx, spec.ny, spec.b, spec.d
+    mp, mw, ma = margin_geometry(spec, bm)
+    p, w, alpha = element_geometry(b, d, spec.seed)
+    ex = np.arange(nx * ny) % nx
+    ey = np.arange(nx * ny) // nx
+    lp = np.stack([(ex[:, None] * d + p[None, :, 0]).ravel(), (ey[:, None] * d + p[None, :, 1]).ravel()], axis=1)
+    lw = np.tile(w, nx * ny)
+    la = np.tile(alpha, nx * ny)
+
+    def kernel(p1, w1, a1, p2, w2, a2):
+        r = np.sqrt(((p1[:, None, :] - p2[None, :, :]) ** 2).sum(-1))
+        r = np.maximum(r, R_FLOOR)
+        coef = np.outer(w1, w2) * np.cos(a1[:, None] - a2[None, :])
+        return coef * np.exp(-1j * K_WAVENUMBER * r) / (4.0 * np.pi * r)
+
+    zb = kernel(mp, mw, ma, lp, lw, la)
+    zc = kernel(mp, mw, ma, mp, mw, ma) + SELF_LOAD * np.eye(len(mp))
+    return zb.astype(dtype), zc.astype(dtype)
+
+
 def scan_phase(nx, ny, d, theta_deg, phi_deg):
     """Progressive port phase a[my][mx] = exp(-j k d sin(theta) (mx cos(phi) + my sin(phi)))."""
     th = np.deg2rad(theta_deg)
