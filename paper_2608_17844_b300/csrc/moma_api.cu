@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <map>
 #include <memory>
 #include <type_traits>
 #include <thread>
@@ -188,6 +189,18 @@ struct moma_array {
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   std::vector<cudaGraphExec_t> gexec;
   int g_nr = -1;
+  // Captured step graphs kept per RHS count, so that calls alternating
+  // between RHS counts (serving, batches) replay instead of re-capturing.
+  struct GraphSet {
+    std::vector<cudaGraphExec_t> g;
+    long long step_launches = 0;
+  };
+  std::map<int, GraphSet> gmres_graphs, pcg_graphs;
+  // Autotuned bin-product shapes per RHS count.
+  struct TuneBin {
+    int tr[2], ns[2], occ[2];
+  };
+  std::map<int, TuneBin> tune_by_nr;
   long long g_step_launches = 0;
   // Autotuned launch shapes (0 = built-in heuristic), per RHS count.
   int tuned_nr = -1;
@@ -586,6 +599,12 @@ void drop_graphs(moma_array *a) {
     if (g) cudaGraphExecDestroy(g);
   a->cg_gexec.clear();
   a->cg_g_nr = -1;
+  for (auto *m : {&a->gmres_graphs, &a->pcg_graphs}) {
+    for (auto &kv : *m)
+      for (auto g : kv.second.g)
+        if (g) cudaGraphExecDestroy(g);
+    m->clear();
+  }
 }
 
 void ensure_ws(moma_array *a, int nr) {
@@ -973,14 +992,31 @@ void autotune_precision(moma_array *a, int nr, int in128) {
 
 void autotune(moma_array *a, int nr) {
   if (a->tuned_nr == nr || a->no_autotune || std::getenv("MOMA_NO_AUTOTUNE")) return;
-  a->tune_axis.clear();
-  a->tune_log.clear();
+  auto it = a->tune_by_nr.find(nr);
+  if (it != a->tune_by_nr.end()) {  // tuned before for this RHS count
+    for (int k = 0; k < 2; ++k) {
+      a->tune_bin_tr[k] = it->second.tr[k];
+      a->tune_bin_ns[k] = it->second.ns[k];
+      a->tune_bin_occ[k] = it->second.occ[k];
+    }
+    a->tuned_nr = nr;
+    return;
+  }
+  // FFT pass shapes accumulate in tune_axis (their signatures include the
+  // RHS count); the bin-product shapes are kept per RHS count.
   a->tune_bin_tr[0] = a->tune_bin_tr[1] = a->tune_bin_ns[0] = a->tune_bin_ns[1] = 0;
   a->tune_bin_occ[0] = a->tune_bin_occ[1] = 1;
   if (a->prec == MOMA_PREC_MIXED) autotune_precision<float>(a, nr, 0);
   // The FP64-class residual runs in double-FP32 pairs in the mixed path.
   if (a->prec == MOMA_PREC_MIXED) autotune_precision<dfl>(a, nr, 1);
   else autotune_precision<double>(a, nr, 1);
+  moma_array::TuneBin t;
+  for (int k = 0; k < 2; ++k) {
+    t.tr[k] = a->tune_bin_tr[k];
+    t.ns[k] = a->tune_bin_ns[k];
+    t.occ[k] = a->tune_bin_occ[k];
+  }
+  a->tune_by_nr[nr] = t;
   a->tuned_nr = nr;
 }
 
@@ -1032,8 +1068,24 @@ void gmres_cycle(moma_array *a, int nr, const std::vector<int> &act, int *inner_
   // With graphs on, step j is captured once (per RHS count) and replayed.
   const bool graphs = a->use_graphs && !a->prof && a->st == a->gs && a->gs != nullptr;
   if (graphs && a->g_nr != nr) {
-    drop_graphs(a);
-    a->gexec.assign(a->m, nullptr);
+    // Park the current RHS count's graphs and take (or start) this one's.
+    if (a->g_nr >= 0) {
+      auto &park = a->gmres_graphs[a->g_nr];
+      park.g.swap(a->gexec);
+      park.step_launches = a->g_step_launches;
+    }
+    a->gexec.clear();
+    auto it = a->gmres_graphs.find(nr);
+    if (it != a->gmres_graphs.end()) {
+      a->gexec.swap(it->second.g);
+      a->g_step_launches = it->second.step_launches;
+      a->gmres_graphs.erase(it);
+    }
+    if (a->gexec.size() != (size_t)a->m) {
+      for (auto g : a->gexec)
+        if (g) cudaGraphExecDestroy(g);
+      a->gexec.assign(a->m, nullptr);
+    }
     a->g_nr = nr;
   }
   int steps = 0;
@@ -1149,9 +1201,23 @@ void pcg_cycle(moma_array *a, int nr, const std::vector<int> &act, int max_inner
   };
   const bool graphs = a->use_graphs && !a->prof && a->st == a->gs && a->gs != nullptr;
   if (graphs && a->cg_g_nr != nr) {
-    for (auto g : a->cg_gexec)
-      if (g) cudaGraphExecDestroy(g);
-    a->cg_gexec.assign(RING, nullptr);
+    if (a->cg_g_nr >= 0) {
+      auto &park = a->pcg_graphs[a->cg_g_nr];
+      park.g.swap(a->cg_gexec);
+      park.step_launches = a->cg_step_launches;
+    }
+    a->cg_gexec.clear();
+    auto it = a->pcg_graphs.find(nr);
+    if (it != a->pcg_graphs.end()) {
+      a->cg_gexec.swap(it->second.g);
+      a->cg_step_launches = it->second.step_launches;
+      a->pcg_graphs.erase(it);
+    }
+    if (a->cg_gexec.size() != (size_t)RING) {
+      for (auto g : a->cg_gexec)
+        if (g) cudaGraphExecDestroy(g);
+      a->cg_gexec.assign(RING, nullptr);
+    }
     a->cg_g_nr = nr;
   }
   const int lag = 2;

@@ -9,6 +9,8 @@
 // lookups, so the cost is O((2Nx-1)(2Ny-1) b^3) instead of O(Nel^2 b^3).
 // P_e = L_e L_e^H by Cholesky in FP64 (Sec. III-A), and P^{-1} is applied
 // as X_e^H X_e with X_e = L_e^{-1} stored packed.
+#include <algorithm>
+
 #include "internal.h"
 
 namespace moma {
@@ -388,44 +390,15 @@ template void launch_tri_inverse<double>(const double2 *, int, int, void *, size
 //    z_k = sum_i conj(X(i,k)) t_i is a warp reduction.
 constexpr int PA_THREADS = 256, PA_WARPS = 8;
 
-template <typename R, int NR, int U, bool X_IN_SMEM>
-__global__ void __launch_bounds__(PA_THREADS) precond_apply_kernel(const typename Cplx<R>::T *__restrict__ X,
-                                                                   size_t x_stride, int nel, int b, int nr,
-                                                                   const typename Cplx<R>::T *__restrict__ x,
-                                                                   typename Cplx<R>::T *__restrict__ y,
-                                                                   unsigned *err, const int *live,
-                                                                   long long vstride, long long voff) {
+// The two triangular products of one element (phases 1 and 2 below), X_e
+// already in shared memory (or global memory) at Xs.
+template <typename R, int NR, int U>
+MOMA_DEV void apply_element(const typename Cplx<R>::T *Xs, int e, int nel, int b, int nr,
+                            const typename Cplx<R>::T *__restrict__ x, typename Cplx<R>::T *__restrict__ y,
+                            typename Cplx<R>::T *xs, typename Cplx<R>::T *ts, typename Cplx<R>::T *tp,
+                            long long vstride, long long voff) {
   using C = typename Cplx<R>::T;
-  extern __shared__ __align__(128) unsigned char smraw[];
-  uint64_t *bar = reinterpret_cast<uint64_t *>(smraw);
-  C *xs = reinterpret_cast<C *>(smraw + 128) + (X_IN_SMEM ? x_stride : 0);  // [b][NR]
-  const C *Xs = X_IN_SMEM ? reinterpret_cast<const C *>(smraw + 128) : X + (size_t)blockIdx.x * x_stride;
-  C *ts = xs + (size_t)b * NR;        // [b][NR]
-  C *tp = ts + (size_t)b * NR;        // [PA_WARPS][b][NR]
-  const int e = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  if (live && *live == 0) return;
-  if (X_IN_SMEM) {
-    if (tid == 0) {
-      mbar_init(bar, 1);
-      fence_mbar_init();
-    }
-    __syncthreads();
-    if (tid == 0) {
-      const uint32_t bytes = (uint32_t)(x_stride * sizeof(C));
-      fence_proxy_async();
-      mbar_expect_tx(bar, bytes);
-      bulk_g2s(const_cast<C *>(Xs), X + (size_t)e * x_stride, bytes, bar);
-    }
-    const bool ok = mbar_wait_bounded(bar, 0, 2000000000ull);
-    if (__syncthreads_or(!ok)) {
-      if (tid == 0) {
-        atomicOr(err, DEVERR_TIMEOUT);
-        mbar_wait_bounded(bar, 0, 2000000000ull);
-      }
-      return;
-    }
-  }
-
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   for (int q0 = 0; q0 < nr; q0 += NR) {
     for (int idx = tid; idx < b * NR; idx += PA_THREADS) {
       const int k = idx / NR, q = q0 + idx % NR;
@@ -505,6 +478,47 @@ __global__ void __launch_bounds__(PA_THREADS) precond_apply_kernel(const typenam
     }
     __syncthreads();
   }
+}
+
+template <typename R, int NR, int U, bool X_IN_SMEM>
+__global__ void __launch_bounds__(PA_THREADS) precond_apply_kernel(const typename Cplx<R>::T *__restrict__ X,
+                                                                   size_t x_stride, int nel, int b, int nr,
+                                                                   const typename Cplx<R>::T *__restrict__ x,
+                                                                   typename Cplx<R>::T *__restrict__ y,
+                                                                   unsigned *err, const int *live,
+                                                                   long long vstride, long long voff) {
+  using C = typename Cplx<R>::T;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smraw);
+  C *xs = reinterpret_cast<C *>(smraw + 128) + (X_IN_SMEM ? x_stride : 0);  // [b][NR]
+  const C *Xs = X_IN_SMEM ? reinterpret_cast<const C *>(smraw + 128) : X + (size_t)blockIdx.x * x_stride;
+  C *ts = xs + (size_t)b * NR;        // [b][NR]
+  C *tp = ts + (size_t)b * NR;        // [PA_WARPS][b][NR]
+  const int e = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  if (live && *live == 0) return;
+  if (X_IN_SMEM) {
+    if (tid == 0) {
+      mbar_init(bar, 1);
+      fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+      const uint32_t bytes = (uint32_t)(x_stride * sizeof(C));
+      fence_proxy_async();
+      mbar_expect_tx(bar, bytes);
+      bulk_g2s(const_cast<C *>(Xs), X + (size_t)e * x_stride, bytes, bar);
+    }
+    const bool ok = mbar_wait_bounded(bar, 0, 2000000000ull);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        atomicOr(err, DEVERR_TIMEOUT);
+        mbar_wait_bounded(bar, 0, 2000000000ull);
+      }
+      return;
+    }
+  }
+
+  apply_element<R, NR, U>(Xs, e, nel, b, nr, x, y, xs, ts, tp, vstride, voff);
 }
 
 template <typename R, int NR, int U>
