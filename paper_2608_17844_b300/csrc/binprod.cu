@@ -18,8 +18,9 @@
 //    (cp.async.bulk), each completing on the stage's "full" mbarrier, and
 //    refills a stage once the eight consumer warps have arrived on its
 //    "empty" mbarrier;
-//  * twelve consumer warps own groups of four rows of a tile, lanes own pairs of
-//    adjacent columns.  Row products of a row group are reduced across the
+//  * eight consumer warps own groups of four rows of a tile, lanes own pairs of
+//    adjacent columns (eight, so that the 32 groups of a b = 128 block, or
+//    the 64 of b = 256, split evenly and no warp idles at the end of a pair).  Row products of a row group are reduced across the
 //    warp by recursive halving (one shuffle tree for all 4 rows x nrhs
 //    values); column products accumulate in registers over the whole block
 //    and are reduced across warps once per pair;
@@ -35,7 +36,7 @@
 
 namespace moma {
 
-constexpr int BP_CONSUMERS = 12;
+constexpr int BP_CONSUMERS = 8;
 constexpr int BP_THREADS = (BP_CONSUMERS + 1) * 32;
 constexpr int BP_ROWS = 4;  // rows per warp group
 constexpr uint64_t BP_WAIT_NS = 2000000000ull;
@@ -108,8 +109,9 @@ MOMA_DEV void load_pair(const double2 *p, double2 (&z)[2]) {
   z[1] = p[1];
 }
 
-// MINB = CTAs per SM the register budget is sized for (2: smaller tiles,
-// twice the warps in flight to hide shared-memory and FMA latency).
+// MINB = CTAs per SM the register budget is sized for (1: 168 registers a
+// thread, 2: 102, 3: 72; more CTAs keep more warps in flight to hide
+// shared-memory and FMA latency, with smaller tiles).
 template <typename R, int NR, int U2, bool HERM, int MINB>
 __global__ void __launch_bounds__(BP_THREADS, MINB) bin_pair_kernel(BinKernelArgs A) {
   using C = typename Cplx<R>::T;
@@ -254,7 +256,7 @@ __global__ void __launch_bounds__(BP_THREADS, MINB) bin_pair_kernel(BinKernelArg
     const C *tile = stage0 + (size_t)s * stage_elems;
     const int r0 = t * TR, rows = ok ? min(TR, b - r0) : 0;
     constexpr int NV = BP_ROWS * NR * 2;
-    // Row group j (rows 4j .. 4j+3 of the block) belongs to warp j mod 12
+    // Row group j (rows 4j .. 4j+3 of the block) belongs to warp j mod 8
     // whatever the tile height, so every warp accumulates the same rows in
     // the same order for any tuned shape: results are bitwise independent
     // of TR, NS and CTAs per SM (tiles start on multiples of 4 rows).
@@ -346,11 +348,13 @@ static void launch_one(const BinProduct &P, int num_sms, cudaStream_t st, int q0
     return 256 + (size_t)ns * tr * row_bytes + (size_t)4 * NR * P.b * sizeof(C) +
            (size_t)BP_CONSUMERS * P.b * NR * sizeof(C);
   };
-  // Two CTAs per SM (smaller tiles, 72-register budget) only where the
-  // per-lane state is small: c64, at most two RHS per chunk and b <= 128.
-  constexpr bool two_ok = sizeof(R) == 4 && NR <= 2 && U2 <= 2;
-  const int occ = (two_ok && P.occ == 2) ? 2 : 1;
-  const size_t cap = occ == 2 ? 110 * 1024 : 220 * 1024;
+  // Two or three CTAs per SM (smaller tiles, 102- or 72-register budget)
+  // only where the per-lane state is small: at most two RHS per chunk and
+  // b <= 128; three only for c64.
+  constexpr bool occ2_ok = NR <= 2 && U2 <= 2;
+  constexpr bool occ3_ok = sizeof(R) == 4 && NR <= 2 && U2 <= 2;
+  const int occ = (P.occ == 3 && occ3_ok) ? 3 : (P.occ == 2 && occ2_ok) ? 2 : 1;
+  const size_t cap = occ == 3 ? 74 * 1024 : occ == 2 ? 110 * 1024 : 220 * 1024;
   // Tiles of whole rows, at most 48 KB and at most one 4-row group per
   // consumer warp; 3 stages (fewer if shared memory runs out).
   int TR = 49152 / row_bytes;
@@ -368,13 +372,25 @@ static void launch_one(const BinProduct &P, int num_sms, cudaStream_t st, int q0
     }
   }
   while (NS > 2 && smem_for(NS, TR) > cap) --NS;
-  while (TR > 4 && smem_for(NS, TR) > cap) TR -= 4;  // wide blocks (b > 160) or two CTAs per SM
+  while (TR > 4 && smem_for(NS, TR) > cap) TR -= 4;  // wide blocks (b > 160) or several CTAs per SM
   const int ntile = (P.b + TR - 1) / TR;
   const size_t smem = smem_for(NS, TR);
   int grid = num_sms * occ;
   if (grid > P.Bp) grid = P.Bp;
   BinKernelArgs a{P, TR, ntile, NS, q0};
-  if constexpr (two_ok) {
+  if constexpr (occ3_ok) {
+    if (occ == 3) {
+      auto kern = bin_pair_kernel<R, NR, U2, HERM, 3>;
+      static int configured3 = 0;
+      if (!configured3) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 74 * 1024);
+        configured3 = 1;
+      }
+      kern<<<grid, BP_THREADS, smem, st>>>(a);
+      return;
+    }
+  }
+  if constexpr (occ2_ok) {
     if (occ == 2) {
       auto kern = bin_pair_kernel<R, NR, U2, HERM, 2>;
       static int configured2 = 0;

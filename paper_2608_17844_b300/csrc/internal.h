@@ -69,7 +69,7 @@ struct BinProduct {
   unsigned *err = nullptr;
   const int *live = nullptr;  // if set and *live == 0 the product does nothing
   int TR = 0, NS = 0;         // rows per tile / pipeline stages (0 = heuristic; autotuner)
-  int occ = 1;                // CTAs per SM (2: small-tile variant, c64 with <= 2 RHS per chunk, b <= 128)
+  int occ = 1;                // CTAs per SM (2, 3: small-tile variants, <= 2 RHS per chunk, b <= 128; 3 for c64 only)
 };
 template <typename R>
 void launch_bin_product(const BinProduct &p, int num_sms, cudaStream_t st);

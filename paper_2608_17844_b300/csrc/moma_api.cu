@@ -940,9 +940,11 @@ void autotune_precision(moma_array *a, int nr, int in128) {
   {
     float best = 1e30f;
     int btr = 0, bns = 0, bocc = 1;
-    for (int occ : {1, 2}) {
-      if (occ == 2 && (is64<R>() || nr > 2 || a->b > 128)) continue;  // the two-CTA variant's domain
-      for (int tr : {8, 16, 24, 32, 48}) {
+    for (int occ : {1, 2, 3}) {
+      // The multi-CTA variants' domain: at most two RHS, b <= 128; three CTAs for c64 only.
+      if (occ > 1 && (nr > 2 || a->b > 128)) continue;
+      if (occ == 3 && is64<R>()) continue;
+      for (int tr : {8, 16, 24, 32}) {
         if (tr > ((a->b + 3) & ~3) && tr != 16) continue;
         if (occ == 1 && tr < 16) continue;
         for (int ns : {2, 3, 4}) {
