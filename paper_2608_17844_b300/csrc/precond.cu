@@ -388,22 +388,33 @@ template void launch_tri_inverse<double>(const double2 *, int, int, void *, size
 //    accumulate X(i,k) x_k in registers; partial t is reduced across warps.
 //  Phase 2, z = X^H t: warps own columns k, lanes own rows i >= k, and
 //    z_k = sum_i conj(X(i,k)) t_i is a warp reduction.
-constexpr int PA_THREADS = 256, PA_WARPS = 8;
+// Sixteen warps per element: each warp's serial chain over its columns
+// (phase 1) or rows (phase 2) is b / 16 long.
+constexpr int PA_THREADS = 512, PA_WARPS = 16;
+
+// x_e of RHS q0 .. q0+NR-1 into shared memory, [b][NR].
+template <typename R, int NR>
+MOMA_DEV void load_x_chunk(const typename Cplx<R>::T *__restrict__ x, typename Cplx<R>::T *xs, int e, int b, int nr,
+                           int q0, long long vstride, long long voff) {
+  using C = typename Cplx<R>::T;
+  for (int idx = threadIdx.x; idx < b * NR; idx += PA_THREADS) {
+    const int k = idx / NR, q = q0 + idx % NR;
+    xs[idx] = q < nr ? x[(size_t)q * vstride + voff + (size_t)e * b + k] : czero<C>();
+  }
+}
 
 // The two triangular products of one element (phases 1 and 2 below), X_e
-// already in shared memory (or global memory) at Xs.
+// already in shared memory (or global memory) at Xs; the first RHS chunk
+// of x_e is already in xs when first_loaded is set.
 template <typename R, int NR, int U>
 MOMA_DEV void apply_element(const typename Cplx<R>::T *Xs, int e, int nel, int b, int nr,
                             const typename Cplx<R>::T *__restrict__ x, typename Cplx<R>::T *__restrict__ y,
                             typename Cplx<R>::T *xs, typename Cplx<R>::T *ts, typename Cplx<R>::T *tp,
-                            long long vstride, long long voff) {
+                            long long vstride, long long voff, bool first_loaded) {
   using C = typename Cplx<R>::T;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   for (int q0 = 0; q0 < nr; q0 += NR) {
-    for (int idx = tid; idx < b * NR; idx += PA_THREADS) {
-      const int k = idx / NR, q = q0 + idx % NR;
-      xs[idx] = q < nr ? x[(size_t)q * vstride + voff + (size_t)e * b + k] : czero<C>();
-    }
+    if (q0 > 0 || !first_loaded) load_x_chunk<R, NR>(x, xs, e, b, nr, q0, vstride, voff);
     __syncthreads();
     C acc[U][NR];
 #pragma unroll
@@ -481,7 +492,7 @@ MOMA_DEV void apply_element(const typename Cplx<R>::T *Xs, int e, int nel, int b
 }
 
 template <typename R, int NR, int U, bool X_IN_SMEM>
-__global__ void __launch_bounds__(PA_THREADS) precond_apply_kernel(const typename Cplx<R>::T *__restrict__ X,
+__global__ void __launch_bounds__(PA_THREADS, U <= 4 ? 2 : 1) precond_apply_kernel(const typename Cplx<R>::T *__restrict__ X,
                                                                    size_t x_stride, int nel, int b, int nr,
                                                                    const typename Cplx<R>::T *__restrict__ x,
                                                                    typename Cplx<R>::T *__restrict__ y,
@@ -508,6 +519,8 @@ __global__ void __launch_bounds__(PA_THREADS) precond_apply_kernel(const typenam
       mbar_expect_tx(bar, bytes);
       bulk_g2s(const_cast<C *>(Xs), X + (size_t)e * x_stride, bytes, bar);
     }
+    // The first RHS chunk of x_e is read while X_e is in flight.
+    load_x_chunk<R, NR>(x, xs, e, b, nr, 0, vstride, voff);
     const bool ok = mbar_wait_bounded(bar, 0, 2000000000ull);
     if (__syncthreads_or(!ok)) {
       if (tid == 0) {
@@ -518,7 +531,7 @@ __global__ void __launch_bounds__(PA_THREADS) precond_apply_kernel(const typenam
     }
   }
 
-  apply_element<R, NR, U>(Xs, e, nel, b, nr, x, y, xs, ts, tp, vstride, voff);
+  apply_element<R, NR, U>(Xs, e, nel, b, nr, x, y, xs, ts, tp, vstride, voff, X_IN_SMEM);
 }
 
 template <typename R, int NR, int U>
