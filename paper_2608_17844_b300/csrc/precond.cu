@@ -10,6 +10,7 @@
 // P_e = L_e L_e^H by Cholesky in FP64 (Sec. III-A), and P^{-1} is applied
 // as X_e^H X_e with X_e = L_e^{-1} stored packed.
 #include <algorithm>
+#include <type_traits>
 
 #include "internal.h"
 
@@ -164,6 +165,33 @@ MOMA_DEV double real_part(dfl2 v) { return (double)v.x; }
 MOMA_DEV double rsqrt_root(double d, double *l) { *l = sqrt(d); return 1.0 / *l; }
 MOMA_DEV dfl rsqrt_root(dfl d, dfl *l) { *l = dsqrt(d); return dfl(1.0f) / *l; }
 
+// Unnormalised double-FP32 accumulator (value s + t) for the CH_NB terms a
+// trailing-update entry receives from one panel: each product's high part
+// joins s through an exact two-sum, the rounding error of that sum and the
+// product's error (FMA two-product) gather in t, and one two-sum at the end
+// renormalises.  Against a renormalised `fma` per term this saves a
+// fast two-sum per term; every step that was exact stays exact.
+struct DfAcc {
+  float s, t;
+};
+MOMA_DEV DfAcc dfacc(dfl c) { return DfAcc{c.hi, c.lo}; }
+MOMA_DEV void dfacc_fma(DfAcc &acc, dfl a, dfl b) {  // acc += a b
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+  const dfl q = df_two_sum(acc.s, p);
+  acc.s = q.hi;
+  acc.t = __fadd_rn(acc.t, __fadd_rn(q.lo, e));
+}
+MOMA_DEV dfl dfacc_value(DfAcc acc) { return df_two_sum(acc.s, acc.t); }
+// acc -= a conj(b) (the Cholesky update term), on the real and imaginary parts.
+MOMA_DEV void dfacc_fms_conj(DfAcc &re, DfAcc &im, const dfl2 &a, const dfl2 &b) {
+  dfacc_fma(re, -a.x, b.x);
+  dfacc_fma(re, -a.y, b.y);
+  dfacc_fma(im, -a.y, b.x);
+  dfacc_fma(im, a.x, b.y);
+}
+
 template <bool IN_SMEM, typename R>
 __global__ void __launch_bounds__(512) box_cholesky_kernel(const double2 *__restrict__ S, int nx, int ny, int b,
                                                            double2 *__restrict__ Lpk, unsigned *err) {
@@ -225,11 +253,24 @@ __global__ void __launch_bounds__(512) box_cholesky_kernel(const double2 *__rest
       const bool two = t2 < npk;
       const short2 ik0 = tab[t], ik1 = two ? tab[t2] : ik0;
       C a0 = A[t], a1 = two ? A[t2] : a0;
+      if constexpr (std::is_same<R, dfl>::value) {
+        DfAcc r0 = dfacc(a0.x), i0 = dfacc(a0.y), r1 = dfacc(a1.x), i1 = dfacc(a1.y);
 #pragma unroll
-      for (int p = 0; p < CH_NB; ++p) {
-        if (p < np) {
-          a0 = cfms_conj(A[pb[p] + ik0.x], A[pb[p] + ik0.y], a0);
-          a1 = cfms_conj(A[pb[p] + ik1.x], A[pb[p] + ik1.y], a1);
+        for (int p = 0; p < CH_NB; ++p) {
+          if (p < np) {
+            dfacc_fms_conj(r0, i0, A[pb[p] + ik0.x], A[pb[p] + ik0.y]);
+            dfacc_fms_conj(r1, i1, A[pb[p] + ik1.x], A[pb[p] + ik1.y]);
+          }
+        }
+        a0 = mk(dfacc_value(r0), dfacc_value(i0));
+        a1 = mk(dfacc_value(r1), dfacc_value(i1));
+      } else {
+#pragma unroll
+        for (int p = 0; p < CH_NB; ++p) {
+          if (p < np) {
+            a0 = cfms_conj(A[pb[p] + ik0.x], A[pb[p] + ik0.y], a0);
+            a1 = cfms_conj(A[pb[p] + ik1.x], A[pb[p] + ik1.y], a1);
+          }
         }
       }
       A[t] = a0;
