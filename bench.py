@@ -217,7 +217,7 @@ def cpu_oracle_sample(spec, blocks, V, seconds):
     per_solve = t_iter * iters
     return {"value": 1.0 / per_solve, "unit": "solves/s", "cores": cores, "kind": "oracle",
             "sample": (f"oracle-I (complex128 GMRES, direct offset-sum product, block Jacobi) on RHS 0 of the same "
-                       f"32x32 b=128 problem for {hist[-1][0]:.1f} s: {hist[-1][1]} iterations at "
+                       f"{spec.nx}x{spec.ny} b={spec.b} problem for {hist[-1][0]:.1f} s: {hist[-1][1]} iterations at "
                        f"{t_iter:.2f} s each, residual {hist[-1][2]:.2e}; "
                        + ("converged" if converged else f"extrapolated to {iters} iterations for 1e-10")),
             "s_per_iteration": t_iter, "iterations_for_1e-10": iters}
@@ -497,7 +497,9 @@ def run_reference(args, world, rank):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * 2 / value if value else None,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD if not args.lattice else f"profiling lattice {args.lattice}, 1 RHS sampled",
+                       "l2": "n/a (CPU)"},
             "cpu_baseline": {k: cb[k] for k in ("kind", "cores", "sample")} | {"value": value} if cb else None,
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
