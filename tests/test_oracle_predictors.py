@@ -111,3 +111,36 @@ def test_s_ideal_structure_and_xi_s_limit():
     # Without coupling S_ideal is diagonal, Z is diagonal and xi_S vanishes.
     assert pr.xi_s(5, 5, 0.1, 0.0, kd) == 0.0
     assert 0 < pr.xi_s(5, 5, 0.1, 0.05, kd) < 1
+
+
+def test_row_phase_excitation_is_the_e_plane_scan():
+    """Eq. 29 against the scan excitation: the inter-element phase of an
+    E-plane scan (phi = 0) at angle theta is psi = -k d sin(theta) in the
+    e^{-j k d sin(theta) m_x} convention of the scan phase."""
+    spec = LatticeSpec(5, 3, 4, 0.6, 0)
+    thetas = [0.0, 20.0, 47.5]
+    kd = 2 * np.pi * spec.d
+    psi = [-kd * np.sin(np.radians(t)) for t in thetas]
+    v_row = pr.row_phase_excitation(spec.nx, spec.ny, spec.b, psi, port_basis=2)
+    v_scan = excitation(spec, [(t, 0.0) for t in thetas], port_basis=2)
+    assert np.abs(v_row - v_scan).max() < 1e-13
+
+
+def test_xi_z_invariants():
+    """Eqs. 24-25: invariant under scaling Z_p; when the centre's coupling
+    decays with distance the closest border element is also the largest
+    (xi_Z = its maximum); a far border element made dominant separates them."""
+    nx, ny = 5, 5
+    n = nx * ny
+    c = pr.centre_index(nx, ny)
+    mx, my = np.arange(n) % nx, np.arange(n) // nx
+    dist = np.hypot(mx - mx[c], my - my[c])
+    zp = np.where(dist > 0, (0.3 - 0.2j) / np.maximum(dist, 1) ** 2, 60 + 20j).astype(np.complex128)
+    zp = np.tile(zp, (n, 1))  # row c is what the predictors read
+    j = pr.closest_border_element(nx, ny)
+    assert pr.xi_z(zp, nx, ny) == pr.xi_z_max(zp, nx, ny)
+    assert abs(pr.xi_z(zp, nx, ny) - abs(0.3 - 0.2j) / (dist[j] ** 2 * abs(60 + 20j))) < 1e-15
+    assert abs(pr.xi_z(3.7j * zp, nx, ny) - pr.xi_z(zp, nx, ny)) < 1e-15
+    corner = 0
+    zp[c, corner] = 10.0
+    assert pr.xi_z_max(zp, nx, ny) == 10.0 / abs(60 + 20j) > pr.xi_z(zp, nx, ny)
