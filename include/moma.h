@@ -125,6 +125,9 @@ typedef struct {
 } moma_solve_info;
 
 /* Create a solver for an nx x ny lattice with b bases per element.
+ * The circulant embedding sizes Mx, My default to the smallest 2^a 3^b 5^c
+ * >= 2N - 1 along each axis (Sec. II-A: any size >= 2N - 1 embeds the MBT
+ * product exactly); opt->mx, opt->my override them (each >= 2N - 1).
  * cuda_stream: a cudaStream_t (NULL = legacy default stream).
  * Allocates the device store for the transformed bins (c128, plus c64 in
  * MIXED mode), the factored preconditioner and the workspaces.
@@ -153,9 +156,16 @@ moma_status moma_create_array(int nx, int ny, int b, const moma_options *opt,
  * Errors: MOMA_ERR_NONFINITE (NaN/Inf in the blocks read), MOMA_ERR_NOT_PD. */
 moma_status moma_set_blocks(moma_array *a, const void *blocks, int dtype);
 
-/* Apply an operator to nrhs vectors x -> y (layout [nrhs][Ny][Nx][b]).
- * dtype MOMA_C128 computes in FP64 from the c128 bins; MOMA_C64 in FP32
- * from the c64 bins (MIXED arrays only).  MOMA_OP_NORMAL needs set_blocks. */
+/* Apply an operator to nrhs vectors x -> y (layout [nrhs][Ny][Nx][b]):
+ * MOMA_OP_Z, y = Z x through the FFT product of the circulant embedding
+ * (Eqs. 2-3); MOMA_OP_ZH, y = Z^H x from the same stored bins, conjugated at
+ * multiplication time (Eq. 6); MOMA_OP_NORMAL, y = P^{-1} Z^H Z x, the
+ * operator of the preconditioned normal equations (Sec. III-A).
+ * dtype MOMA_C128 computes in FP64-class arithmetic from the c128 bins;
+ * MOMA_C64 in FP32 from the c64 bins (MIXED arrays only).  MOMA_OP_NORMAL
+ * runs in the array's inner precision (MOMA_C64 for MIXED arrays,
+ * MOMA_C128 for FP64 arrays; MOMA_ERR_ARG otherwise).  All three need
+ * set_blocks (MOMA_ERR_STATE otherwise). */
 moma_status moma_matvec(moma_array *a, int op, int nrhs, const void *x, void *y, int dtype);
 
 /* Allocation-free variant of moma_matvec for MOMA_OP_Z and MOMA_OP_ZH (no
@@ -187,8 +197,9 @@ moma_status moma_matvec_noalloc(moma_array *a, int op, int nrhs, const void *x, 
 moma_status moma_apply_precond(moma_array *a, int nrhs, const void *x, void *y, int dtype);
 
 /* Copy one transformed bin Zhat_k (b x b, c128 or c64) for circulant
- * frequency (kx, ky), resolving the pair storage (transposes if k is the
- * stored partner).  Inspection aid for tests. */
+ * frequency (kx, ky): the 2D DFT of the first block column of the circulant
+ * embedding (Eqs. 3, 11), resolving the pair storage (transposed if k is
+ * the stored partner, Zhat_{-k} = Zhat_k^T).  Inspection aid for tests. */
 moma_status moma_get_bin(moma_array *a, int kx, int ky, int dtype, void *out);
 
 /* Copy the preconditioner block P_e (b x b c128, full Hermitian) of element
@@ -282,7 +293,8 @@ moma_status moma_xi_z(const void *Zp, int nx, int ny, double *out);
 moma_status moma_xi_s(int nx, int ny, double s_cc_re, double s_cc_im, double s1_re, double s1_im, double kd,
                       double z0, double *xi_s);
 
-/* Per-kernel timing over the calls made since moma_profile(a, 1), measured
+/* Runtime instrumentation (no counterpart in the paper).
+ * Per-kernel timing over the calls made since moma_profile(a, 1), measured
  * with CUDA events recorded on the array's stream around each launch of a
  * kernel family.  kernel: 0 = c64 bin product, 1 = c128 bin product,
  * 2 = preconditioner apply, 3 = c64 lattice FFT passes, 4 = block-bin
@@ -297,17 +309,18 @@ moma_status moma_profile(moma_array *a, int enable);
 moma_status moma_kernel_stats(moma_array *a, int kernel, long long *launches, double *total_ms);
 
 /* Rebind the array to another CUDA stream (the old stream is synchronised
- * first).  Lets a pool of workers reuse resident arrays on their streams. */
+ * first).  Lets a pool of workers reuse resident arrays on their streams.
+ * Runtime plumbing, no counterpart in the paper. */
 moma_status moma_set_stream(moma_array *a, void *cuda_stream);
 
 /* Text summary of the launch shapes the autotuner picked for this array
  * (empty before the first solve).  Each solve first times candidate shapes
- * of the bin product (rows per staged tile, pipeline stages) and of every
- * lattice-FFT pass (threads per line) on its own workspace, once per RHS
- * count, and keeps the fastest. */
+ * of the bin product (rows per staged tile, pipeline stages, CTAs per SM)
+ * and of every lattice-FFT pass (threads per line) on its own workspace,
+ * once per RHS count, and keeps the fastest.  No counterpart in the paper. */
 moma_status moma_tuning_report(const moma_array *a, char *buf, size_t len);
 
-/* The CUDA stream the array currently runs on. */
+/* The CUDA stream the array currently runs on (runtime plumbing). */
 void *moma_array_stream(const moma_array *a);
 
 /* Ragged batches (no counterpart in the paper): n independent arrays of
@@ -325,25 +338,33 @@ moma_status moma_solve_batch(int n, moma_array *const *arrays, const int *nrhs, 
                              void *const *I, const moma_solve_opts *opts, moma_solve_info *infos, int workers,
                              moma_status *statuses);
 
-/* Free the set-up scratch kept after moma_set_blocks (device copy of the
+/* Memory management, no counterpart in the paper.
+ * Free the set-up scratch kept after moma_set_blocks (device copy of the
  * blocks, block-transform intermediate, Gram/summed-area table, FP64
  * Cholesky factors).  The bins and the inverse factors stay; solves and
  * products are unaffected; moma_get_precond_block then reports
  * MOMA_ERR_STATE.  For keeping many arrays resident. */
 moma_status moma_release_setup(moma_array *a);
 
-/* Upper estimate of the device bytes an array needs: stored bins, factors,
+/* Memory management, no counterpart in the paper.
+ * Upper estimate of the device bytes an array needs: stored bins, factors,
  * workspaces for nrhs right-hand sides and, if with_setup, the set-up
  * scratch.  0 on invalid sizes.  Used for admission by HBM footprint. */
 size_t moma_estimate_bytes(int nx, int ny, int b, const moma_options *opt, int nrhs, int with_setup);
 
-/* Number of kernel launches issued on the array's stream since creation. */
+/* Runtime instrumentation (no counterpart in the paper).
+ * Number of kernel launches issued on the array's stream since creation. */
 long long moma_launch_count(moma_array *a);
 
 /* Device bytes held by the array (bins, preconditioner, workspaces). */
 size_t moma_device_bytes(const moma_array *a);
 
+/* Release every device buffer, stream and event of the array (after its
+ * stream has finished).  NULL is ignored.  No counterpart in the paper. */
 void moma_destroy(moma_array *a);
+/* Message of the last failing call on this thread (empty if none); the
+ * string stays valid until the thread's next failing call.  No counterpart
+ * in the paper. */
 const char *moma_last_error(void);
 
 /* ------------------------------------------------------------------ serving
