@@ -1,0 +1,71 @@
+"""The ctypes binding against the C header, on the CPU: every struct the
+binding mirrors has the C compiler's size and field offsets (a small C
+program including include/moma.h prints them), and every prototype in the
+header has as many parameters as the binding's argtypes."""
+import ctypes
+import os
+import re
+import shutil
+import subprocess
+
+import pytest
+
+import paper_2608_17844_b300 as m
+from paper_2608_17844_b300 import moma as mb
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "moma.h")
+STRUCTS = [mb.moma_options, mb.moma_solve_opts, mb.moma_solve_info, mb.moma_server_opts, mb.moma_request,
+           mb.moma_result, mb.moma_server_stats]
+
+
+@pytest.fixture(scope="module")
+def c_layout(tmp_path_factory):
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    d = tmp_path_factory.mktemp("abi")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "moma.h"', "int main(void) {"]
+    for s in STRUCTS:
+        n = s.__name__
+        lines.append(f'  printf("{n} %zu\\n", sizeof({n}));')
+        for f, _ in s._fields_:
+            lines.append(f'  printf("{n}.{f} %zu\\n", offsetof({n}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = d / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = d / "layout"
+    subprocess.run([cc, "-std=c11", "-Wall", "-Werror", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)],
+                   check=True, capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    return {k: int(v) for k, v in (l.split() for l in out.splitlines())}
+
+
+@pytest.mark.parametrize("s", STRUCTS, ids=lambda s: s.__name__)
+def test_struct_size_and_offsets_match_c(c_layout, s):
+    n = s.__name__
+    assert ctypes.sizeof(s) == c_layout[n]
+    for f, _ in s._fields_:
+        assert getattr(s, f).offset == c_layout[f"{n}.{f}"], f
+
+
+def _prototypes():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    protos = {}
+    for mt in re.finditer(r"\b(moma_\w+)\s*\(([^;{}]*?)\)\s*;", text):
+        name, args = mt.group(1), " ".join(mt.group(2).split())
+        protos[name] = 0 if args in ("", "void") else args.count(",") + 1
+    return protos
+
+
+def test_every_prototype_has_the_bindings_argument_count(moma_lib):
+    protos = _prototypes()
+    assert set(protos) == set(m.EXPORTS)
+    L = m.lib()
+    for name, nargs in protos.items():
+        argtypes = getattr(L, name).argtypes
+        if name == "moma_last_error":
+            assert nargs == 0 and not argtypes
+            continue
+        assert argtypes is not None and len(argtypes) == nargs, name
