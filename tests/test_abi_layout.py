@@ -69,3 +69,18 @@ def test_every_prototype_has_the_bindings_argument_count(moma_lib):
             assert nargs == 0 and not argtypes
             continue
         assert argtypes is not None and len(argtypes) == nargs, name
+
+
+@pytest.mark.parametrize("lang", ["c", "c++"])
+def test_header_compiles_cleanly(tmp_path, lang):
+    """The header stands alone in C11 and C++17 with warnings as errors."""
+    cc = shutil.which("gcc" if lang == "c" else "g++")
+    if cc is None:
+        pytest.skip("no compiler")
+    src = tmp_path / ("h.c" if lang == "c" else "h.cpp")
+    src.write_text('#include "moma.h"\nint main(void) {\n  moma_status (*f)(moma_array *, int) = moma_profile;\n'
+                   '  (void)f;\n  return sizeof(moma_request) == 0;\n}\n')
+    std = "-std=c11" if lang == "c" else "-std=c++17"
+    r = subprocess.run([cc, std, "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.dirname(HEADER),
+                        "-c", str(src), "-o", str(tmp_path / "h.o")], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
