@@ -38,9 +38,15 @@ def parse():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--fp64-steps", type=int, default=2, help="steps of the plain FP64 solve (0 = skip)")
-    ap.add_argument("--cpu-seconds", type=float, default=20.0, help="bounded oracle sample (0 = skip)")
+    ap.add_argument("--fp64-steps", type=int, default=-1,
+                    help="timed steps of the plain FP64 solve and of the FP64-residual variant "
+                         "(-1 = same as --steps, 0 = skip)")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg (cpu_baseline)")
+    ap.add_argument("--ref-seconds", type=float, default=200.0,
+                    help="reference arm: wall-time budget for whole oracle solves (at least one step runs)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--quick", action="store_true",
+                    help="headline workload only (no scan / ragged / serving sub-measurements)")
     ap.add_argument("--ragged", action="store_true",
                     help="ragged batch: 24 square lattices 2x2..48x48, b=96, x 3 spacings, one broadside solve each")
     ap.add_argument("--scan", action="store_true",
@@ -51,7 +57,8 @@ def parse():
                     help="serving mode: Poisson request stream through the continuous-batching server")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-rate", type=float, default=200.0)
-    ap.add_argument("--serve-keys", type=int, default=8)
+    ap.add_argument("--serve-keys", type=int, default=0,
+                    help="0: every request draws its own lattice and spacing; K > 0: K resident lattice keys")
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--nrhs", type=int, default=0,
                     help="profiling: this many scan-angle RHS instead of the workload's two")
@@ -140,32 +147,59 @@ def make_inputs(lattice=None, nrhs=0):
     return spec, blocks, V
 
 
-def bin_product_bytes(spec, nr):
-    """Algorithmic bytes of one c64 bin-product launch: the stored bins once
-    (one b x b block per {k,-k} pair) plus the bin vectors in and out."""
-    def smooth(n):
-        m = n
-        while True:
-            k = m
-            for r in (2, 3, 5):
-                while k % r == 0:
-                    k //= r
-            if k == 1:
-                return m
-            m += 1
-    mx, my = smooth(2 * spec.nx - 1), smooth(2 * spec.ny - 1)
+def smooth235(n):
+    """Smallest 2^a 3^b 5^c >= n (the library's default circulant size)."""
+    m = max(1, n)
+    while True:
+        k = m
+        for r in (2, 3, 5):
+            while k % r == 0:
+                k //= r
+        if k == 1:
+            return m
+        m += 1
+
+
+def pair_count(mx, my):
+    """Number of {k, -k} classes of the Mx x My circulant frequencies (one
+    stored b x b block per class)."""
+    return sum(1 for ky in range(my) for kx in range(mx)
+               if ky * mx + kx <= ((my - ky) % my) * mx + ((mx - kx) % mx))
+
+
+def bin_product_bytes(spec, nr, padded=False):
+    """Bytes of one c64 bin-product launch: the transformed blocks once (one
+    b x b block per {k,-k} pair) plus the bin vectors in and out.
+
+    padded=False: the algorithmic count, on the paper's circulant size
+    M = 2N - 1 per axis (Sec. II-A), whatever size the library pads to.
+    padded=True: the bytes the kernel really streams, on the library's
+    padded sizes (smallest 2^a 3^b 5^c >= 2N - 1) and rows of even length."""
+    if padded:
+        mx, my = smooth235(2 * spec.nx - 1), smooth235(2 * spec.ny - 1)
+        ldb = spec.b + (spec.b % 2)
+    else:
+        mx, my = 2 * spec.nx - 1, 2 * spec.ny - 1
+        ldb = spec.b
     B = mx * my
-    pairs = sum(1 for ky in range(my) for kx in range(mx)
-                if ky * mx + kx <= ((my - ky) % my) * mx + ((mx - kx) % mx))
-    ldb = spec.b + (spec.b % 2)
+    pairs = pair_count(mx, my)
     return pairs * spec.b * ldb * 8 + 2 * B * nr * spec.b * 8, pairs, B
 
 
-def measured_traffic(alg_bytes, spec, nr):
+def matvec_bytes(spec, nr):
+    """Algorithmic bytes of one Z application, c64 (the MLFFT product of
+    Eq. 3): the transformed blocks once (pair storage on M = 2N - 1), the bin
+    vectors in and out of the per-bin product, and the lattice vector in and
+    out."""
+    alg_bin, _, _ = bin_product_bytes(spec, nr, padded=False)
+    return alg_bin + 2 * spec.nx * spec.ny * spec.b * nr * 8
+
+
+def measured_traffic(alg_bytes_padded, spec, nr):
     """DRAM bytes per launch of the c64 bin product from the committed ncu
     capture (profiles/bin_pair_kernel_c64_traffic.txt), scaled from the
-    captured lattice to this launch by the algorithmic bytes; None if the
-    kernel source changed since the capture."""
+    captured lattice to this launch by the streamed (padded) bytes; None if
+    the kernel source changed since the capture."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "bin_pair_kernel_c64_traffic.txt")
     src = os.path.join(ROOT, "paper_2608_17844_b300", "csrc", "binprod.cu")
@@ -179,126 +213,179 @@ def measured_traffic(alg_bytes, spec, nr):
     pairs, bins, nrc, b = (int(kv[k]) for k in ("pairs", "bins", "nrhs", "b"))
     alg_captured = pairs * b * (b + b % 2) * 8 + 2 * bins * nrc * b * 8
     measured = int(kv["dram_read_bytes"]) + int(kv["dram_write_bytes"])
-    return measured / alg_captured * alg_bytes
+    return measured / alg_captured * alg_bytes_padded
 
 
-def cpu_oracle_sample(spec, blocks, V, seconds):
-    """Time the oracle (oracle-I: GMRES on Z I = V with the direct offset-sum
-    product, complex128) on RHS 0 of the workload for a bounded wall time;
-    extrapolate to one full solve from the measured time per iteration and
-    the observed geometric residual reduction per iteration."""
+def named_elements(nx, ny):
+    """(mx, my) of the centre (floor(Nx/2), floor(Ny/2)), edge (0, floor(Ny/2))
+    and corner (0, 0) elements."""
+    return {"centre": (nx // 2, ny // 2), "edge": (0, ny // 2), "corner": (0, 0)}
+
+
+def oracle_solves(spec, blocks, V, qs):
+    """The CPU oracle (oracle-I: restarted GMRES on Z I = V with the direct
+    offset-sum product and block Jacobi, complex128) run to a relative
+    residual of 1e-10 on the RHS columns qs, one complete solve each.
+    Returns (seconds per solve, currents [len(qs)][Ny][Nx][b], iterations,
+    residuals)."""
     from oracle import iterative
-    cores = len(os.sched_getaffinity(0))
     b128 = blocks.astype(np.complex128)
-    hist = []
-    t0 = time.perf_counter()
-
-    class Stop(Exception):
-        pass
-
-    def cb(q, it, rel):
-        hist.append((time.perf_counter() - t0, it, rel))
-        if time.perf_counter() - t0 > seconds:
-            raise Stop()
-
-    try:
-        iterative.gmres(b128, spec.nx, spec.ny, V[:1], tol=1e-10, restart=60, max_iter=500, callback=cb)
-        converged = True
-    except Stop:
-        converged = False
-    if not hist:
-        return None
-    t_iter = hist[-1][0] / hist[-1][1]
-    if converged:
-        iters = hist[-1][1]
-    else:
-        rho = hist[-1][2] ** (1.0 / hist[-1][1])
-        iters = int(np.ceil(np.log(1e-10) / np.log(rho))) if 0 < rho < 1 else float("inf")
-    per_solve = t_iter * iters
-    return {"value": 1.0 / per_solve, "unit": "solves/s", "cores": cores, "kind": "oracle",
-            "sample": (f"oracle-I (complex128 GMRES, direct offset-sum product, block Jacobi) on RHS 0 of the same "
-                       f"{spec.nx}x{spec.ny} b={spec.b} problem for {hist[-1][0]:.1f} s: {hist[-1][1]} iterations at "
-                       f"{t_iter:.2f} s each, residual {hist[-1][2]:.2e}; "
-                       + ("converged" if converged else f"extrapolated to {iters} iterations for 1e-10")),
-            "s_per_iteration": t_iter, "iterations_for_1e-10": iters}
+    secs, cur, its, res = [], [], [], []
+    for q in qs:
+        t0 = time.perf_counter()
+        I, info = iterative.gmres(b128, spec.nx, spec.ny, V[q:q + 1], tol=1e-10, restart=60, max_iter=500)
+        secs.append(time.perf_counter() - t0)
+        cur.append(I[0])
+        its.append(info[0]["iters"])
+        res.append(info[0]["rel_residual"])
+    return secs, np.array(cur), its, res
 
 
-def run_serving(args):
-    """Serving stream shaped like BASELINE config 5: Poisson arrivals
-    (rate --serve-rate, seed 7) of requests with Nx, Ny ~ U{4..40}, b = 128,
-    1-32 scan-angle RHS.  Blocks come from a pool of --serve-keys lattices
-    (spacing on the 5-point grid 0.3..0.7) generated once on the host, so
-    arrays are built on first use and then served from residency."""
-    import torch
-    import paper_2608_17844_b300 as m
-    from synth import LatticeSpec, offset_blocks, excitation
-    rng = np.random.default_rng(7)
+def cpu_baseline_leg(spec, blocks, V, I_gpu):
+    """cpu_baseline: one complete oracle solve (RHS 0 of the workload),
+    timed on the host cores.  The same leg certifies the GPU result it is
+    handed: the oracle's Z_a against the GPU's for RHS 0 (every port), and
+    the GPU currents' residual recomputed by the oracle's FP64 direct
+    offset sum for every RHS."""
+    from oracle import mbt
+    cores = len(os.sched_getaffinity(0))
+    secs, I0, its, res = oracle_solves(spec, blocks, V, [0])
+    b128 = blocks.astype(np.complex128)
+    za_o = V[0, ..., 0] / I0[0, ..., 0]
+    za_g = V[0, ..., 0] / I_gpu[0, ..., 0]
+    za_err = float(np.max(np.abs(za_g - za_o) / np.abs(za_o)))
+    cert = []
+    for q in range(V.shape[0]):
+        r = V[q] - mbt.matvec(b128, spec.nx, spec.ny, I_gpu[q:q + 1])[0]
+        cert.append(float(np.linalg.norm(r) / np.linalg.norm(V[q])))
+    return {"value": 1.0 / secs[0], "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "sample": (f"oracle-I (complex128 GMRES(60), direct offset-sum product, block Jacobi) on RHS 0 of the "
+                       f"same {spec.nx}x{spec.ny} b={spec.b} problem, run to convergence: {its[0]} iterations, "
+                       f"{secs[0]:.1f} s, final residual {res[0]:.2e} (converged)"),
+            "seconds": secs[0], "iterations": its[0], "oracle_rel_residual": res[0],
+            "certify_gpu": {"za_rel_err_rhs0_all_ports": za_err, "za_bar": 1e-8,
+                            "direct_sum_rel_residual": cert, "residual_bar": 1e-10}}
+
+
+def serve_requests(rate, seconds, keys, seed=7):
+    """Request stream of the serving workload: Poisson arrivals at `rate`
+    per second for `seconds`.  Per request, in this order: inter-arrival
+    time, Nx ~ U{4..40}, Ny ~ U{4..40}, spacing d ~ U(0.3, 0.7) wavelengths
+    (keys = 0) or one of `keys` resident lattices with d on the 5-point grid
+    0.3..0.7 (keys > 0), nrhs ~ U{1..32}, then nrhs scan angles
+    (theta ~ U[0, 60], phi ~ U[0, 90) degrees).  b = 128, block seed 0."""
+    from synth import LatticeSpec
+    rng = np.random.default_rng(seed)
     pool = []
-    for k in range(args.serve_keys):
+    for _ in range(keys):
         nx, ny = int(rng.integers(4, 41)), int(rng.integers(4, 41))
-        d = float(rng.choice([0.3, 0.4, 0.5, 0.6, 0.7]))
-        spec = LatticeSpec(nx, ny, 128, d, 0)
-        pool.append((spec, offset_blocks(spec, np.complex64)))
-    reqs = []
-    t = 0.0
-    while t < args.serve_seconds:
-        t += float(rng.exponential(1.0 / args.serve_rate))
-        k = int(rng.integers(len(pool)))
+        pool.append(LatticeSpec(nx, ny, 128, float(rng.choice([0.3, 0.4, 0.5, 0.6, 0.7])), 0))
+    reqs, t = [], 0.0
+    while True:
+        t += float(rng.exponential(1.0 / rate))
+        if t >= seconds:
+            break
+        if keys:
+            k = int(rng.integers(len(pool)))
+            spec = pool[k]
+        else:
+            nx, ny = int(rng.integers(4, 41)), int(rng.integers(4, 41))
+            d = float(rng.uniform(0.3, 0.7))
+            spec, k = LatticeSpec(nx, ny, 128, d, 0), len(reqs)
         nr = int(rng.integers(1, 33))
         angles = [(float(rng.uniform(0, 60)), float(rng.uniform(0, 90))) for _ in range(nr)]
-        reqs.append((t, k, angles))
+        reqs.append((t, k, spec, angles))
+    return reqs
+
+
+def serve_stream(rate, seconds, keys, slots):
+    """One serving run: the request blocks (c64, generated on the GPU before
+    the clock starts; each request of the continuous draw has its own
+    lattice and spacing, hence its own blocks) are submitted at their
+    arrival times to the continuous-batching server; each request's latency
+    is submit -> result.  Returns a dict of the run's figures."""
+    import torch
+    import paper_2608_17844_b300 as m
+    from synth import offset_blocks_torch, excitation
     torch.cuda.set_device(0)
-    s = m.moma_server_create(slots=args.serve_slots)
-    max_outstanding = 64
-    outstanding = []
-    lat, hits, solved, errors = [], 0, 0, 0
+    reqs = serve_requests(rate, seconds, keys)
+    blocks, seen = {}, {}
+    for (_, k, spec, _) in reqs:
+        if k not in blocks:
+            blocks[k] = offset_blocks_torch(spec, "cuda")
+    torch.cuda.synchronize()
+    gen_bytes = sum(b.numel() * 8 for b in blocks.values())
+    s = m.moma_server_create(slots=slots)
+    outstanding, lat, qms, hits, solved, errors = [], [], [], 0, 0, 0
     t0 = time.perf_counter()
 
     def collect(block):
         nonlocal hits, solved, errors
-        while outstanding and (block or len(outstanding) >= max_outstanding):
+        while outstanding and (block or outstanding[0][0] is None):
             tk, bufs = outstanding.pop(0)
             r = m.moma_server_wait(s, tk, -1.0)
             lat.append(r["total_ms"])
+            qms.append(r["queue_ms"])
             hits += r["resident_hit"]
             if r["status"] == 0:
                 solved += bufs[0].shape[0]
             else:
                 errors += 1
-            block = block and bool(outstanding)
 
-    for (ta, k, angles) in reqs:
+    for (ta, k, spec, angles) in reqs:
         now = time.perf_counter() - t0
         if ta > now:
             time.sleep(ta - now)
-        spec, blocks = pool[k]
         V = excitation(spec, angles)
         I = np.zeros_like(V)
-        tk = m.moma_server_submit(s, k + 1, blocks, V, I)
+        tk = m.moma_server_submit(s, k + 1, blocks[k], V, I)
         outstanding.append((tk, (V, I)))
-        collect(False)
     collect(True)
     wall = time.perf_counter() - t0
     stats = m.moma_server_get_stats(s)
     m.moma_server_destroy(s)
+    del blocks
+    torch.cuda.empty_cache()
     lat = np.array(lat)
-    line = {"metric": "serving: solves/s with p50/p99 request latency", "mode": "serve",
-            "value": solved / wall, "unit": "solves/s", "n_gpus": 1, "higher_is_better": True,
-            "offered_req_per_s": len(reqs) / reqs[-1][0], "achieved_req_per_s": len(reqs) / wall,
-            "requests": len(reqs), "errors": errors, "p50_ms": float(np.percentile(lat, 50)),
-            "p99_ms": float(np.percentile(lat, 99)), "resident_hit_rate": hits / len(reqs),
-            "slots": args.serve_slots, "server": stats, "data": "synthetic",
-            "config": {"workload": f"Poisson {args.serve_rate}/s, {args.serve_keys} lattice keys Nx,Ny~U{{4..40}}, "
-                                   f"b=128, d on 0.3..0.7 grid, 1-32 RHS", "max_outstanding": max_outstanding}}
-    print(json.dumps(line, default=str), flush=True)
+    n_rhs = sum(len(r[3]) for r in reqs)
+    return {"offered_req_per_s": len(reqs) / seconds, "requests": len(reqs), "rhs": n_rhs,
+            "completed_req_per_s": len(reqs) / wall, "solves_per_s": solved / wall, "wall_s": wall,
+            "errors": errors, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "queue_p50_ms": float(np.percentile(qms, 50)), "resident_hit_rate": hits / len(reqs),
+            "slots": slots, "request_blocks_gb": gen_bytes / 1e9, "server": stats}
 
 
-def run_ragged(args):
-    """Ragged batch shaped like BASELINE config 4: square lattices 2x2 ..
-    48x48 (step 2), b = 96, spacings 0.3 / 0.5 / 0.7, one broadside solve
-    each (72 problems).  One step = batched set-up (block transform,
-    preconditioner) of all 72 arrays + batched solve + port quantities.
-    Blocks are generated on the GPU (synth.offset_blocks_torch, c64)."""
+def run_serving(args, sub=False):
+    """Serving workload: Poisson arrivals (seed 7) of requests with
+    Nx, Ny ~ U{4..40}, b = 128, spacing d ~ U(0.3, 0.7), 1-32 scan-angle
+    RHS, through the continuous-batching server (HBM-footprint admission,
+    resident arrays, LRU eviction).  Reported at the offered rate (200/s
+    default) and below saturation; plus the residency variant (d on a
+    5-point grid, a few lattice keys, so arrays are served resident)."""
+    runs = {}
+    if sub:
+        plan = [("continuous_200", args.serve_rate, 1.5, 0), ("continuous_below_saturation", 15.0, 4.0, 0),
+                ("resident_keys_200", args.serve_rate, 1.5, 8)]
+    else:
+        plan = [(f"{'keys%d' % args.serve_keys if args.serve_keys else 'continuous'}_{args.serve_rate:g}",
+                 args.serve_rate, args.serve_seconds, args.serve_keys)]
+    for name, rate, secs, keys in plan:
+        runs[name] = serve_stream(rate, secs, keys, args.serve_slots)
+    head = runs[plan[0][0]]
+    return {"metric": "serving: solves/s with p50/p99 request latency", "mode": "serve",
+            "value": head["solves_per_s"], "unit": "solves/s", "n_gpus": 1, "higher_is_better": True,
+            "p50_ms": head["p50_ms"], "p99_ms": head["p99_ms"], "runs": runs, "data": "synthetic",
+            "config": {"workload": "Poisson arrivals (seed 7); per request Nx,Ny~U{4..40}, b=128, d~U(0.3,0.7) "
+                                   "(or 8 keys with d on a 5-point grid), 1-32 scan RHS; c64 blocks",
+                       "slots": args.serve_slots}}
+
+
+def run_ragged(args, sub=False):
+    """Ragged workload: square lattices 2x2 .. 48x48 (step 2), b = 96,
+    spacings 0.3 / 0.5 / 0.7, one broadside solve each (72 problems).  One
+    step = batched set-up (block transform, preconditioner) of all 72 arrays
+    + batched solve + port quantities.  Blocks are generated on the GPU
+    (synth.offset_blocks_torch, c64)."""
     import torch
     import paper_2608_17844_b300 as m
     from synth import LatticeSpec, offset_blocks_torch, excitation
@@ -317,10 +404,10 @@ def run_ragged(args):
             m.moma_active_impedance(h, I, V, za)
         return infos
 
-    for _ in range(max(1, args.warmup)):
+    for _ in range(max(1, min(args.warmup, 2))):
         infos = step()
     torch.cuda.synchronize()
-    steps = max(1, min(args.steps, 5))
+    steps = max(1, min(args.steps, 3 if sub else 5))
     t0 = time.perf_counter()
     for _ in range(steps):
         infos = step()
@@ -330,13 +417,16 @@ def run_ragged(args):
     line = {"metric": "ragged batch: solves/s (set-up + solve per problem)", "mode": "ragged",
             "value": len(specs) / dt, "unit": "solves/s", "ms_per_step": 1000 * dt, "steps": steps,
             "problems": len(specs), "converged": sum(x["converged"] for x in infos),
+            "max_rel_residual": max(x["max_rel_residual"] for x in infos),
             "inner_iters": [x["inner_iters"] for x in infos],
             "device_bytes": sum(m.moma_device_bytes(h) for h in hs), "data": "synthetic",
             "config": {"workload": "2x2..48x48 step 2, b=96, d in {0.3,0.5,0.7}, broadside, c64 blocks"},
             "centre_Za": {k: f"{v.real:.6f}{v.imag:+.6f}j" for k, v in list(centre.items())[::6]}}
     for h in hs:
         m.moma_destroy(h)
-    print(json.dumps(line, default=str), flush=True)
+    del blocks
+    torch.cuda.empty_cache()
+    return line
 
 
 def tf32_peak():
@@ -346,7 +436,7 @@ def tf32_peak():
         return json.load(f)["bf16_tflops"] * 1.1 / 2.25, "of measured (bf16 burst x nominal tf32/bf16)"
 
 
-def run_scan(args):
+def run_scan(args, sub=False):
     """Scan workload: 24 x 24 lattice, b = 256 (N = 147456), 64 RHS per
     array (8 x 8 grid of scan angles, theta in [0, 60], phi in [0, 90)) at
     three element spacings (0.3, 0.5, 0.7 wavelengths: three arrays, c64
@@ -373,10 +463,10 @@ def run_scan(args):
             m.moma_active_impedance(h, I, V, za)
         return infos
 
-    for _ in range(max(1, args.warmup)):
+    for _ in range(max(1, min(args.warmup, 2))):
         infos = step()
     torch.cuda.synchronize()
-    steps = max(1, min(args.steps, 5))
+    steps = max(1, min(args.steps, 3 if sub else 5))
     clk = ClockSampler(0)
     clk.start()
     t0 = time.perf_counter()
@@ -401,11 +491,14 @@ def run_scan(args):
     for h in hs:
         m.moma_profile(h, 0)
     spec = specs[0]
-    B = 48 * 48
-    flops_launch = 8.0 * B * spec.b * spec.b * nr  # complex b x b by b x nr per bin
+    mxp, myp = smooth235(2 * spec.nx - 1), smooth235(2 * spec.ny - 1)
+    flops_launch = 8.0 * (2 * spec.nx - 1) * (2 * spec.ny - 1) * spec.b * spec.b * nr  # on M = 2N-1 bins
     tc = fam.get("bin_tc", {"launches": 0, "ms": 0.0})
     peak, peak_src = tf32_peak()
-    achieved = flops_launch / (tc["ms"] / tc["launches"] * 1e-3) / 1e12 if tc["launches"] else None
+    us = 1000.0 * tc["ms"] / tc["launches"] if tc["launches"] else None
+    achieved = flops_launch / (us * 1e-6) / 1e12 if us else None
+    alg_bytes = bin_product_bytes(spec, nr)[0]
+    hbm_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6400.0)
     line = {"metric": "scan workload: RHS solved/s (set-up + solve, 3 spacings x 64 RHS)", "mode": "scan",
             "value": len(specs) * nr / dt, "unit": "solves/s", "ms_per_step": 1000 * dt, "steps": steps,
             "converged": sum(x["converged"] for x in infos),
@@ -413,21 +506,28 @@ def run_scan(args):
             "inner_iters": [x["inner_iters"] for x in infos], "outer_iters": [x["outer_iters"] for x in infos],
             "device_bytes": sum(m.moma_device_bytes(h) for h in hs), "data": "synthetic", "dtype": "c64+c128",
             "config": {"workload": "24x24 lattice, b=256 (N=147456), 64 RHS (8x8 scan grid), d in {0.3,0.5,0.7}, "
-                                   "c64 blocks, GMRES(50) + FP64 refinement to 1e-10"},
+                                   "c64 blocks, GMRES(50) + FP64 refinement to 1e-10",
+                       "circulant": f"{mxp}x{myp} (padded from {2 * spec.nx - 1})"},
             "kernels_profiled_step": fam,
-            "roofline": {"kernel": "bin_mma_kernel (tcgen05 kind::tf32, 3xTF32)", "bound": "tensor",
-                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak if achieved else None,
-                         "issued_frac": 3 * achieved / peak if achieved else None,
-                         "flops_per_launch": flops_launch, "peak_source": peak_src},
+            "roofline": {"kernel": "bin_mma_kernel (tcgen05 kind::tf32, 3xTF32)", "bound": "hbm",
+                         "achieved": alg_bytes / (us * 1e-6) / 1e9 if us else None, "peak": hbm_peak,
+                         "unit": "GB/s", "frac": alg_bytes / (us * 1e-6) / 1e9 / hbm_peak if us else None,
+                         "alg_bytes_per_launch": alg_bytes, "avg_launch_us": us,
+                         "alg_basis": "c64 pair store on M = 2N-1 + bin vectors in and out",
+                         "tensor": {"achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                                    "frac": achieved / peak if achieved else None,
+                                    "issued_frac": 3 * achieved / peak if achieved else None,
+                                    "flops_per_launch": flops_launch, "peak_source": peak_src}},
             "clocks": clocks,
             "centre_Za_broadside": {f"d={s.d}": f"{complex(za[0, 12, 12].item()):.6f}" for s, za in zip(specs, zas)}}
     for h in hs:
         m.moma_destroy(h)
-    print(json.dumps(line, default=str), flush=True)
+    del blocks
+    torch.cuda.empty_cache()
+    return line
 
 
-def run_predictors(args):
+def run_predictors(args, sub=False):
     """Analysis workloads on top of the solver (Sec. II-E): the all-port
     passive impedance matrix Z_p of a 16 x 16 lattice (b = 128, 256 unit
     port excitations in RHS chunks of 64 on the tensor-core path, FP64
@@ -478,31 +578,84 @@ def run_predictors(args):
     t0 = time.perf_counter()
     xs = m.moma_xi_s(32, 32, 0.1 + 0.05j, -0.15 + 0.07j, np.pi, 50.0)
     out["xi_s"] = {"lattice": "32x32", "value": xs, "seconds": time.perf_counter() - t0}
-    print(json.dumps(out, default=str), flush=True)
+    return out
+
+
+def headline_config(args, nr, world):
+    """The workload description shared by both arms' JSON lines."""
+    return {"workload": WORKLOAD if not (args.lattice or args.nrhs)
+            else f"profiling lattice {args.lattice or 'C2'}, {nr} RHS",
+            "rhs_per_step": nr * world, "parallelism": f"replicas x{world}",
+            "l2": "inputs larger than L2 (c64 blocks 520 MB; stored bins 269 MB c64 + 537 MB c128)"}
 
 
 def run_reference(args, world, rank):
-    """Reference arm: the CPU oracle as it stands, on the host cores."""
+    """Reference arm: the CPU oracle as it stands, on the host cores.  One
+    step = the workload's RHS columns each solved to completion by oracle-I
+    (the paper publishes no implementation to install).  Whole steps run
+    until --steps are done or the next one would pass --ref-seconds (at
+    least one step runs); the line reports the steps actually timed."""
     if rank != 0:
         return
-    spec, blocks, V = make_inputs(args.lattice)
-    per_step = max(5.0, min(30.0, 120.0 / max(1, args.steps + args.warmup)))
-    vals = []
-    cb = None
-    for s in range(args.warmup + args.steps):
-        cb = cpu_oracle_sample(spec, blocks, V, per_step)
-        if s >= args.warmup and cb:
-            vals.append(cb["value"])
-    value = float(np.mean(vals)) if vals else None
+    spec, blocks, V = make_inputs(args.lattice, args.nrhs)
+    nr = V.shape[0]
+    cores = len(os.sched_getaffinity(0))
+    # Warm-up: one oracle product (thread pools, page-in), untimed.
+    warm = min(args.warmup, 1)
+    if warm:
+        from oracle import mbt
+        mbt.matvec(blocks.astype(np.complex128), spec.nx, spec.ny, V[:1])
+    step_s, iters = [], []
+    t_all = time.perf_counter()
+    while len(step_s) < max(1, args.steps):
+        if step_s and (time.perf_counter() - t_all) + float(np.mean(step_s)) > args.ref_seconds:
+            break
+        t0 = time.perf_counter()
+        _, _, its, _ = oracle_solves(spec, blocks, V, list(range(nr)))
+        step_s.append(time.perf_counter() - t0)
+        iters.append(its)
+    total = float(np.sum(step_s))
+    value = nr * len(step_s) / total
+    sample = (f"oracle-I (complex128 GMRES(60), direct offset-sum product, block Jacobi): {len(step_s)} whole "
+              f"step(s) of {nr} RHS each solved to rel. residual 1e-10 ({iters} iterations), {total:.1f} s on "
+              f"{cores} host cores; {args.steps} steps requested, whole steps only")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * 2 / value if value else None,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
-            "data": "synthetic",
-            "config": {"workload": WORKLOAD if not args.lattice else f"profiling lattice {args.lattice}, 1 RHS sampled",
-                       "l2": "n/a (CPU)"},
-            "cpu_baseline": {k: cb[k] for k in ("kind", "cores", "sample")} | {"value": value} if cb else None,
+            "steps": len(step_s), "steps_requested": args.steps, "warmup": warm, "warmup_requested": args.warmup,
+            "ms_per_step": 1000.0 * total / len(step_s), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "config": headline_config(args, nr, 1),
+            "cpu_baseline": {"kind": "oracle", "cores": cores, "sample": sample, "value": value},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def timed_variant(m, torch, spec, blocks_d, V_d, za_d, gam_d, stream, steps, warmup, precision, flags=0,
+                  solver=0):
+    """Whole steps (set-up + solve + port quantities) of one solver variant
+    on the headline problem, CUDA events on the stream around `steps` steps
+    after `warmup` untimed ones.  Returns (ms per step, last solve info,
+    currents)."""
+    h = m.moma_create_array(spec.nx, spec.ny, spec.b, precision, stream=stream, flags=flags)
+    I = torch.zeros_like(V_d)
+    info = None
+    try:
+        for _ in range(max(1, warmup)):
+            m.moma_set_blocks(h, blocks_d)
+            info = m.moma_solve(h, V_d, I, solver=solver)
+        torch.cuda.synchronize()
+        a_ = torch.cuda.Event(enable_timing=True)
+        b_ = torch.cuda.Event(enable_timing=True)
+        a_.record(stream)
+        for _ in range(steps):
+            m.moma_set_blocks(h, blocks_d)
+            info = m.moma_solve(h, V_d, I, solver=solver)
+            m.moma_active_impedance(h, I, V_d, za_d, gam_d)
+        b_.record(stream)
+        torch.cuda.synchronize()
+        ms = a_.elapsed_time(b_) / steps
+    finally:
+        m.moma_destroy(h)
+    return ms, info, I
 
 
 def main():
@@ -511,24 +664,15 @@ def main():
     if args.impl == "reference":
         run_reference(args, world, rank)
         return
-    if args.serve:
-        if rank == 0:
-            run_serving(args)
-        return
-    if args.ragged:
-        if rank == 0:
-            run_ragged(args)
-        return
-    if args.scan:
-        if rank == 0:
-            run_scan(args)
-        return
-    if args.predictors:
-        if rank == 0:
-            run_predictors(args)
-        return
+    modes = [("serve", run_serving), ("ragged", run_ragged), ("scan", run_scan), ("predictors", run_predictors)]
+    for flag, fn in modes:
+        if getattr(args, flag):
+            if rank == 0:
+                print(json.dumps(fn(args), default=str), flush=True)
+            return
     import torch
     import paper_2608_17844_b300 as m
+    from paper_2608_17844_b300 import replicas
 
     torch.cuda.set_device(local)
     dist = None
@@ -593,11 +737,11 @@ def main():
     clocks.wait_first()
     total_ms, steps_ms, launches, _ = timed_region(False)
     clk = clocks.stop()
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * nr * args.steps / (total_ms / 1000.0)
+    dev = "cuda" if dist is not None else "cpu"
+    value = replicas.aggregate_throughput(nr * args.steps, total_ms / 1000.0, device=dev)
+    total_ms = 1000.0 * replicas.max_over_ranks(total_ms / 1000.0, device=dev)
+    I_head = I_d.cpu().numpy()
+    za_head = za_d.cpu().numpy()
     # Same steps again with CUDA events around every kernel launch (graphs
     # off): per-kernel durations for the roofline and the breakdown.
     prof_total_ms, _, _, stats = timed_region(True)
@@ -617,70 +761,70 @@ def main():
 
     # Roofline of the dominant kernel: the c64 bin product.
     n_bin, ms_bin = stats["bin_c64"]
+    n_fft, ms_fft = stats["fft_c64"]
     alg_bytes, pairs, B = bin_product_bytes(spec, nr)
+    pad_bytes = bin_product_bytes(spec, nr, padded=True)[0]
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except OSError:
         pass
     hbm_peak = peaks.get("hbm_gbs", 6400.0)
+    peak_src = "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback 6.4 TB/s (of fallback)"
     achieved = alg_bytes / (ms_bin / n_bin / 1000.0) / 1e9 if n_bin else None
-    traffic = measured_traffic(alg_bytes, spec, nr)
+    traffic = measured_traffic(pad_bytes, spec, nr)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak if achieved else None,
                 "traffic": int(traffic) if traffic else None,
-                "traffic_source": "ncu dram bytes of the 24x24 capture scaled by algorithmic bytes" if traffic
+                "traffic_source": "ncu dram bytes of the 24x24 capture scaled by streamed bytes" if traffic
                 else "kernel changed since the ncu capture",
                 "kernel": "bin_pair_kernel<float> (c64 per-bin product, Z and Z^H legs)",
-                "alg_bytes_per_launch": alg_bytes, "launches": n_bin, "avg_launch_us": 1000.0 * ms_bin / n_bin if n_bin else None,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback 6.4 TB/s"}
+                "alg_bytes_per_launch": alg_bytes, "alg_basis": f"{pairs} pairs of the {2 * spec.nx - 1}x"
+                f"{2 * spec.ny - 1} circulant (M = 2N-1), {nr} RHS",
+                "streamed_bytes_per_launch": pad_bytes, "launches": n_bin,
+                "avg_launch_us": 1000.0 * ms_bin / n_bin if n_bin else None, "peak_source": peak_src}
+    # The whole Z application (FFT passes + bin product), per application.
+    mv_bytes = matvec_bytes(spec, nr)
+    mv_us = 1000.0 * (ms_bin + ms_fft) / n_bin if n_bin else None
+    matvec_roofline = {"bound": "hbm", "alg_bytes_per_application": mv_bytes,
+                       "us_per_application": mv_us, "bin_us": 1000.0 * ms_bin / n_bin if n_bin else None,
+                       "fft_us": 1000.0 * ms_fft / n_bin if n_bin else None, "fft_launches_per_application":
+                       n_fft / n_bin if n_bin else None,
+                       "achieved": mv_bytes / (mv_us * 1e-6) / 1e9 if mv_us else None, "peak": hbm_peak,
+                       "unit": "GB/s", "frac": mv_bytes / (mv_us * 1e-6) / 1e9 / hbm_peak if mv_us else None,
+                       "floor_us": mv_bytes / (hbm_peak * 1e9) * 1e6, "peak_source": peak_src}
     kernel_share = {k: {"launches": n, "ms": ms} for k, (n, ms) in stats.items()}
+    m.moma_destroy(h)
 
-    # Plain FP64 GPU solve on the same problem (the comparison solver).
-    fp64 = None
-    if args.fp64_steps > 0:
-        h64 = m.moma_create_array(spec.nx, spec.ny, spec.b, m.MOMA_PREC_FP64, stream=stream)
-        I64 = torch.zeros_like(V_d)
-        m.moma_set_blocks(h64, blocks_d)
-        m.moma_solve(h64, V_d, I64)
-        torch.cuda.synchronize()
-        a_ = torch.cuda.Event(enable_timing=True)
-        b_ = torch.cuda.Event(enable_timing=True)
-        a_.record(stream)
-        for _ in range(args.fp64_steps):
-            m.moma_set_blocks(h64, blocks_d)
-            inf64 = m.moma_solve(h64, V_d, I64)
-            m.moma_active_impedance(h64, I64, V_d, za_d, gam_d)
-        b_.record(stream)
-        torch.cuda.synchronize()
-        ms64 = a_.elapsed_time(b_) / args.fp64_steps
-        m.moma_destroy(h64)
-        fp64 = {"value": nr / (ms64 / 1000.0), "unit": "solves/s", "ms_per_step": ms64, "info": inf64,
-                "speedup_mixed_vs_fp64": value / world / (nr / (ms64 / 1000.0))}
-
-    # The paper's PCG solver (Sec. II-C) on the same problem and path.
-    pcg = None
-    if args.fp64_steps > 0:
-        infos_pcg = []
-        for _ in range(2):
-            m.moma_set_blocks(h, blocks_d)
-            infos_pcg.append(m.moma_solve(h, V_d, I_d, solver=m.MOMA_SOLVER_PCG))
-        torch.cuda.synchronize()
-        a_ = torch.cuda.Event(enable_timing=True)
-        b_ = torch.cuda.Event(enable_timing=True)
-        a_.record(stream)
-        for _ in range(args.fp64_steps + 1):
-            m.moma_set_blocks(h, blocks_d)
-            inf_pcg = m.moma_solve(h, V_d, I_d, solver=m.MOMA_SOLVER_PCG)
-            m.moma_active_impedance(h, I_d, V_d, za_d, gam_d)
-        b_.record(stream)
-        torch.cuda.synchronize()
-        ms_pcg = a_.elapsed_time(b_) / (args.fp64_steps + 1)
-        pcg = {"value": nr / (ms_pcg / 1000.0), "unit": "solves/s", "ms_per_step": ms_pcg, "info": inf_pcg}
+    fp_steps = args.steps if args.fp64_steps < 0 else args.fp64_steps
+    fp64 = fp64r = pcg = None
+    if fp_steps > 0:
+        # Plain FP64 GPU solve on the same problem (the comparison solver).
+        ms64, inf64, _ = timed_variant(m, torch, spec, blocks_d, V_d, za_d, gam_d, stream, fp_steps, args.warmup,
+                                       m.MOMA_PREC_FP64)
+        v64 = nr / (ms64 / 1000.0)
+        fp64 = {"value": v64, "unit": "solves/s", "ms_per_step": ms64, "steps": fp_steps, "info": inf64,
+                "speedup_mixed_vs_fp64": value / world / v64}
+        # Mixed path with its FP64-class stages (block-bin transform,
+        # refinement residual Z I, block Cholesky) in FP64 instead of
+        # double-FP32.
+        msr, infr, Ir = timed_variant(m, torch, spec, blocks_d, V_d, za_d, gam_d, stream, fp_steps, args.warmup,
+                                      m.MOMA_PREC_MIXED, flags=m.MOMA_FLAG_FP64_RESIDUAL)
+        za_r = za_d.cpu().numpy()
+        fp64r = {"value": nr / (msr / 1000.0), "unit": "solves/s", "ms_per_step": msr, "steps": fp_steps,
+                 "info": infr, "speedup_vs_fp64": (nr / (msr / 1000.0)) / v64,
+                 "za_max_rel_diff_vs_headline": float(np.max(np.abs(za_r - za_head) / np.abs(za_head))),
+                 "dtype": "c64 inner; block-bin transform, refinement residual Z I and block Cholesky in FP64"}
+        # The paper's PCG solver (Sec. II-C) on the same problem and path.
+        msp, infp, _ = timed_variant(m, torch, spec, blocks_d, V_d, za_d, gam_d, stream, fp_steps, args.warmup,
+                                     m.MOMA_PREC_MIXED, solver=m.MOMA_SOLVER_PCG)
+        pcg = {"value": nr / (msp / 1000.0), "unit": "solves/s", "ms_per_step": msp, "steps": fp_steps,
+               "info": infp}
 
     # End to end through the C ABI with host buffers (pinned), copies inside.
     e2e = None
     if not args.no_e2e:
+        h = m.moma_create_array(spec.nx, spec.ny, spec.b, m.MOMA_PREC_MIXED, stream=stream)
         hb = torch.from_numpy(blocks).pin_memory()
         hV = torch.from_numpy(V).pin_memory()
         hI = torch.zeros_like(hV).pin_memory()
@@ -692,50 +836,57 @@ def main():
             m.moma_solve(h, hV, hI)
             m.moma_active_impedance(h, hI, hV, hz, hg)
 
-        host_step()
+        for _ in range(args.warmup):
+            host_step()
         barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
             host_step()
         barrier()
         dt = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([dt], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
+        m.moma_destroy(h)
         # Host blocks: the library copies the offsets with dy >= 0 (Ny of the
         # 2Ny-1 rows; the rest follow from reciprocity); V goes in twice
         # (solve, port quantities) and I once.
-        e2e = {"value": world * nr * args.steps / dt, "unit": "solves/s",
+        e2e = {"value": replicas.aggregate_throughput(nr * args.steps, dt, device=dev), "unit": "solves/s",
                "h2d_bytes_per_step": int(blocks.nbytes // (2 * spec.ny - 1) * spec.ny + 2 * V.nbytes + V.nbytes),
                "d2h_bytes_per_step": int(V.nbytes + 2 * hz.numel() * 16)}
 
-    za = za_d.cpu().numpy()
-    from oracle.ports import named_elements
-    ports = {n: [complex(za[q, ey, ex]) for q in range(nr)] for n, (ex, ey) in named_elements(spec.nx, spec.ny).items()}
-    m.moma_destroy(h)
+    ports = {n: [complex(za_head[q, ey, ex]) for q in range(nr)]
+             for n, (ex, ey) in named_elements(spec.nx, spec.ny).items()}
+
+    subs = {}
+    if rank == 0 and not args.quick and not (args.lattice or args.nrhs):
+        sub_args = argparse.Namespace(**vars(args))
+        for name, fn in (("scan", run_scan), ("ragged", run_ragged), ("serve", run_serving)):
+            try:
+                subs[name] = fn(sub_args, sub=True)
+            except Exception as ex:  # a failed sub-measurement is reported, not hidden
+                subs[name] = {"error": repr(ex)}
 
     cpu = None
-    if rank == 0 and args.cpu_seconds > 0:
-        cpu = cpu_oracle_sample(spec, blocks, V, args.cpu_seconds)
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline_leg(spec, blocks, V, I_head)
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "c64 (FP32) inner + f64 refinement",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64 inner (FP32 FFTs, bin products, GMRES vectors); refinement residual Z I, block-bin "
+                     "transform and block Cholesky in double-FP32 (~48 bit); FP64 residual subtraction, "
+                     "Hessenberg/Givens, factor storage",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD if not (args.lattice or args.nrhs)
-                       else f"profiling lattice {args.lattice or 'C2'}, {nr} RHS",
-                       "rhs_per_step": nr * world, "parallelism": f"replicas x{world}",
-                       "l2": "inputs larger than L2 (c64 blocks 520 MB; stored bins 269 MB c64 + 537 MB c128)"},
+            "config": headline_config(args, nr, world),
             "step_ms": {"p50": statistics.median(steps_ms), "p99": float(np.percentile(steps_ms, 99)),
                         "min": min(steps_ms), "max": max(steps_ms)},
             "profiled_ms_per_step": prof_total_ms / args.steps,
-            "phases": phases, "roofline": roofline, "kernels": kernel_share, "cpu_baseline": cpu,
-            "e2e": e2e, "gpu_launches": launches, "clocks": clk, "fp64_plain": fp64, "pcg_mixed": pcg,
+            "phases": phases, "roofline": roofline, "matvec_roofline": matvec_roofline, "kernels": kernel_share,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk, "fp64_plain": fp64,
+            "mixed_fp64_residual": fp64r, "pcg_mixed": pcg,
             "ports_Za": {k: [f"{z.real:.10f}{z.imag:+.10f}j" for z in v] for k, v in ports.items()},
         }
+        line.update(subs)
         print(json.dumps(line, default=str), flush=True)
     if dist is not None:
         dist.destroy_process_group()

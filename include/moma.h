@@ -61,8 +61,15 @@ typedef enum { MOMA_C128 = 0, MOMA_C64 = 1 } moma_dtype;
 typedef enum {
     MOMA_PREC_FP64 = 0,  /* plain: every stage in FP64 / complex128 */
     MOMA_PREC_MIXED = 1  /* inner GMRES, FFTs and bin products in FP32/c64;
-                            FP64 for the refinement residual V - Z I, the
-                            Hessenberg least squares and the Cholesky factor */
+                            FP64 for the Hessenberg least squares, the
+                            storage of the Cholesky factor and the final
+                            subtraction of the refinement residual V - Z I.
+                            The FP64-class stages -- the transform into the
+                            c128-class bins, the residual's product Z I and
+                            the block Cholesky factorisation -- run in
+                            double-FP32 arithmetic (two floats, ~48
+                            significant bits) by default, or in FP64 with
+                            MOMA_FLAG_FP64_RESIDUAL. */
 } moma_precision;
 
 typedef enum {
@@ -78,8 +85,12 @@ enum {
     MOMA_FLAG_NO_AUTOTUNE = 2,   /* use the built-in launch-shape heuristics */
     MOMA_FLAG_NO_TENSOR = 4,     /* no tensor-core path: c64 bin products, preconditioner apply
                                     and (set-up) Gram products on the CUDA cores */
-    MOMA_FLAG_TENSOR_ALWAYS = 8  /* c64 bin products on the tensor cores from one RHS up
+    MOMA_FLAG_TENSOR_ALWAYS = 8, /* c64 bin products on the tensor cores from one RHS up
                                     (default: from 16 RHS; MIXED arrays, 128 <= b <= 256, b even) */
+    MOMA_FLAG_FP64_RESIDUAL = 16 /* MIXED arrays: compute the block-bin transform, the refinement
+                                    residual's Z I (bin product and FFTs) and the block Cholesky in
+                                    FP64 instead of double-FP32 (slower on B300, whose FP64 rate is
+                                    ~1/58 of FP32; results agree to ~1e-13) */
 };
 /* The tensor-core products (MIXED arrays): every circulant bin's block
  * Zhat_k (Eq. 3) is kept whole as a pair of TF32 values (hi + lo) and
@@ -180,16 +191,35 @@ moma_status moma_matvec(moma_array *a, int op, int nrhs, const void *x, void *y,
  * library holds until the process exits.
  *  - x, y: device memory only, layout [nrhs][Ny][Nx][b], dtype as in
  *    moma_matvec; host pointers are rejected with MOMA_ERR_ARG.
- *  - Sizes whose scratch exceeds 32 MiB are rejected with MOMA_ERR_ARG and a
- *    message stating the bytes needed (call again with fewer RHS).
- *  - The first call on a device looks up the array's device address (with
- *    that device current); make that first call before any stream capture.
+ *  - x and y must be on the device the array was created on (the one whose
+ *    copy of the scratch array, stream and stored bins the product uses);
+ *    buffers on another device are rejected with MOMA_ERR_ARG.
+ *  - Scratch needed: align256(nrhs*Ny*Mx*b*s) + 2*align256(Mx*My*nrhs*b*s)
+ *    bytes, s = 16 (MOMA_C128) or 8 (MOMA_C64), Mx, My the circulant sizes,
+ *    align256 rounding up to a multiple of 256.  Requests above 32 MiB are
+ *    rejected with MOMA_ERR_ARG and a message stating the bytes needed (call
+ *    again with fewer RHS).
+ *  - The first call on a device looks up the device address of the array
+ *    (cudaGetSymbolAddress, with the array's device made current for that
+ *    call and the caller's current device restored).  The address is cached
+ *    for the life of the device's primary context: after a
+ *    cudaDeviceReset, destroy and recreate the handles before calling again.
+ *  - The call is synchronous (it waits for its stream before returning, to
+ *    report device-side errors) and must not be called while the stream is
+ *    being captured into a CUDA graph.
  *  - All calls in the process share the one array: calls whose GPU work
  *    overlaps (other streams, other handles, other threads) race on it.  The
  *    scratch is fully rewritten before it is read, so no state leaks from one
  *    call into the next.
- * Errors: as moma_matvec, plus MOMA_ERR_ARG for host pointers, MOMA_OP_NORMAL
- * or oversized requests. */
+ *  - The product always runs on the CUDA cores with the built-in launch
+ *    shapes: its bin product is the streaming kernel moma_matvec uses below
+ *    16 RHS.  From 16 RHS on a MIXED array with 128 <= b <= 256, moma_matvec
+ *    switches its c64 product to the tensor cores (3xTF32), so the two
+ *    results then differ by that path's rounding, ~2e-6 relative; below 16
+ *    RHS, and for MOMA_C128, they agree to FP32 (c64) or ~1e-13 (c128)
+ *    rounding.
+ * Errors: as moma_matvec, plus MOMA_ERR_ARG for host pointers, buffers on
+ * another device, MOMA_OP_NORMAL or oversized requests. */
 moma_status moma_matvec_noalloc(moma_array *a, int op, int nrhs, const void *x, void *y, int dtype);
 
 /* y = P^{-1} x with the factored block-diagonal preconditioner (Eq. 38

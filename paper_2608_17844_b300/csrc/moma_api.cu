@@ -17,6 +17,7 @@
 
 #include "moma.h"
 #include "krylov.h"
+#include "noalloc_check.h"
 
 using namespace moma;
 
@@ -136,6 +137,11 @@ struct moma_array {
   size_t mx_stride = 0;
   int Mx = 0, My = 0, B = 0, Bp = 0, ldb = 0;
   int prec = MOMA_PREC_MIXED, m = 50;
+  // Arithmetic of the FP64-class stages of a MIXED array (the block-bin
+  // transform into the c128-class bins, the refinement residual's Z I and the
+  // block Cholesky): double-FP32 pairs (df = true, the default) or FP64
+  // (MOMA_FLAG_FP64_RESIDUAL).  Always false for FP64 arrays.
+  bool df = false;
   cudaStream_t st = nullptr;
   int dev = 0, num_sms = 148;
   size_t dev_bytes = 0;
@@ -750,7 +756,7 @@ void finish_preconditioner(moma_array *a) {
   const size_t npk = (size_t)a->b * (a->b + 1) / 2;
   a->Lpk.ensure((size_t)a->nel * npk * sizeof(double2), a->dev_bytes);
   a->timed(PK_CHOL, [&] { launch_box_cholesky(a->S.as<double2>(), a->nx, a->ny, a->b, a->Lpk.as<double2>(), a->err,
-                                                      a->prec == MOMA_PREC_MIXED, a->st); });
+                                                      a->df, a->st); });
   check_launch(a);
   using C = typename Cplx<R>::T;
   size_t xs = npk;
@@ -775,8 +781,9 @@ void set_blocks_impl(moma_array *a, const void *blocks, int dtype) {
   // b(b+1)/2 entries i <= j are transformed; the y pass scatters each bin's
   // values into the stored block of its pair (transposed for the partner).
   // FP64 in the plain path; double-FP32 pairs (c128-class bins stored as
-  // dfl2) in the mixed path, where B300's FP64 rate would bound it.
-  const bool df = a->prec == MOMA_PREC_MIXED;
+  // dfl2) in the mixed path, where B300's FP64 rate would bound it, unless
+  // the array asked for FP64 there (MOMA_FLAG_FP64_RESIDUAL).
+  const bool df = a->df;
   const int nt = a->b * (a->b + 1) / 2;
   a->T.ensure((size_t)ndy * a->Mx * nt * sizeof(double2), a->dev_bytes);
   a->S.ensure((size_t)nD * bb * sizeof(double2), a->dev_bytes);
@@ -1009,8 +1016,9 @@ void autotune(moma_array *a, int nr) {
   a->tune_bin_tr[0] = a->tune_bin_tr[1] = a->tune_bin_ns[0] = a->tune_bin_ns[1] = 0;
   a->tune_bin_occ[0] = a->tune_bin_occ[1] = 1;
   if (a->prec == MOMA_PREC_MIXED) autotune_precision<float>(a, nr, 0);
-  // The FP64-class residual runs in double-FP32 pairs in the mixed path.
-  if (a->prec == MOMA_PREC_MIXED) autotune_precision<dfl>(a, nr, 1);
+  // The FP64-class residual runs in double-FP32 pairs in the default mixed
+  // path, in FP64 otherwise.
+  if (a->df) autotune_precision<dfl>(a, nr, 1);
   else autotune_precision<double>(a, nr, 1);
   moma_array::TuneBin t;
   for (int k = 0; k < 2; ++k) {
@@ -1286,12 +1294,11 @@ void pcg_cycle(moma_array *a, int nr, const std::vector<int> &act, int max_inner
   check_launch(a);
 }
 
-template <typename R>
+// R: inner (Krylov) arithmetic; H: arithmetic of the refinement residual
+// V - Z I (FP64, or double-FP32 pairs of ~48 bits in the default mixed path).
+template <typename R, typename H>
 void solve_impl(moma_array *a, int nr, const void *Vin, void *Iout, const moma_solve_opts *o, moma_solve_info *info,
                 double *relres) {
-  // Arithmetic of the refinement residual V - Z I: FP64 in the plain path,
-  // double-FP32 pairs (~48 bits) in the mixed path.
-  using H = typename std::conditional<std::is_same<R, float>::value, dfl, double>::type;
   const double tol = (o && o->tol > 0) ? o->tol : 1e-10;
   const double itol = (o && o->inner_tol > 0) ? o->inner_tol : (is64<R>() ? tol * 0.1 : 1e-5);
   const int max_outer = (o && o->max_outer > 0) ? o->max_outer : 30;
@@ -1457,6 +1464,7 @@ moma_status moma_create_array(int nx, int ny, int b, const moma_options *opt, vo
     // and the bin product's per-warp column sums must fit in shared memory).
     if (b > 256) throw MomaError(MOMA_ERR_ARG, "b too large for this build (b <= 256)");
     a->prec = prec;
+    a->df = prec == MOMA_PREC_MIXED && !(opt && (opt->flags & MOMA_FLAG_FP64_RESIDUAL));
     a->m = (opt && opt->restart > 0) ? opt->restart : 50;
     a->use_graphs = !(opt && (opt->flags & MOMA_FLAG_NO_GRAPHS));
     a->no_autotune = opt && (opt->flags & MOMA_FLAG_NO_AUTOTUNE);
@@ -1513,7 +1521,7 @@ moma_status moma_matvec(moma_array *a, int op, int nrhs, const void *x, void *y,
     CK(cudaMemcpyAsync(a->Vw.p, x, bytes, cudaMemcpyDefault, a->st));
     if (d64) {
       if (op == MOMA_OP_NORMAL) apply_normal<double>(a, nrhs, a->Vw.p, a->yw.p);
-      else if (a->prec == MOMA_PREC_MIXED) apply_z<dfl>(a, nrhs, a->Vw.p, a->yw.p, op == MOMA_OP_ZH);
+      else if (a->df) apply_z<dfl>(a, nrhs, a->Vw.p, a->yw.p, op == MOMA_OP_ZH);
       else apply_z<double>(a, nrhs, a->Vw.p, a->yw.p, op == MOMA_OP_ZH);
     } else {
       if (op == MOMA_OP_NORMAL) apply_normal<float>(a, nrhs, a->Vw.p, a->yw.p);
@@ -1564,8 +1572,8 @@ moma_status moma_get_bin(moma_array *a, int kx, int ky, int dtype, void *out) {
     CK(cudaMemcpy(blk.data(), (const unsigned char *)src + (size_t)s * b * ldb * esz, blk.size(),
                   cudaMemcpyDeviceToHost));
     const bool transpose = k != canon;
-    // In the mixed path the c128-class bins are stored as double-FP32 pairs.
-    const bool from_df = dtype == MOMA_C128 && a->prec == MOMA_PREC_MIXED;
+    // In the default mixed path the c128-class bins are stored as double-FP32 pairs.
+    const bool from_df = dtype == MOMA_C128 && a->df;
     for (int i = 0; i < b; ++i)
       for (int j = 0; j < b; ++j) {
         const int si = transpose ? j : i, sj = transpose ? i : j;
@@ -1612,8 +1620,9 @@ moma_status moma_solve(moma_array *a, int nrhs, const void *V, void *I, const mo
     }
     ensure_ws(a, nrhs);
     ensure_tc(a, nrhs);
-    if (a->prec == MOMA_PREC_FP64) solve_impl<double>(a, nrhs, V, I, opts, info, rel_residual);
-    else solve_impl<float>(a, nrhs, V, I, opts, info, rel_residual);
+    if (a->prec == MOMA_PREC_FP64) solve_impl<double, double>(a, nrhs, V, I, opts, info, rel_residual);
+    else if (a->df) solve_impl<float, dfl>(a, nrhs, V, I, opts, info, rel_residual);
+    else solve_impl<float, double>(a, nrhs, V, I, opts, info, rel_residual);
   });
 }
 
@@ -1994,27 +2003,49 @@ constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mutex;
 void *g_noalloc_ptr[kMaxDevices] = {nullptr};
 
-// Device address of the scratch array on the current device (first call per
-// device resolves it with cudaGetSymbolAddress, with that device current).
+// Device address of the scratch array on device `dev` (the array's device).
+// The first call per device resolves it with cudaGetSymbolAddress while
+// that device is current, then restores the caller's current device.  The
+// cached address stays valid while the device's primary context lives,
+// i.e. for the whole process unless the caller resets the device.
 void *noalloc_scratch(int dev) {
   if (dev < 0 || dev >= kMaxDevices) throw MomaError(MOMA_ERR_ARG, "device index out of range");
   std::lock_guard<std::mutex> lock(g_noalloc_mutex);
   if (!g_noalloc_ptr[dev]) {
+    int prev = 0;
+    CK(cudaGetDevice(&prev));
+    if (prev != dev) CK(cudaSetDevice(dev));
     void *p = nullptr;
-    CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (prev != dev) cudaSetDevice(prev);
+    CK(e);
     g_noalloc_ptr[dev] = p;
   }
   return g_noalloc_ptr[dev];
 }
 
-size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
+// Host-side classification of a caller pointer (no allocation).
+PtrWhere where_is(const void *p) {
+  PtrWhere w;
+  if (!p) return w;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return w;
+  }
+  w.is_device = (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) ? 1 : 0;
+  w.device = at.device;
+  return w;
+}
 
 template <typename R>
 void noalloc_product(moma_array *a, int nr, const void *x, void *y, int herm, unsigned char *scratch) {
   const size_t esz = sizeof(typename Cplx<R>::T);
+  auto a256 = [](size_t n) { return (n + 255) & ~size_t(255); };
+  // Layout of noalloc_scratch_need: t1 [nr][Ny][Mx][b], then bx, by [B][nr][b].
   unsigned char *t1 = scratch;
-  unsigned char *bx = t1 + align256((size_t)nr * a->ny * a->Mx * a->b * esz);
-  unsigned char *by = bx + align256((size_t)a->B * nr * a->b * esz);
+  unsigned char *bx = t1 + a256((size_t)nr * a->ny * a->Mx * a->b * esz);
+  unsigned char *by = bx + a256((size_t)a->B * nr * a->b * esz);
   const int c = st_code<R>(), lc = lat_code<R>();
   launch_axis_pass<R>(pass_fx(a, nr, x, t1, lc, c), a->fx, a->st);
   check_launch(a);
@@ -2045,18 +2076,12 @@ extern "C" moma_status moma_matvec_noalloc(moma_array *a, int op, int nrhs, cons
     if (!d64 && a->prec != MOMA_PREC_MIXED) throw MomaError(MOMA_ERR_ARG, "c64 operators need a MIXED array");
     if (nrhs < 0) throw MomaError(MOMA_ERR_ARG, "nrhs < 0");
     if (nrhs == 0) return;
-    if (!is_device_ptr(x) || !is_device_ptr(y)) throw MomaError(MOMA_ERR_ARG, "x and y must be device memory");
     const size_t esz = d64 ? sizeof(double2) : sizeof(float2);
-    const size_t need = align256((size_t)nrhs * a->ny * a->Mx * a->b * esz) +
-                        2 * align256((size_t)a->B * nrhs * a->b * esz);
-    if (need > kNoAllocScratchBytes)
-      throw MomaError(MOMA_ERR_ARG, "moma_matvec_noalloc needs " + std::to_string(need) +
-                                        " bytes of scratch; the fixed maximum is " +
-                                        std::to_string(kNoAllocScratchBytes) + " (use fewer RHS per call)");
-    int dev = 0;
-    CK(cudaGetDevice(&dev));
-    unsigned char *scratch = static_cast<unsigned char *>(noalloc_scratch(dev));
-    if (d64 && a->prec == MOMA_PREC_MIXED) noalloc_product<dfl>(a, nrhs, x, y, op == MOMA_OP_ZH, scratch);
+    const size_t need = noalloc_scratch_need(nrhs, a->ny, a->Mx, a->B, a->b, esz);
+    const std::string why = noalloc_check(a->dev, where_is(x), where_is(y), need, kNoAllocScratchBytes);
+    if (!why.empty()) throw MomaError(MOMA_ERR_ARG, why);
+    unsigned char *scratch = static_cast<unsigned char *>(noalloc_scratch(a->dev));
+    if (d64 && a->df) noalloc_product<dfl>(a, nrhs, x, y, op == MOMA_OP_ZH, scratch);
     else if (d64) noalloc_product<double>(a, nrhs, x, y, op == MOMA_OP_ZH, scratch);
     else noalloc_product<float>(a, nrhs, x, y, op == MOMA_OP_ZH, scratch);
     sync_and_check(a);

@@ -46,6 +46,7 @@ class MomaError(RuntimeError):
 
 
 MOMA_FLAG_NO_GRAPHS, MOMA_FLAG_NO_AUTOTUNE, MOMA_FLAG_NO_TENSOR, MOMA_FLAG_TENSOR_ALWAYS = 1, 2, 4, 8
+MOMA_FLAG_FP64_RESIDUAL = 16
 
 
 class moma_options(ctypes.Structure):

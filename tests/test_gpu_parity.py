@@ -17,6 +17,7 @@ from oracle import dense, mbt, ports
 pytestmark = pytest.mark.gpu
 
 FP64, MIXED = 0, 1
+MIXED_F64R = 101  # a MIXED array with MOMA_FLAG_FP64_RESIDUAL (FP64 instead of double-FP32 residual stages)
 RAW_ERRORS = {}
 
 
@@ -35,7 +36,10 @@ def smooth(n):
 def make(m, nx, ny, b, prec, d=0.5, seed=0, dtype=np.complex128, mx=0, my=0):
     spec = LatticeSpec(nx, ny, b, d, seed)
     blocks = offset_blocks(spec, dtype)
-    h = m.moma_create_array(nx, ny, b, prec, mx, my)
+    if prec == MIXED_F64R:
+        h = m.moma_create_array(nx, ny, b, MIXED, mx, my, flags=m.MOMA_FLAG_FP64_RESIDUAL)
+    else:
+        h = m.moma_create_array(nx, ny, b, prec, mx, my)
     m.moma_set_blocks(h, blocks)
     return spec, blocks.astype(np.complex128), h
 
@@ -93,16 +97,18 @@ def test_padded_circulant_sizes(moma_lib, cuda):
 
 @pytest.mark.parametrize("nx,ny,b", CASES)
 @pytest.mark.parametrize("op", [0, 1])
-def test_matvec_fp64_and_c64(moma_lib, cuda, nx, ny, b, op):
+@pytest.mark.parametrize("prec", [MIXED, MIXED_F64R])
+def test_matvec_fp64_and_c64(moma_lib, cuda, nx, ny, b, op, prec):
     m = moma_lib
-    spec, blocks, h = make(m, nx, ny, b, MIXED)
+    spec, blocks, h = make(m, nx, ny, b, prec)
     try:
         x = rand_vec(3, spec)
         ref = mbt.matvec(blocks, nx, ny, x) if op == 0 else mbt.matvec_h(blocks, nx, ny, x)
         y = np.zeros_like(x)
         m.moma_matvec(h, op, x, y)
         assert relerr(y, ref) < 1e-12
-        RAW_ERRORS[f"matvec{'H' if op else ''}_dfl {nx}x{ny}x{b}"] = relerr(y, ref)
+        RAW_ERRORS[f"matvec{'H' if op else ''}_{'fp64' if prec == MIXED_F64R else 'dfl'} {nx}x{ny}x{b}"] = \
+            relerr(y, ref)
         assert np.abs(y - ref).max() <= 1e-11 * np.abs(ref).max()
         x32 = x.astype(np.complex64)
         y32 = np.zeros_like(x32)
@@ -173,7 +179,7 @@ SOLVE_CASES = [(1, 1, 3, 0.5), (2, 1, 1, 0.5), (3, 2, 4, 0.3), (4, 4, 32, 0.5), 
 
 
 @pytest.mark.parametrize("nx,ny,b,d", SOLVE_CASES)
-@pytest.mark.parametrize("prec", [FP64, MIXED])
+@pytest.mark.parametrize("prec", [FP64, MIXED, MIXED_F64R])
 def test_solve_matches_dense_lu(moma_lib, cuda, nx, ny, b, d, prec):
     m = moma_lib
     spec, blocks, h = make(m, nx, ny, b, prec, d=d)

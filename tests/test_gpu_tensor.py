@@ -72,23 +72,35 @@ def test_tensor_products_match_oracle(moma_lib, cuda, nx, ny, b, nr):
 
 
 def test_tensor_normal_operator(moma_lib, cuda):
+    """P^{-1} Z^H Z x (Sec. III-A) with the tensor path forced, element by
+    element against the oracle's normal operator (dense-definition blocks of
+    Eq. 37, direct offset sums), and against the CUDA-core path."""
     m = moma_lib
     spec = LatticeSpec(3, 3, 128, 0.5, 4)
     blocks = offset_blocks(spec, np.complex64)
+    b128 = blocks.astype(np.complex128)
     x = rand_vec(24, spec, seed=5)
+    ref = mbt.normal_operator(b128, spec.nx, spec.ny, x.astype(np.complex128))
     ys = []
     for flags in (m.MOMA_FLAG_TENSOR_ALWAYS, m.MOMA_FLAG_NO_TENSOR):
         h = m.moma_create_array(3, 3, 128, MIXED, flags=flags)
         try:
             m.moma_set_blocks(h, blocks)
+            m.moma_profile(h, 1)
             y = np.zeros_like(x)
             m.moma_matvec(h, m.MOMA_OP_NORMAL, x, y)
-            ys.append(y)
+            n_tc = m.moma_kernel_stats(h, "bin_tc")[0]
+            m.moma_profile(h, 0)
+            ys.append((y, n_tc))
         finally:
             m.moma_destroy(h)
-    e = relerr(ys[0], ys[1])
-    print("normal operator tensor vs cuda cores:", e)
-    assert e <= 5e-5
+    (yt, nt), (yc, nc) = ys
+    assert nt == 2 and nc == 0
+    scale = np.abs(ref).max()
+    et, ec = np.abs(yt - ref).max() / scale, np.abs(yc - ref).max() / scale
+    print(f"normal operator, max |y - oracle| / max |oracle|: tensor {et:.3g}, cuda cores {ec:.3g}")
+    assert et <= 1e-4 and ec <= 1e-5
+    assert relerr(yt, ref) <= 5e-5
 
 
 def test_solve_takes_tensor_path_and_matches_dense(moma_lib, cuda):
@@ -117,7 +129,11 @@ def test_solve_takes_tensor_path_and_matches_dense(moma_lib, cuda):
     z = dense.assemble(b128, spec.nx, spec.ny)
     i_ref = dense.solve(z, V)
     za_ref = ports.active_impedance(i_ref, V)
-    assert relerr(za, za_ref) <= 1e-8
+    # The Z_a bar is per port: the largest relative error over every port of every RHS.
+    err = np.max(np.abs(za - za_ref) / np.abs(za_ref))
+    print("tensor-path solve, max per-port Z_a rel err:", err)
+    assert err <= 1e-8
+    assert dense.relative_residual(z, I, V).max() <= 1e-10  # the oracle's own residual of the GPU currents
 
 
 @pytest.mark.parametrize("nx,ny,b,nr", [(3, 2, 128, 20), (2, 2, 160, 33), (2, 1, 256, 16)])
@@ -170,8 +186,11 @@ def test_wide_blocks_b256_solve_matches_dense(moma_lib, cuda, prec, nr):
         m.moma_destroy(h)
     print(f"b=256 prec={prec} nr={nr}:", info)
     assert info["converged"] == 1 and rr.max() <= 1e-10
-    i_ref = dense.solve(dense.assemble(b128, spec.nx, spec.ny), V)
-    assert relerr(za, ports.active_impedance(i_ref, V)) <= 1e-8
+    z = dense.assemble(b128, spec.nx, spec.ny)
+    i_ref = dense.solve(z, V)
+    za_ref = ports.active_impedance(i_ref, V)
+    assert np.max(np.abs(za - za_ref) / np.abs(za_ref)) <= 1e-8
+    assert dense.relative_residual(z, I, V).max() <= 1e-10
 
 
 @pytest.mark.parametrize("nx,ny,b", [(3, 2, 128), (2, 2, 160)])

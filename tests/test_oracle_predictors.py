@@ -144,3 +144,68 @@ def test_xi_z_invariants():
     corner = 0
     zp[c, corner] = 10.0
     assert pr.xi_z_max(zp, nx, ny) == 10.0 / abs(60 + 20j) > pr.xi_z(zp, nx, ny)
+
+
+def test_s_ideal_phase_hand_values():
+    """S_ideal's off-neighbour entries (reading of Eq. 36 in the module
+    docstring): s1 dist^-2 exp(-j k d (dist - 1)).  With k d chosen so that
+    the extra distance is a quarter turn the phase factor is exactly -j, so
+    the entries are written out by hand: a sign error in the phase flips
+    them, a wrong power of the distance rescales them."""
+    s1 = -0.2 + 0.1j  # s1 * (-j) = 0.1 + 0.2j
+    # 3 x 3 lattice; element e = mx + 3 my.  Diagonal neighbour (0,0)-(1,1):
+    # dist sqrt(2), k d (sqrt(2) - 1) = pi / 2.
+    kd = (np.pi / 2) / (np.sqrt(2.0) - 1.0)
+    s = pr.s_ideal(3, 3, 0.3, s1, kd)
+    assert abs(s[0, 4] - (0.1 + 0.2j) / 2) < 1e-15
+    assert abs(s[4, 0] - (0.1 + 0.2j) / 2) < 1e-15
+    # Two cells along x, (0,0)-(2,0): dist 2, k d = pi / 2 -> phase -j, |.| = |s1| / 4.
+    s = pr.s_ideal(3, 3, 0.3, s1, np.pi / 2)
+    assert abs(s[0, 2] - (0.1 + 0.2j) / 4) < 1e-15
+    # (0,0)-(2,2): dist 2 sqrt(2), phase exp(-j (pi/2)(2 sqrt 2 - 1)); with k d = pi / (2 sqrt 2 - 1)
+    # the phase is exp(-j pi) = -1, |.| = |s1| / 8.
+    s = pr.s_ideal(3, 3, 0.3, s1, np.pi / (2 * np.sqrt(2.0) - 1.0))
+    assert abs(s[0, 8] - (0.2 - 0.1j) / 8) < 1e-15
+    # Nearest neighbours carry s1 itself whatever k d is; the diagonal is s_cc.
+    assert s[4, 5] == s1 and s[4, 1] == s1 and s[4, 4] == 0.3
+
+
+def test_z_from_s_satisfies_its_defining_relation():
+    """Eq. 31: Z_p (I - S) = Z0 (I + S) (the factors commute), for a
+    generic S, and s_from_z inverts it."""
+    rng = np.random.default_rng(3)
+    n = 7
+    s = 0.2 * (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
+    z = pr.z_from_s(s, 50.0)
+    eye = np.eye(n)
+    assert np.abs(z @ (eye - s) - 50.0 * (eye + s)).max() < 1e-12
+    assert np.abs(pr.s_from_z(z, 50.0) - s).max() < 1e-13
+
+
+@pytest.mark.parametrize("nx,ny,s_cc,s1,kd", [(3, 3, 0.5, 0.02 + 0.01j, np.pi),
+                                                (5, 4, -0.3 + 0.2j, 0.05 - 0.02j, 2.2),
+                                                (4, 5, 0.1j, 0.03, 3.9)])
+def test_xi_s_against_a_neumann_series(nx, ny, s_cc, s1, kd):
+    """xi_S (Eq. 36) by a second route: with S = s_cc I + T the converted
+    matrix is Z0 (I + S)(I - S)^{-1} = Z0 (-I + (2/c) sum_n (T/c)^n),
+    c = 1 - s_cc, a convergent series here (||T / c|| < 1); its entries
+    [c, j] and [c, c], at the hand-counted centre and closest border
+    element, give xi_S.  Catches a swapped S <-> Z conversion, the wrong
+    border element or the wrong denominator."""
+    s = pr.s_ideal(nx, ny, s_cc, s1, kd)
+    t = s - s_cc * np.eye(nx * ny)
+    c = 1.0 - s_cc
+    assert np.linalg.norm(t / c, 2) < 0.5
+    acc = np.eye(nx * ny, dtype=np.complex128)
+    term = np.eye(nx * ny, dtype=np.complex128)
+    for _ in range(80):
+        term = term @ (t / c)
+        acc = acc + term
+    z = 50.0 * (-np.eye(nx * ny) + (2.0 / c) * acc)
+    cen = {(3, 3): 4, (5, 4): 12, (4, 5): 10}[(nx, ny)]      # (floor(Nx/2), floor(Ny/2))
+    # Closest border element: 3x3 -> (0,1) (distance 1, centre row, smaller index than (2,1));
+    # 5x4 -> (2,3), one row above the centre (2,2); 4x5 -> (3,2), one column right of (2,2).
+    j = {(3, 3): 3, (5, 4): 17, (4, 5): 11}[(nx, ny)]
+    assert pr.centre_index(nx, ny) == cen and pr.closest_border_element(nx, ny) == j
+    want = abs(z[cen, j]) / abs(z[cen, cen])
+    assert abs(pr.xi_s(nx, ny, s_cc, s1, kd, 50.0) - want) < 1e-12 * want
