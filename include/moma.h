@@ -87,10 +87,20 @@ enum {
                                     and (set-up) Gram products on the CUDA cores */
     MOMA_FLAG_TENSOR_ALWAYS = 8, /* c64 bin products on the tensor cores from one RHS up
                                     (default: from 16 RHS; MIXED arrays, 128 <= b <= 256, b even) */
-    MOMA_FLAG_FP64_RESIDUAL = 16 /* MIXED arrays: compute the block-bin transform, the refinement
+    MOMA_FLAG_FP64_RESIDUAL = 16, /* MIXED arrays: compute the block-bin transform, the refinement
                                     residual's Z I (bin product and FFTs) and the block Cholesky in
                                     FP64 instead of double-FP32 (slower on B300, whose FP64 rate is
                                     ~1/58 of FP32; results agree to ~1e-13) */
+    MOMA_FLAG_AXIS_FFT = 32,     /* lattice transforms of the c64 / FP64 products as one launch per
+                                    lattice axis instead of one 2D launch per transform (the 2D
+                                    kernels are the default where the grid fits shared memory) */
+    MOMA_FLAG_PRECOND_PER_ELEMENT = 64, /* c64 preconditioner apply with one CTA per element instead of
+                                    the streaming kernel (default for even b <= 160 and fewer
+                                    than 16 RHS) */
+    MOMA_FLAG_SPLIT_ARNOLDI = 128 /* GMRES orthogonalisation as three sweep launches and a scaling
+                                    launch per Arnoldi step instead of one cooperative launch
+                                    (the default where its grid fits on the device at once);
+                                    results are bitwise the same */
 };
 /* The tensor-core products (MIXED arrays): every circulant bin's block
  * Zhat_k (Eq. 3) is kept whole as a pair of TF32 values (hi + lo) and

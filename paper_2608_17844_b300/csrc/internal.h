@@ -58,6 +58,25 @@ struct AxisPass {
 template <typename R>
 void launch_axis_pass(const AxisPass &p, const FftTables &t, cudaStream_t st);
 
+// Two-dimensional lattice transforms in one launch (lattice2d.cu): mode 0
+// F2 lattice -> bins, 1 I2 bins -> lattice, 2 I2MF2 bins -> bins (inverse,
+// lattice mask, forward).  Lattice vectors [nr][ldv] with element (y, x) at
+// (y Nx + x) b; bins [My][Mx][nr][b].  R = float (c64) or double (c128).
+struct Lattice2D {
+  int mode = 0;
+  const void *in = nullptr;
+  void *out = nullptr;
+  int nx = 0, ny = 0, b = 0, nr = 0;
+  long long ldv = 0;
+  const int *live = nullptr;  // if set and *live == 0 the transform does nothing
+  int J = 0;                  // basis indices per CTA (1, 2, 4; 0 = heuristic)
+  int threads = 0;            // threads per CTA (0 = 256)
+};
+template <typename R>
+bool lattice2d_fits(int Mx, int My, int J);
+template <typename R>
+void launch_lattice2d(const Lattice2D &p, const FftTables &fx, const FftTables &fy, cudaStream_t st);
+
 // --------------------------------------------------------- bin product ----
 struct BinProduct {
   const void *Z = nullptr;    // pair storage [Bp][b][ldb]
@@ -126,6 +145,14 @@ void launch_tri_inverse(const double2 *Lpk, int nel, int b, void *X, size_t x_st
 template <typename R>
 void launch_precond_apply(const void *X, size_t x_stride, int nel, int b, int nr, const void *x, void *y,
                           unsigned *err, const int *live, long long vstride, long long voff, cudaStream_t st);
+
+// Streaming c64 application of X_e^H X_e from 8 x 8-blocked factors
+// (precond_blk.cu): one persistent CTA per SM, a ring of bulk copies.
+size_t xblk_entries(int b);  // complex entries per element of the blocked factor
+bool precond_blk_supported(int b, int nr, long long vstride, long long voff);
+void launch_xblk_pack(const void *Xpk, size_t x_stride, int nel, int b, void *Xb, cudaStream_t st);
+void launch_precond_blk(const void *Xb, int nel, int b, int nr, const void *x, void *y, unsigned *err,
+                        const int *live, long long vstride, long long voff, int num_sms, cudaStream_t st);
 
 // -------------------------------------------------------------- margin ----
 // y += margin terms of Z (herm = 0) or Z^H (herm = 1) for vectors

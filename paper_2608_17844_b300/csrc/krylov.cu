@@ -215,6 +215,160 @@ __global__ void __launch_bounds__(KT) cgs_kernel(KrylovCtl c, typename Cplx<R>::
   if (tid == 0) c.counters[q] = 0;
 }
 
+// Grid-wide barrier of the fused Arnoldi step (all CTAs co-resident: the
+// kernel is launched cooperatively).  A monotonically increasing counter,
+// zeroed once per GMRES cycle; a CTA waits until every CTA has arrived at
+// this generation.  The wait is bounded (2 s): on timeout the CTA records
+// DEVERR_TIMEOUT and reports failure, and the kernel returns.
+MOMA_DEV bool grid_barrier(unsigned *count, unsigned nblocks, unsigned *err) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned old = atomicAdd(count, 1u);
+    const unsigned target = (old / nblocks + 1u) * nblocks;
+    int ok = 1;
+    const uint64_t t0 = global_ns();
+    for (unsigned it = 1;; ++it) {
+      unsigned v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
+      if ((int)(v - target) >= 0) break;
+      if ((it & 255u) == 0 && global_ns() - t0 > 2000000000ull) {
+        atomicOr(err, DEVERR_TIMEOUT);
+        ok = 0;
+        break;
+      }
+    }
+    __threadfence();
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+// The fused Arnoldi step: CTA (chunk, q) keeps its chunk of w = V[j + 1] in
+// registers through the three sweeps; the per-chunk partial sums of each
+// sweep go to their own buffer and, after a grid barrier, every CTA of RHS q
+// adds them in the same fixed order as the last-block reduction of
+// cgs_kernel, so the step is bitwise the three-launch version.
+template <typename R>
+__global__ void __launch_bounds__(KT) arnoldi_fused_kernel(KrylovCtl c, typename Cplx<R>::T *V, size_t vstride,
+                                                            int N, int j) {
+  using C = typename Cplx<R>::T;
+  __shared__ C red[8 * KG];
+  __shared__ C hs[MOMA_MAX_RESTART + 1];
+  __shared__ double2 hd[MOMA_MAX_RESTART + 1];
+  const int q = blockIdx.y, chunk = blockIdx.x, tid = threadIdx.x, nch = gridDim.x;
+  const unsigned nblocks = gridDim.x * gridDim.y;
+  if (*c.nact == 0) return;  // uniform: nact changes only after the last barrier
+  const bool act = c.active[q] != 0;
+  const int m = c.m, wid = tid >> 5, lane = tid & 31;
+  const size_t qoff = (size_t)q * N;
+  C *w = V + (size_t)(j + 1) * vstride + qoff;
+  const int n0 = chunk * KT * KEPT;
+  C wv[KEPT];
+#pragma unroll
+  for (int t = 0; t < KEPT; ++t) {
+    const int n = n0 + tid + KT * t;
+    wv[t] = (act && n < N) ? w[n] : czero<C>();
+  }
+  // Sweep partial dot products V_i^H w (i <= j) into buf.
+  auto dots = [&](double2 *buf) {
+    for (int i0 = 0; i0 <= j; i0 += KG) {
+      C accr[KG];
+#pragma unroll
+      for (int ii = 0; ii < KG; ++ii) accr[ii] = czero<C>();
+#pragma unroll
+      for (int ii = 0; ii < KG; ++ii) {
+        const int i = i0 + ii;
+        if (i <= j) {
+          const C *vi = V + (size_t)i * vstride + qoff;
+#pragma unroll
+          for (int t = 0; t < KEPT; ++t) {
+            const int n = n0 + tid + KT * t;
+            if (n < N) accr[ii] = cfmac(vi[n], wv[t], accr[ii]);
+          }
+        }
+      }
+      block_sum<C, KG>(accr, red);
+      if (tid == 0)
+        for (int ii = 0; ii < KG && i0 + ii <= j; ++ii)
+          buf[((size_t)q * nch + chunk) * (m + 1) + i0 + ii] = cvt<double2>(accr[ii]);
+    }
+  };
+  // h_i = sum over chunks (fixed order) into hd (FP64) and hs (precision C).
+  auto gather = [&](const double2 *buf) {
+    const double2 *pq = buf + (size_t)q * nch * (m + 1);
+    for (int i = wid; i <= j; i += KT / 32) {
+      const double2 sm = chunk_sum(pq, nch, m + 1, i);
+      if (lane == 0) {
+        hd[i] = sm;
+        hs[i] = cvt<C>(sm);
+      }
+    }
+    __syncthreads();
+  };
+  auto update = [&]() {  // w -= V h
+    for (int i = 0; i <= j; ++i) {
+      const C hi = hs[i];
+      const C *vi = V + (size_t)i * vstride + qoff;
+#pragma unroll
+      for (int t = 0; t < KEPT; ++t) {
+        const int n = n0 + tid + KT * t;
+        if (n < N) wv[t] = csub(wv[t], cmul(vi[n], hi));
+      }
+    }
+  };
+
+  if (act) dots(c.partial);
+  if (!grid_barrier(c.gbar, nblocks, c.err)) return;
+  if (act) {
+    gather(c.partial);
+    if (chunk == 0)
+      for (int i = tid; i <= j; i += KT) c.hacc[(size_t)q * (m + 1) + i] = hd[i];
+    update();
+    dots(c.partial2);
+  }
+  if (!grid_barrier(c.gbar, nblocks, c.err)) return;
+  double nrm = 0.0;
+  if (act) {
+    gather(c.partial2);
+    if (chunk == 0)
+      for (int i = tid; i <= j; i += KT) {
+        double2 *ha = c.hacc + (size_t)q * (m + 1) + i;
+        *ha = cadd(*ha, hd[i]);
+      }
+    update();
+    C acc[1] = {czero<C>()};
+#pragma unroll
+    for (int t = 0; t < KEPT; ++t) acc[0].x += wv[t].x * wv[t].x + wv[t].y * wv[t].y;
+    block_sum<C, 1>(acc, red);
+    if (tid == 0) c.partial3[(size_t)q * nch + chunk] = cvt<double2>(acc[0]);
+  }
+  if (!grid_barrier(c.gbar, nblocks, c.err)) return;
+  if (!act) return;
+  {
+    __shared__ double nrm_s;
+    if (wid == 0) {
+      double2 s = make_double2(0, 0);
+      for (int ch = lane; ch < nch; ch += 32) s = cadd(s, c.partial3[(size_t)q * nch + ch]);
+      s = warp_sum(s);
+      if (lane == 0) nrm_s = sqrt(s.x);
+    }
+    __syncthreads();
+    nrm = nrm_s;
+  }
+  // Givens update (one thread per RHS); every CTA scales its chunk by
+  // 1 / ||w|| (a frozen column's new vector is never read again).
+  if (chunk == 0 && tid == 0) givens_step(c, q, j, nrm);
+  const R sc = (nrm > 0.0 && isfinite(nrm)) ? (R)(1.0 / nrm) : (R)0;
+#pragma unroll
+  for (int t = 0; t < KEPT; ++t) {
+    const int n = n0 + tid + KT * t;
+    if (n < N) w[n] = cscale(wv[t], sc);
+  }
+}
+
 // V[slot] *= inv_norm[q] (zero for frozen columns).
 template <typename R>
 __global__ void scale_kernel(KrylovCtl c, typename Cplx<R>::T *v, size_t vstride, int N, int nr) {
@@ -375,6 +529,33 @@ void launch_ports(const double2 *I, const double2 *V, int nel, int b, int nr, in
                   double2 *Gam, unsigned *err, long long ldv, cudaStream_t st) {
   ports_kernel<<<(nel * nr + 255) / 256, 256, 0, st>>>(I, V, nel, b, nr, pb, z0, Za, Gam, err, ldv);
 }
+
+template <typename R>
+bool arnoldi_fused_fits(int N, int nr, int num_sms) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, arnoldi_fused_kernel<R>, KT, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return (long long)krylov_chunks(N) * nr <= (long long)per_sm * num_sms;
+}
+template <typename R>
+void launch_arnoldi_fused(const KrylovCtl &c, void *V, size_t vstride, int N, int nr, int j, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(krylov_chunks(N), nr);
+  cfg.blockDim = dim3(KT);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, arnoldi_fused_kernel<R>, c, reinterpret_cast<typename Cplx<R>::T *>(V), vstride, N, j);
+}
+template bool arnoldi_fused_fits<float>(int, int, int);
+template bool arnoldi_fused_fits<double>(int, int, int);
+template void launch_arnoldi_fused<float>(const KrylovCtl &, void *, size_t, int, int, int, cudaStream_t);
+template void launch_arnoldi_fused<double>(const KrylovCtl &, void *, size_t, int, int, int, cudaStream_t);
 
 template void launch_cgs<float>(const KrylovCtl &, void *, size_t, int, int, int, int, cudaStream_t);
 template void launch_cgs<double>(const KrylovCtl &, void *, size_t, int, int, int, int, cudaStream_t);

@@ -29,6 +29,9 @@ struct KrylovCtl {
   double2 *sn;           // [nr][m]
   double2 *g;            // [nr][m+1]
   double2 *y;            // [nr][m]
+  double2 *partial2;     // [nr][nchunk][m+1]  (fused step: second and third sweeps)
+  double2 *partial3;     // [nr][nchunk]
+  unsigned *gbar;        // [1] grid-barrier counter of the fused step (zeroed per cycle)
 };
 
 enum : int { CG_PQ = 0, CG_RZ = 1, CG_RZ0 = 2 };  // modes of launch_cg_reduce
@@ -59,6 +62,14 @@ template <typename R>
 void launch_cgs(const KrylovCtl &c, void *V, size_t vstride, int N, int nr, int j, int flags, cudaStream_t st);
 template <typename R>
 void launch_scale(const KrylovCtl &c, void *v, size_t vstride, int N, int nr, cudaStream_t st);
+// One whole Arnoldi orthogonalisation step j (the three CGS2 sweeps, the
+// Givens update and the scaling of the new basis vector) as one cooperative
+// launch with grid barriers; false if the grid cannot be co-resident (the
+// caller then issues the separate sweeps).
+template <typename R>
+bool arnoldi_fused_fits(int N, int nr, int num_sms);
+template <typename R>
+void launch_arnoldi_fused(const KrylovCtl &c, void *V, size_t vstride, int N, int nr, int j, cudaStream_t st);
 void launch_backsolve(const KrylovCtl &c, int nr, cudaStream_t st);
 template <typename R>
 void launch_lincomb(const KrylovCtl &c, const void *V, size_t vstride, int N, int nr, double2 *I,

@@ -153,6 +153,8 @@ struct moma_array {
   DevBuf bin_slot, tri, tri_in;  // symmetric block-transform tables
   DevBuf Z128, Z64;  // pair storage [Bp][b][ldb]
   DevBuf Xinv;       // inverse factors, packed row-major, inner precision
+  DevBuf Xblk;       // c64 inverse factors in 8 x 8 blocks for the streaming apply (precond_blk.cu)
+  bool xblk_ready = false;
   // Tensor-core products (inner precision c64, many RHS): split full bins,
   // the partner table, split X_e and X_e^H; built on first use after
   // set_blocks.
@@ -213,6 +215,10 @@ struct moma_array {
   bool no_autotune = false;
   int tune_bin_tr[2] = {0, 0}, tune_bin_ns[2] = {0, 0}, tune_bin_occ[2] = {1, 1};  // [c64, c128]
   std::vector<std::pair<long long, int>> tune_axis;       // pass signature -> threads per line
+  std::vector<std::pair<long long, int2>> tune_l2d;       // 2D transform signature -> (J, threads)
+  bool axis_fft = false;  // lattice transforms one launch per axis instead of the 2D kernels
+  bool no_blk_precond = false;  // c64 preconditioner through the per-element kernel only
+  bool no_fused_arnoldi = false;  // CGS2 sweeps as separate launches
   std::string tune_log;
   const int *live = nullptr;  // operator kernels skip their work while *live == 0
 
@@ -504,23 +510,69 @@ void precond(moma_array *a, int nr, const void *x, void *y) {
     precond_margin<R>(a, nr, x, y);
     return;
   }
-  a->timed(PK_PREC, [&] {
-    launch_precond_apply<R>(a->Xinv.p, a->x_stride, a->nel, a->b, nr, x, y, a->err, a->live, a->ldv, 0, a->st);
-  });
+  if (std::is_same<R, float>::value && a->xblk_ready && precond_blk_supported(a->b, nr, a->ldv, 0)) {
+    a->timed(PK_PREC, [&] {
+      launch_precond_blk(a->Xblk.p, a->nel, a->b, nr, x, y, a->err, a->live, a->ldv, 0, a->num_sms, a->st);
+    });
+  } else {
+    a->timed(PK_PREC, [&] {
+      launch_precond_apply<R>(a->Xinv.p, a->x_stride, a->nel, a->b, nr, x, y, a->err, a->live, a->ldv, 0, a->st);
+    });
+  }
   check_launch(a);
   precond_margin<R>(a, nr, x, y);
+}
+
+// The 2D lattice transforms (one launch per transform) serve the c64 and
+// FP64 products; the double-FP32 residual path keeps the per-axis passes.
+template <typename R> bool use_l2d(const moma_array *a) {
+  if constexpr (std::is_same<R, dfl>::value) return false;
+  else return !a->axis_fft && lattice2d_fits<R>(a->Mx, a->My, 1);
+}
+
+long long l2d_sig(int mode, int nr, int is64v) { return ((long long)mode * 1000003LL + nr) * 4 + is64v; }
+
+template <typename R>
+void l2d(moma_array *a, int mode, int nr, const void *in, void *out) {
+  Lattice2D p;
+  p.mode = mode; p.in = in; p.out = out; p.nx = a->nx; p.ny = a->ny; p.b = a->b; p.nr = nr; p.ldv = a->ldv;
+  p.live = a->live;
+  const long long sig = l2d_sig(mode, nr, is64<R>());
+  for (auto &kv : a->tune_l2d)
+    if (kv.first == sig) { p.J = kv.second.x; p.threads = kv.second.y; }
+  a->timed(is64<R>() ? PK_FFT128 : PK_FFT64, [&] { launch_lattice2d<R>(p, a->fx, a->fy, a->st); });
+  check_launch(a);
 }
 
 // lattice -> bins (Fx then Fy); in may be c128 when R is double.
 template <typename R>
 void lattice_to_bins(moma_array *a, int nr, const void *in, int in128) {
+  if (use_l2d<R>(a)) {
+    l2d<R>(a, 0, nr, in, a->bx.p);
+    return;
+  }
   axis<R>(a, pass_fx(a, nr, in, a->t1.p, in128, st_code<R>()), a->fx);
   axis<R>(a, pass_fy(a, nr, a->t1.p, a->bx.p, st_code<R>()), a->fy);
 }
 template <typename R>
 void bins_to_lattice(moma_array *a, int nr, const void *bins, void *out) {
+  if (use_l2d<R>(a)) {
+    l2d<R>(a, 1, nr, bins, out);
+    return;
+  }
   axis<R>(a, pass_iy(a, nr, bins, a->t1.p, st_code<R>()), a->fy);
   axis<R>(a, pass_ix(a, nr, a->t1.p, out, st_code<R>(), false, lat_code<R>()), a->fx);
+}
+// Between the Z and Z^H legs: inverse, lattice mask, forward (by -> bx).
+template <typename R>
+void mask_between_legs(moma_array *a, int nr) {
+  if (use_l2d<R>(a)) {
+    l2d<R>(a, 2, nr, a->by.p, a->bx.p);
+    return;
+  }
+  axis<R>(a, pass_iy(a, nr, a->by.p, a->t1.p, is64<R>()), a->fy);
+  axis<R>(a, pass_ix(a, nr, a->t1.p, a->t1.p, is64<R>(), true), a->fx);
+  axis<R>(a, pass_fy(a, nr, a->t1.p, a->bx.p, is64<R>()), a->fy);
 }
 
 // y = Z x (herm = 0) or Z^H x (herm = 1), lattice in/out in precision R.
@@ -543,9 +595,7 @@ void apply_normal(moma_array *a, int nr, const void *x, void *y) {
   }
   lattice_to_bins<R>(a, nr, x, is64<R>());
   binprod<R>(a, nr, a->bx.p, a->by.p, 0);
-  axis<R>(a, pass_iy(a, nr, a->by.p, a->t1.p, is64<R>()), a->fy);
-  axis<R>(a, pass_ix(a, nr, a->t1.p, a->t1.p, is64<R>(), true), a->fx);
-  axis<R>(a, pass_fy(a, nr, a->t1.p, a->bx.p, is64<R>()), a->fy);
+  mask_between_legs<R>(a, nr);
   binprod<R>(a, nr, a->bx.p, a->by.p, 1);
   bins_to_lattice<R>(a, nr, a->by.p, a->lat_tmp.p);
   precond<R>(a, nr, a->lat_tmp.p, y);
@@ -561,9 +611,7 @@ void apply_zhz(moma_array *a, int nr, const void *x, void *y) {
   }
   lattice_to_bins<R>(a, nr, x, is64<R>());
   binprod<R>(a, nr, a->bx.p, a->by.p, 0);
-  axis<R>(a, pass_iy(a, nr, a->by.p, a->t1.p, is64<R>()), a->fy);
-  axis<R>(a, pass_ix(a, nr, a->t1.p, a->t1.p, is64<R>(), true), a->fx);
-  axis<R>(a, pass_fy(a, nr, a->t1.p, a->bx.p, is64<R>()), a->fy);
+  mask_between_legs<R>(a, nr);
   binprod<R>(a, nr, a->bx.p, a->by.p, 1);
   bins_to_lattice<R>(a, nr, a->by.p, y);
 }
@@ -649,6 +697,8 @@ void ensure_ws(moma_array *a, int nr) {
   const size_t o_cg_act = take(nr * sizeof(int)), o_cg_nact = take(sizeof(int)), o_cg_it = take(nr * sizeof(int));
   const size_t o_cg_s = take((size_t)5 * nr * sizeof(double)), o_cg_cnt = take(nr * sizeof(unsigned));
   const size_t o_cg_part = take((size_t)nr * nch * sizeof(double));
+  const size_t o_part2 = take((size_t)nr * nch * (m + 1) * c), o_part3 = take((size_t)nr * nch * c);
+  const size_t o_gbar = take(sizeof(unsigned));
   a->kbuf.ensure(off, a->dev_bytes);
   unsigned char *base = a->kbuf.as<unsigned char>();
   CK(cudaMemset(base, 0, off));
@@ -670,6 +720,9 @@ void ensure_ws(moma_array *a, int nr) {
   k.sn = reinterpret_cast<double2 *>(base + o_sn);
   k.g = reinterpret_cast<double2 *>(base + o_g);
   k.y = reinterpret_cast<double2 *>(base + o_y);
+  k.partial2 = reinterpret_cast<double2 *>(base + o_part2);
+  k.partial3 = reinterpret_cast<double2 *>(base + o_part3);
+  k.gbar = reinterpret_cast<unsigned *>(base + o_gbar);
   k.err = a->err;
   a->rnorm = reinterpret_cast<double *>(base + o_rn);
   a->vnorm = reinterpret_cast<double *>(base + o_vn);
@@ -765,6 +818,14 @@ void finish_preconditioner(moma_array *a) {
   a->Xinv.ensure((size_t)a->nel * xs * sizeof(C), a->dev_bytes);
   a->timed(PK_TRINV, [&] { launch_tri_inverse<R>(a->Lpk.as<double2>(), a->nel, a->b, a->Xinv.p, xs, a->st); });
   check_launch(a);
+  // c64 factors also in the blocked layout of the streaming apply.
+  a->xblk_ready = false;
+  if (std::is_same<R, float>::value && !a->no_blk_precond && precond_blk_supported(a->b, 1, 2, 0)) {
+    a->Xblk.ensure((size_t)a->nel * xblk_entries(a->b) * sizeof(float2), a->dev_bytes);
+    a->timed(PK_TRINV, [&] { launch_xblk_pack(a->Xinv.p, a->x_stride, a->nel, a->b, a->Xblk.p, a->st); });
+    check_launch(a);
+    a->xblk_ready = true;
+  }
 }
 
 void set_blocks_impl(moma_array *a, const void *blocks, int dtype) {
@@ -972,6 +1033,30 @@ void autotune_precision(moma_array *a, int nr, int in128) {
              st_code<R>() == 2 ? "dfl" : (is64<R>() ? "c128" : "c64"), nr, btr, bns, bocc, 1000.0f * best / 2);
     a->tune_log += buf;
   }
+  // 2D lattice transforms: basis indices per CTA x threads per CTA.
+  if (use_l2d<R>(a)) {
+    static const char *names[3] = {"F2", "I2", "I2MF2"};
+    for (int mode = 0; mode < 3; ++mode) {
+      float best = 1e30f;
+      int bj = 0, bt = 0;
+      for (int J : {1, 2, 4}) {
+        if (!lattice2d_fits<R>(a->Mx, a->My, J)) continue;
+        for (int th : {128, 256, 512}) {
+          Lattice2D p;
+          p.mode = mode; p.nx = a->nx; p.ny = a->ny; p.b = a->b; p.nr = nr; p.ldv = a->ldv; p.J = J; p.threads = th;
+          p.in = mode == 0 ? a->lat_in.p : a->by.p;
+          p.out = mode == 1 ? a->lat_tmp.p : a->bx.p;
+          const float ms = time_launch(a, [&] { launch_lattice2d<R>(p, a->fx, a->fy, a->st); });
+          if (ms < best) { best = ms; bj = J; bt = th; }
+        }
+      }
+      a->tune_l2d.push_back({l2d_sig(mode, nr, is64<R>()), make_int2(bj, bt)});
+      snprintf(buf, sizeof(buf), "%s<%s> nr=%d: J=%d threads=%d (%.1f us)\n", names[mode], is64<R>() ? "c128" : "c64",
+               nr, bj, bt, 1000.0f * best / 2);
+      a->tune_log += buf;
+    }
+    return;
+  }
   // Lattice FFT passes of the products and the normal operator.
   const int c = st_code<R>();
   struct Cand { AxisPass p; const FftTables *t; const char *name; };
@@ -1060,10 +1145,21 @@ void gmres_cycle(moma_array *a, int nr, const std::vector<int> &act, int *inner_
   // One Arnoldi step: the normal operator, the three CGS2 sweeps (the last
   // one applies the Givens rotation), the scaling of the new basis vector,
   // and the copy of the active-column count for the host's lagged poll.
+  // The sweeps and the scaling run as one cooperative launch when the grid
+  // can be co-resident (its barrier counter restarts with every cycle).
+  const bool fused = !a->no_fused_arnoldi && arnoldi_fused_fits<R>((int)a->ldv, nr, a->num_sms);
+  if (fused) CK(cudaMemsetAsync(c.gbar, 0, sizeof(unsigned), a->st));
   auto enqueue_step = [&](int j) {
     a->live = c.nact;  // steps queued after convergence cost only their launches
     apply_normal<R>(a, nr, V + (size_t)j * vstride, V + (size_t)(j + 1) * vstride);
     a->live = nullptr;
+    if (fused) {
+      a->timed(PK_KRYLOV, [&] { launch_arnoldi_fused<R>(c, V, vstride, (int)a->ldv, nr, j, a->st); });
+      check_launch(a);
+      CK(cudaMemcpyAsync(a->h_nact + j, c.nact, sizeof(int), cudaMemcpyDeviceToHost, a->st));
+      CK(cudaEventRecord(a->poll_ev[j], a->st));
+      return;
+    }
     a->timed(PK_KRYLOV, [&] { launch_cgs<R>(c, V, vstride, (int)a->ldv, nr, j, KF_DOTS, a->st); });
     check_launch(a);
     a->timed(PK_KRYLOV, [&] { launch_cgs<R>(c, V, vstride, (int)a->ldv, nr, j, KF_UPDATE | KF_DOTS | KF_ACCUM, a->st); });
@@ -1415,7 +1511,7 @@ void destroy_impl(moma_array *a) {
   DevBuf *bufs[] = {&a->tabs, &a->pairs, &a->slot_of, &a->bin_slot, &a->tri, &a->tri_in, &a->Z128, &a->Z64, &a->Xinv, &a->blk, &a->T, &a->S,
                     &a->Lpk, &a->lat_in, &a->lat_tmp, &a->t1, &a->bx, &a->by, &a->Vk, &a->Iw, &a->Vw,
                     &a->rw, &a->yw, &a->kbuf, &a->errbuf, &a->one_blk, &a->portsb, &a->zp_V, &a->zp_I, &a->zp_Y, &a->zp_tmp,
-                    &a->tcA, &a->tcP, &a->partner, &a->gramA, &a->gramY, &a->lat_u, &a->mZB128,
+                    &a->tcA, &a->tcP, &a->partner, &a->Xblk, &a->gramA, &a->gramY, &a->lat_u, &a->mZB128,
                     &a->mZC128, &a->mZB64, &a->mZC64, &a->mP, &a->mL, &a->mX};
   for (DevBuf *b : bufs) b->release(a->dev_bytes);
   if (a->cs) {
@@ -1469,6 +1565,9 @@ moma_status moma_create_array(int nx, int ny, int b, const moma_options *opt, vo
     a->use_graphs = !(opt && (opt->flags & MOMA_FLAG_NO_GRAPHS));
     a->no_autotune = opt && (opt->flags & MOMA_FLAG_NO_AUTOTUNE);
     a->no_tensor = opt && (opt->flags & MOMA_FLAG_NO_TENSOR);
+    a->axis_fft = opt && (opt->flags & MOMA_FLAG_AXIS_FFT);
+    a->no_blk_precond = opt && (opt->flags & MOMA_FLAG_PRECOND_PER_ELEMENT);
+    a->no_fused_arnoldi = opt && (opt->flags & MOMA_FLAG_SPLIT_ARNOLDI);
     if (opt && (opt->flags & MOMA_FLAG_TENSOR_ALWAYS)) a->tc_min_nr = 1;
     if (a->m > MOMA_MAX_RESTART) throw MomaError(MOMA_ERR_ARG, "restart too large");
     const int mx = (opt && opt->mx > 0) ? opt->mx : next_smooth(2 * nx - 1);
@@ -1962,6 +2061,7 @@ size_t moma_estimate_bytes(int nx, int ny, int b, const moma_options *opt, int n
   const size_t c = 16, esz = prec == MOMA_PREC_FP64 ? 16 : 8;
   size_t bytes = Bp * b * ldb * c + (prec == MOMA_PREC_MIXED ? Bp * b * ldb * 8 : 0);  // stored bins
   bytes += nel * (nt + 2) * esz;                                                        // inverse factors
+  if (prec == MOMA_PREC_MIXED) bytes += nel * xblk_entries(b) * 8;                    // blocked c64 factors
   bytes += B * 16 + nt * 12 + 4096;                                                     // tables
   const size_t nr = (size_t)nrhs, nch = (N + 1023) / 1024;
   bytes += nr * N * c * 6 + nr * ny * Mx * b * c + 2 * B * nr * b * c;                 // solve vectors

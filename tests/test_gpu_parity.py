@@ -374,3 +374,47 @@ def test_host_blocks_read_only_upper_rows(moma_lib, cuda, nx, ny, b, prec):
             m.moma_destroy(h)
     assert np.array_equal(out[0], out[1])
     assert np.array_equal(out[0], out[2])
+
+
+@pytest.mark.parametrize("nx,ny,b,nr", [(1, 1, 16, 1), (2, 1, 18, 2), (5, 3, 32, 3), (7, 5, 24, 2), (6, 6, 48, 5),
+                                         (16, 12, 32, 2), (40, 40, 16, 3), (4, 3, 128, 2), (3, 3, 160, 15)])
+def test_fused_transforms_and_streaming_preconditioner(moma_lib, cuda, nx, ny, b, nr):
+    """The 2D lattice transforms (one launch per transform) and the
+    streaming preconditioner apply against the per-axis passes and the
+    per-element apply (MOMA_FLAG_AXIS_FFT | MOMA_FLAG_PRECOND_PER_ELEMENT),
+    and both against the oracle: Z x, Z^H x, P^{-1} x and P^{-1} Z^H Z x
+    (Sec. III-A), c64, element by element.  (40, 40, 16) has 1600 elements,
+    so every persistent CTA of the streaming apply wraps its copy ring."""
+    m = moma_lib
+    spec = LatticeSpec(nx, ny, b, 0.5, 6)
+    blocks = offset_blocks(spec, np.complex64)
+    b128 = blocks.astype(np.complex128)
+    x = rand_vec(nr, spec, seed=9, dtype=np.complex64)
+    xo = x.astype(np.complex128)
+    p = mbt.precond_blocks(b128, nx, ny)
+    ref = {"z": mbt.matvec(b128, nx, ny, xo), "zh": mbt.matvec_h(b128, nx, ny, xo),
+           "p": mbt.precond_solve(p, xo), "n": mbt.normal_operator(b128, nx, ny, xo, p)}
+    out = {}
+    for name, flags in (("fused", m.MOMA_FLAG_NO_TENSOR),
+                        ("split", m.MOMA_FLAG_NO_TENSOR | m.MOMA_FLAG_AXIS_FFT | m.MOMA_FLAG_PRECOND_PER_ELEMENT)):
+        h = m.moma_create_array(nx, ny, b, MIXED, flags=flags)
+        try:
+            m.moma_set_blocks(h, blocks)
+            res = {}
+            for key, fn in (("z", lambda y: m.moma_matvec(h, 0, x, y)), ("zh", lambda y: m.moma_matvec(h, 1, x, y)),
+                            ("p", lambda y: m.moma_apply_precond(h, x, y)),
+                            ("n", lambda y: m.moma_matvec(h, 2, x, y))):
+                y = np.full_like(x, np.nan)
+                fn(y)
+                res[key] = y.astype(np.complex128)
+            out[name] = res
+        finally:
+            m.moma_destroy(h)
+    for key in ("z", "zh", "p", "n"):
+        scale = np.abs(ref[key]).max()
+        ef = np.abs(out["fused"][key] - ref[key]).max() / scale
+        es = np.abs(out["split"][key] - ref[key]).max() / scale
+        RAW_ERRORS[f"fused_{key} {nx}x{ny}x{b} nr={nr}"] = ef
+        print(f"{key} {nx}x{ny}x{b} nr={nr}: fused {ef:.3g}, per-axis/per-element {es:.3g}")
+        assert np.all(np.isfinite(out["fused"][key]))
+        assert ef <= 1e-5 and es <= 1e-5

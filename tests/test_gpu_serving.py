@@ -92,3 +92,33 @@ def test_server_reports_per_request_errors(moma_lib, cuda):
         assert m.moma_server_wait(s, t, 60.0)["status"] == 0
     finally:
         m.moma_server_destroy(s)
+
+
+def test_alone_equals_mix_at_b128_with_tensor_core_requests(moma_lib, cuda):
+    """Requests shaped like the serving workload (b = 128, 16-32 scan RHS,
+    which take the tensor-core product and preconditioner, plus a few small
+    ones on the CUDA cores), admitted concurrently: every result is bitwise
+    the stand-alone one and matches the dense oracle per port."""
+    m = moma_lib
+    specs = [LatticeSpec(5, 4, 128, 0.45, 0), LatticeSpec(6, 3, 128, 0.62, 0), LatticeSpec(4, 4, 128, 0.33, 0)]
+    blocks = [offset_blocks(s, np.complex64) for s in specs]
+    rng = np.random.default_rng(17)
+    reqs = []
+    for i in range(7):
+        k = i % len(specs)
+        nr = int(rng.integers(16, 33)) if i < 5 else int(rng.integers(1, 4))
+        angles = [(float(rng.uniform(0, 60)), float(rng.uniform(0, 90))) for _ in range(nr)]
+        reqs.append((k, excitation(specs[k], angles)))
+    alone, r_alone, _ = _run(m, specs, blocks, reqs, 1, 0, False)
+    mix, r_mix, st_mix = _run(m, specs, blocks, reqs, 4, 0, True)
+    assert all(r["status"] == 0 for r in r_alone + r_mix), [r["message"] for r in r_alone + r_mix]
+    assert st_mix["completed"] == len(reqs)
+    for (ia, za_a), (im, za_m) in zip(alone, mix):
+        assert np.array_equal(ia, im) and np.array_equal(za_a, za_m)
+    for (k, V), (I, za) in zip(reqs, alone):
+        z = dense.assemble(blocks[k].astype(np.complex128), specs[k].nx, specs[k].ny)
+        assert dense.relative_residual(z, I, V).max() <= 1e-10
+        za_ref = ports.active_impedance(dense.solve(z, V), V)
+        err = np.max(np.abs(za - za_ref) / np.abs(za_ref))
+        print(f"b=128 request {specs[k].nx}x{specs[k].ny}, {V.shape[0]} RHS: max per-port Z_a rel err {err:.3g}")
+        assert err <= 1e-8
