@@ -793,6 +793,16 @@ def main():
                        "achieved": mv_bytes / (mv_us * 1e-6) / 1e9 if mv_us else None, "peak": hbm_peak,
                        "unit": "GB/s", "frac": mv_bytes / (mv_us * 1e-6) / 1e9 / hbm_peak if mv_us else None,
                        "floor_us": mv_bytes / (hbm_peak * 1e9) * 1e6, "peak_source": peak_src}
+    # The block preconditioner apply (Eq. 38 through X_e^H X_e): the packed
+    # c64 factor triangles once plus x in and y out, per launch.
+    n_pre, ms_pre = stats["precond"]
+    pre_bytes = spec.nx * spec.ny * (spec.b * (spec.b + 1) // 2) * 8 + 2 * spec.nx * spec.ny * spec.b * nr * 8
+    pre_us = 1000.0 * ms_pre / n_pre if n_pre else None
+    precond_roofline = {"bound": "hbm", "kernel": "precond_blk_kernel (c64 X_e^H X_e, streaming)",
+                        "alg_bytes_per_launch": pre_bytes, "avg_launch_us": pre_us, "launches": n_pre,
+                        "achieved": pre_bytes / (pre_us * 1e-6) / 1e9 if pre_us else None, "peak": hbm_peak,
+                        "unit": "GB/s", "frac": pre_bytes / (pre_us * 1e-6) / 1e9 / hbm_peak if pre_us else None,
+                        "peak_source": peak_src}
     kernel_share = {k: {"launches": n, "ms": ms} for k, (n, ms) in stats.items()}
     m.moma_destroy(h)
 
@@ -881,7 +891,8 @@ def main():
             "step_ms": {"p50": statistics.median(steps_ms), "p99": float(np.percentile(steps_ms, 99)),
                         "min": min(steps_ms), "max": max(steps_ms)},
             "profiled_ms_per_step": prof_total_ms / args.steps,
-            "phases": phases, "roofline": roofline, "matvec_roofline": matvec_roofline, "kernels": kernel_share,
+            "phases": phases, "roofline": roofline, "matvec_roofline": matvec_roofline,
+            "precond_roofline": precond_roofline, "kernels": kernel_share,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk, "fp64_plain": fp64,
             "mixed_fp64_residual": fp64r, "pcg_mixed": pcg,
             "ports_Za": {k: [f"{z.real:.10f}{z.imag:+.10f}j" for z in v] for k, v in ports.items()},

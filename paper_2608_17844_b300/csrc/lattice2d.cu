@@ -105,6 +105,7 @@ __global__ void __launch_bounds__(512) lattice2d_kernel(L2Args A, const typename
     twy[i] = twy_g[i];
     posy[i] = posy_g[i];
   }
+  __syncthreads();  // the tables are read by every thread from here on
   const C zero = mk(R(0), R(0));
   const long long bins_row = (long long)A.nr * b;  // elements between consecutive bins
   const C *in = reinterpret_cast<const C *>(A.in);

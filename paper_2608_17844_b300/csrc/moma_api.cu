@@ -1230,8 +1230,9 @@ void gmres_cycle(moma_array *a, int nr, const std::vector<int> &act, int *inner_
       volatile int *hn = a->h_nact;
       const auto t0 = std::chrono::steady_clock::now();
       while (hn[j - lag] == -1) {
-        if (cudaStreamQuery(a->st) == cudaSuccess && hn[j - lag] == -1)
-          throw MomaError(MOMA_ERR_CUDA, "poll copy did not arrive");
+        const cudaError_t q = cudaStreamQuery(a->st);
+        if (q != cudaSuccess && q != cudaErrorNotReady) CK(q);  // a device fault: report it now
+        if (q == cudaSuccess && hn[j - lag] == -1) throw MomaError(MOMA_ERR_CUDA, "poll copy did not arrive");
         if (std::chrono::steady_clock::now() - t0 > std::chrono::seconds(60))
           throw MomaError(MOMA_ERR_TIMEOUT, "inner iteration poll timed out");
         std::this_thread::yield();
@@ -1362,8 +1363,9 @@ void pcg_cycle(moma_array *a, int nr, const std::vector<int> &act, int max_inner
       const int ps = (it - lag) % RING;
       const auto t0 = std::chrono::steady_clock::now();
       while (hn[ps] == -1) {
-        if (cudaStreamQuery(a->st) == cudaSuccess && hn[ps] == -1)
-          throw MomaError(MOMA_ERR_CUDA, "poll copy did not arrive");
+        const cudaError_t q = cudaStreamQuery(a->st);
+        if (q != cudaSuccess && q != cudaErrorNotReady) CK(q);  // a device fault: report it now
+        if (q == cudaSuccess && hn[ps] == -1) throw MomaError(MOMA_ERR_CUDA, "poll copy did not arrive");
         if (std::chrono::steady_clock::now() - t0 > std::chrono::seconds(60))
           throw MomaError(MOMA_ERR_TIMEOUT, "inner iteration poll timed out");
         std::this_thread::yield();
