@@ -199,12 +199,12 @@ def measured_traffic(alg_bytes_padded, spec, nr):
     """DRAM bytes per launch of the c64 bin product from the committed ncu
     capture (profiles/bin_pair_kernel_c64_traffic.txt), scaled from the
     captured lattice to this launch by the streamed (padded) bytes; None if
-    the kernel source changed since the capture."""
+    the kernel source the record names changed since the capture."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "bin_pair_kernel_c64_traffic.txt")
-    src = os.path.join(ROOT, "paper_2608_17844_b300", "csrc", "binprod.cu")
     try:
         kv = dict(l.strip().split("=", 1) for l in open(path) if "=" in l and not l.startswith("#"))
+        src = os.path.join(ROOT, kv.get("kernel_source", "paper_2608_17844_b300/csrc/binprod.cu"))
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
     except OSError:
         return None
@@ -868,7 +868,8 @@ def main():
     subs = {}
     if rank == 0 and not args.quick and not (args.lattice or args.nrhs):
         sub_args = argparse.Namespace(**vars(args))
-        for name, fn in (("scan", run_scan), ("ragged", run_ragged), ("serve", run_serving)):
+        for name, fn in (("scan", run_scan), ("ragged", run_ragged), ("serve", run_serving),
+                         ("predictors", run_predictors)):
             try:
                 subs[name] = fn(sub_args, sub=True)
             except Exception as ex:  # a failed sub-measurement is reported, not hidden

@@ -427,6 +427,12 @@ static void launch_nr(const BinProduct &P, int num_sms, cudaStream_t st, int q0)
 
 template <typename R>
 void launch_bin_product(const BinProduct &P, int num_sms, cudaStream_t st) {
+  if constexpr (std::is_same<R, float>::value) {
+    if (bin_rc_supported(P.b) && P.ldb == P.b) {
+      launch_bin_rc(P, num_sms, st);
+      return;
+    }
+  }
   // RHS are processed in chunks of up to NRMAX columns (the kernel masks
   // columns past nr); each chunk streams the bins once.
   constexpr int NRMAX = sizeof(R) == 4 ? 4 : 2;

@@ -1,0 +1,322 @@
+// The c64 per-bin product of Eq. 3 for b a multiple of 32 (64 <= b <= 256):
+// y_ka = Zhat x_ka and y_kb = Zhat^T x_kb from one stored block per pair
+// {k, -k} (reciprocity, Sec. II-D), or conj(Zhat) and conj(Zhat)^T for Z^H
+// (Eq. 6), as in binprod.cu, with a different split of the work that needs
+// no cross-lane reduction trees.
+//
+// A tile is 32 rows of the stored block.  The producer copies each row with
+// its own bulk copy into a stage whose rows are b + 2 complex values apart,
+// so that 16-byte loads are free of bank conflicts both along a row and down
+// a column.  The eight consumer warps read every tile twice, once per leg:
+//  * row warps 0..3 own rows 8w .. 8w+7 of the tile; lane (r, c) = (lane % 8,
+//    lane / 8) takes the column pairs 8i + 2c, i = 0 .. b/8 - 1, of row r, so
+//    the row leg sum_j Zhat_rj x_R,j is finished by adding the four lanes of
+//    the row (two shuffles) and stored once per tile;
+//  * column warps 4..7 own column pairs (lane = pair) and a slice of the
+//    tile's rows, and accumulate the column leg sum_i Zhat_ij x_C,i in
+//    registers over the whole block; the slices are added in a fixed order
+//    once per pair.
+// Every sum has a fixed order (tile height fixed at 32 rows), so results do
+// not depend on the pipeline depth or CTAs per SM that the autotuner picks.
+// Waits are bounded like those of binprod.cu; a timeout sets DEVERR_TIMEOUT,
+// the CTA drains its copies and exits.
+#include <algorithm>
+
+#include "internal.h"
+
+namespace moma {
+
+namespace {
+
+constexpr int RC_TR = 32;
+constexpr int RC_CONS = 8;
+constexpr int RC_THREADS = (RC_CONS + 1) * 32;
+constexpr uint64_t RC_WAIT_NS = 2000000000ull;
+
+struct RcArgs {
+  BinProduct P;
+  int NS, q0, lds;
+};
+
+MOMA_DEV void rc_consumer_bar() { asm volatile("bar.sync 1, %0;" ::"n"(RC_CONS * 32) : "memory"); }
+MOMA_DEV void rc_cp_async8(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+MOMA_DEV void rc_cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+MOMA_DEV void rc_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+MOMA_DEV float2 rc_sum4(float2 v) {  // the four lanes of a row (lane bits 3 and 4)
+  v.x += __shfl_xor_sync(0xffffffffu, v.x, 8);
+  v.y += __shfl_xor_sync(0xffffffffu, v.y, 8);
+  v.x += __shfl_xor_sync(0xffffffffu, v.x, 16);
+  v.y += __shfl_xor_sync(0xffffffffu, v.y, 16);
+  return v;
+}
+
+template <int NR, bool HERM, int MINB>
+__global__ void __launch_bounds__(RC_THREADS, MINB) bin_rc_kernel(RcArgs A) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  const BinProduct &P = A.P;
+  if (P.live && *P.live == 0) return;
+  const int b = P.b, ldb = P.ldb, nr = P.nr, q0 = A.q0, NS = A.NS, lds = A.lds;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  uint64_t *full = reinterpret_cast<uint64_t *>(sm);
+  uint64_t *empty = full + NS;
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(empty + NS);
+  float2 *stage0 = reinterpret_cast<float2 *>(sm + 256);
+  const size_t stage_elems = (size_t)RC_TR * lds;
+  float2 *xbuf = stage0 + NS * stage_elems;      // [2 buffers][R | C][NR][b]
+  float2 *redC = xbuf + (size_t)4 * NR * b;      // [4 column warps][32 lanes][2][NR]
+  const float2 *Z = reinterpret_cast<const float2 *>(P.Z);
+  const float2 *X = reinterpret_cast<const float2 *>(P.x);
+  float2 *Y = reinterpret_cast<float2 *>(P.y);
+  const int ntile = b / RC_TR;
+  const int npair = (P.Bp - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int total = npair * ntile;
+  if (total <= 0) return;
+  if (tid == 0) {
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], RC_CONS);
+    }
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  if (w == RC_CONS) {
+    // ------------------------------------------------------------ producer --
+    if (lane != 0) return;
+    int issued = 0;
+    const uint32_t row_bytes = (uint32_t)(ldb * sizeof(float2));
+    for (int i = 0; i < total; ++i) {
+      const int s = i % NS;
+      const uint32_t par = (uint32_t)(((i / NS) & 1) ^ 1);
+      bool ok = mbar_try_wait(&empty[s], par);
+      if (!ok) {
+        const uint64_t t0 = global_ns();
+        for (uint32_t it = 0; !ok; ++it) {
+          ok = mbar_try_wait(&empty[s], par);
+          if (!ok && (it & 255u) == 255u && (*abort_flag || global_ns() - t0 > RC_WAIT_NS)) break;
+        }
+      }
+      if (!ok) {
+        if (!*abort_flag) atomicOr(P.err, DEVERR_TIMEOUT);
+        *abort_flag = 1;
+        break;
+      }
+      const int pk = i / ntile, t = i % ntile;
+      const long long p = (long long)blockIdx.x + (long long)pk * gridDim.x;
+      const float2 *src = Z + ((size_t)p * b + (size_t)t * RC_TR) * ldb;
+      float2 *dst = stage0 + (size_t)s * stage_elems;
+      fence_proxy_async();
+      mbar_expect_tx(&full[s], row_bytes * RC_TR);
+      for (int rr = 0; rr < RC_TR; ++rr) bulk_g2s(dst + (size_t)rr * lds, src + (size_t)rr * ldb, row_bytes, &full[s]);
+      issued = i + 1;
+    }
+    for (int i = max(0, issued - NS); i < issued; ++i)
+      mbar_wait_bounded(&full[i % NS], (uint32_t)((i / NS) & 1), RC_WAIT_NS);
+    return;
+  }
+
+  // ------------------------------------------------------------ consumers --
+  auto load_x = [&](int pk, int buf) {
+    const int p = (int)blockIdx.x + pk * (int)gridDim.x;
+    const int2 pr = P.pairs[p];
+    const int kR = HERM ? pr.y : pr.x, kC = HERM ? pr.x : pr.y;
+    float2 *xr_s = xbuf + (size_t)buf * 2 * NR * b;
+    float2 *xc_s = xr_s + (size_t)NR * b;
+    for (int idx = tid; idx < NR * b; idx += RC_CONS * 32) {
+      const int qq = idx / b, c = idx % b, q = q0 + qq;
+      if (q < nr) rc_cp_async8(&xr_s[idx], &X[((size_t)kR * nr + q) * b + c]);
+      else xr_s[idx] = make_float2(0.f, 0.f);
+      if (q < nr && pr.x != pr.y) rc_cp_async8(&xc_s[idx], &X[((size_t)kC * nr + q) * b + c]);
+      else xc_s[idx] = make_float2(0.f, 0.f);
+    }
+  };
+  load_x(0, 0);
+  rc_cp_async_wait_all();
+  rc_consumer_bar();
+
+  // Column warps: G groups of 32 column pairs, 4 / G row slices per tile.
+  const int G = (b / 2 + 31) / 32, nslice = 4 / G, rps = RC_TR / nslice;
+  const int kw = w - 4, cgrp = kw % G, slice = kw / G;
+  const bool col_active = w >= 4 && kw < G * nslice;
+  const int cpair = 32 * cgrp + lane, cc = 2 * cpair;
+  const int r8 = lane & 7, c4 = lane >> 3;
+
+  float2 accC[2][NR];
+  int kR = 0, kC = 0;
+  bool selfp = false;
+  const float2 *xr_s = xbuf, *xc_s = xbuf + (size_t)NR * b;
+
+  for (int i = 0; i < total; ++i) {
+    const int pk = i / ntile, t = i % ntile, buf = pk & 1;
+    if (t == 0) {
+      const int p = (int)blockIdx.x + pk * (int)gridDim.x;
+      const int2 pr = P.pairs[p];
+      selfp = pr.x == pr.y;
+      kR = HERM ? pr.y : pr.x;
+      kC = HERM ? pr.x : pr.y;
+      xr_s = xbuf + (size_t)buf * 2 * NR * b;
+      xc_s = xr_s + (size_t)NR * b;
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int qq = 0; qq < NR; ++qq) accC[h][qq] = make_float2(0.f, 0.f);
+      if (pk + 1 < npair) load_x(pk + 1, buf ^ 1);  // overlaps this pair's tiles
+    }
+    const int s = i % NS;
+    bool ok = false;
+    if (!*abort_flag) {
+      const uint32_t par = (uint32_t)((i / NS) & 1);
+      ok = mbar_try_wait(&full[s], par);
+      if (!ok) {
+        const uint64_t t0 = global_ns();
+        for (uint32_t it = 0; !ok; ++it) {
+          ok = mbar_try_wait(&full[s], par);
+          if (!ok && (it & 255u) == 255u && (*abort_flag || global_ns() - t0 > RC_WAIT_NS)) break;
+        }
+        if (!ok && !*abort_flag) {
+          atomicOr(P.err, DEVERR_TIMEOUT);
+          *abort_flag = 1;
+        }
+      }
+    }
+    const float2 *tile = stage0 + (size_t)s * stage_elems;
+    const int r0 = t * RC_TR;
+    if (ok) {
+      if (w < 4) {
+        // Row leg: row rl of the tile, columns 8i + 2 c4 (+1).
+        const int rl = 8 * w + r8;
+        const float2 *zrow = tile + (size_t)rl * lds;
+        float2 acc[NR];
+#pragma unroll
+        for (int qq = 0; qq < NR; ++qq) acc[qq] = make_float2(0.f, 0.f);
+        for (int c = 2 * c4; c < b; c += 8) {
+          const float4 z4 = *reinterpret_cast<const float4 *>(zrow + c);
+          float2 z0 = make_float2(z4.x, z4.y), z1 = make_float2(z4.z, z4.w);
+          if (HERM) {
+            z0.y = -z0.y;
+            z1.y = -z1.y;
+          }
+#pragma unroll
+          for (int qq = 0; qq < NR; ++qq) {
+            acc[qq] = cfma(z0, xr_s[qq * b + c], acc[qq]);
+            acc[qq] = cfma(z1, xr_s[qq * b + c + 1], acc[qq]);
+          }
+        }
+#pragma unroll
+        for (int qq = 0; qq < NR; ++qq) acc[qq] = rc_sum4(acc[qq]);
+        if (c4 == 0)
+#pragma unroll
+          for (int qq = 0; qq < NR; ++qq)
+            if (q0 + qq < nr) Y[((size_t)kR * nr + q0 + qq) * b + r0 + rl] = acc[qq];
+      } else if (col_active && !selfp && cc < b) {
+        // Column leg: column pair cc, rows of this warp's slice.
+        for (int rl = slice * rps; rl < (slice + 1) * rps; ++rl) {
+          const float4 z4 = *reinterpret_cast<const float4 *>(tile + (size_t)rl * lds + cc);
+          float2 z0 = make_float2(z4.x, z4.y), z1 = make_float2(z4.z, z4.w);
+          if (HERM) {
+            z0.y = -z0.y;
+            z1.y = -z1.y;
+          }
+#pragma unroll
+          for (int qq = 0; qq < NR; ++qq) {
+            const float2 xc = xc_s[qq * b + r0 + rl];
+            accC[0][qq] = cfma(z0, xc, accC[0][qq]);
+            accC[1][qq] = cfma(z1, xc, accC[1][qq]);
+          }
+        }
+      }
+    }
+    __syncwarp();
+    if (lane == 0) rc_arrive(&empty[s]);
+
+    if (t == ntile - 1) {
+      if (col_active && !selfp && cc < b)
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int qq = 0; qq < NR; ++qq) redC[(((size_t)kw * 32 + lane) * 2 + h) * NR + qq] = accC[h][qq];
+      rc_cp_async_wait_all();  // this thread's prefetch of the next pair's x has landed
+      rc_consumer_bar();       // redC complete; orders the prefetch before its use
+      if (col_active && slice == 0 && !selfp && cc < b && !*abort_flag) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int qq = 0; qq < NR; ++qq) {
+            float2 v = make_float2(0.f, 0.f);
+            for (int sl = 0; sl < nslice; ++sl) {
+              const float2 u = redC[((((size_t)(sl * G + cgrp)) * 32 + lane) * 2 + h) * NR + qq];
+              v.x += u.x;
+              v.y += u.y;
+            }
+            if (q0 + qq < nr) Y[((size_t)kC * nr + q0 + qq) * b + cc + h] = v;
+          }
+      }
+      rc_consumer_bar();  // redC may be rewritten by the next pair
+    }
+  }
+}
+
+size_t rc_smem(int b, int NR, int NS) {
+  return 256 + (size_t)NS * RC_TR * (b + 2) * sizeof(float2) + (size_t)4 * NR * b * sizeof(float2) +
+         (size_t)4 * 32 * 2 * NR * sizeof(float2);
+}
+
+template <int NR, bool HERM>
+void rc_launch(const BinProduct &P, int num_sms, cudaStream_t st, int q0) {
+  int occ = P.occ == 2 ? 2 : 1;
+  const size_t cap = occ == 2 ? 110 * 1024 : 225 * 1024;
+  int NS = (P.NS >= 2 && P.NS <= 6) ? P.NS : 4;
+  while (NS > 2 && rc_smem(P.b, NR, NS) > cap) --NS;
+  if (rc_smem(P.b, NR, NS) > cap) {  // two CTAs do not fit: one CTA per SM
+    occ = 1;
+    NS = std::min(NS, 3);
+    while (NS > 2 && rc_smem(P.b, NR, NS) > 225 * 1024) --NS;
+  }
+  const size_t smem = rc_smem(P.b, NR, NS);
+  int grid = num_sms * occ;
+  if (grid > P.Bp) grid = P.Bp;
+  RcArgs a{P, NS, q0, P.b + 2};
+  if (occ == 2) {
+    auto kern = bin_rc_kernel<NR, HERM, 2>;
+    static int configured = 0;
+    if (!configured) {
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 112 * 1024);
+      configured = 1;
+    }
+    kern<<<grid, RC_THREADS, smem, st>>>(a);
+  } else {
+    auto kern = bin_rc_kernel<NR, HERM, 1>;
+    static int configured = 0;
+    if (!configured) {
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+      configured = 1;
+    }
+    kern<<<grid, RC_THREADS, smem, st>>>(a);
+  }
+}
+
+template <int NR>
+void rc_launch_h(const BinProduct &P, int num_sms, cudaStream_t st, int q0) {
+  if (P.herm) rc_launch<NR, true>(P, num_sms, st, q0);
+  else rc_launch<NR, false>(P, num_sms, st, q0);
+}
+
+}  // namespace
+
+bool bin_rc_supported(int b) { return b % 32 == 0 && b >= 64 && b <= 256; }
+
+void launch_bin_rc(const BinProduct &P, int num_sms, cudaStream_t st) {
+  for (int q0 = 0; q0 < P.nr; q0 += 4) {
+    const int left = P.nr - q0;
+    if (left == 1) rc_launch_h<1>(P, num_sms, st, q0);
+    else if (left == 2) rc_launch_h<2>(P, num_sms, st, q0);
+    else rc_launch_h<4>(P, num_sms, st, q0);
+  }
+}
+
+}  // namespace moma

@@ -92,6 +92,10 @@ struct BinProduct {
 };
 template <typename R>
 void launch_bin_product(const BinProduct &p, int num_sms, cudaStream_t st);
+// The c64 product for b = 64, 96, ..., 256 with row and column warps
+// (binprod_rc.cu); launch_bin_product<float> takes it for those sizes.
+bool bin_rc_supported(int b);
+void launch_bin_rc(const BinProduct &p, int num_sms, cudaStream_t st);
 
 // Tensor-core products (tcgen05, 3xTF32) for many right-hand sides.  A
 // TcMats holds T complex b x b matrices, each split into exact TF32 pairs

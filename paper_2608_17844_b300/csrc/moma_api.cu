@@ -1008,14 +1008,19 @@ void autotune_precision(moma_array *a, int nr, int in128) {
   {
     float best = 1e30f;
     int btr = 0, bns = 0, bocc = 1;
+    // The c64 row/column-warp kernel (b = 64 .. 256, multiple of 32) has a
+    // fixed 32-row tile: only its pipeline depth and CTAs per SM are tuned.
+    const bool rc = std::is_same<R, float>::value && bin_rc_supported(a->b) && a->ldb == a->b;
     for (int occ : {1, 2, 3}) {
       // The multi-CTA variants' domain: at most two RHS, b <= 128; three CTAs for c64 only.
       if (occ > 1 && (nr > 2 || a->b > 128)) continue;
-      if (occ == 3 && is64<R>()) continue;
+      if (occ == 3 && (is64<R>() || rc)) continue;
       for (int tr : {8, 16, 24, 32}) {
         if (tr > ((a->b + 3) & ~3) && tr != 16) continue;
         if (occ == 1 && tr < 16) continue;
-        for (int ns : {2, 3, 4}) {
+        if (rc && tr != 32) continue;
+        for (int ns : {2, 3, 4, 6}) {
+          if (!rc && ns == 6) continue;
           BinProduct P;
           P.Z = is64<R>() ? a->Z128.p : a->Z64.p;
           P.pairs = a->pairs.as<int2>();

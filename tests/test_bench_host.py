@@ -48,17 +48,25 @@ def test_c2_bin_product_bytes_value():
 
 
 def test_measured_traffic_follows_the_capture_and_its_source_hash(tmp_path, monkeypatch):
+    """The traffic record scales to a launch by streamed bytes while the
+    kernel source it names is unchanged, and is withdrawn (None) after."""
+    import hashlib
     spec = LatticeSpec(32, 32, 128, 0.5, 0)
     alg = bench.bin_product_bytes(spec, 2, padded=True)[0]
-    t = bench.measured_traffic(alg, spec, 2)
-    assert t is not None and 0.99 * alg <= t <= 1.05 * alg  # the capture read each stored bin once
-    # A copy of the tree whose kernel source differs from the captured one.
     (tmp_path / "profiles").mkdir()
-    (tmp_path / "paper_2608_17844_b300" / "csrc").mkdir(parents=True)
+    src = tmp_path / "paper_2608_17844_b300" / "csrc" / "kernel.cu"
+    src.parent.mkdir(parents=True)
+    src.write_text("// the captured kernel\n")
+    sha = hashlib.sha256(src.read_bytes()).hexdigest()
+    # a 24 x 24 capture that read each stored bin once plus 0.2 % extra
+    cap_alg = 1154 * 128 * 128 * 8 + 2 * 2304 * 2 * 128 * 8
     (tmp_path / "profiles" / "bin_pair_kernel_c64_traffic.txt").write_text(
-        open(os.path.join(bench.ROOT, "profiles", "bin_pair_kernel_c64_traffic.txt")).read())
-    (tmp_path / "paper_2608_17844_b300" / "csrc" / "binprod.cu").write_text("// changed\n")
+        f"kernel_source=paper_2608_17844_b300/csrc/kernel.cu\nkernel_source_sha256={sha}\npairs=1154\nbins=2304\n"
+        f"nrhs=2\nb=128\ndram_read_bytes={int(cap_alg * 1.002)}\ndram_write_bytes=0\n")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    t = bench.measured_traffic(alg, spec, 2)
+    assert t == pytest.approx(1.002 * alg, rel=1e-6)
+    src.write_text("// changed\n")
     assert bench.measured_traffic(alg, spec, 2) is None
 
 

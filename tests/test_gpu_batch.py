@@ -74,8 +74,10 @@ def test_autotuner_reports_choices(moma_lib, cuda):
             I = np.zeros_like(V)
             m.moma_solve(x, V, I)
         rep = m.moma_tuning_report(h)
-        # inner passes in c64, the refinement residual's in double-FP32 pairs
-        assert "bin_product<c64>" in rep and "IxMaskFx<c64>" in rep and "Fx<dfl>" in rep and "bin_product<dfl>" in rep
+        # inner product and 2D lattice transforms in c64; the refinement
+        # residual's per-axis passes and product in double-FP32 pairs
+        assert "bin_product<c64>" in rep and "bin_product<dfl>" in rep and "Fx<dfl>" in rep
+        assert all(f"{t}<c64>" in rep for t in ("F2", "I2", "I2MF2")), rep
         assert m.moma_tuning_report(h2) == ""
     finally:
         m.moma_destroy(h)
