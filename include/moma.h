@@ -82,7 +82,10 @@ typedef struct moma_array moma_array; /* opaque; owns all device state */
 
 enum {
     MOMA_FLAG_NO_GRAPHS = 1,     /* launch the inner steps directly instead of replaying CUDA graphs */
-    MOMA_FLAG_NO_AUTOTUNE = 2,   /* use the built-in launch-shape heuristics */
+    MOMA_FLAG_NO_AUTOTUNE = 2,   /* no launch-shape timing trials: shapes tuned earlier in this
+                                    process for the same device, lattice, b, precision and RHS
+                                    count, else the built-in heuristics (arrays of the serving
+                                    loop are created this way); shapes never change results */
     MOMA_FLAG_NO_TENSOR = 4,     /* no tensor-core path: c64 bin products, preconditioner apply
                                     and (set-up) Gram products on the CUDA cores */
     MOMA_FLAG_TENSOR_ALWAYS = 8, /* c64 bin products on the tensor cores from one RHS up

@@ -8,6 +8,7 @@
 #include <memory>
 #include <type_traits>
 #include <thread>
+#include <tuple>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -1089,8 +1090,30 @@ void autotune_precision(moma_array *a, int nr, int in128) {
   }
 }
 
+// Process-wide cache of tuned launch shapes.  The shapes depend only on the
+// device, the lattice and circulant sizes, b, the precision and the RHS
+// count (never on the blocks' values, and they never change a result), so
+// an array of a shape tuned before in this process takes them without
+// timing trials -- the serving loop's arrays, which skip the trials, and
+// ragged batches of repeated shapes.
+struct TuneKey {
+  int dev, nx, ny, b, Mx, My, nr, prec, df, axis_fft;
+  long long ldv;
+  bool operator<(const TuneKey &o) const {
+    return std::tie(dev, nx, ny, b, Mx, My, nr, prec, df, axis_fft, ldv) <
+           std::tie(o.dev, o.nx, o.ny, o.b, o.Mx, o.My, o.nr, o.prec, o.df, o.axis_fft, o.ldv);
+  }
+};
+struct TuneEntry {
+  moma_array::TuneBin bin;
+  std::vector<std::pair<long long, int>> axis;
+  std::vector<std::pair<long long, int2>> l2d;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneEntry> g_tune_cache;
+
 void autotune(moma_array *a, int nr) {
-  if (a->tuned_nr == nr || a->no_autotune || std::getenv("MOMA_NO_AUTOTUNE")) return;
+  if (a->tuned_nr == nr) return;
   auto it = a->tune_by_nr.find(nr);
   if (it != a->tune_by_nr.end()) {  // tuned before for this RHS count
     for (int k = 0; k < 2; ++k) {
@@ -1101,10 +1124,31 @@ void autotune(moma_array *a, int nr) {
     a->tuned_nr = nr;
     return;
   }
+  const TuneKey key{a->dev, a->nx, a->ny, a->b, a->Mx, a->My, nr, a->prec, a->df ? 1 : 0, a->axis_fft ? 1 : 0,
+                    a->ldv};
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto f = g_tune_cache.find(key);
+    if (f != g_tune_cache.end()) {  // tuned before in this process for this shape
+      for (int k = 0; k < 2; ++k) {
+        a->tune_bin_tr[k] = f->second.bin.tr[k];
+        a->tune_bin_ns[k] = f->second.bin.ns[k];
+        a->tune_bin_occ[k] = f->second.bin.occ[k];
+      }
+      a->tune_axis.insert(a->tune_axis.end(), f->second.axis.begin(), f->second.axis.end());
+      a->tune_l2d.insert(a->tune_l2d.end(), f->second.l2d.begin(), f->second.l2d.end());
+      a->tune_by_nr[nr] = f->second.bin;
+      a->tuned_nr = nr;
+      a->tune_log += "nr=" + std::to_string(nr) + ": shapes from the process-wide cache\n";
+      return;
+    }
+  }
+  if (a->no_autotune || std::getenv("MOMA_NO_AUTOTUNE")) return;
   // FFT pass shapes accumulate in tune_axis (their signatures include the
   // RHS count); the bin-product shapes are kept per RHS count.
   a->tune_bin_tr[0] = a->tune_bin_tr[1] = a->tune_bin_ns[0] = a->tune_bin_ns[1] = 0;
   a->tune_bin_occ[0] = a->tune_bin_occ[1] = 1;
+  const size_t n_axis0 = a->tune_axis.size(), n_l2d0 = a->tune_l2d.size();
   if (a->prec == MOMA_PREC_MIXED) autotune_precision<float>(a, nr, 0);
   // The FP64-class residual runs in double-FP32 pairs in the default mixed
   // path, in FP64 otherwise.
@@ -1118,6 +1162,12 @@ void autotune(moma_array *a, int nr) {
   }
   a->tune_by_nr[nr] = t;
   a->tuned_nr = nr;
+  TuneEntry e;
+  e.bin = t;
+  e.axis.assign(a->tune_axis.begin() + n_axis0, a->tune_axis.end());
+  e.l2d.assign(a->tune_l2d.begin() + n_l2d0, a->tune_l2d.end());
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune_cache.emplace(key, std::move(e));
 }
 
 template <typename R>

@@ -67,10 +67,14 @@ struct moma_server {
 
 namespace {
 
+// Arrays of the serving loop skip the launch-shape timing trials (tens of
+// milliseconds for an array seen once); they take shapes tuned before in
+// this process for the same shape, else the built-in heuristics.
 moma_options array_opts(const moma_server *s) {
   moma_options o{};
   o.precision = s->o.precision;
   o.restart = s->o.restart;
+  o.flags = MOMA_FLAG_NO_AUTOTUNE;
   return o;
 }
 

@@ -78,10 +78,37 @@ def test_autotuner_reports_choices(moma_lib, cuda):
         # residual's per-axis passes and product in double-FP32 pairs
         assert "bin_product<c64>" in rep and "bin_product<dfl>" in rep and "Fx<dfl>" in rep
         assert all(f"{t}<c64>" in rep for t in ("F2", "I2", "I2MF2")), rep
-        assert m.moma_tuning_report(h2) == ""
+        # No timing trials without autotuning: the array takes the shapes the
+        # first one tuned (process-wide cache for the same shape) or heuristics.
+        rep2 = m.moma_tuning_report(h2)
+        assert "bin_product" not in rep2 and "F2<" not in rep2
     finally:
         m.moma_destroy(h)
         m.moma_destroy(h2)
+
+
+def test_tuned_shapes_are_shared_across_arrays_of_a_shape(moma_lib, cuda):
+    """A second array of the same shape and RHS count takes the first one's
+    tuned launch shapes from the process-wide cache (no timing trials), and
+    its solution is bitwise the first one's."""
+    m = moma_lib
+    spec = LatticeSpec(9, 7, 24, 0.45, 2)
+    blocks = offset_blocks(spec, np.complex64)
+    V = excitation(spec, [(0, 0), (20, 70), (45, 10)])
+    out, reps = [], []
+    for flags in (0, 0, m.MOMA_FLAG_NO_AUTOTUNE):
+        h = m.moma_create_array(spec.nx, spec.ny, spec.b, flags=flags)
+        try:
+            m.moma_set_blocks(h, blocks)
+            I = np.zeros_like(V)
+            m.moma_solve(h, V, I)
+            out.append(I)
+            reps.append(m.moma_tuning_report(h))
+        finally:
+            m.moma_destroy(h)
+    assert all("process-wide cache" in r for r in reps[1:]), reps
+    assert all("bin_product" not in r for r in reps[1:])
+    assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[2])
 
 
 @pytest.mark.parametrize("prec", [0, 1])
