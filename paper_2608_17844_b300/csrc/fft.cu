@@ -222,6 +222,12 @@ static void launch_typed(const AxisPass &p, const FftTables &t, cudaStream_t st)
 template <typename R>
 void launch_axis_pass(const AxisPass &p, const FftTables &t, cudaStream_t st) {
   if (p.ninner <= 0 || p.n1 * p.n2 <= 0) return;
+  if constexpr (std::is_same<R, float>::value) {
+    if (axis_reg_supported(p, t.plan.M) && (int)t.tw32_host.size() == t.plan.M) {
+      launch_axis_reg(p, t, st);
+      return;
+    }
+  }
   const int io = p.in_c128 * 3 + p.out_c128;
   if constexpr (std::is_same<R, dfl>::value) {
     switch (io) {

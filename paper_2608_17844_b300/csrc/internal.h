@@ -20,6 +20,7 @@ struct FftTables {
   float2 *tw32 = nullptr;   // [M]
   dfl2 *twdf = nullptr;     // [M] twiddles as double-FP32 pairs
   int *pos = nullptr;       // [M]
+  std::vector<float2> tw32_host;  // host copy of tw32 (kernel-parameter twiddles of fftreg.cu)
 };
 
 FftPlan make_plan(int M);
@@ -54,9 +55,13 @@ struct AxisPass {
   int G = 0;                       // threads per line (0 = heuristic; set by the autotuner)
 };
 
-// Launch one axis pass computing in precision R (float or double).
+// Launch one axis pass computing in precision R (float or double).  Plain
+// c64 passes of length M <= 64 run on the register-resident kernels of
+// fftreg.cu (one thread per line).
 template <typename R>
 void launch_axis_pass(const AxisPass &p, const FftTables &t, cudaStream_t st);
+bool axis_reg_supported(const AxisPass &p, int M);
+void launch_axis_reg(const AxisPass &p, const FftTables &t, cudaStream_t st);
 
 // Two-dimensional lattice transforms in one launch (lattice2d.cu): mode 0
 // F2 lattice -> bins, 1 I2 bins -> lattice, 2 I2MF2 bins -> bins (inverse,

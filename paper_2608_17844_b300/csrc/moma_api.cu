@@ -319,6 +319,7 @@ void build_tables(moma_array *a) {
       tdf[t].y = dfl(t64[t].y);
       ps[t] = (*pp[d])[t];
     }
+    tt[d]->tw32_host.assign(t32, t32 + M);
   }
   CK(cudaMemcpy(a->tabs.p, host.data(), bytes, cudaMemcpyHostToDevice));
 
@@ -528,7 +529,16 @@ void precond(moma_array *a, int nr, const void *x, void *y) {
 // FP64 products; the double-FP32 residual path keeps the per-axis passes.
 template <typename R> bool use_l2d(const moma_array *a) {
   if constexpr (std::is_same<R, dfl>::value) return false;
-  else return !a->axis_fft && lattice2d_fits<R>(a->Mx, a->My, 1);
+  else {
+    // c64 grids whose axes both fit the register-resident line kernels run
+    // as per-axis passes on those; the 2D kernels serve the rest.
+    if (std::is_same<R, float>::value && a->Mx <= 64 && a->My <= 64) {
+      AxisPass probe;
+      probe.in_c128 = probe.out_c128 = 0;
+      if (axis_reg_supported(probe, a->Mx) && axis_reg_supported(probe, a->My)) return false;
+    }
+    return !a->axis_fft && lattice2d_fits<R>(a->Mx, a->My, 1);
+  }
 }
 
 long long l2d_sig(int mode, int nr, int is64v) { return ((long long)mode * 1000003LL + nr) * 4 + is64v; }
@@ -1074,6 +1084,7 @@ void autotune_precision(moma_array *a, int nr, int in128) {
       {pass_ix(a, nr, a->t1.p, a->lat_tmp.p, c, false, lat_code<R>()), &a->fx, "Ix"},
   };
   for (const Cand &cd : cands) {
+    if (std::is_same<R, float>::value && axis_reg_supported(cd.p, cd.t->plan.M)) continue;  // no launch shape to tune
     float best = 1e30f;
     int bg = 0;
     for (int G : {1, 2, 4, 8, 16, 32}) {
