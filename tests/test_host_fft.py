@@ -17,7 +17,8 @@ def exe():
     os.makedirs(os.path.dirname(EXE), exist_ok=True)
     nvcc = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "bin", "nvcc")
     cmd = [nvcc, "-std=c++17", "-O1", "-I", CSRC, "-I", os.path.join(ROOT, "include"),
-           os.path.join(ROOT, "tests", "native", "fft_host_check.cu"), os.path.join(CSRC, "fft.cu"), "-o", EXE,
+           os.path.join(ROOT, "tests", "native", "fft_host_check.cu"), os.path.join(CSRC, "fft.cu"),
+           os.path.join(CSRC, "fftreg.cu"), "--expt-relaxed-constexpr", "-o", EXE,
            "-gencode", "arch=compute_103a,code=sm_103a"]
     subprocess.run(cmd, check=True, capture_output=True)
     return EXE
