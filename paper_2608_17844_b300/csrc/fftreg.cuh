@@ -4,6 +4,8 @@
 // in fft.cu, computed as constant expressions so that every register index
 // is known at compile time.
 #pragma once
+#include <utility>
+
 #include "fft.cuh"
 
 namespace moma {
@@ -67,13 +69,23 @@ MOMA_HD void rg_dit(float2 (&v)[M], const float2 *tw) {
   }
 }
 
+// Digit-reversed position of point N as a template constant, so that the
+// scatter below indexes registers with true compile-time constants.
+template <int M, int N>
+struct RgPos {
+  static constexpr int value = rg_pos(M, N);
+};
+template <int M, int... N>
+MOMA_HD void rg_scatter(float2 (&u)[M], const float2 (&v)[M], std::integer_sequence<int, N...>) {
+  ((u[RgPos<M, N>::value] = v[N]), ...);
+}
+
 // v (natural order) -> DFT of v in natural order.  The input is first moved
 // to its digit-reversed positions (a register renaming).
 template <int M>
 MOMA_HD void rg_fft(float2 (&v)[M], const float2 *tw) {
   float2 u[M];
-#pragma unroll
-  for (int n = 0; n < M; ++n) u[rg_pos(M, n)] = v[n];
+  rg_scatter<M>(u, v, std::make_integer_sequence<int, M>{});
   rg_dit<M, rg_nst(M) - 1>(u, tw);
 #pragma unroll
   for (int n = 0; n < M; ++n) v[n] = u[n];

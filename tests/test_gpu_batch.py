@@ -74,10 +74,10 @@ def test_autotuner_reports_choices(moma_lib, cuda):
             I = np.zeros_like(V)
             m.moma_solve(x, V, I)
         rep = m.moma_tuning_report(h)
-        # inner product and 2D lattice transforms in c64; the refinement
-        # residual's per-axis passes and product in double-FP32 pairs
-        assert "bin_product<c64>" in rep and "bin_product<dfl>" in rep and "Fx<dfl>" in rep
-        assert all(f"{t}<c64>" in rep for t in ("F2", "I2", "I2MF2")), rep
+        # inner product in c64 (its lattice passes are register-resident:
+        # no launch shape to tune); the refinement residual's per-axis
+        # passes and product in double-FP32 pairs
+        assert "bin_product<c64>" in rep and "bin_product<dfl>" in rep and "Fx<dfl>" in rep, rep
         # No timing trials without autotuning: the array takes the shapes the
         # first one tuned (process-wide cache for the same shape) or heuristics.
         rep2 = m.moma_tuning_report(h2)
