@@ -351,6 +351,21 @@ moma_status moma_xi_s(int nx, int ny, double s_cc_re, double s_cc_im, double s1_
 moma_status moma_profile(moma_array *a, int enable);
 moma_status moma_kernel_stats(moma_array *a, int kernel, long long *launches, double *total_ms);
 
+/* Device time of one operator application, measured back to back (runtime
+ * instrumentation, no counterpart in the paper).  The operator is enqueued
+ * `reps` times on the array's stream between two CUDA events, after one
+ * untimed application, on the solver's own workspace (contents irrelevant:
+ * no kernel's run time depends on the values), so the figure is device
+ * execution time without per-launch event overhead.  what:
+ *   MOMA_TIME_Z       one c64 Z application: lattice FFT passes + bin product (Eq. 3)
+ *   MOMA_TIME_BIN     the c64 per-bin product alone
+ *   MOMA_TIME_PRECOND the c64 preconditioner apply P^{-1} (Eq. 38)
+ *   MOMA_TIME_NORMAL  the c64 normal operator P^{-1} Z^H Z (Sec. III-A)
+ * MIXED arrays after set_blocks; nrhs RHS (the kernels the solve would
+ * take for that many RHS).  Writes microseconds per application. */
+enum { MOMA_TIME_Z = 0, MOMA_TIME_BIN = 1, MOMA_TIME_PRECOND = 2, MOMA_TIME_NORMAL = 3 };
+moma_status moma_time_operator(moma_array *a, int what, int nrhs, int reps, double *us_per_application);
+
 /* Rebind the array to another CUDA stream (the old stream is synchronised
  * first).  Lets a pool of workers reuse resident arrays on their streams.
  * Runtime plumbing, no counterpart in the paper. */

@@ -422,9 +422,16 @@ __global__ void tc_split_bins_kernel(const float2 *Z, int b, int ldb, const int2
 }
 
 // Elementwise split of T whole c64 b x b matrices (row-major) into hi / lo.
-__global__ void tc_split_plain_kernel(const float2 *Z, size_t n, float *hi, float *lo) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    put_split(hi, lo, i, Z[i]);
+// Also the finiteness check of the blocks it reads (err: DEVERR_NONFINITE),
+// so that the set-up does not read the blocks once more just for it.
+__global__ void tc_split_plain_kernel(const float2 *Z, size_t n, float *hi, float *lo, unsigned *err) {
+  bool bad = false;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float2 v = Z[i];
+    bad |= !isfinite(v.x) || !isfinite(v.y);
+    put_split(hi, lo, i, v);
+  }
+  if (err && __syncthreads_or(bad) && threadIdx.x == 0) atomicOr(err, DEVERR_NONFINITE);
 }
 
 // Full X_e = L_e^{-1} (zero above the diagonal) from the packed column-major
@@ -563,11 +570,11 @@ void tc_split_bins(TcMats &m, const void *Z64, int ldb, const int2 *bin_slot, cu
   encode_maps(m);
 }
 
-void tc_split_plain(TcMats &m, const void *Z64, cudaStream_t st) {
+void tc_split_plain(TcMats &m, const void *Z64, cudaStream_t st, unsigned *err) {
   const size_t n = (size_t)m.T * m.b * m.b;
   size_t g = (n + 255) / 256;
   if (g > 16384) g = 16384;
-  tc_split_plain_kernel<<<(int)g, 256, 0, st>>>(static_cast<const float2 *>(Z64), n, m.hi, m.lo);
+  tc_split_plain_kernel<<<(int)g, 256, 0, st>>>(static_cast<const float2 *>(Z64), n, m.hi, m.lo, err);
   encode_maps(m);
 }
 

@@ -125,8 +125,9 @@ bool tc_supported(int b);
 size_t tc_bytes(int T, int b);  // hi + lo
 // Every bin's full block from the pair storage (transposed for the partner).
 void tc_split_bins(TcMats &m, const void *Z64, int ldb, const int2 *bin_slot, cudaStream_t st);
-// T whole row-major c64 matrices (e.g. offset blocks), split elementwise.
-void tc_split_plain(TcMats &m, const void *Z64, cudaStream_t st);
+// T whole row-major c64 matrices (e.g. offset blocks), split elementwise;
+// err (if set) receives DEVERR_NONFINITE for a non-finite input value.
+void tc_split_plain(TcMats &m, const void *Z64, cudaStream_t st, unsigned *err = nullptr);
 // X_e and X_e^H from the packed inverse factors (c64).
 void tc_split_factor(TcMats &X, TcMats &XH, const void *Xpk, size_t x_stride, cudaStream_t st);
 void launch_tc_product(const TcMats &m, const TcProduct &P, int num_sms, cudaStream_t st);

@@ -915,7 +915,7 @@ void set_blocks_impl(moma_array *a, const void *blocks, int dtype) {
       P.x_ts = P.y_ts = bb; P.x_rs = P.y_rs = a->b; P.nr = a->b; P.conj = 1; P.err = a->err;
       a->timed(PK_GRAM, [&] {
         try {
-          tc_split_plain(mA, zb, a->st);
+          tc_split_plain(mA, zb, a->st, a->err);
           check_launch(a);
           launch_tc_product(mA, P, a->num_sms, a->st);
         } catch (const std::runtime_error &e) {
@@ -932,7 +932,7 @@ void set_blocks_impl(moma_array *a, const void *blocks, int dtype) {
   const int nrows = ndy - r0;
   // Gram products on the tensor cores (3xTF32) for c64 blocks in the mixed
   // path when the block size suits the MMA kernel.
-  a->tgram = df && dtype == MOMA_C64 && !a->no_tensor && tc_supported(a->b);
+  a->tgram = a->prec == MOMA_PREC_MIXED && dtype == MOMA_C64 && !a->no_tensor && tc_supported(a->b);
   if (a->tgram) {
     a->gramA.ensure(tc_bytes(nD, a->b), a->dev_bytes);
     a->gramY.ensure((size_t)nD * bb * sizeof(float2), a->dev_bytes);
@@ -947,7 +947,9 @@ void set_blocks_impl(moma_array *a, const void *blocks, int dtype) {
       CK(cudaEventRecord(a->ev_chunk[c], a->cs));
       CK(cudaStreamWaitEvent(a->st, a->ev_chunk[c], 0));
     }
-    check_finite(a, dst, (size_t)(y1 - y0) * ndx * bb * 2, dtype == MOMA_C128);
+    // The tensor-core Gram split reads every block of these rows and checks
+    // them itself; otherwise a separate pass does.
+    if (!a->tgram) check_finite(a, dst, (size_t)(y1 - y0) * ndx * bb * 2, dtype == MOMA_C128);
     rows_work(y0, y1);
     if (host) {
       // Mirror rows of [y0, y1) below dy = 0: [2Ny-1-y1, 2Ny-1-y0) within [0, yh).
@@ -2085,6 +2087,45 @@ moma_status moma_kernel_stats(moma_array *a, int kernel, long long *launches, do
     a->flush_events();
     if (launches) *launches = a->st_launch[kernel];
     if (total_ms) *total_ms = a->st_ms[kernel];
+  });
+}
+
+moma_status moma_time_operator(moma_array *a, int what, int nrhs, int reps, double *us) {
+  if (!a) { g_last_error = "array is NULL"; return MOMA_ERR_ARG; }
+  return guarded([&] {
+    if (!a->have_blocks) throw MomaError(MOMA_ERR_STATE, "set_blocks must precede moma_time_operator");
+    if (a->prec != MOMA_PREC_MIXED) throw MomaError(MOMA_ERR_ARG, "c64 operators need a MIXED array");
+    if (what < MOMA_TIME_Z || what > MOMA_TIME_NORMAL || nrhs < 1 || reps < 1 || !us)
+      throw MomaError(MOMA_ERR_ARG, "bad what, nrhs, reps or output");
+    ensure_ws(a, nrhs);
+    ensure_tc(a, nrhs);
+    autotune(a, nrhs);
+    CK(cudaMemsetAsync(a->Vw.p, 0, (size_t)nrhs * a->ldv * sizeof(float2), a->st));
+    auto once = [&] {
+      switch (what) {
+        case MOMA_TIME_Z: apply_z<float>(a, nrhs, a->Vw.p, a->yw.p, 0); break;
+        case MOMA_TIME_BIN: binprod<float>(a, nrhs, a->bx.p, a->by.p, 0); break;
+        case MOMA_TIME_PRECOND: precond<float>(a, nrhs, a->Vw.p, a->yw.p); break;
+        default: apply_normal<float>(a, nrhs, a->Vw.p, a->yw.p); break;
+      }
+    };
+    const bool prof = a->prof;
+    a->prof = false;
+    once();
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaEventRecord(e0, a->st));
+    for (int r = 0; r < reps; ++r) once();
+    CK(cudaEventRecord(e1, a->st));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    a->prof = prof;
+    sync_and_check(a);
+    *us = 1000.0 * ms / reps;
   });
 }
 

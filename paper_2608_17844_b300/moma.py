@@ -36,6 +36,7 @@ EXPORTS = [
     "moma_set_blocks_batch", "moma_solve_batch", "moma_port_impedance",
     "moma_column_coupling", "moma_s_to_z", "moma_s_ideal", "moma_xi_z", "moma_xi_s", "moma_set_margin",
     "moma_server_create", "moma_server_submit", "moma_server_wait", "moma_server_get_stats", "moma_server_destroy",
+    "moma_time_operator",
 ]
 
 
@@ -55,6 +56,7 @@ class moma_options(ctypes.Structure):
 
 
 MOMA_SOLVER_GMRES, MOMA_SOLVER_PCG = 0, 1
+MOMA_TIME_Z, MOMA_TIME_BIN, MOMA_TIME_PRECOND, MOMA_TIME_NORMAL = 0, 1, 2, 3
 
 
 class moma_solve_opts(ctypes.Structure):
@@ -137,6 +139,7 @@ def lib():
                                    ctypes.POINTER(moma_solve_opts), ctypes.POINTER(moma_solve_info), i,
                                    ctypes.POINTER(i)]
     L.moma_release_setup.argtypes = [vp]
+    L.moma_time_operator.argtypes = [vp, i, i, i, ctypes.POINTER(ctypes.c_double)]
     L.moma_estimate_bytes.argtypes = [i, i, i, ctypes.POINTER(moma_options), i, i]
     L.moma_estimate_bytes.restype = ctypes.c_size_t
     L.moma_server_create.argtypes = [ctypes.POINTER(moma_server_opts), ctypes.POINTER(vp)]
@@ -311,6 +314,13 @@ def moma_last_error():
 
 def moma_set_stream(h, stream):
     _check(lib().moma_set_stream(h, _stream_handle(stream)))
+
+
+def moma_time_operator(h, what, nrhs, reps=20):
+    """Microseconds per back-to-back application of a c64 operator (MOMA_TIME_*)."""
+    us = ctypes.c_double()
+    _check(lib().moma_time_operator(h, what, nrhs, reps, ctypes.byref(us)))
+    return us.value
 
 
 def moma_release_setup(h):
