@@ -193,7 +193,7 @@ MOMA_DEV void dfacc_fms_conj(DfAcc &re, DfAcc &im, const dfl2 &a, const dfl2 &b)
 }
 
 template <bool IN_SMEM, typename R>
-__global__ void __launch_bounds__(1024) box_cholesky_kernel(const double2 *__restrict__ S, int nx, int ny, int b,
+__global__ void __launch_bounds__(512) box_cholesky_kernel(const double2 *__restrict__ S, int nx, int ny, int b,
                                                            double2 *__restrict__ Lpk, unsigned *err) {
   using C = typename Cplx<R>::T;
   static_assert(sizeof(C) == sizeof(double2), "the factor is stored in place of its FP64 output");
@@ -299,10 +299,8 @@ static void launch_chol_typed(const double2 *S, int nx, int ny, int b, double2 *
     cudaFuncSetAttribute(box_cholesky_kernel<false, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
     configured = 1;
   }
-  // 32 warps per element: the shared-memory triangle allows one CTA per SM,
-  // and the double-FP32 update chains need that many warps to hide latency.
-  if (matb + tabb <= 200 * 1024) box_cholesky_kernel<true, R><<<nel, 1024, matb + tabb, st>>>(S, nx, ny, b, Lpk, err);
-  else box_cholesky_kernel<false, R><<<nel, 1024, tabb, st>>>(S, nx, ny, b, Lpk, err);
+  if (matb + tabb <= 200 * 1024) box_cholesky_kernel<true, R><<<nel, 512, matb + tabb, st>>>(S, nx, ny, b, Lpk, err);
+  else box_cholesky_kernel<false, R><<<nel, 512, tabb, st>>>(S, nx, ny, b, Lpk, err);
 }
 
 void launch_box_cholesky(const double2 *S, int nx, int ny, int b, double2 *Lpk, unsigned *err, bool df,
