@@ -712,7 +712,10 @@ void ensure_ws(moma_array *a, int nr) {
   const size_t o_gbar = take(sizeof(unsigned));
   a->kbuf.ensure(off, a->dev_bytes);
   unsigned char *base = a->kbuf.as<unsigned char>();
-  CK(cudaMemset(base, 0, off));
+  // Ordered on the array's stream: a plain cudaMemset would run on the legacy
+  // default stream, which non-blocking streams (batch workers, servers) do
+  // not wait for, and could land after the solve has started writing here.
+  CK(cudaMemsetAsync(base, 0, off, a->st));
   KrylovCtl &k = a->ctl;
   k.m = m;
   k.active = reinterpret_cast<int *>(base + o_active);
@@ -1651,13 +1654,14 @@ moma_status moma_create_array(int nx, int ny, int b, const moma_options *opt, vo
     CK(cudaDeviceGetAttribute(&a->num_sms, cudaDevAttrMultiProcessorCount, a->dev));
     build_tables(a);
     a->Z128.ensure((size_t)a->Bp * b * a->ldb * sizeof(double2), a->dev_bytes);
-    CK(cudaMemset(a->Z128.p, 0, a->Z128.cap));
+    CK(cudaMemsetAsync(a->Z128.p, 0, a->Z128.cap, a->st));  // stream-ordered (see ensure_ws)
     if (prec == MOMA_PREC_MIXED) {
       a->Z64.ensure((size_t)a->Bp * b * a->ldb * sizeof(float2), a->dev_bytes);
-      CK(cudaMemset(a->Z64.p, 0, a->Z64.cap));
+      CK(cudaMemsetAsync(a->Z64.p, 0, a->Z64.cap, a->st));
     }
     a->errbuf.ensure(256, a->dev_bytes);
-    CK(cudaMemset(a->errbuf.p, 0, 256));
+    CK(cudaMemsetAsync(a->errbuf.p, 0, 256, a->st));
+    CK(cudaStreamSynchronize(a->st));
     a->err = a->errbuf.as<unsigned>();
     CK(cudaMallocHost(&a->h_nact, (MOMA_MAX_RESTART + 8) * sizeof(int)));
     CK(cudaMallocHost(&a->h_err, 64));

@@ -137,3 +137,32 @@ def test_fused_arnoldi_step_equals_separate_sweeps(moma_lib, cuda, prec, nx, ny,
     assert np.array_equal(res[0], res[1]) and np.array_equal(res[0], res[2])
     z = dense.assemble(blocks.astype(np.complex128), spec.nx, spec.ny)
     assert dense.relative_residual(z, res[0], V).max() <= 1e-10
+
+
+def test_fresh_arrays_on_worker_streams_never_skip_the_solve(moma_lib, cuda):
+    """Many fresh arrays set up and solved concurrently on the batch's
+    non-blocking worker streams (workspaces allocated and zeroed inside the
+    calls): every solve must run (outer_iters >= 1 from the zero start),
+    reach the tolerance, and return nonzero port currents.  A workspace
+    zeroing that was not ordered on the array's stream once let a solve see
+    ||V|| = 0 and stop at I = 0."""
+    m, torch = moma_lib, cuda
+    specs = [LatticeSpec(n, n + (k % 3), 12 + 2 * (k % 4), 0.3 + 0.1 * (k % 5), 0) for k, n in
+             enumerate([2, 3, 4, 5, 6, 7, 8] * 6)]
+    for rep in range(3):
+        hs = [m.moma_create_array(s.nx, s.ny, s.b) for s in specs]
+        try:
+            blocks = [torch.from_numpy(offset_blocks(s, np.complex64)).cuda() for s in specs]
+            Vs = [torch.from_numpy(excitation(s, [(0, 0)])).cuda() for s in specs]
+            Is = [torch.zeros_like(v) for v in Vs]
+            m.moma_set_blocks_batch(hs, blocks, workers=8)
+            infos = m.moma_solve_batch(hs, Vs, Is, workers=8)
+            torch.cuda.synchronize()
+            for s, info, I in zip(specs, infos, Is):
+                ip = I.cpu().numpy()[..., 0]
+                assert info["converged"] == 1 and info["outer_iters"] >= 1 and 0 < info["max_rel_residual"] <= 1e-10, \
+                    (rep, s, info)
+                assert np.abs(ip).min() > 0, (rep, s)
+        finally:
+            for h in hs:
+                m.moma_destroy(h)
