@@ -100,10 +100,15 @@ enum {
     MOMA_FLAG_PRECOND_PER_ELEMENT = 64, /* c64 preconditioner apply with one CTA per element instead of
                                     the streaming kernel (default for even b <= 160 and fewer
                                     than 16 RHS) */
-    MOMA_FLAG_SPLIT_ARNOLDI = 128 /* GMRES orthogonalisation as three sweep launches and a scaling
+    MOMA_FLAG_SPLIT_ARNOLDI = 128, /* GMRES orthogonalisation as three sweep launches and a scaling
                                     launch per Arnoldi step instead of one cooperative launch
                                     (the default where its grid fits on the device at once);
                                     results are bitwise the same */
+    MOMA_FLAG_NO_PDL = 256       /* launch the c64 operator kernels (register lattice passes,
+                                    row/column bin product, streaming preconditioner) in plain
+                                    stream order instead of with programmatic dependent launch,
+                                    which lets a kernel be scheduled while its predecessor
+                                    finishes; results are bitwise the same */
 };
 /* The tensor-core products (MIXED arrays): every circulant bin's block
  * Zhat_k (Eq. 3) is kept whole as a pair of TF32 values (hi + lo) and
@@ -352,11 +357,14 @@ moma_status moma_profile(moma_array *a, int enable);
 moma_status moma_kernel_stats(moma_array *a, int kernel, long long *launches, double *total_ms);
 
 /* Device time of one operator application, measured back to back (runtime
- * instrumentation, no counterpart in the paper).  The operator is enqueued
- * `reps` times on the array's stream between two CUDA events, after one
- * untimed application, on the solver's own workspace (contents irrelevant:
- * no kernel's run time depends on the values), so the figure is device
- * execution time without per-launch event overhead.  what:
+ * instrumentation, no counterpart in the paper).  After one untimed
+ * application, `reps` applications are captured as one CUDA graph on the
+ * solver's internal stream (as the solve replays its inner steps), replayed
+ * once untimed and once between two CUDA events, on the solver's own
+ * workspace (contents irrelevant: no kernel's run time depends on the
+ * values), so the figure is device execution time without host launch gaps
+ * or per-launch event overhead.  Arrays created with MOMA_FLAG_NO_GRAPHS
+ * time `reps` direct launches on the array's stream instead.  what:
  *   MOMA_TIME_Z       one c64 Z application: lattice FFT passes + bin product (Eq. 3)
  *   MOMA_TIME_BIN     the c64 per-bin product alone
  *   MOMA_TIME_PRECOND the c64 preconditioner apply P^{-1} (Eq. 38)

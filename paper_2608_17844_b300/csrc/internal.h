@@ -53,14 +53,19 @@ struct AxisPass {
   int in_c128 = 1, out_c128 = 1;  // element types of in / out: 0 c64, 1 c128, 2 dfl2
   const int *live = nullptr;       // if set and *live == 0 the pass does nothing
   int G = 0;                       // threads per line (0 = heuristic; set by the autotuner)
+  int pdl = 0;                     // register passes: programmatic dependent launch (common.cuh)
 };
 
 // Launch one axis pass computing in precision R (float or double).  Plain
 // c64 passes of length M <= 64 run on the register-resident kernels of
-// fftreg.cu (one thread per line).
+// fftreg.cu (one thread, or 2, 4, 8 lanes, per line).
 template <typename R>
 void launch_axis_pass(const AxisPass &p, const FftTables &t, cudaStream_t st);
 bool axis_reg_supported(const AxisPass &p, int M);
+// Lanes sharing one line in the register passes: P in {1, 2, 4, 8} with
+// P^2 | M (valid), and the choice for a pass (a fixed rule of its geometry).
+bool axis_lanes_valid(int M, int P);
+int lanes_per_line(const AxisPass &p, int M);
 void launch_axis_reg(const AxisPass &p, const FftTables &t, cudaStream_t st);
 
 // Two-dimensional lattice transforms in one launch (lattice2d.cu): mode 0
@@ -94,6 +99,7 @@ struct BinProduct {
   const int *live = nullptr;  // if set and *live == 0 the product does nothing
   int TR = 0, NS = 0;         // rows per tile / pipeline stages (0 = heuristic; autotuner)
   int occ = 1;                // CTAs per SM (2, 3: small-tile variants, <= 2 RHS per chunk, b <= 128; 3 for c64 only)
+  int pdl = 0;                // row/column kernel: programmatic dependent launch (common.cuh)
 };
 template <typename R>
 void launch_bin_product(const BinProduct &p, int num_sms, cudaStream_t st);
@@ -147,7 +153,7 @@ void launch_box_cholesky(const double2 *S, int nx, int ny, int b, double2 *Lpk, 
                          cudaStream_t st);
 // Full P_e (b x b, FP64) of one element from the summed-area table.
 void launch_box_one(const double2 *S, int nx, int ny, int b, int ex, int ey, double2 *out, cudaStream_t st);
-// Inverse factor X_e = L_e^{-1}, packed row-major lower, in precision R.
+// Inverse factor X_e = L_e^{-1}, packed column-major lower (as L_e), in precision R.
 template <typename R>
 void launch_tri_inverse(const double2 *Lpk, int nel, int b, void *X, size_t x_stride, cudaStream_t st);
 // y_e = X_e^H X_e x_e for each element; vectors: RHS q, element e, basis k at
@@ -156,13 +162,16 @@ template <typename R>
 void launch_precond_apply(const void *X, size_t x_stride, int nel, int b, int nr, const void *x, void *y,
                           unsigned *err, const int *live, long long vstride, long long voff, cudaStream_t st);
 
-// Streaming c64 application of X_e^H X_e from 8 x 8-blocked factors
-// (precond_blk.cu): one persistent CTA per SM, a ring of bulk copies.
-size_t xblk_entries(int b);  // complex entries per element of the blocked factor
+// Streaming c64 application of P_e^{-1} = X_e^H X_e, stored Hermitian in
+// 8 x 8 blocks (precond_blk.cu): one persistent CTA per SM, a ring of bulk
+// copies, one pass per element.  launch_pinv_pack forms the blocks from the
+// packed inverse factors (c64, column-major lower, x_stride entries apart).
+size_t xblk_entries(int b);  // complex entries per element of the blocked P_e^{-1}
 bool precond_blk_supported(int b, int nr, long long vstride, long long voff);
-void launch_xblk_pack(const void *Xpk, size_t x_stride, int nel, int b, void *Xb, cudaStream_t st);
-void launch_precond_blk(const void *Xb, int nel, int b, int nr, const void *x, void *y, unsigned *err,
-                        const int *live, long long vstride, long long voff, int num_sms, cudaStream_t st);
+void launch_pinv_pack(const void *Xpk, size_t x_stride, int nel, int b, void *Qb, cudaStream_t st);
+void launch_precond_blk(const void *Qb, int nel, int b, int nr, const void *x, void *y, unsigned *err,
+                        const int *live, long long vstride, long long voff, int num_sms, cudaStream_t st,
+                        bool pdl = false);
 
 // -------------------------------------------------------------- margin ----
 // y += margin terms of Z (herm = 0) or Z^H (herm = 1) for vectors

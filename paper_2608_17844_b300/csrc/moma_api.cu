@@ -154,7 +154,7 @@ struct moma_array {
   DevBuf bin_slot, tri, tri_in;  // symmetric block-transform tables
   DevBuf Z128, Z64;  // pair storage [Bp][b][ldb]
   DevBuf Xinv;       // inverse factors, packed row-major, inner precision
-  DevBuf Xblk;       // c64 inverse factors in 8 x 8 blocks for the streaming apply (precond_blk.cu)
+  DevBuf Xblk;       // c64 P_e^{-1} = X_e^H X_e in 8 x 8 blocks for the streaming apply (precond_blk.cu)
   bool xblk_ready = false;
   // Tensor-core products (inner precision c64, many RHS): split full bins,
   // the partner table, split X_e and X_e^H; built on first use after
@@ -219,6 +219,7 @@ struct moma_array {
   std::vector<std::pair<long long, int2>> tune_l2d;       // 2D transform signature -> (J, threads)
   bool axis_fft = false;  // lattice transforms one launch per axis instead of the 2D kernels
   bool no_blk_precond = false;  // c64 preconditioner through the per-element kernel only
+  bool pdl = true;              // programmatic dependent launch of the c64 operator kernels
   bool no_fused_arnoldi = false;  // CGS2 sweeps as separate launches
   std::string tune_log;
   const int *live = nullptr;  // operator kernels skip their work while *live == 0
@@ -443,6 +444,7 @@ int tuned_G(const moma_array *a, long long sig) {
 template <typename R>
 void axis(moma_array *a, AxisPass p, const FftTables &t) {
   p.live = a->live;
+  p.pdl = a->pdl;
   if (p.G == 0) p.G = tuned_G(a, axis_sig(p, t.plan.M, st_code<R>()));
   a->timed(is64<R>() ? PK_FFT128 : PK_FFT64, [&] { launch_axis_pass<R>(p, t, a->st); });
   check_launch(a);
@@ -468,6 +470,7 @@ void binprod(moma_array *a, int nr, const void *x, void *y, int herm) {
   P.TR = a->tune_bin_tr[is64<R>()];
   P.NS = a->tune_bin_ns[is64<R>()];
   P.occ = a->tune_bin_occ[is64<R>()];
+  P.pdl = a->pdl;
   a->timed(is64<R>() ? PK_BIN128 : PK_BIN64, [&] { launch_bin_product<R>(P, a->num_sms, a->st); });
   check_launch(a);
 }
@@ -514,7 +517,7 @@ void precond(moma_array *a, int nr, const void *x, void *y) {
   }
   if (std::is_same<R, float>::value && a->xblk_ready && precond_blk_supported(a->b, nr, a->ldv, 0)) {
     a->timed(PK_PREC, [&] {
-      launch_precond_blk(a->Xblk.p, a->nel, a->b, nr, x, y, a->err, a->live, a->ldv, 0, a->num_sms, a->st);
+      launch_precond_blk(a->Xblk.p, a->nel, a->b, nr, x, y, a->err, a->live, a->ldv, 0, a->num_sms, a->st, a->pdl);
     });
   } else {
     a->timed(PK_PREC, [&] {
@@ -832,11 +835,11 @@ void finish_preconditioner(moma_array *a) {
   a->Xinv.ensure((size_t)a->nel * xs * sizeof(C), a->dev_bytes);
   a->timed(PK_TRINV, [&] { launch_tri_inverse<R>(a->Lpk.as<double2>(), a->nel, a->b, a->Xinv.p, xs, a->st); });
   check_launch(a);
-  // c64 factors also in the blocked layout of the streaming apply.
+  // c64: also P_e^{-1} = X_e^H X_e in the blocked layout of the streaming apply.
   a->xblk_ready = false;
   if (std::is_same<R, float>::value && !a->no_blk_precond && precond_blk_supported(a->b, 1, 2, 0)) {
     a->Xblk.ensure((size_t)a->nel * xblk_entries(a->b) * sizeof(float2), a->dev_bytes);
-    a->timed(PK_TRINV, [&] { launch_xblk_pack(a->Xinv.p, a->x_stride, a->nel, a->b, a->Xblk.p, a->st); });
+    a->timed(PK_TRINV, [&] { launch_pinv_pack(a->Xinv.p, a->x_stride, a->nel, a->b, a->Xblk.p, a->st); });
     check_launch(a);
     a->xblk_ready = true;
   }
@@ -1089,7 +1092,9 @@ void autotune_precision(moma_array *a, int nr, int in128) {
       {pass_ix(a, nr, a->t1.p, a->lat_tmp.p, c, false, lat_code<R>()), &a->fx, "Ix"},
   };
   for (const Cand &cd : cands) {
-    if (std::is_same<R, float>::value && axis_reg_supported(cd.p, cd.t->plan.M)) continue;  // no launch shape to tune
+    // Register passes take a fixed lanes-per-line rule (the split changes
+    // the rounding, and tuned shapes never change results).
+    if (std::is_same<R, float>::value && axis_reg_supported(cd.p, cd.t->plan.M)) continue;
     float best = 1e30f;
     int bg = 0;
     for (int G : {1, 2, 4, 8, 16, 32}) {
@@ -1465,6 +1470,34 @@ void pcg_cycle(moma_array *a, int nr, const std::vector<int> &act, int max_inner
 
 // R: inner (Krylov) arithmetic; H: arithmetic of the refinement residual
 // V - Z I (FP64, or double-FP32 pairs of ~48 bits in the default mixed path).
+// Inside a solve (and the operator timing) the array works on an internal
+// non-blocking stream, capturable into CUDA graphs, ordered after the
+// array's own stream on entry and before it on exit.  Without graphs (or
+// while profiling) the array's stream is used directly.
+struct StreamSwitch {
+  moma_array *a;
+  cudaStream_t user;
+  bool on = false;
+  StreamSwitch(moma_array *a_) : a(a_), user(a_->st) {
+    if (!a->use_graphs || a->prof) return;
+    if (!a->gs) {
+      CK(cudaStreamCreateWithFlags(&a->gs, cudaStreamNonBlocking));
+      CK(cudaEventCreateWithFlags(&a->ev_in, cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&a->ev_out, cudaEventDisableTiming));
+    }
+    CK(cudaEventRecord(a->ev_in, user));
+    CK(cudaStreamWaitEvent(a->gs, a->ev_in, 0));
+    a->st = a->gs;
+    on = true;
+  }
+  ~StreamSwitch() {
+    if (!on) return;
+    cudaEventRecord(a->ev_out, a->gs);
+    cudaStreamWaitEvent(user, a->ev_out, 0);
+    a->st = user;
+  }
+};
+
 template <typename R, typename H>
 void solve_impl(moma_array *a, int nr, const void *Vin, void *Iout, const moma_solve_opts *o, moma_solve_info *info,
                 double *relres) {
@@ -1477,29 +1510,7 @@ void solve_impl(moma_array *a, int nr, const void *Vin, void *Iout, const moma_s
 
   // The solve runs on an internal non-blocking stream (capturable into
   // graphs), ordered after the array's stream on entry and before it on exit.
-  struct StreamSwitch {
-    moma_array *a;
-    cudaStream_t user;
-    bool on = false;
-    StreamSwitch(moma_array *a_) : a(a_), user(a_->st) {
-      if (!a->use_graphs || a->prof) return;
-      if (!a->gs) {
-        CK(cudaStreamCreateWithFlags(&a->gs, cudaStreamNonBlocking));
-        CK(cudaEventCreateWithFlags(&a->ev_in, cudaEventDisableTiming));
-        CK(cudaEventCreateWithFlags(&a->ev_out, cudaEventDisableTiming));
-      }
-      CK(cudaEventRecord(a->ev_in, user));
-      CK(cudaStreamWaitEvent(a->gs, a->ev_in, 0));
-      a->st = a->gs;
-      on = true;
-    }
-    ~StreamSwitch() {
-      if (!on) return;
-      cudaEventRecord(a->ev_out, a->gs);
-      cudaStreamWaitEvent(user, a->ev_out, 0);
-      a->st = user;
-    }
-  } sw(a);
+  StreamSwitch sw(a);
   autotune(a, nr);
 
   // Inputs into the solver's own buffers.
@@ -1641,6 +1652,7 @@ moma_status moma_create_array(int nx, int ny, int b, const moma_options *opt, vo
     a->axis_fft = opt && (opt->flags & MOMA_FLAG_AXIS_FFT);
     a->no_blk_precond = opt && (opt->flags & MOMA_FLAG_PRECOND_PER_ELEMENT);
     a->no_fused_arnoldi = opt && (opt->flags & MOMA_FLAG_SPLIT_ARNOLDI);
+    a->pdl = !(opt && (opt->flags & MOMA_FLAG_NO_PDL));
     if (opt && (opt->flags & MOMA_FLAG_TENSOR_ALWAYS)) a->tc_min_nr = 1;
     if (a->m > MOMA_MAX_RESTART) throw MomaError(MOMA_ERR_ARG, "restart too large");
     const int mx = (opt && opt->mx > 0) ? opt->mx : next_smooth(2 * nx - 1);
@@ -2113,21 +2125,51 @@ moma_status moma_time_operator(moma_array *a, int what, int nrhs, int reps, doub
         default: apply_normal<float>(a, nrhs, a->Vw.p, a->yw.p); break;
       }
     };
-    const bool prof = a->prof;
+    struct ProfOff {
+      moma_array *a;
+      bool was;
+      ~ProfOff() { a->prof = was; }
+    } prof_off{a, a->prof};
     a->prof = false;
+    StreamSwitch sw(a);
     once();
+    // With graphs (the default) the applications are captured as one CUDA
+    // graph and replayed, as the solve replays its inner steps: launches
+    // follow each other on the device without host launch gaps.
+    cudaGraphExec_t ge = nullptr;
+    if (sw.on) {
+      cudaGraph_t g = nullptr;
+      CK(cudaStreamBeginCapture(a->st, cudaStreamCaptureModeThreadLocal));
+      try {
+        for (int r = 0; r < reps; ++r) once();
+      } catch (...) {
+        cudaStreamEndCapture(a->st, &g);
+        if (g) cudaGraphDestroy(g);
+        throw;
+      }
+      CK(cudaStreamEndCapture(a->st, &g));
+      const cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
+      cudaGraphDestroy(g);
+      CK(ie);
+      CK(cudaGraphLaunch(ge, a->st));  // warm-up replay
+    }
+    struct ExecGuard {
+      cudaGraphExec_t e;
+      ~ExecGuard() { if (e) cudaGraphExecDestroy(e); }
+    } guard{ge};
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     CK(cudaEventRecord(e0, a->st));
-    for (int r = 0; r < reps; ++r) once();
+    if (ge) CK(cudaGraphLaunch(ge, a->st));
+    else
+      for (int r = 0; r < reps; ++r) once();
     CK(cudaEventRecord(e1, a->st));
     CK(cudaEventSynchronize(e1));
     float ms = 0;
     CK(cudaEventElapsedTime(&ms, e0, e1));
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    a->prof = prof;
     sync_and_check(a);
     *us = 1000.0 * ms / reps;
   });
@@ -2174,7 +2216,7 @@ size_t moma_estimate_bytes(int nx, int ny, int b, const moma_options *opt, int n
   const size_t c = 16, esz = prec == MOMA_PREC_FP64 ? 16 : 8;
   size_t bytes = Bp * b * ldb * c + (prec == MOMA_PREC_MIXED ? Bp * b * ldb * 8 : 0);  // stored bins
   bytes += nel * (nt + 2) * esz;                                                        // inverse factors
-  if (prec == MOMA_PREC_MIXED) bytes += nel * xblk_entries(b) * 8;                    // blocked c64 factors
+  if (prec == MOMA_PREC_MIXED) bytes += nel * xblk_entries(b) * 8;                    // blocked c64 P_e^{-1}
   bytes += B * 16 + nt * 12 + 4096;                                                     // tables
   const size_t nr = (size_t)nrhs, nch = (N + 1023) / 1024;
   bytes += nr * N * c * 6 + nr * ny * Mx * b * c + 2 * B * nr * b * c;                 // solve vectors

@@ -145,13 +145,15 @@ MOMA_DEV double2 box_entry(const double2 *S, int ndx, int bb, int x0, int x1, in
 // ------------------------------------------------------- box + Cholesky ---
 // One CTA per element.  The packed lower triangle of P_e is assembled from
 // the summed-area table (row by row, so reads of the table are contiguous)
-// and factored in FP64 by a blocked right-looking Cholesky: a panel of CH_NB
+// and factored by a blocked right-looking Cholesky: a panel of CH_NB
 // columns is factored column by column, then the trailing triangle receives
 // the rank-CH_NB update A(i,k) -= sum_p L(i,p) conj(L(k,p)) in one sweep.
-// The trailing triangle is contiguous in the packed column-major layout, so
-// the sweep hands consecutive packed entries to consecutive threads (an
-// (i, k) table in shared memory gives each entry's row and column): every
-// lane does useful FP64 work however short the remaining columns are.
+// The sweep is register-tiled: a thread owns a 2 x 2 tile of (i, k) entries
+// (rows i0, i0 + 1; columns k0, k0 + 1), so each of the panel's values it
+// loads serves two multiply-adds; tile t of the trailing triangle (row-major
+// enumeration of tile rows ti >= tile columns tk) is found from t by a
+// square root, so no index table is kept.  A diagonal tile skips its entry
+// above the diagonal; the last tile row of an odd trailing size has one row.
 // L_e (packed column-major) is written to Lpk.
 constexpr int CH_NB = 8;
 
@@ -201,7 +203,6 @@ __global__ void __launch_bounds__(512) box_cholesky_kernel(const double2 *__rest
   const int e = blockIdx.x, ex = e % nx, ey = e / nx;
   const int npk = b * (b + 1) / 2;
   C *A = IN_SMEM ? reinterpret_cast<C *>(smraw) : reinterpret_cast<C *>(Lpk + (size_t)e * npk);
-  short2 *tab = reinterpret_cast<short2 *>(smraw + (IN_SMEM ? (size_t)npk * sizeof(C) : 0));
   const int ndx = 2 * nx - 1, bb = b * b;
   const int x0 = nx - 1 - ex, x1 = 2 * nx - 2 - ex, y0 = ny - 1 - ey, y1 = 2 * ny - 2 - ey;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
@@ -214,7 +215,6 @@ __global__ void __launch_bounds__(512) box_cholesky_kernel(const double2 *__rest
     const int k = t - i * (i + 1) / 2;
     const int q = colbase(k, b) + i - k;
     A[q] = cvt<C>(box_entry(S, ndx, bb, x0, x1, y0, y1, i * b + k));
-    tab[q] = make_short2((short)i, (short)k);
   }
   __syncthreads();
 
@@ -240,41 +240,67 @@ __global__ void __launch_bounds__(512) box_cholesky_kernel(const double2 *__rest
       }
       __syncthreads();
     }
-    // Trailing rank-(je - jb) update over the contiguous packed triangle
-    // starting at (je, je); two entries per thread in flight.
+    // Trailing rank-(je - jb) update in 2 x 2 register tiles.
     const int np = je - jb;
     int pb[CH_NB];
 #pragma unroll
     for (int p = 0; p < CH_NB; ++p) pb[p] = p < np ? colbase(jb + p, b) - (jb + p) : 0;
-    const int t0 = je < b ? colbase(je, b) : npk;
-    const int nthr = blockDim.x;
-    for (int t = t0 + tid; t < npk; t += 2 * nthr) {
-      const int t2 = t + nthr;
-      const bool two = t2 < npk;
-      const short2 ik0 = tab[t], ik1 = two ? tab[t2] : ik0;
-      C a0 = A[t], a1 = two ? A[t2] : a0;
+    const int nt = (b - je + 1) / 2, ntiles = nt * (nt + 1) / 2;
+    for (int t = tid; t < ntiles; t += blockDim.x) {
+      int ti = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+      while (ti * (ti + 1) / 2 > t) --ti;
+      while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+      const int tk = t - ti * (ti + 1) / 2;
+      const int i0 = je + 2 * ti, k0 = je + 2 * tk;
+      const bool r1 = i0 + 1 < b;    // second row present
+      const bool up = ti != tk;      // (i0, k0 + 1) lies on or below the diagonal
+      C *c0 = A + colbase(k0, b) - k0;
+      C *c1 = A + colbase(k0 + 1, b) - (k0 + 1);  // dereferenced only where k0 + 1 <= i < b
+      C a00 = c0[i0];
+      C a10 = r1 ? c0[i0 + 1] : czero<C>();
+      C a01 = up ? c1[i0] : czero<C>();
+      C a11 = r1 ? c1[i0 + 1] : czero<C>();
       if constexpr (std::is_same<R, dfl>::value) {
-        DfAcc r0 = dfacc(a0.x), i0 = dfacc(a0.y), r1 = dfacc(a1.x), i1 = dfacc(a1.y);
+        DfAcc r00 = dfacc(a00.x), j00 = dfacc(a00.y), r10 = dfacc(a10.x), j10 = dfacc(a10.y);
+        DfAcc r01 = dfacc(a01.x), j01 = dfacc(a01.y), r11 = dfacc(a11.x), j11 = dfacc(a11.y);
 #pragma unroll
         for (int p = 0; p < CH_NB; ++p) {
           if (p < np) {
-            dfacc_fms_conj(r0, i0, A[pb[p] + ik0.x], A[pb[p] + ik0.y]);
-            dfacc_fms_conj(r1, i1, A[pb[p] + ik1.x], A[pb[p] + ik1.y]);
+            const C *lp = A + pb[p];
+            const C li0 = lp[i0], lk0 = lp[k0];
+            const C li1 = r1 ? lp[i0 + 1] : czero<C>();
+            const C lk1 = (up || r1) ? lp[k0 + 1] : czero<C>();
+            dfacc_fms_conj(r00, j00, li0, lk0);
+            dfacc_fms_conj(r10, j10, li1, lk0);
+            dfacc_fms_conj(r01, j01, li0, lk1);
+            dfacc_fms_conj(r11, j11, li1, lk1);
           }
         }
-        a0 = mk(dfacc_value(r0), dfacc_value(i0));
-        a1 = mk(dfacc_value(r1), dfacc_value(i1));
+        a00 = mk(dfacc_value(r00), dfacc_value(j00));
+        a10 = mk(dfacc_value(r10), dfacc_value(j10));
+        a01 = mk(dfacc_value(r01), dfacc_value(j01));
+        a11 = mk(dfacc_value(r11), dfacc_value(j11));
       } else {
 #pragma unroll
         for (int p = 0; p < CH_NB; ++p) {
           if (p < np) {
-            a0 = cfms_conj(A[pb[p] + ik0.x], A[pb[p] + ik0.y], a0);
-            a1 = cfms_conj(A[pb[p] + ik1.x], A[pb[p] + ik1.y], a1);
+            const C *lp = A + pb[p];
+            const C li0 = lp[i0], lk0 = lp[k0];
+            const C li1 = r1 ? lp[i0 + 1] : czero<C>();
+            const C lk1 = (up || r1) ? lp[k0 + 1] : czero<C>();
+            a00 = cfms_conj(li0, lk0, a00);
+            a10 = cfms_conj(li1, lk0, a10);
+            a01 = cfms_conj(li0, lk1, a01);
+            a11 = cfms_conj(li1, lk1, a11);
           }
         }
       }
-      A[t] = a0;
-      if (two) A[t2] = a1;
+      c0[i0] = a00;
+      if (r1) {
+        c0[i0 + 1] = a10;
+        c1[i0 + 1] = a11;
+      }
+      if (up) c1[i0] = a01;
     }
     __syncthreads();
   }
@@ -289,9 +315,9 @@ __global__ void __launch_bounds__(512) box_cholesky_kernel(const double2 *__rest
 
 template <typename R>
 static void launch_chol_typed(const double2 *S, int nx, int ny, int b, double2 *Lpk, unsigned *err, cudaStream_t st) {
-  // Shared memory: the packed triangle (if it fits) and the (i, k) table.
+  // Shared memory: the packed triangle, if it fits.
   const size_t npk = (size_t)b * (b + 1) / 2;
-  const size_t matb = npk * sizeof(double2), tabb = npk * sizeof(short2);
+  const size_t matb = npk * sizeof(double2);
   const int nel = nx * ny;
   static int configured = 0;
   if (!configured) {
@@ -299,8 +325,8 @@ static void launch_chol_typed(const double2 *S, int nx, int ny, int b, double2 *
     cudaFuncSetAttribute(box_cholesky_kernel<false, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
     configured = 1;
   }
-  if (matb + tabb <= 200 * 1024) box_cholesky_kernel<true, R><<<nel, 512, matb + tabb, st>>>(S, nx, ny, b, Lpk, err);
-  else box_cholesky_kernel<false, R><<<nel, 512, tabb, st>>>(S, nx, ny, b, Lpk, err);
+  if (matb <= 200 * 1024) box_cholesky_kernel<true, R><<<nel, 512, matb, st>>>(S, nx, ny, b, Lpk, err);
+  else box_cholesky_kernel<false, R><<<nel, 512, 0, st>>>(S, nx, ny, b, Lpk, err);
 }
 
 void launch_box_cholesky(const double2 *S, int nx, int ny, int b, double2 *Lpk, unsigned *err, bool df,

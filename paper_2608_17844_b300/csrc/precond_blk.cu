@@ -1,23 +1,26 @@
-// Streaming application of the block preconditioner P^{-1} = X_e^H X_e,
-// X_e = L_e^{-1} (Eq. 38, factored as in Sec. III-A), for the c64 inner
-// solve: one persistent CTA per SM walks its elements with an NS-deep ring
-// of bulk copies, so the next elements' factors are in flight while the
-// current one is applied.
+// Streaming application of the block preconditioner P^{-1} (Eq. 38; P_e
+// factored as in Sec. III-A, P_e^{-1} = X_e^H X_e with X_e = L_e^{-1}) for
+// the c64 inner solve: one persistent CTA per SM walks its elements with an
+// NS-deep ring of bulk copies, so the next elements' blocks are in flight
+// while the current one is applied.
 //
-// Storage of X_e (built once per set-up from the packed factor): the b x b
-// lower triangle padded to bp = 8 ceil(b / 8) and cut into 8 x 8 blocks;
-// block (p, q), q <= p, is block number p (p + 1) / 2 + q, and entry (i, k)
-// of a block (row i, column k inside it) sits at k * 8 + (i ^ k).  The XOR
-// swizzle makes both products below free of shared-memory bank conflicts:
-//  * t = X x: warp p owns the 8 rows of panel p and walks its blocks
-//    (p, 0..p); lane (r = lane % 8, c = lane / 8) reads entries (r, c) and
-//    (r, c + 4);
-//  * z = X^H t: warp w owns the 8 columns of panel w and walks the blocks
-//    (w..P-1, w); lane (k = lane % 8, c) reads entries (c, k) and (c + 4, k).
-// Warp w therefore touches w + 1 blocks in the first product and P - w in
-// the second: every warp does P + 1 blocks per element and no partial sums
-// cross warps (only the four lanes of a row or column are added, by
-// shuffles).
+// Stored per element (built once per set-up from the packed inverse
+// factor): the Hermitian Q_e = P_e^{-1} = X_e^H X_e, its lower triangle
+// padded to bp = 8 ceil(b / 8) and cut into 8 x 8 blocks, diagonal blocks
+// whole; block (p, q), q <= p, is block number p (p + 1) / 2 + q, and entry
+// (i, k) of a block (row i, column k inside it) sits at k * 8 + (i ^ k).
+// y = Q x is one pass with no intermediate vector: warp w owns the 8 rows
+// of panel w, y_w = sum_{q <= w} Q(w, q) x_q + sum_{p > w} Q(p, w)^H x_p,
+//  * row part: lane (r = lane % 8, c = lane / 8) reads entries (r, c) and
+//    (r, c + 4) of blocks (w, 0..w);
+//  * column part: lane (k = lane % 8, c) reads entries (c, k) and (c + 4, k)
+//    of blocks (w+1..P-1, w);
+// both free of shared-memory bank conflicts by the XOR swizzle.  Every
+// warp touches P blocks per element, and no partial sums cross warps (only
+// the four lanes of a row are added, by shuffles).  Q_e holds as many
+// bytes as the blocked X_e, so the stream is the same, but the apply is
+// one product instead of two dependent ones (the second waited at a
+// barrier for the whole first).
 #include <stdexcept>
 
 #include "internal.h"
@@ -50,24 +53,61 @@ MOMA_DEV float2 sum4(float2 v) {  // add the four lanes c = 0..3 of a row / colu
   return v;
 }
 
-__global__ void xblk_pack_kernel(const float2 *__restrict__ Xpk, size_t x_stride, int b, int P, float2 *Xb,
-                                 size_t xbs) {
-  const int e = blockIdx.x, blk = blockIdx.y, t = threadIdx.x;  // 64 threads: entry (i, k) = (t / 8, t % 8)
-  int p = 0;
-  while ((p + 1) * (p + 2) / 2 <= blk) ++p;
-  const int q = blk - p * (p + 1) / 2;
-  const int i = t >> 3, k = t & 7, I = 8 * p + i, K = 8 * q + k;
-  float2 v = make_float2(0.f, 0.f);
-  if (I < b && K < b && I >= K) v = Xpk[(size_t)e * x_stride + (size_t)K * b - (size_t)K * (K - 1) / 2 + (I - K)];
-  Xb[(size_t)e * xbs + (size_t)blk * 64 + k * 8 + (i ^ k)] = v;
+// Q_e = X_e^H X_e from the packed inverse factor (column-major lower: X(m, j)
+// at j b - j (j - 1) / 2 + m - j), staged in shared memory transposed to
+// row-major lower (X(m, j) at m (m + 1) / 2 + j) so that a row m serves all
+// of a tile's columns; Q(I, K) = sum over m >= max(I, K) of
+// conj(X(m, I)) X(m, K).  A thread computes a 2 x 2 tile
+// (rows I0, I0 + 1; columns K0, K0 + 1) of one 8 x 8 block, so each value
+// it loads serves two multiply-adds; FP32 accumulation (the apply is c64).
+// Padding rows and columns (>= b) are zero.
+constexpr int PACK_THREADS = 512;
+
+__global__ void __launch_bounds__(PACK_THREADS) pinv_pack_kernel(const float2 *__restrict__ Xpk, size_t x_stride,
+                                                                 int b, int P, float2 *Qb, size_t qbs) {
+  extern __shared__ __align__(16) unsigned char smx[];
+  float2 *Xs = reinterpret_cast<float2 *>(smx);
+  const int e = blockIdx.x, npk = b * (b + 1) / 2;
+  for (int t = threadIdx.x; t < npk; t += blockDim.x) {
+    int m = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+    while (m * (m + 1) / 2 > t) --m;
+    while ((m + 1) * (m + 2) / 2 <= t) ++m;
+    const int j = t - m * (m + 1) / 2;
+    Xs[t] = Xpk[(size_t)e * x_stride + (size_t)j * b - (size_t)j * (j - 1) / 2 + (m - j)];
+  }
+  __syncthreads();
+  const int ntiles = P * (P + 1) / 2 * 16;
+  for (int tt = threadIdx.x; tt < ntiles; tt += blockDim.x) {
+    const int blk = tt >> 4, i0 = ((tt >> 2) & 3) * 2, k0 = (tt & 3) * 2;
+    int p = 0;
+    while ((p + 1) * (p + 2) / 2 <= blk) ++p;
+    const int q = blk - p * (p + 1) / 2;
+    const int I0 = 8 * p + i0, K0 = 8 * q + k0;
+    float2 a00 = make_float2(0.f, 0.f), a01 = a00, a10 = a00, a11 = a00;
+    for (int m = max(I0, K0); m < b; ++m) {
+      const float2 *row = Xs + m * (m + 1) / 2;
+      const float2 xi0 = row[I0], xk0 = row[K0];  // I0, K0 <= m
+      const float2 xi1 = I0 + 1 <= m ? row[I0 + 1] : make_float2(0.f, 0.f);
+      const float2 xk1 = K0 + 1 <= m ? row[K0 + 1] : make_float2(0.f, 0.f);
+      a00 = cfmac(xi0, xk0, a00);
+      a01 = cfmac(xi0, xk1, a01);
+      a10 = cfmac(xi1, xk0, a10);
+      a11 = cfmac(xi1, xk1, a11);
+    }
+    float2 *out = Qb + (size_t)e * qbs + (size_t)blk * 64;
+    out[k0 * 8 + (i0 ^ k0)] = a00;
+    out[(k0 + 1) * 8 + (i0 ^ (k0 + 1))] = a01;
+    out[k0 * 8 + ((i0 + 1) ^ k0)] = a10;
+    out[(k0 + 1) * 8 + ((i0 + 1) ^ (k0 + 1))] = a11;
+  }
 }
 
 __global__ void __launch_bounds__(1024, 1) precond_blk_kernel(PbArgs A) {
   extern __shared__ __align__(128) unsigned char sm[];
+  pdl_enter();
   uint64_t *bar = reinterpret_cast<uint64_t *>(sm);  // [PB_MAX_NS]
   const int P = A.P, bp = 8 * P, b = A.b, nr = A.nr, ns = A.ns;
-  float2 *ts = reinterpret_cast<float2 *>(sm + 128);  // [bp][2]
-  unsigned char *stages = sm + 128 + ((size_t)bp * 2 * sizeof(float2) + 127) / 128 * 128;
+  unsigned char *stages = sm + 128;
   if (A.live && *A.live == 0) return;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int r8 = lane & 7, c4 = lane >> 3;
@@ -119,37 +159,29 @@ __global__ void __launch_bounds__(1024, 1) precond_blk_kernel(PbArgs A) {
     for (int q0 = 0; q0 < nr; q0 += 2) {
       const bool two = q0 + 1 < nr;
       const float2 *x0 = xs + (size_t)q0 * bp, *x1 = xs + (size_t)(two ? q0 + 1 : q0) * bp;
-      if (w < P) {  // t = X x, rows of panel w
+      if (w < P) {
         float2 a0 = make_float2(0.f, 0.f), a1 = a0;
+        // Row part: blocks (w, 0..w), the diagonal block whole.
         const float2 *row = Xs + (size_t)(w * (w + 1) / 2) * 64;
         for (int q = 0; q <= w; ++q) {
           const float2 *blk = row + q * 64;
 #pragma unroll
           for (int m = 0; m < 2; ++m) {
             const int k = c4 + 4 * m;
-            const float2 xv = blk[k * 8 + (r8 ^ k)];
-            a0 = cfma2(xv, x0[8 * q + k], a0);
-            a1 = cfma2(xv, x1[8 * q + k], a1);
+            const float2 qv = blk[k * 8 + (r8 ^ k)];
+            a0 = cfma2(qv, x0[8 * q + k], a0);
+            a1 = cfma2(qv, x1[8 * q + k], a1);
           }
         }
-        a0 = sum4(a0);
-        a1 = sum4(a1);
-        if (c4 == 0) {
-          ts[(8 * w + r8) * 2] = a0;
-          ts[(8 * w + r8) * 2 + 1] = a1;
-        }
-      }
-      __syncthreads();
-      if (w < P) {  // z = X^H t, columns of panel w
-        float2 a0 = make_float2(0.f, 0.f), a1 = a0;
-        for (int p = w; p < P; ++p) {
+        // Column part: blocks (w+1..P-1, w), conjugate-transposed.
+        for (int p = w + 1; p < P; ++p) {
           const float2 *blk = Xs + (size_t)(p * (p + 1) / 2 + w) * 64;
 #pragma unroll
           for (int m = 0; m < 2; ++m) {
             const int i = c4 + 4 * m;
-            const float2 xv = blk[r8 * 8 + (i ^ r8)];
-            a0 = cfmac(xv, ts[(8 * p + i) * 2], a0);
-            a1 = cfmac(xv, ts[(8 * p + i) * 2 + 1], a1);
+            const float2 qv = blk[r8 * 8 + (i ^ r8)];
+            a0 = cfmac(qv, x0[8 * p + i], a0);
+            a1 = cfmac(qv, x1[8 * p + i], a1);
           }
         }
         a0 = sum4(a0);
@@ -160,8 +192,8 @@ __global__ void __launch_bounds__(1024, 1) precond_blk_kernel(PbArgs A) {
           if (two) A.y[(q0 + 1) * A.vstride + A.voff + e * b + k] = a1;
         }
       }
-      __syncthreads();
     }
+    __syncthreads();  // every warp is done with stage s before it is refilled
     if (tid == 0) issue(it + ns);
   }
 }
@@ -174,7 +206,7 @@ size_t stage_bytes(int b, int nr) {
 
 int stages_for(int b, int nr) {
   const int P = (b + 7) / 8;
-  const size_t head = 128 + ((size_t)8 * P * 2 * sizeof(float2) + 127) / 128 * 128;
+  const size_t head = 128;
   const size_t sb = stage_bytes(b, nr);
   if (head + sb > PB_SMEM) return 0;
   return (int)std::min<size_t>(PB_MAX_NS, (PB_SMEM - head) / sb);
@@ -192,18 +224,25 @@ bool precond_blk_supported(int b, int nr, long long vstride, long long voff) {
          stages_for(b, nr) >= 2;
 }
 
-void launch_xblk_pack(const void *Xpk, size_t x_stride, int nel, int b, void *Xb, cudaStream_t st) {
+void launch_pinv_pack(const void *Xpk, size_t x_stride, int nel, int b, void *Qb, cudaStream_t st) {
   const int P = (b + 7) / 8;
-  dim3 grid(nel, P * (P + 1) / 2);
-  xblk_pack_kernel<<<grid, 64, 0, st>>>(reinterpret_cast<const float2 *>(Xpk), x_stride, b, P,
-                                        reinterpret_cast<float2 *>(Xb), xblk_entries(b));
+  const size_t smem = (size_t)b * (b + 1) / 2 * sizeof(float2);
+  if (smem > PB_SMEM) throw std::runtime_error("pinv_pack: block too large");
+  static bool configured = false;
+  if (!configured) {
+    cudaFuncSetAttribute(pinv_pack_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PB_SMEM);
+    configured = true;
+  }
+  pinv_pack_kernel<<<nel, PACK_THREADS, smem, st>>>(reinterpret_cast<const float2 *>(Xpk), x_stride, b, P,
+                                                    reinterpret_cast<float2 *>(Qb), xblk_entries(b));
 }
 
-void launch_precond_blk(const void *Xb, int nel, int b, int nr, const void *x, void *y, unsigned *err,
-                        const int *live, long long vstride, long long voff, int num_sms, cudaStream_t st) {
+void launch_precond_blk(const void *Qb, int nel, int b, int nr, const void *x, void *y, unsigned *err,
+                        const int *live, long long vstride, long long voff, int num_sms, cudaStream_t st,
+                        bool pdl) {
   if (!precond_blk_supported(b, nr, vstride, voff)) throw std::runtime_error("precond_blk: unsupported shape");
   PbArgs a;
-  a.Xb = reinterpret_cast<const float2 *>(Xb);
+  a.Xb = reinterpret_cast<const float2 *>(Qb);
   a.xbs = xblk_entries(b);
   a.nel = nel;
   a.b = b;
@@ -217,14 +256,14 @@ void launch_precond_blk(const void *Xb, int nel, int b, int nr, const void *x, v
   a.voff = voff;
   a.err = err;
   a.live = live;
-  const size_t smem = 128 + ((size_t)8 * a.P * 2 * sizeof(float2) + 127) / 128 * 128 + (size_t)a.ns * a.stage_bytes;
+  const size_t smem = 128 + (size_t)a.ns * a.stage_bytes;
   static bool configured = false;
   if (!configured) {
     cudaFuncSetAttribute(precond_blk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PB_SMEM);
     configured = true;
   }
   const int grid = std::min(nel, num_sms);
-  precond_blk_kernel<<<grid, 32 * a.P, smem, st>>>(a);
+  launch_kernel(pdl, precond_blk_kernel, dim3(grid), dim3(32 * a.P), smem, st, a);
 }
 
 }  // namespace moma

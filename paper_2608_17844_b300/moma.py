@@ -48,6 +48,7 @@ class MomaError(RuntimeError):
 
 MOMA_FLAG_NO_GRAPHS, MOMA_FLAG_NO_AUTOTUNE, MOMA_FLAG_NO_TENSOR, MOMA_FLAG_TENSOR_ALWAYS = 1, 2, 4, 8
 MOMA_FLAG_FP64_RESIDUAL, MOMA_FLAG_AXIS_FFT, MOMA_FLAG_PRECOND_PER_ELEMENT, MOMA_FLAG_SPLIT_ARNOLDI = 16, 32, 64, 128
+MOMA_FLAG_NO_PDL = 256
 
 
 class moma_options(ctypes.Structure):

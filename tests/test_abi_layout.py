@@ -84,3 +84,27 @@ def test_header_compiles_cleanly(tmp_path, lang):
     r = subprocess.run([cc, std, "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.dirname(HEADER),
                         "-c", str(src), "-o", str(tmp_path / "h.o")], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_enum_constants_match_the_header(tmp_path):
+    """Every MOMA_* enumerator the binding defines (flags, precisions,
+    operators, timing selectors, status codes) has the header's value, as
+    the C compiler evaluates it."""
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    text = open(HEADER).read()
+    names = sorted(n for n in set(re.findall(r"\b(MOMA_[A-Z0-9_]+)\s*=", text)) if hasattr(mb, n))
+    assert any(n.startswith("MOMA_FLAG_") for n in names) and "MOMA_FLAG_NO_PDL" in names
+    lines = ['#include <stdio.h>', '#include "moma.h"', "int main(void) {"]
+    lines += [f'  printf("{n} %lld\\n", (long long){n});' for n in names]
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "enums.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "enums"
+    subprocess.run([cc, "-std=c11", "-Wall", "-Werror", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)],
+                   check=True, capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = dict(l.split() for l in out if l.strip())
+    for n in names:
+        assert int(got[n]) == int(getattr(mb, n)), n

@@ -445,3 +445,35 @@ def test_row_column_warp_bin_product(moma_lib, cuda, nx, ny, b, nr, op):
     err = np.abs(y - ref).max() / np.abs(ref).max()
     RAW_ERRORS[f"rc_bin{'H' if op else ''} {nx}x{ny}x{b} nr={nr}"] = err
     assert np.all(np.isfinite(y)) and err <= 1e-5, err
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("nx,ny,b,nr", [(32, 3, 8, 1), (24, 20, 4, 2), (16, 30, 6, 1), (10, 32, 5, 3)])
+def test_split_lattice_transforms(moma_lib, cuda, nx, ny, b, nr):
+    """Lattice axes whose circulant length takes the split register
+    transform (2 or 4 lanes per line: M = 64, 48 and 32 -> 4 lanes, 60, 40
+    and 20 -> 2 at these line counts) beside an axis on one thread per line
+    (M = 5): Z x, Z^H x and P^{-1} Z^H Z x (Eq. 3, Eq. 6, Sec. III-A; the
+    last includes the inverse / lattice mask / forward pass) element by
+    element against the oracle's direct offset sums, c64.  Eight lanes per
+    line (never chosen by the rule) are checked on the host."""
+    m = moma_lib
+    spec = LatticeSpec(nx, ny, b, 0.5, 12)
+    blocks = offset_blocks(spec, np.complex64)
+    b128 = blocks.astype(np.complex128)
+    x = rand_vec(nr, spec, seed=21, dtype=np.complex64)
+    xo = x.astype(np.complex128)
+    p = mbt.precond_blocks(b128, nx, ny)
+    ref = {0: mbt.matvec(b128, nx, ny, xo), 1: mbt.matvec_h(b128, nx, ny, xo),
+           2: mbt.normal_operator(b128, nx, ny, xo, p)}
+    h = m.moma_create_array(nx, ny, b, MIXED, flags=m.MOMA_FLAG_NO_TENSOR)
+    try:
+        m.moma_set_blocks(h, blocks)
+        for op in (0, 1, 2):
+            y = np.full_like(x, np.nan)
+            m.moma_matvec(h, op, x, y)
+            err = np.abs(y - ref[op]).max() / np.abs(ref[op]).max()
+            RAW_ERRORS[f"split_fft op{op} {nx}x{ny}x{b} nr={nr}"] = err
+            assert np.all(np.isfinite(y)) and err <= 1e-5, (op, err)
+    finally:
+        m.moma_destroy(h)
