@@ -100,15 +100,10 @@ enum {
     MOMA_FLAG_PRECOND_PER_ELEMENT = 64, /* c64 preconditioner apply with one CTA per element instead of
                                     the streaming kernel (default for even b <= 160 and fewer
                                     than 16 RHS) */
-    MOMA_FLAG_SPLIT_ARNOLDI = 128, /* GMRES orthogonalisation as three sweep launches and a scaling
+    MOMA_FLAG_SPLIT_ARNOLDI = 128 /* GMRES orthogonalisation as three sweep launches and a scaling
                                     launch per Arnoldi step instead of one cooperative launch
                                     (the default where its grid fits on the device at once);
                                     results are bitwise the same */
-    MOMA_FLAG_NO_PDL = 256       /* launch the c64 operator kernels (register lattice passes,
-                                    row/column bin product, streaming preconditioner) in plain
-                                    stream order instead of with programmatic dependent launch,
-                                    which lets a kernel be scheduled while its predecessor
-                                    finishes; results are bitwise the same */
 };
 /* The tensor-core products (MIXED arrays): every circulant bin's block
  * Zhat_k (Eq. 3) is kept whole as a pair of TF32 values (hi + lo) and
@@ -167,8 +162,8 @@ moma_status moma_create_array(int nx, int ny, int b, const moma_options *opt,
 /* Load the offset blocks (Eq. 1) and build everything derived from them:
  * the transformed first column of the circulant embedding, one block per
  * (k, -k) bin pair since Zhat_{-k} = Zhat_k^T (Eqs. 3, 6, 11); the blocks
- * of P = blockdiag(Z^H Z) by summed-area box sums of the offset Gram
- * products Z_D^H Z_D (Eq. 37); their Cholesky factors P_e = L_e L_e^H
+ * of P = blockdiag(Z^H Z) as box sums (sliding windows over the offset
+ * grid) of the offset Gram products Z_D^H Z_D (Eq. 37); their Cholesky factors P_e = L_e L_e^H
  * (Sec. III-A) and the inverse factors used to apply P^{-1}.
  * blocks: [2Ny-1][2Nx-1][b][b] of dtype (moma_dtype), offset (dx, dy) at
  * index (dy + Ny - 1, dx + Nx - 1), host or device.  The library assumes
@@ -347,7 +342,7 @@ moma_status moma_xi_s(int nx, int ny, double s_cc_re, double s_cc_im, double s1_
  * kernel family.  kernel: 0 = c64 bin product, 1 = c128 bin product,
  * 2 = preconditioner apply, 3 = c64 lattice FFT passes, 4 = block-bin
  * transform (set-up), 5 = c128 lattice FFT passes, 6 = offset Gram
- * products, 7 = summed-area table, 8 = box sums + Cholesky, 9 = inverse
+ * products, 7 = box sums, 8 = Cholesky, 9 = inverse
  * factors, 10 = Arnoldi/Givens/update kernels, 11 = residual and
  * conversion kernels, 12 = tensor-core c64 bin product, 13 = tensor-core
  * preconditioner apply.  Writes the number of
@@ -406,7 +401,7 @@ moma_status moma_solve_batch(int n, moma_array *const *arrays, const int *nrhs, 
 
 /* Memory management, no counterpart in the paper.
  * Free the set-up scratch kept after moma_set_blocks (device copy of the
- * blocks, block-transform intermediate, Gram/summed-area table, FP64
+ * blocks, block-transform intermediate, Gram products, box sums, FP64
  * Cholesky factors).  The bins and the inverse factors stay; solves and
  * products are unaffected; moma_get_precond_block then reports
  * MOMA_ERR_STATE.  For keeping many arrays resident. */

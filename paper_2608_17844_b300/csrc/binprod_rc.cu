@@ -57,7 +57,6 @@ MOMA_DEV float2 rc_sum4(float2 v) {  // the four lanes of a row (lane bits 3 and
 template <int NR, bool HERM, int MINB>
 __global__ void __launch_bounds__(RC_THREADS, MINB) bin_rc_kernel(RcArgs A) {
   extern __shared__ __align__(128) unsigned char sm[];
-  pdl_enter();
   const BinProduct &P = A.P;
   if (P.live && *P.live == 0) return;
   const int b = P.b, ldb = P.ldb, nr = P.nr, q0 = A.q0, NS = A.NS, lds = A.lds;
@@ -289,7 +288,7 @@ void rc_launch(const BinProduct &P, int num_sms, cudaStream_t st, int q0) {
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 112 * 1024);
       configured = 1;
     }
-    launch_kernel(P.pdl != 0, kern, dim3(grid), dim3(RC_THREADS), smem, st, a);
+    kern<<<grid, RC_THREADS, smem, st>>>(a);
   } else {
     auto kern = bin_rc_kernel<NR, HERM, 1>;
     static int configured = 0;
@@ -297,7 +296,7 @@ void rc_launch(const BinProduct &P, int num_sms, cudaStream_t st, int q0) {
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
       configured = 1;
     }
-    launch_kernel(P.pdl != 0, kern, dim3(grid), dim3(RC_THREADS), smem, st, a);
+    kern<<<grid, RC_THREADS, smem, st>>>(a);
   }
 }
 

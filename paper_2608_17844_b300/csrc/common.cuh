@@ -203,40 +203,6 @@ MOMA_DEV void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar
       : "memory");
 }
 
-// ---- programmatic dependent launch (sm_90+) ------------------------------
-// A kernel launched with the programmatic-stream-serialization attribute
-// may be scheduled while its predecessor in the stream is still running.
-// pdl_enter() must come before the kernel's first access to global memory
-// that another kernel writes or reads: it waits until the predecessor has
-// completed and its writes are visible (griddepcontrol.wait), then allows
-// the successor to be scheduled in turn.  Without the attribute both
-// instructions do nothing.  Every kernel launched with the attribute calls
-// it unconditionally, so completion stays transitive along the stream.
-MOMA_DEV void pdl_enter() {
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-
-// Launch `kernel` on `st`, with the programmatic-stream-serialization
-// attribute when `pdl` (the kernel must then call pdl_enter first).
-template <typename... KArgs, typename... Args>
-inline cudaError_t launch_kernel(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
-                                 cudaStream_t st, Args &&...args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = block;
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute at[1];
-  if (pdl) {
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-  }
-  return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args &&>(args)...);
-}
-
 // Device-side error bits reported back to the host.
 enum : unsigned {
   DEVERR_TIMEOUT = 1u,

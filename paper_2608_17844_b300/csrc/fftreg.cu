@@ -41,7 +41,6 @@ struct RegArgs {
 
 template <int M>
 __global__ void __launch_bounds__(128) axis_reg_kernel(const __grid_constant__ RegArgs A) {
-  pdl_enter();
   const AxisPass &p = A.p;
   if (p.live && *p.live == 0) return;
   const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -89,7 +88,6 @@ __global__ void __launch_bounds__(kLaneThreads) axis_lane_kernel(const __grid_co
   using S = LaneShape<M, P>;
   constexpr int Q = S::Q, L = S::L;
   __shared__ float2 xbuf[kLaneThreads / 32][Q * kLaneLd];
-  pdl_enter();
   const AxisPass &p = A.p;
   if (p.live && *p.live == 0) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -159,8 +157,7 @@ void launch_lanes(const AxisPass &p, const FftTables &t, cudaStream_t st) {
   const long long nlines = (long long)p.n1 * p.n2 * p.ninner;
   const long long warps = (nlines + LaneShape<M, P>::L - 1) / LaneShape<M, P>::L;
   const long long blocks = (warps + kLaneThreads / 32 - 1) / (kLaneThreads / 32);
-  launch_kernel(p.pdl != 0, axis_lane_kernel<M, P>, dim3((unsigned)blocks), dim3(kLaneThreads), 0, st, a,
-                (const float2 *)t.tw32);
+  axis_lane_kernel<M, P><<<(unsigned)blocks, kLaneThreads, 0, st>>>(a, t.tw32);
 }
 
 template <int M>
@@ -179,7 +176,7 @@ void launch_m(const AxisPass &p, const FftTables &t, cudaStream_t st) {
   const long long nlines = (long long)p.n1 * p.n2 * p.ninner;
   const int threads = 128;
   const long long blocks = (nlines + threads - 1) / threads;
-  launch_kernel(p.pdl != 0, axis_reg_kernel<M>, dim3((unsigned)blocks), dim3(threads), 0, st, a);
+  axis_reg_kernel<M><<<(unsigned)blocks, threads, 0, st>>>(a);
 }
 
 }  // namespace

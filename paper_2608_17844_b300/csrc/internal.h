@@ -53,7 +53,6 @@ struct AxisPass {
   int in_c128 = 1, out_c128 = 1;  // element types of in / out: 0 c64, 1 c128, 2 dfl2
   const int *live = nullptr;       // if set and *live == 0 the pass does nothing
   int G = 0;                       // threads per line (0 = heuristic; set by the autotuner)
-  int pdl = 0;                     // register passes: programmatic dependent launch (common.cuh)
 };
 
 // Launch one axis pass computing in precision R (float or double).  Plain
@@ -99,7 +98,6 @@ struct BinProduct {
   const int *live = nullptr;  // if set and *live == 0 the product does nothing
   int TR = 0, NS = 0;         // rows per tile / pipeline stages (0 = heuristic; autotuner)
   int occ = 1;                // CTAs per SM (2, 3: small-tile variants, <= 2 RHS per chunk, b <= 128; 3 for c64 only)
-  int pdl = 0;                // row/column kernel: programmatic dependent launch (common.cuh)
 };
 template <typename R>
 void launch_bin_product(const BinProduct &p, int num_sms, cudaStream_t st);
@@ -142,17 +140,20 @@ void launch_tc_product(const TcMats &m, const TcProduct &P, int num_sms, cudaStr
 // G_D = Z_D^H Z_D for every offset, output FP64 [nD][b][b].
 template <typename R>
 void launch_gram(const void *blocks, int blocks_c128, int nD, int b, double2 *G, cudaStream_t st);
-// In-place 2D inclusive prefix sum over the (2Ny-1) x (2Nx-1) offset grid.
-void launch_sat(double2 *S, int ndy, int ndx, int bb, cudaStream_t st);
-// The same from Y (c64, [nD][b][b]) with Y_{-D} = conj(G_D) (the tensor-core
-// Gram products of the reflected offsets): S = prefix sums of conj(Y_{-D}).
-void launch_sat_from_reflected(const float2 *Y, double2 *S, int ndy, int ndx, int bb, cudaStream_t st);
-// Box sums + Cholesky: L_e (packed lower, column-major, FP64) for each element.
+// Box sums P_e (Eq. 37) by separable sliding windows, FP64, lower
+// triangles only (row-major, b(b+1)/2 entries per element): G_D from S
+// (FP64 [nD][b][b]) or, if Y is set, conj(Y_{-D}) (the tensor-core Gram
+// products of the reflected offsets, c64).  W holds box_window_entries()
+// complex entries: the row windows, then the P_e ([Ny][Nx][b(b+1)/2], at
+// box_sums_of(W)).
+size_t box_window_entries(int nx, int ny, int b);
+void launch_box_sums(const double2 *S, const float2 *Y, int nx, int ny, int b, double2 *W, cudaStream_t st);
+const double2 *box_sums_of(const double2 *W, int nx, int ny, int b);
+// Cholesky of every P_e: L_e (packed lower, column-major, FP64) into Lpk.
 // df: factor in double-FP32 arithmetic (output still FP64).
-void launch_box_cholesky(const double2 *S, int nx, int ny, int b, double2 *Lpk, unsigned *err, bool df,
-                         cudaStream_t st);
-// Full P_e (b x b, FP64) of one element from the summed-area table.
-void launch_box_one(const double2 *S, int nx, int ny, int b, int ex, int ey, double2 *out, cudaStream_t st);
+void launch_box_cholesky(const double2 *Pbox, int nel, int b, double2 *Lpk, unsigned *err, bool df, cudaStream_t st);
+// Full P_e (b x b, FP64) of one element from the box sums.
+void launch_box_one(const double2 *Pbox, int nx, int b, int ex, int ey, double2 *out, cudaStream_t st);
 // Inverse factor X_e = L_e^{-1}, packed column-major lower (as L_e), in precision R.
 template <typename R>
 void launch_tri_inverse(const double2 *Lpk, int nel, int b, void *X, size_t x_stride, cudaStream_t st);
@@ -170,8 +171,7 @@ size_t xblk_entries(int b);  // complex entries per element of the blocked P_e^{
 bool precond_blk_supported(int b, int nr, long long vstride, long long voff);
 void launch_pinv_pack(const void *Xpk, size_t x_stride, int nel, int b, void *Qb, cudaStream_t st);
 void launch_precond_blk(const void *Qb, int nel, int b, int nr, const void *x, void *y, unsigned *err,
-                        const int *live, long long vstride, long long voff, int num_sms, cudaStream_t st,
-                        bool pdl = false);
+                        const int *live, long long vstride, long long voff, int num_sms, cudaStream_t st);
 
 // -------------------------------------------------------------- margin ----
 // y += margin terms of Z (herm = 0) or Z^H (herm = 1) for vectors

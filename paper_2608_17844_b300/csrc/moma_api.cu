@@ -122,7 +122,7 @@ __global__ void reciprocal_fill_kernel(C *Z, int ndy, int ndx, int b, int m0) {
 
 enum {
   PK_BIN64 = 0, PK_BIN128 = 1, PK_PREC = 2, PK_FFT64 = 3, PK_BLOCKFFT = 4, PK_FFT128 = 5,
-  PK_GRAM = 6, PK_SAT = 7, PK_CHOL = 8, PK_TRINV = 9, PK_KRYLOV = 10, PK_MISC = 11, PK_BINTC = 12, PK_PRECTC = 13, PK_N = 14
+  PK_GRAM = 6, PK_BOX = 7, PK_CHOL = 8, PK_TRINV = 9, PK_KRYLOV = 10, PK_MISC = 11, PK_BINTC = 12, PK_PRECTC = 13, PK_N = 14
 };
 
 }  // namespace
@@ -153,7 +153,7 @@ struct moma_array {
   DevBuf pairs, slot_of;
   DevBuf bin_slot, tri, tri_in;  // symmetric block-transform tables
   DevBuf Z128, Z64;  // pair storage [Bp][b][ldb]
-  DevBuf Xinv;       // inverse factors, packed row-major, inner precision
+  DevBuf Xinv;       // inverse factors, packed column-major, inner precision
   DevBuf Xblk;       // c64 P_e^{-1} = X_e^H X_e in 8 x 8 blocks for the streaming apply (precond_blk.cu)
   bool xblk_ready = false;
   // Tensor-core products (inner precision c64, many RHS): split full bins,
@@ -169,6 +169,8 @@ struct moma_array {
 
   // set-up workspace
   DevBuf blk, T, S, Lpk;
+  DevBuf Wb;                     // box-sum windows when S cannot hold them
+  const double2 *pbox = nullptr;  // the box sums P_e (lower triangles), in S or Wb
   cudaStream_t cs = nullptr;  // host-to-device copies of the blocks
   DevBuf gramA, gramY;        // tensor-core Gram products: split blocks, reflected products
   bool tgram = false;         // this set-up's Gram products ran on the tensor cores
@@ -219,7 +221,6 @@ struct moma_array {
   std::vector<std::pair<long long, int2>> tune_l2d;       // 2D transform signature -> (J, threads)
   bool axis_fft = false;  // lattice transforms one launch per axis instead of the 2D kernels
   bool no_blk_precond = false;  // c64 preconditioner through the per-element kernel only
-  bool pdl = true;              // programmatic dependent launch of the c64 operator kernels
   bool no_fused_arnoldi = false;  // CGS2 sweeps as separate launches
   std::string tune_log;
   const int *live = nullptr;  // operator kernels skip their work while *live == 0
@@ -444,7 +445,6 @@ int tuned_G(const moma_array *a, long long sig) {
 template <typename R>
 void axis(moma_array *a, AxisPass p, const FftTables &t) {
   p.live = a->live;
-  p.pdl = a->pdl;
   if (p.G == 0) p.G = tuned_G(a, axis_sig(p, t.plan.M, st_code<R>()));
   a->timed(is64<R>() ? PK_FFT128 : PK_FFT64, [&] { launch_axis_pass<R>(p, t, a->st); });
   check_launch(a);
@@ -470,7 +470,6 @@ void binprod(moma_array *a, int nr, const void *x, void *y, int herm) {
   P.TR = a->tune_bin_tr[is64<R>()];
   P.NS = a->tune_bin_ns[is64<R>()];
   P.occ = a->tune_bin_occ[is64<R>()];
-  P.pdl = a->pdl;
   a->timed(is64<R>() ? PK_BIN128 : PK_BIN64, [&] { launch_bin_product<R>(P, a->num_sms, a->st); });
   check_launch(a);
 }
@@ -517,7 +516,7 @@ void precond(moma_array *a, int nr, const void *x, void *y) {
   }
   if (std::is_same<R, float>::value && a->xblk_ready && precond_blk_supported(a->b, nr, a->ldv, 0)) {
     a->timed(PK_PREC, [&] {
-      launch_precond_blk(a->Xblk.p, a->nel, a->b, nr, x, y, a->err, a->live, a->ldv, 0, a->num_sms, a->st, a->pdl);
+      launch_precond_blk(a->Xblk.p, a->nel, a->b, nr, x, y, a->err, a->live, a->ldv, 0, a->num_sms, a->st);
     });
   } else {
     a->timed(PK_PREC, [&] {
@@ -811,22 +810,29 @@ void gram_chunk(moma_array *a, const void *blk, int blk128, int d0, int nd) {
   check_launch(a);
 }
 
-// Summed-area table, box sums + Cholesky, inverse factors (after every
-// offset's Gram product is in S).
+// Box sums, Cholesky, inverse factors (after every offset's Gram product is
+// in S, or in gramY for the tensor-core Gram products).
 template <typename R>
 void finish_preconditioner(moma_array *a) {
-  const int bb = a->b * a->b;
-  a->timed(PK_SAT, [&] {
-    if (a->tgram)
-      launch_sat_from_reflected(a->gramY.as<float2>(), a->S.as<double2>(), 2 * a->ny - 1, 2 * a->nx - 1, bb, a->st);
-    else
-      launch_sat(a->S.as<double2>(), 2 * a->ny - 1, 2 * a->nx - 1, bb, a->st);
+  // The sliding-window sums go to S where the Gram products are not in it
+  // and it is large enough, else to their own buffer.
+  const size_t wents = box_window_entries(a->nx, a->ny, a->b);
+  double2 *W;
+  if (a->tgram && wents * sizeof(double2) <= a->S.cap) {
+    W = a->S.as<double2>();
+  } else {
+    a->Wb.ensure(wents * sizeof(double2), a->dev_bytes);
+    W = a->Wb.as<double2>();
+  }
+  a->timed(PK_BOX, [&] {
+    launch_box_sums(a->tgram ? nullptr : a->S.as<double2>(), a->tgram ? a->gramY.as<float2>() : nullptr, a->nx,
+                    a->ny, a->b, W, a->st);
   });
   check_launch(a);
+  a->pbox = box_sums_of(W, a->nx, a->ny, a->b);
   const size_t npk = (size_t)a->b * (a->b + 1) / 2;
   a->Lpk.ensure((size_t)a->nel * npk * sizeof(double2), a->dev_bytes);
-  a->timed(PK_CHOL, [&] { launch_box_cholesky(a->S.as<double2>(), a->nx, a->ny, a->b, a->Lpk.as<double2>(), a->err,
-                                                      a->df, a->st); });
+  a->timed(PK_CHOL, [&] { launch_box_cholesky(a->pbox, a->nel, a->b, a->Lpk.as<double2>(), a->err, a->df, a->st); });
   check_launch(a);
   using C = typename Cplx<R>::T;
   size_t xs = npk;
@@ -909,7 +915,7 @@ void set_blocks_impl(moma_array *a, const void *blocks, int dtype) {
     if (a->tgram) {
       // Tensor cores: item D with A = Z_D (conjugated) and RHS rows Z_D[j]
       // gives y_D[j][i] = sum_k conj(Z_D[i][k]) Z_D[j][k], which by
-      // reciprocity is G_{-D}[i][j]; the summed-area pass reads it back
+      // reciprocity is G_{-D}[i][j]; the box-sum pass reads it back
       // reflected and conjugated.
       TcMats mA;
       mA.b = a->b; mA.T = nd;
@@ -1596,7 +1602,7 @@ void destroy_impl(moma_array *a) {
                     &a->Lpk, &a->lat_in, &a->lat_tmp, &a->t1, &a->bx, &a->by, &a->Vk, &a->Iw, &a->Vw,
                     &a->rw, &a->yw, &a->kbuf, &a->errbuf, &a->one_blk, &a->portsb, &a->zp_V, &a->zp_I, &a->zp_Y, &a->zp_tmp,
                     &a->tcA, &a->tcP, &a->partner, &a->Xblk, &a->gramA, &a->gramY, &a->lat_u, &a->mZB128,
-                    &a->mZC128, &a->mZB64, &a->mZC64, &a->mP, &a->mL, &a->mX};
+                    &a->mZC128, &a->mZB64, &a->mZC64, &a->mP, &a->mL, &a->mX, &a->Wb};
   for (DevBuf *b : bufs) b->release(a->dev_bytes);
   if (a->cs) {
     cudaStreamSynchronize(a->cs);
@@ -1652,7 +1658,6 @@ moma_status moma_create_array(int nx, int ny, int b, const moma_options *opt, vo
     a->axis_fft = opt && (opt->flags & MOMA_FLAG_AXIS_FFT);
     a->no_blk_precond = opt && (opt->flags & MOMA_FLAG_PRECOND_PER_ELEMENT);
     a->no_fused_arnoldi = opt && (opt->flags & MOMA_FLAG_SPLIT_ARNOLDI);
-    a->pdl = !(opt && (opt->flags & MOMA_FLAG_NO_PDL));
     if (opt && (opt->flags & MOMA_FLAG_TENSOR_ALWAYS)) a->tc_min_nr = 1;
     if (a->m > MOMA_MAX_RESTART) throw MomaError(MOMA_ERR_ARG, "restart too large");
     const int mx = (opt && opt->mx > 0) ? opt->mx : next_smooth(2 * nx - 1);
@@ -1781,11 +1786,11 @@ moma_status moma_get_precond_block(moma_array *a, int ex, int ey, void *out) {
   if (!a) { g_last_error = "array is NULL"; return MOMA_ERR_ARG; }
   return guarded([&] {
     if (!a->have_blocks) throw MomaError(MOMA_ERR_STATE, "no blocks");
-    if (!a->S.p) throw MomaError(MOMA_ERR_STATE, "set-up scratch was released");
+    if (!a->pbox) throw MomaError(MOMA_ERR_STATE, "set-up scratch was released");
     if (ex < 0 || ex >= a->nx || ey < 0 || ey >= a->ny || !out) throw MomaError(MOMA_ERR_ARG, "bad element");
     const size_t bytes = (size_t)a->b * a->b * sizeof(double2);
     a->one_blk.ensure(bytes, a->dev_bytes);
-    launch_box_one(a->S.as<double2>(), a->nx, a->ny, a->b, ex, ey, a->one_blk.as<double2>(), a->st);
+    launch_box_one(a->pbox, a->nx, a->b, ex, ey, a->one_blk.as<double2>(), a->st);
     check_launch(a);
     copy_out(a, out, a->one_blk.p, bytes);
     sync_and_check(a);
@@ -2200,6 +2205,8 @@ moma_status moma_release_setup(moma_array *a) {
     a->gramY.release(a->dev_bytes);
     a->T.release(a->dev_bytes);
     a->S.release(a->dev_bytes);
+    a->Wb.release(a->dev_bytes);
+    a->pbox = nullptr;
     a->Lpk.release(a->dev_bytes);
   });
 }
@@ -2223,6 +2230,7 @@ size_t moma_estimate_bytes(int nx, int ny, int b, const moma_options *opt, int n
   bytes += (size_t)(m + 1) * nr * N * esz + nr * nch * (m + 1) * c + nr * m * (m + 1) * c;  // Krylov
   bytes += 2 * nr * nel * c;                                                            // ports
   if (with_setup) bytes += nD * b * b * (c + 8) + (size_t)(2 * ny - 1) * Mx * nt * c + nel * nt * c;
+  if (with_setup) bytes += box_window_entries(nx, ny, b) * c;                           // box-sum windows
   const bool tens_setup = prec == MOMA_PREC_MIXED && !(opt && (opt->flags & MOMA_FLAG_NO_TENSOR)) && tc_supported(b);
   if (with_setup && tens_setup) bytes += tc_bytes((int)nD, b) + nD * b * b * 8;  // tensor-core Gram scratch
   const bool tensor = !(opt && (opt->flags & MOMA_FLAG_NO_TENSOR));

@@ -5,8 +5,9 @@
 // where D = j - e runs over the offsets that keep j inside the lattice:
 // W(e) = [-ex, Nx-1-ex] x [-ey, Ny-1-ey].  Following the paper's recipe
 // (precompute all block products, then sum subsets), G is formed once per
-// offset and P_e is read off a 2D summed-area table of G with four corner
-// lookups, so the cost is O((2Nx-1)(2Ny-1) b^3) instead of O(Nel^2 b^3).
+// offset and the box sums P_e are two passes of sliding windows over the
+// offset grid (rows, then columns), so the cost is O((2Nx-1)(2Ny-1) b^3)
+// for the products and O(Nx Ny b^2) per pass instead of O(Nel^2 b^3).
 // P_e = L_e L_e^H by Cholesky in FP64 (Sec. III-A), and P^{-1} is applied
 // as X_e^H X_e with X_e = L_e^{-1} stored packed.
 #include <algorithm>
@@ -79,75 +80,98 @@ void launch_gram(const void *blocks, int blocks_c128, int nD, int b, double2 *G,
 template void launch_gram<float>(const void *, int, int, int, double2 *, cudaStream_t);
 template void launch_gram<double>(const void *, int, int, int, double2 *, cudaStream_t);
 
-// ------------------------------------------------------ summed-area table --
-// S[y][x][e] <- sum_{y' <= y, x' <= x} S[y'][x'][e], in place, FP64.
-__global__ void sat_x_kernel(double2 *S, int ndx, int bb) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= bb) return;
-  double2 *row = S + (size_t)blockIdx.y * ndx * bb + e;
-  double2 run = make_double2(0, 0);
-  for (int x = 0; x < ndx; ++x) {
-    run = cadd(run, row[(size_t)x * bb]);
-    row[(size_t)x * bb] = run;
-  }
-}
-__global__ void sat_y_kernel(double2 *S, int ndy, int ndx, int bb) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= bb) return;
-  double2 *col = S + (size_t)blockIdx.y * bb + e;
-  double2 run = make_double2(0, 0);
-  for (int y = 0; y < ndy; ++y) {
-    run = cadd(run, col[(size_t)y * ndx * bb]);
-    col[(size_t)y * ndx * bb] = run;
-  }
-}
-// x pass from the reflected tensor-core Gram products:
-// S[y][x][e] = sum_{x' <= x} conj(Y[ndy-1-y][ndx-1-x'][e]).
-__global__ void sat_x_reflected_kernel(const float2 *Y, double2 *S, int ndy, int ndx, int bb) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= bb) return;
-  const int y = blockIdx.y;
-  const float2 *src = Y + (size_t)(ndy - 1 - y) * ndx * bb + e;
-  double2 *row = S + (size_t)y * ndx * bb + e;
-  double2 run = make_double2(0, 0);
-  for (int x = 0; x < ndx; ++x) {
-    const float2 g = src[(size_t)(ndx - 1 - x) * bb];
-    run.x += (double)g.x;
-    run.y -= (double)g.y;
-    row[(size_t)x * bb] = run;
-  }
-}
-void launch_sat_from_reflected(const float2 *Y, double2 *S, int ndy, int ndx, int bb, cudaStream_t st) {
-  sat_x_reflected_kernel<<<dim3((bb + 255) / 256, ndy), 256, 0, st>>>(Y, S, ndy, ndx, bb);
-  sat_y_kernel<<<dim3((bb + 255) / 256, ndx), 256, 0, st>>>(S, ndy, ndx, bb);
+// ---------------------------------------------------------------- box sums --
+// P_e = sum of G_D over the offsets of the element's box (Eq. 37): offset
+// indices x' in [Nx-1-ex, 2Nx-2-ex], y' in [Ny-1-ey, 2Ny-2-ey] of the
+// (2Ny-1) x (2Nx-1) grid.  Separable sliding windows in FP64: first the
+// row windows R[y'][ex] = sum over the x' window (one pass over each row of
+// G, each step adding the offset entering the window and subtracting the
+// one leaving it), then P[ey][ex] = the same over y' of R.  Only the lower
+// triangle is formed (P_e is Hermitian): entry t = i (i + 1) / 2 + k,
+// i >= k, row-major, taken from position i b + k of the b x b blocks, so
+// consecutive threads read consecutive entries of a block row.
+// G_D comes either from S (FP64, [D][b][b]) or, for the tensor-core Gram
+// products of the reflected offsets, as conj(Y_{-D}) (c64).
+MOMA_DEV int tri_row(int t) {  // row i of row-major lower-triangle entry t
+  int i = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+  while (i * (i + 1) / 2 > t) --i;
+  while ((i + 1) * (i + 2) / 2 <= t) ++i;
+  return i;
 }
 
-void launch_sat(double2 *S, int ndy, int ndx, int bb, cudaStream_t st) {
-  sat_x_kernel<<<dim3((bb + 255) / 256, ndy), 256, 0, st>>>(S, ndx, bb);
-  sat_y_kernel<<<dim3((bb + 255) / 256, ndx), 256, 0, st>>>(S, ndy, ndx, bb);
-}
-
-// Entry (i, k) of P_e from the summed-area table: box over offset indices
-// x' in [Nx-1-ex, 2Nx-2-ex], y' in [Ny-1-ey, 2Ny-2-ey].
-MOMA_DEV double2 box_entry(const double2 *S, int ndx, int bb, int x0, int x1, int y0, int y1, int ent) {
-  auto at = [&](int y, int x) -> double2 {
-    if (x < 0 || y < 0) return make_double2(0, 0);
-    return S[((size_t)y * ndx + x) * bb + ent];
+template <bool REFL>
+__global__ void box_rows_kernel(const double2 *__restrict__ S, const float2 *__restrict__ Y, double2 *__restrict__ R,
+                                int nx, int ndy, int b) {
+  const int npk = b * (b + 1) / 2;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= npk) return;
+  const int y = blockIdx.y, ndx = 2 * nx - 1, i = tri_row(t), k = t - i * (i + 1) / 2;
+  const size_t bb = (size_t)b * b, ent = (size_t)i * b + k;
+  auto G = [&](int x) -> double2 {
+    if constexpr (REFL) {
+      const float2 g = Y[((size_t)(ndy - 1 - y) * ndx + (ndx - 1 - x)) * bb + ent];
+      return make_double2((double)g.x, -(double)g.y);
+    } else {
+      return S[((size_t)y * ndx + x) * bb + ent];
+    }
   };
-  double2 v = at(y1, x1);
-  v = csub(v, at(y0 - 1, x1));
-  v = csub(v, at(y1, x0 - 1));
-  v = cadd(v, at(y0 - 1, x0 - 1));
-  return v;
+  // The loops are unrolled so that several independent loads are in flight
+  // ahead of the dependent FP64 additions.
+  double2 run = make_double2(0, 0);
+#pragma unroll 8
+  for (int x = nx - 1; x <= 2 * nx - 2; ++x) run = cadd(run, G(x));
+  double2 *out = R + (size_t)y * nx * npk + t;
+  out[0] = run;
+#pragma unroll 8
+  for (int ex = 1; ex < nx; ++ex) {  // window [nx-1-ex, 2nx-2-ex]
+    run = csub(cadd(run, G(nx - 1 - ex)), G(2 * nx - 1 - ex));
+    out[(size_t)ex * npk] = run;
+  }
 }
 
+__global__ void box_cols_kernel(const double2 *__restrict__ R, double2 *__restrict__ Pbox, int nx, int ny, int b) {
+  const int npk = b * (b + 1) / 2;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= npk) return;
+  const int ex = blockIdx.y;
+  auto Rv = [&](int y) { return R[((size_t)y * nx + ex) * npk + t]; };
+  double2 run = make_double2(0, 0);
+#pragma unroll 8
+  for (int y = ny - 1; y <= 2 * ny - 2; ++y) run = cadd(run, Rv(y));
+  Pbox[(size_t)ex * npk + t] = run;
+#pragma unroll 8
+  for (int ey = 1; ey < ny; ++ey) {  // window [ny-1-ey, 2ny-2-ey]
+    run = csub(cadd(run, Rv(ny - 1 - ey)), Rv(2 * ny - 1 - ey));
+    Pbox[((size_t)ey * nx + ex) * npk + t] = run;
+  }
+}
+
+size_t box_window_entries(int nx, int ny, int b) {
+  return ((size_t)(2 * ny - 1) * nx + (size_t)nx * ny) * ((size_t)b * (b + 1) / 2);
+}
+
+void launch_box_sums(const double2 *S, const float2 *Y, int nx, int ny, int b, double2 *W, cudaStream_t st) {
+  const int npk = b * (b + 1) / 2, ndy = 2 * ny - 1;
+  double2 *R = W, *Pbox = W + (size_t)ndy * nx * npk;
+  const dim3 g1((npk + 255) / 256, ndy), g2((npk + 255) / 256, nx);
+  if (Y) box_rows_kernel<true><<<g1, 256, 0, st>>>(S, Y, R, nx, ndy, b);
+  else box_rows_kernel<false><<<g1, 256, 0, st>>>(S, Y, R, nx, ndy, b);
+  box_cols_kernel<<<g2, 256, 0, st>>>(R, Pbox, nx, ny, b);
+}
+
+const double2 *box_sums_of(const double2 *W, int nx, int ny, int b) {
+  return W + (size_t)(2 * ny - 1) * nx * ((size_t)b * (b + 1) / 2);
+}
 
 // ------------------------------------------------------- box + Cholesky ---
-// One CTA per element.  The packed lower triangle of P_e is assembled from
-// the summed-area table (row by row, so reads of the table are contiguous)
-// and factored by a blocked right-looking Cholesky: a panel of CH_NB
-// columns is factored column by column, then the trailing triangle receives
-// the rank-CH_NB update A(i,k) -= sum_p L(i,p) conj(L(k,p)) in one sweep.
+// One CTA per element.  The lower triangle of P_e is loaded from the box
+// sums (row by row, contiguous) into the packed column-major layout and
+// factored by a blocked right-looking Cholesky over panels of CH_NB
+// columns, three CTA barriers per panel: (1) one warp factors the panel's
+// CH_NB x CH_NB diagonal block column by column (warp synchronisation
+// only); (2) every row below it is solved against that block by its own
+// thread (L21 = A21 L11^{-H}); (3) the trailing triangle receives the
+// rank-CH_NB update A(i,k) -= sum_p L(i,p) conj(L(k,p)) in one sweep.
 // The sweep is register-tiled: a thread owns a 2 x 2 tile of (i, k) entries
 // (rows i0, i0 + 1; columns k0, k0 + 1), so each of the panel's values it
 // loads serves two multiply-adds; tile t of the trailing triangle (row-major
@@ -194,57 +218,91 @@ MOMA_DEV void dfacc_fms_conj(DfAcc &re, DfAcc &im, const dfl2 &a, const dfl2 &b)
   dfacc_fma(im, a.x, b.y);
 }
 
-template <bool IN_SMEM, typename R>
-__global__ void __launch_bounds__(512) box_cholesky_kernel(const double2 *__restrict__ S, int nx, int ny, int b,
-                                                           double2 *__restrict__ Lpk, unsigned *err) {
-  using C = typename Cplx<R>::T;
-  static_assert(sizeof(C) == sizeof(double2), "the factor is stored in place of its FP64 output");
-  extern __shared__ __align__(16) unsigned char smraw[];
-  const int e = blockIdx.x, ex = e % nx, ey = e / nx;
-  const int npk = b * (b + 1) / 2;
-  C *A = IN_SMEM ? reinterpret_cast<C *>(smraw) : reinterpret_cast<C *>(Lpk + (size_t)e * npk);
-  const int ndx = 2 * nx - 1, bb = b * b;
-  const int x0 = nx - 1 - ex, x1 = 2 * nx - 2 - ex, y0 = ny - 1 - ey, y1 = 2 * ny - 2 - ey;
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
+// The packed lower triangle of columns j0 .. b-1 of a b x b matrix,
+// column-major: entry (i, k), k >= j0, at col(k)[i].  j0 = 0 is the whole
+// matrix; the trailing triangle of a hybrid factorisation lives in shared
+// memory with its own, smaller column bases.
+template <typename C>
+struct Tri {
+  C *base;
+  int j0, n;  // first column, order n = b - j0
+  MOMA_DEV int off(int k) const { return colbase(k - j0, n) - k; }
+  MOMA_DEV C *col(int k) const { return base + off(k); }
+};
 
-  // Assemble: linear index t runs over the lower triangle row by row.
-  for (int t = tid; t < npk; t += blockDim.x) {
-    int i = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
-    while (i * (i + 1) / 2 > t) --i;
-    while ((i + 1) * (i + 2) / 2 <= t) ++i;
-    const int k = t - i * (i + 1) / 2;
-    const int q = colbase(k, b) + i - k;
-    A[q] = cvt<C>(box_entry(S, ndx, bb, x0, x1, y0, y1, i * b + k));
-  }
-  __syncthreads();
-
-  for (int jb = 0; jb < b; jb += CH_NB) {
+// Panels jb = jfirst, jfirst + CH_NB, ... < jlast of the blocked
+// right-looking factorisation on T (every column from jfirst on lives in
+// T).  Returns false (after setting DEVERR_NOT_PD) if a pivot is not
+// positive.
+template <typename R, typename C>
+MOMA_DEV bool chol_panels(const Tri<C> T, int b, int jfirst, int jlast, R *inv_diag, int *not_pd, unsigned *err) {
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  for (int jb = jfirst; jb < jlast; jb += CH_NB) {
     const int je = min(jb + CH_NB, b);
-    // Panel: columns jb .. je-1, unblocked.
-    for (int j = jb; j < je; ++j) {
-      C *cj = A + colbase(j, b) - j;  // cj[i] = A(i, j), i >= j
-      const double d = real_part(cj[j]);
-      if (!(d > 0.0) || !isfinite(d)) {  // uniform: every thread reads the same value
-        if (tid == 0) atomicOr(err, DEVERR_NOT_PD);
-        return;
+    // (1) Diagonal block A(jb:je, jb:je), unblocked, by warp 0 alone (warp
+    // synchronisation only): column j is scaled by 1 / L(j, j) and the
+    // block's remaining lower entries (i, k), j < k <= i < je -- at most 28,
+    // one per lane -- receive -L(i, j) conj(L(k, j)).
+    if (w == 0) {
+      for (int j = jb; j < je; ++j) {
+        C *cj = T.col(j);  // cj[i] = A(i, j), i >= j
+        const double d = real_part(cj[j]);
+        if (!(d > 0.0) || !isfinite(d)) {  // uniform over the warp: every lane reads the same value
+          if (lane == 0) *not_pd = 1;
+          break;
+        }
+        R l;
+        const R inv_l = rsqrt_root(cj[j].x, &l);
+        __syncwarp();  // every lane has read A(j, j) before it is overwritten
+        if (lane == 0) {
+          cj[j] = mk(l, (R)0);
+          inv_diag[j - jb] = inv_l;
+        }
+        if (lane < je - j - 1) cj[j + 1 + lane] = cscale(cj[j + 1 + lane], inv_l);
+        __syncwarp();
+        const int m = je - j - 1;
+        if (lane < m * (m + 1) / 2) {
+          int kk = 0, r = lane;
+          while (r >= m - kk) {
+            r -= m - kk;
+            ++kk;
+          }
+          const int k = j + 1 + kk, i = k + r;
+          C *ck = T.col(k);
+          ck[i] = cfms_conj(cj[i], cj[k], ck[i]);
+        }
+        __syncwarp();
       }
-      R l;
-      const R inv_l = rsqrt_root(cj[j].x, &l);
-      __syncthreads();  // everyone has read d before the column is overwritten
-      for (int i = j + tid; i < b; i += blockDim.x) cj[i] = (i == j) ? mk(l, (R)0) : cscale(cj[i], inv_l);
-      __syncthreads();
-      for (int k = j + 1 + w; k < je; k += nw) {
-        C *ck = A + colbase(k, b) - k;
-        const C lkj = cj[k];
-        for (int i = k + lane; i < b; i += 32) ck[i] = cfms_conj(cj[i], lkj, ck[i]);
-      }
-      __syncthreads();
     }
-    // Trailing rank-(je - jb) update in 2 x 2 register tiles.
+    __syncthreads();
+    if (*not_pd) {
+      if (tid == 0) atomicOr(err, DEVERR_NOT_PD);
+      return false;
+    }
+    // (2) Rows below the block, one thread each: row i of L21 solves
+    // x L11^H = A(i, jb:je), x_k = (A(i, jb+k) - sum_{p<k} x_p conj(L(jb+k, jb+p))) / L(jb+k, jb+k).
     const int np = je - jb;
+    for (int i = je + tid; i < b; i += blockDim.x) {
+      // x_p (p < k) are read back from the row, where this thread stored them.
+#pragma unroll 1
+      for (int k = 0; k < np; ++k) {
+        C *ck = T.col(jb + k);
+        C v = ck[i];
+        if constexpr (std::is_same<R, dfl>::value) {
+          DfAcc re = dfacc(v.x), im = dfacc(v.y);
+          for (int p = 0; p < k; ++p) dfacc_fms_conj(re, im, T.col(jb + p)[i], T.col(jb + p)[jb + k]);
+          v = mk(dfacc_value(re), dfacc_value(im));
+        } else {
+          for (int p = 0; p < k; ++p) v = cfms_conj(T.col(jb + p)[i], T.col(jb + p)[jb + k], v);
+        }
+        ck[i] = cscale(v, inv_diag[k]);
+      }
+    }
+    __syncthreads();
+    // (3) Trailing rank-(je - jb) update in 2 x 2 register tiles.
     int pb[CH_NB];
 #pragma unroll
-    for (int p = 0; p < CH_NB; ++p) pb[p] = p < np ? colbase(jb + p, b) - (jb + p) : 0;
+    for (int p = 0; p < CH_NB; ++p) pb[p] = p < np ? T.off(jb + p) : 0;
     const int nt = (b - je + 1) / 2, ntiles = nt * (nt + 1) / 2;
     for (int t = tid; t < ntiles; t += blockDim.x) {
       int ti = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
@@ -254,8 +312,8 @@ __global__ void __launch_bounds__(512) box_cholesky_kernel(const double2 *__rest
       const int i0 = je + 2 * ti, k0 = je + 2 * tk;
       const bool r1 = i0 + 1 < b;    // second row present
       const bool up = ti != tk;      // (i0, k0 + 1) lies on or below the diagonal
-      C *c0 = A + colbase(k0, b) - k0;
-      C *c1 = A + colbase(k0 + 1, b) - (k0 + 1);  // dereferenced only where k0 + 1 <= i < b
+      C *c0 = T.col(k0);
+      C *c1 = T.col(k0 + 1);  // dereferenced only where k0 + 1 <= i < b
       C a00 = c0[i0];
       C a10 = r1 ? c0[i0 + 1] : czero<C>();
       C a01 = up ? c1[i0] : czero<C>();
@@ -266,7 +324,7 @@ __global__ void __launch_bounds__(512) box_cholesky_kernel(const double2 *__rest
 #pragma unroll
         for (int p = 0; p < CH_NB; ++p) {
           if (p < np) {
-            const C *lp = A + pb[p];
+            const C *lp = T.base + pb[p];
             const C li0 = lp[i0], lk0 = lp[k0];
             const C li1 = r1 ? lp[i0 + 1] : czero<C>();
             const C lk1 = (up || r1) ? lp[k0 + 1] : czero<C>();
@@ -284,7 +342,7 @@ __global__ void __launch_bounds__(512) box_cholesky_kernel(const double2 *__rest
 #pragma unroll
         for (int p = 0; p < CH_NB; ++p) {
           if (p < np) {
-            const C *lp = A + pb[p];
+            const C *lp = T.base + pb[p];
             const C li0 = lp[i0], lk0 = lp[k0];
             const C li1 = r1 ? lp[i0 + 1] : czero<C>();
             const C lk1 = (up || r1) ? lp[k0 + 1] : czero<C>();
@@ -304,46 +362,102 @@ __global__ void __launch_bounds__(512) box_cholesky_kernel(const double2 *__rest
     }
     __syncthreads();
   }
-  // FP64 output (in place for the global-memory variant: each thread
-  // converts the entries it reads).
+  return true;
+}
+
+// One CTA per element.  Columns 0 .. j0-1 are factored with the matrix in
+// global memory (the element's Lpk slot, in the working precision), the
+// rest with the trailing triangle of order b - j0 in shared memory: j0 is
+// the smallest panel boundary at which that triangle fits the launch's
+// shared-memory budget, chosen so that two CTAs share an SM (j0 = 0: the
+// whole factorisation in shared memory; j0 = b: none of it).
+template <typename R, int MINB>
+__global__ void __launch_bounds__(512, MINB) box_cholesky_kernel(const double2 *__restrict__ Pbox, int b, int j0,
+                                                                 double2 *__restrict__ Lpk, unsigned *err) {
+  using C = typename Cplx<R>::T;
+  static_assert(sizeof(C) == sizeof(double2), "the factor is stored in place of its FP64 output");
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ R inv_diag[CH_NB];  // 1 / L(j, j) of the current panel
+  __shared__ int not_pd;
+  const int e = blockIdx.x, tid = threadIdx.x;
+  const int npk = b * (b + 1) / 2, n0 = b - j0;
+  C *Ag = reinterpret_cast<C *>(Lpk + (size_t)e * npk);
+  C *As = reinterpret_cast<C *>(smraw);
+  const Tri<C> Tg{Ag, 0, b}, Ts{As, j0, n0};
+  if (tid == 0) not_pd = 0;
+
+  // Load P_e (row-major lower triangle): columns < j0 into global memory,
+  // the rest into shared memory (into global memory as well while the
+  // first panels still update them).
+  const double2 *src = Pbox + (size_t)e * npk;
+  for (int t = tid; t < npk; t += blockDim.x) {
+    const int i = tri_row(t), k = t - i * (i + 1) / 2;
+    const C v = cvt<C>(src[t]);
+    if (j0 > 0) Tg.col(k)[i] = v;
+    else Ts.col(k)[i] = v;
+  }
+  __syncthreads();
+  if (j0 > 0) {
+    if (!chol_panels<R>(Tg, b, 0, j0, inv_diag, &not_pd, err)) return;
+    if (j0 < b) {  // move the trailing triangle into shared memory
+      for (int q = tid; q < n0 * (n0 + 1) / 2; q += blockDim.x) {
+        int kk = 0;  // column of packed entry q of the order-n0 triangle
+        while (colbase(kk + 1, n0) <= q) ++kk;
+        const int k = j0 + kk, i = k + (q - colbase(kk, n0));
+        Ts.col(k)[i] = Tg.col(k)[i];
+      }
+      __syncthreads();
+    }
+  }
+  if (j0 < b && !chol_panels<R>(Ts, b, j0, b, inv_diag, &not_pd, err)) return;
+  // FP64 output: the global-memory columns in place (each thread converts
+  // the entries it reads), the shared-memory triangle copied out.
   double2 *dst = Lpk + (size_t)e * npk;
-  for (int q = tid; q < npk; q += blockDim.x) {
-    const C v = A[q];
-    dst[q] = cvt<double2>(v);
+  for (int k = 0; k < b; ++k) {
+    const C *ck = k < j0 ? Tg.col(k) : Ts.col(k);
+    for (int i = k + tid; i < b; i += blockDim.x) dst[colbase(k, b) + i - k] = cvt<double2>(ck[i]);
   }
 }
 
 template <typename R>
-static void launch_chol_typed(const double2 *S, int nx, int ny, int b, double2 *Lpk, unsigned *err, cudaStream_t st) {
-  // Shared memory: the packed triangle, if it fits.
-  const size_t npk = (size_t)b * (b + 1) / 2;
-  const size_t matb = npk * sizeof(double2);
-  const int nel = nx * ny;
+static void launch_chol_typed(const double2 *Pbox, int nel, int b, double2 *Lpk, unsigned *err, cudaStream_t st) {
+  // Two CTAs per SM where the trailing triangle of the later panels fits
+  // 110 KB of shared memory; the first panels then run in global memory.
+  constexpr size_t kHalf = 110 * 1024, kWhole = 210 * 1024;
+  auto tri_bytes = [](int n) { return (size_t)n * (n + 1) / 2 * sizeof(double2); };
   static int configured = 0;
   if (!configured) {
-    cudaFuncSetAttribute(box_cholesky_kernel<true, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
-    cudaFuncSetAttribute(box_cholesky_kernel<false, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+    cudaFuncSetAttribute(box_cholesky_kernel<R, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHalf);
+    cudaFuncSetAttribute(box_cholesky_kernel<R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWhole);
     configured = 1;
   }
-  if (matb <= 200 * 1024) box_cholesky_kernel<true, R><<<nel, 512, matb, st>>>(S, nx, ny, b, Lpk, err);
-  else box_cholesky_kernel<false, R><<<nel, 512, 0, st>>>(S, nx, ny, b, Lpk, err);
+  int j0 = 0;
+  while (j0 < b && tri_bytes(b - j0) > kHalf) j0 += CH_NB;
+  if (j0 < b && j0 <= 2 * CH_NB) {
+    box_cholesky_kernel<R, 2><<<nel, 512, tri_bytes(b - j0), st>>>(Pbox, b, j0, Lpk, err);
+    return;
+  }
+  j0 = 0;
+  while (j0 < b && tri_bytes(b - j0) > kWhole) j0 += CH_NB;
+  box_cholesky_kernel<R, 1><<<nel, 512, j0 < b ? tri_bytes(b - j0) : 0, st>>>(Pbox, b, j0, Lpk, err);
 }
 
-void launch_box_cholesky(const double2 *S, int nx, int ny, int b, double2 *Lpk, unsigned *err, bool df,
-                         cudaStream_t st) {
-  if (df) launch_chol_typed<dfl>(S, nx, ny, b, Lpk, err, st);
-  else launch_chol_typed<double>(S, nx, ny, b, Lpk, err, st);
+void launch_box_cholesky(const double2 *Pbox, int nel, int b, double2 *Lpk, unsigned *err, bool df, cudaStream_t st) {
+  if (df) launch_chol_typed<dfl>(Pbox, nel, b, Lpk, err, st);
+  else launch_chol_typed<double>(Pbox, nel, b, Lpk, err, st);
 }
 
-// Full P_e of one element (debug / inspection).
-__global__ void box_one_kernel(const double2 *S, int nx, int ny, int b, int ex, int ey, double2 *out) {
-  const int ndx = 2 * nx - 1, bb = b * b;
-  const int x0 = nx - 1 - ex, x1 = 2 * nx - 2 - ex, y0 = ny - 1 - ey, y1 = 2 * ny - 2 - ey;
-  for (int ent = blockIdx.x * blockDim.x + threadIdx.x; ent < bb; ent += gridDim.x * blockDim.x)
-    out[ent] = box_entry(S, ndx, bb, x0, x1, y0, y1, ent);
+// Full P_e (b x b, FP64) of one element from its lower triangle (debug /
+// inspection): the upper entries are the conjugates of their mirrors.
+__global__ void box_one_kernel(const double2 *Pe, int b, double2 *out) {
+  for (int ent = blockIdx.x * blockDim.x + threadIdx.x; ent < b * b; ent += gridDim.x * blockDim.x) {
+    const int i = ent / b, k = ent % b;
+    out[ent] = i >= k ? Pe[i * (i + 1) / 2 + k] : cconj(Pe[k * (k + 1) / 2 + i]);
+  }
 }
-void launch_box_one(const double2 *S, int nx, int ny, int b, int ex, int ey, double2 *out, cudaStream_t st) {
-  box_one_kernel<<<(b * b + 255) / 256, 256, 0, st>>>(S, nx, ny, b, ex, ey, out);
+void launch_box_one(const double2 *Pbox, int nx, int b, int ex, int ey, double2 *out, cudaStream_t st) {
+  box_one_kernel<<<(b * b + 255) / 256, 256, 0, st>>>(Pbox + ((size_t)ey * nx + ex) * ((size_t)b * (b + 1) / 2), b,
+                                                      out);
 }
 
 // ---------------------------------------------------- inverse factor -----

@@ -104,7 +104,6 @@ __global__ void __launch_bounds__(PACK_THREADS) pinv_pack_kernel(const float2 *_
 
 __global__ void __launch_bounds__(1024, 1) precond_blk_kernel(PbArgs A) {
   extern __shared__ __align__(128) unsigned char sm[];
-  pdl_enter();
   uint64_t *bar = reinterpret_cast<uint64_t *>(sm);  // [PB_MAX_NS]
   const int P = A.P, bp = 8 * P, b = A.b, nr = A.nr, ns = A.ns;
   unsigned char *stages = sm + 128;
@@ -238,8 +237,7 @@ void launch_pinv_pack(const void *Xpk, size_t x_stride, int nel, int b, void *Qb
 }
 
 void launch_precond_blk(const void *Qb, int nel, int b, int nr, const void *x, void *y, unsigned *err,
-                        const int *live, long long vstride, long long voff, int num_sms, cudaStream_t st,
-                        bool pdl) {
+                        const int *live, long long vstride, long long voff, int num_sms, cudaStream_t st) {
   if (!precond_blk_supported(b, nr, vstride, voff)) throw std::runtime_error("precond_blk: unsupported shape");
   PbArgs a;
   a.Xb = reinterpret_cast<const float2 *>(Qb);
@@ -263,7 +261,7 @@ void launch_precond_blk(const void *Qb, int nel, int b, int nr, const void *x, v
     configured = true;
   }
   const int grid = std::min(nel, num_sms);
-  launch_kernel(pdl, precond_blk_kernel, dim3(grid), dim3(32 * a.P), smem, st, a);
+  precond_blk_kernel<<<grid, 32 * a.P, smem, st>>>(a);
 }
 
 }  // namespace moma

@@ -24,7 +24,7 @@ MOMA_C128, MOMA_C64 = 0, 1
 MOMA_PREC_FP64, MOMA_PREC_MIXED = 0, 1
 MOMA_OP_Z, MOMA_OP_ZH, MOMA_OP_NORMAL = 0, 1, 2
 KERNEL_IDS = {"bin_c64": 0, "bin_c128": 1, "precond": 2, "fft_c64": 3, "block_fft": 4, "fft_c128": 5,
-              "gram": 6, "sat": 7, "cholesky": 8, "tri_inverse": 9, "krylov": 10, "misc": 11,
+              "gram": 6, "box_sums": 7, "cholesky": 8, "tri_inverse": 9, "krylov": 10, "misc": 11,
               "bin_tc": 12, "precond_tc": 13}
 
 # Every symbol include/moma.h declares, for the export check.
@@ -48,7 +48,6 @@ class MomaError(RuntimeError):
 
 MOMA_FLAG_NO_GRAPHS, MOMA_FLAG_NO_AUTOTUNE, MOMA_FLAG_NO_TENSOR, MOMA_FLAG_TENSOR_ALWAYS = 1, 2, 4, 8
 MOMA_FLAG_FP64_RESIDUAL, MOMA_FLAG_AXIS_FFT, MOMA_FLAG_PRECOND_PER_ELEMENT, MOMA_FLAG_SPLIT_ARNOLDI = 16, 32, 64, 128
-MOMA_FLAG_NO_PDL = 256
 
 
 class moma_options(ctypes.Structure):

@@ -95,7 +95,7 @@ def test_enum_constants_match_the_header(tmp_path):
         pytest.skip("no C compiler")
     text = open(HEADER).read()
     names = sorted(n for n in set(re.findall(r"\b(MOMA_[A-Z0-9_]+)\s*=", text)) if hasattr(mb, n))
-    assert any(n.startswith("MOMA_FLAG_") for n in names) and "MOMA_FLAG_NO_PDL" in names
+    assert any(n.startswith("MOMA_FLAG_") for n in names) and "MOMA_FLAG_SPLIT_ARNOLDI" in names
     lines = ['#include <stdio.h>', '#include "moma.h"', "int main(void) {"]
     lines += [f'  printf("{n} %lld\\n", (long long){n});' for n in names]
     lines += ["  return 0;", "}"]
