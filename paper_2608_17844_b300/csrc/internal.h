@@ -140,20 +140,21 @@ void launch_tc_product(const TcMats &m, const TcProduct &P, int num_sms, cudaStr
 // G_D = Z_D^H Z_D for every offset, output FP64 [nD][b][b].
 template <typename R>
 void launch_gram(const void *blocks, int blocks_c128, int nD, int b, double2 *G, cudaStream_t st);
-// Box sums P_e (Eq. 37) by separable sliding windows, FP64, lower
-// triangles only (row-major, b(b+1)/2 entries per element): G_D from S
-// (FP64 [nD][b][b]) or, if Y is set, conj(Y_{-D}) (the tensor-core Gram
-// products of the reflected offsets, c64).  W holds box_window_entries()
-// complex entries: the row windows, then the P_e ([Ny][Nx][b(b+1)/2], at
-// box_sums_of(W)).
+// Box sums P_e (Eq. 37) by separable sliding windows, lower triangles only
+// (row-major, b(b+1)/2 entries per element): G_D from S (FP64 [nD][b][b],
+// summed in FP64) or, if Y is set, conj(Y_{-D}) (the tensor-core Gram
+// products of the reflected offsets, c64, summed in double-FP32).  W holds
+// box_window_entries() 16-byte complex entries: the row windows, then the
+// P_e ([Ny][Nx][b(b+1)/2], at box_sums_of(W)), stored as dfl2 if df (the
+// double-FP32 factorisation reads them) else as double2.
 size_t box_window_entries(int nx, int ny, int b);
-void launch_box_sums(const double2 *S, const float2 *Y, int nx, int ny, int b, double2 *W, cudaStream_t st);
+void launch_box_sums(const double2 *S, const float2 *Y, int nx, int ny, int b, double2 *W, bool df, cudaStream_t st);
 const double2 *box_sums_of(const double2 *W, int nx, int ny, int b);
-// Cholesky of every P_e: L_e (packed lower, column-major, FP64) into Lpk.
-// df: factor in double-FP32 arithmetic (output still FP64).
+// Cholesky of every P_e (box sums in the precision df selects): L_e (packed
+// lower, column-major, FP64) into Lpk.  df: double-FP32 arithmetic.
 void launch_box_cholesky(const double2 *Pbox, int nel, int b, double2 *Lpk, unsigned *err, bool df, cudaStream_t st);
 // Full P_e (b x b, FP64) of one element from the box sums.
-void launch_box_one(const double2 *Pbox, int nx, int b, int ex, int ey, double2 *out, cudaStream_t st);
+void launch_box_one(const double2 *Pbox, int nx, int b, int ex, int ey, bool df, double2 *out, cudaStream_t st);
 // Inverse factor X_e = L_e^{-1}, packed column-major lower (as L_e), in precision R.
 template <typename R>
 void launch_tri_inverse(const double2 *Lpk, int nel, int b, void *X, size_t x_stride, cudaStream_t st);

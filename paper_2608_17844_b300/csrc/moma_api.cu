@@ -171,6 +171,7 @@ struct moma_array {
   DevBuf blk, T, S, Lpk;
   DevBuf Wb;                     // box-sum windows when S cannot hold them
   const double2 *pbox = nullptr;  // the box sums P_e (lower triangles), in S or Wb
+  bool pbox_df = false;           // ... stored as double-FP32 pairs
   cudaStream_t cs = nullptr;  // host-to-device copies of the blocks
   DevBuf gramA, gramY;        // tensor-core Gram products: split blocks, reflected products
   bool tgram = false;         // this set-up's Gram products ran on the tensor cores
@@ -826,10 +827,11 @@ void finish_preconditioner(moma_array *a) {
   }
   a->timed(PK_BOX, [&] {
     launch_box_sums(a->tgram ? nullptr : a->S.as<double2>(), a->tgram ? a->gramY.as<float2>() : nullptr, a->nx,
-                    a->ny, a->b, W, a->st);
+                    a->ny, a->b, W, a->df, a->st);
   });
   check_launch(a);
   a->pbox = box_sums_of(W, a->nx, a->ny, a->b);
+  a->pbox_df = a->df;
   const size_t npk = (size_t)a->b * (a->b + 1) / 2;
   a->Lpk.ensure((size_t)a->nel * npk * sizeof(double2), a->dev_bytes);
   a->timed(PK_CHOL, [&] { launch_box_cholesky(a->pbox, a->nel, a->b, a->Lpk.as<double2>(), a->err, a->df, a->st); });
@@ -1790,7 +1792,7 @@ moma_status moma_get_precond_block(moma_array *a, int ex, int ey, void *out) {
     if (ex < 0 || ex >= a->nx || ey < 0 || ey >= a->ny || !out) throw MomaError(MOMA_ERR_ARG, "bad element");
     const size_t bytes = (size_t)a->b * a->b * sizeof(double2);
     a->one_blk.ensure(bytes, a->dev_bytes);
-    launch_box_one(a->pbox, a->nx, a->b, ex, ey, a->one_blk.as<double2>(), a->st);
+    launch_box_one(a->pbox, a->nx, a->b, ex, ey, a->pbox_df, a->one_blk.as<double2>(), a->st);
     check_launch(a);
     copy_out(a, out, a->one_blk.p, bytes);
     sync_and_check(a);

@@ -80,89 +80,6 @@ void launch_gram(const void *blocks, int blocks_c128, int nD, int b, double2 *G,
 template void launch_gram<float>(const void *, int, int, int, double2 *, cudaStream_t);
 template void launch_gram<double>(const void *, int, int, int, double2 *, cudaStream_t);
 
-// ---------------------------------------------------------------- box sums --
-// P_e = sum of G_D over the offsets of the element's box (Eq. 37): offset
-// indices x' in [Nx-1-ex, 2Nx-2-ex], y' in [Ny-1-ey, 2Ny-2-ey] of the
-// (2Ny-1) x (2Nx-1) grid.  Separable sliding windows in FP64: first the
-// row windows R[y'][ex] = sum over the x' window (one pass over each row of
-// G, each step adding the offset entering the window and subtracting the
-// one leaving it), then P[ey][ex] = the same over y' of R.  Only the lower
-// triangle is formed (P_e is Hermitian): entry t = i (i + 1) / 2 + k,
-// i >= k, row-major, taken from position i b + k of the b x b blocks, so
-// consecutive threads read consecutive entries of a block row.
-// G_D comes either from S (FP64, [D][b][b]) or, for the tensor-core Gram
-// products of the reflected offsets, as conj(Y_{-D}) (c64).
-MOMA_DEV int tri_row(int t) {  // row i of row-major lower-triangle entry t
-  int i = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
-  while (i * (i + 1) / 2 > t) --i;
-  while ((i + 1) * (i + 2) / 2 <= t) ++i;
-  return i;
-}
-
-template <bool REFL>
-__global__ void box_rows_kernel(const double2 *__restrict__ S, const float2 *__restrict__ Y, double2 *__restrict__ R,
-                                int nx, int ndy, int b) {
-  const int npk = b * (b + 1) / 2;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= npk) return;
-  const int y = blockIdx.y, ndx = 2 * nx - 1, i = tri_row(t), k = t - i * (i + 1) / 2;
-  const size_t bb = (size_t)b * b, ent = (size_t)i * b + k;
-  auto G = [&](int x) -> double2 {
-    if constexpr (REFL) {
-      const float2 g = Y[((size_t)(ndy - 1 - y) * ndx + (ndx - 1 - x)) * bb + ent];
-      return make_double2((double)g.x, -(double)g.y);
-    } else {
-      return S[((size_t)y * ndx + x) * bb + ent];
-    }
-  };
-  // The loops are unrolled so that several independent loads are in flight
-  // ahead of the dependent FP64 additions.
-  double2 run = make_double2(0, 0);
-#pragma unroll 8
-  for (int x = nx - 1; x <= 2 * nx - 2; ++x) run = cadd(run, G(x));
-  double2 *out = R + (size_t)y * nx * npk + t;
-  out[0] = run;
-#pragma unroll 8
-  for (int ex = 1; ex < nx; ++ex) {  // window [nx-1-ex, 2nx-2-ex]
-    run = csub(cadd(run, G(nx - 1 - ex)), G(2 * nx - 1 - ex));
-    out[(size_t)ex * npk] = run;
-  }
-}
-
-__global__ void box_cols_kernel(const double2 *__restrict__ R, double2 *__restrict__ Pbox, int nx, int ny, int b) {
-  const int npk = b * (b + 1) / 2;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= npk) return;
-  const int ex = blockIdx.y;
-  auto Rv = [&](int y) { return R[((size_t)y * nx + ex) * npk + t]; };
-  double2 run = make_double2(0, 0);
-#pragma unroll 8
-  for (int y = ny - 1; y <= 2 * ny - 2; ++y) run = cadd(run, Rv(y));
-  Pbox[(size_t)ex * npk + t] = run;
-#pragma unroll 8
-  for (int ey = 1; ey < ny; ++ey) {  // window [ny-1-ey, 2ny-2-ey]
-    run = csub(cadd(run, Rv(ny - 1 - ey)), Rv(2 * ny - 1 - ey));
-    Pbox[((size_t)ey * nx + ex) * npk + t] = run;
-  }
-}
-
-size_t box_window_entries(int nx, int ny, int b) {
-  return ((size_t)(2 * ny - 1) * nx + (size_t)nx * ny) * ((size_t)b * (b + 1) / 2);
-}
-
-void launch_box_sums(const double2 *S, const float2 *Y, int nx, int ny, int b, double2 *W, cudaStream_t st) {
-  const int npk = b * (b + 1) / 2, ndy = 2 * ny - 1;
-  double2 *R = W, *Pbox = W + (size_t)ndy * nx * npk;
-  const dim3 g1((npk + 255) / 256, ndy), g2((npk + 255) / 256, nx);
-  if (Y) box_rows_kernel<true><<<g1, 256, 0, st>>>(S, Y, R, nx, ndy, b);
-  else box_rows_kernel<false><<<g1, 256, 0, st>>>(S, Y, R, nx, ndy, b);
-  box_cols_kernel<<<g2, 256, 0, st>>>(R, Pbox, nx, ny, b);
-}
-
-const double2 *box_sums_of(const double2 *W, int nx, int ny, int b) {
-  return W + (size_t)(2 * ny - 1) * nx * ((size_t)b * (b + 1) / 2);
-}
-
 // ------------------------------------------------------- box + Cholesky ---
 // One CTA per element.  The lower triangle of P_e is loaded from the box
 // sums (row by row, contiguous) into the packed column-major layout and
@@ -216,6 +133,146 @@ MOMA_DEV void dfacc_fms_conj(DfAcc &re, DfAcc &im, const dfl2 &a, const dfl2 &b)
   dfacc_fma(re, -a.y, b.y);
   dfacc_fma(im, -a.y, b.x);
   dfacc_fma(im, a.x, b.y);
+}
+
+// ---------------------------------------------------------------- box sums --
+// P_e = sum of G_D over the offsets of the element's box (Eq. 37): offset
+// indices x' in [Nx-1-ex, 2Nx-2-ex], y' in [Ny-1-ey, 2Ny-2-ey] of the
+// (2Ny-1) x (2Nx-1) grid.  Separable sliding windows: first the row windows
+// R[y'][ex] = sum over the x' window (one pass over each row of G, each
+// step adding the offset entering the window and subtracting the one
+// leaving it), then P[ey][ex] = the same over y' of R.  Only the lower
+// triangle is formed (P_e is Hermitian): entry t = i (i + 1) / 2 + k,
+// i >= k, row-major, taken from position i b + k of the b x b blocks, so
+// consecutive threads read consecutive entries of a block row.
+// G_D comes either from S (FP64, [D][b][b]) or, for the tensor-core Gram
+// products of the reflected offsets, as conj(Y_{-D}) (c64).  The sums run
+// in FP64 (ACC = double) or, for the c64 products, in double-FP32 (ACC =
+// dfl: B300's FP64 rate would bound the pass), stored as pairs; P_e is
+// written in the precision of the factorisation that reads it (OUT =
+// double2 or dfl2).
+MOMA_DEV int tri_row(int t) {  // row i of row-major lower-triangle entry t
+  int i = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+  while (i * (i + 1) / 2 > t) --i;
+  while ((i + 1) * (i + 2) / 2 <= t) ++i;
+  return i;
+}
+
+// Running sums of complex terms: FP64, or double-FP32 accumulators whose
+// additions are exact two-sums (errors gathered in the low part) and which
+// are renormalised at every output.
+struct WinD {
+  double2 v = make_double2(0, 0);
+  MOMA_DEV void add(double2 a) { v = cadd(v, a); }
+  MOMA_DEV void sub(double2 a) { v = csub(v, a); }
+  MOMA_DEV void add(float2 a) { v = cadd(v, make_double2(a.x, a.y)); }
+  MOMA_DEV void sub(float2 a) { v = csub(v, make_double2(a.x, a.y)); }
+  MOMA_DEV double2 out() const { return v; }
+};
+struct WinF {
+  DfAcc re{0.f, 0.f}, im{0.f, 0.f};
+  MOMA_DEV static void acc(DfAcc &a, float x) {
+    const dfl q = df_two_sum(a.s, x);
+    a.s = q.hi;
+    a.t = __fadd_rn(a.t, q.lo);
+  }
+  MOMA_DEV void add(float2 a) { acc(re, a.x); acc(im, a.y); }
+  MOMA_DEV void sub(float2 a) { acc(re, -a.x); acc(im, -a.y); }
+  MOMA_DEV void add(const dfl2 &a) {
+    acc(re, a.x.hi); re.t = __fadd_rn(re.t, a.x.lo);
+    acc(im, a.y.hi); im.t = __fadd_rn(im.t, a.y.lo);
+  }
+  MOMA_DEV void sub(const dfl2 &a) {
+    acc(re, -a.x.hi); re.t = __fsub_rn(re.t, a.x.lo);
+    acc(im, -a.y.hi); im.t = __fsub_rn(im.t, a.y.lo);
+  }
+  MOMA_DEV dfl2 out() {
+    const dfl r = df_fast_two_sum(re.s, re.t), i = df_fast_two_sum(im.s, im.t);
+    re = DfAcc{r.hi, r.lo};
+    im = DfAcc{i.hi, i.lo};
+    return dfl2{r, i};
+  }
+};
+template <typename ACC> struct WinOf;
+template <> struct WinOf<double> { using W = WinD; using T = double2; };
+template <> struct WinOf<dfl> { using W = WinF; using T = dfl2; };
+
+template <bool REFL, typename ACC>
+__global__ void box_rows_kernel(const double2 *__restrict__ S, const float2 *__restrict__ Y,
+                                typename WinOf<ACC>::T *__restrict__ R, int nx, int ndy, int b) {
+  const int npk = b * (b + 1) / 2;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= npk) return;
+  const int y = blockIdx.y, ndx = 2 * nx - 1, i = tri_row(t), k = t - i * (i + 1) / 2;
+  const size_t bb = (size_t)b * b, ent = (size_t)i * b + k;
+  auto G = [&](int x) {
+    if constexpr (REFL) {
+      const float2 g = Y[((size_t)(ndy - 1 - y) * ndx + (ndx - 1 - x)) * bb + ent];
+      return make_float2(g.x, -g.y);
+    } else {
+      return S[((size_t)y * ndx + x) * bb + ent];
+    }
+  };
+  typename WinOf<ACC>::W run;
+  // Unrolled so that several independent loads are in flight ahead of the
+  // dependent additions.
+#pragma unroll 8
+  for (int x = nx - 1; x <= 2 * nx - 2; ++x) run.add(G(x));
+  auto *out = R + (size_t)y * nx * npk + t;
+  out[0] = run.out();
+#pragma unroll 8
+  for (int ex = 1; ex < nx; ++ex) {  // window [nx-1-ex, 2nx-2-ex]
+    run.add(G(nx - 1 - ex));
+    run.sub(G(2 * nx - 1 - ex));
+    out[(size_t)ex * npk] = run.out();
+  }
+}
+
+template <typename ACC, typename OUT>
+__global__ void box_cols_kernel(const typename WinOf<ACC>::T *__restrict__ R, OUT *__restrict__ Pbox, int nx, int ny,
+                                int b) {
+  const int npk = b * (b + 1) / 2;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= npk) return;
+  const int ex = blockIdx.y;
+  auto Rv = [&](int y) { return R[((size_t)y * nx + ex) * npk + t]; };
+  typename WinOf<ACC>::W run;
+#pragma unroll 8
+  for (int y = ny - 1; y <= 2 * ny - 2; ++y) run.add(Rv(y));
+  Pbox[(size_t)ex * npk + t] = cvt<OUT>(run.out());
+#pragma unroll 8
+  for (int ey = 1; ey < ny; ++ey) {  // window [ny-1-ey, 2ny-2-ey]
+    run.add(Rv(ny - 1 - ey));
+    run.sub(Rv(2 * ny - 1 - ey));
+    Pbox[((size_t)ey * nx + ex) * npk + t] = cvt<OUT>(run.out());
+  }
+}
+
+size_t box_window_entries(int nx, int ny, int b) {
+  return ((size_t)(2 * ny - 1) * nx + (size_t)nx * ny) * ((size_t)b * (b + 1) / 2);
+}
+
+template <bool REFL, typename ACC>
+static void box_sums_typed(const double2 *S, const float2 *Y, int nx, int ny, int b, double2 *W, bool df,
+                           cudaStream_t st) {
+  using T = typename WinOf<ACC>::T;
+  static_assert(sizeof(T) == sizeof(double2), "window sums are 16-byte complex values");
+  const int npk = b * (b + 1) / 2, ndy = 2 * ny - 1;
+  T *R = reinterpret_cast<T *>(W);
+  double2 *P = W + (size_t)ndy * nx * npk;
+  const dim3 g1((npk + 255) / 256, ndy), g2((npk + 255) / 256, nx);
+  box_rows_kernel<REFL, ACC><<<g1, 256, 0, st>>>(S, Y, R, nx, ndy, b);
+  if (df) box_cols_kernel<ACC, dfl2><<<g2, 256, 0, st>>>(R, reinterpret_cast<dfl2 *>(P), nx, ny, b);
+  else box_cols_kernel<ACC, double2><<<g2, 256, 0, st>>>(R, P, nx, ny, b);
+}
+
+void launch_box_sums(const double2 *S, const float2 *Y, int nx, int ny, int b, double2 *W, bool df, cudaStream_t st) {
+  if (Y) box_sums_typed<true, dfl>(S, Y, nx, ny, b, W, df, st);
+  else box_sums_typed<false, double>(S, Y, nx, ny, b, W, df, st);
+}
+
+const double2 *box_sums_of(const double2 *W, int nx, int ny, int b) {
+  return W + (size_t)(2 * ny - 1) * nx * ((size_t)b * (b + 1) / 2);
 }
 
 // The packed lower triangle of columns j0 .. b-1 of a b x b matrix,
@@ -389,10 +446,10 @@ __global__ void __launch_bounds__(512, MINB) box_cholesky_kernel(const double2 *
   // Load P_e (row-major lower triangle): columns < j0 into global memory,
   // the rest into shared memory (into global memory as well while the
   // first panels still update them).
-  const double2 *src = Pbox + (size_t)e * npk;
+  const C *src = reinterpret_cast<const C *>(Pbox) + (size_t)e * npk;  // stored in the working precision
   for (int t = tid; t < npk; t += blockDim.x) {
     const int i = tri_row(t), k = t - i * (i + 1) / 2;
-    const C v = cvt<C>(src[t]);
+    const C v = src[t];
     if (j0 > 0) Tg.col(k)[i] = v;
     else Ts.col(k)[i] = v;
   }
@@ -449,15 +506,19 @@ void launch_box_cholesky(const double2 *Pbox, int nel, int b, double2 *Lpk, unsi
 
 // Full P_e (b x b, FP64) of one element from its lower triangle (debug /
 // inspection): the upper entries are the conjugates of their mirrors.
-__global__ void box_one_kernel(const double2 *Pe, int b, double2 *out) {
+template <typename T>
+__global__ void box_one_kernel(const T *Pe, int b, double2 *out) {
   for (int ent = blockIdx.x * blockDim.x + threadIdx.x; ent < b * b; ent += gridDim.x * blockDim.x) {
     const int i = ent / b, k = ent % b;
-    out[ent] = i >= k ? Pe[i * (i + 1) / 2 + k] : cconj(Pe[k * (k + 1) / 2 + i]);
+    const double2 v = cvt<double2>(Pe[i >= k ? i * (i + 1) / 2 + k : k * (k + 1) / 2 + i]);
+    out[ent] = i >= k ? v : cconj(v);
   }
 }
-void launch_box_one(const double2 *Pbox, int nx, int b, int ex, int ey, double2 *out, cudaStream_t st) {
-  box_one_kernel<<<(b * b + 255) / 256, 256, 0, st>>>(Pbox + ((size_t)ey * nx + ex) * ((size_t)b * (b + 1) / 2), b,
-                                                      out);
+void launch_box_one(const double2 *Pbox, int nx, int b, int ex, int ey, bool df, double2 *out, cudaStream_t st) {
+  const size_t off = ((size_t)ey * nx + ex) * ((size_t)b * (b + 1) / 2);
+  const int grid = (b * b + 255) / 256;
+  if (df) box_one_kernel<<<grid, 256, 0, st>>>(reinterpret_cast<const dfl2 *>(Pbox) + off, b, out);
+  else box_one_kernel<<<grid, 256, 0, st>>>(Pbox + off, b, out);
 }
 
 // ---------------------------------------------------- inverse factor -----
