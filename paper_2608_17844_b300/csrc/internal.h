@@ -156,8 +156,12 @@ void launch_box_cholesky(const double2 *Pbox, int nel, int b, double2 *Lpk, unsi
 // Full P_e (b x b, FP64) of one element from the box sums.
 void launch_box_one(const double2 *Pbox, int nx, int b, int ex, int ey, bool df, double2 *out, cudaStream_t st);
 // Inverse factor X_e = L_e^{-1}, packed column-major lower (as L_e), in precision R.
+// Qb (c64 only, may be null): also P_e^{-1} = X_e^H X_e in the blocked layout
+// of launch_precond_blk; returns whether it was written (the blocked c64
+// kernel, b a multiple of 8 up to 160), else launch_pinv_pack must form it.
 template <typename R>
-void launch_tri_inverse(const double2 *Lpk, int nel, int b, void *X, size_t x_stride, cudaStream_t st);
+bool launch_tri_inverse(const double2 *Lpk, int nel, int b, void *X, size_t x_stride, cudaStream_t st,
+                        void *Qb = nullptr);
 // y_e = X_e^H X_e x_e for each element; vectors: RHS q, element e, basis k at
 // q * vstride + voff + e * b + k (vstride <= 0: nel * b).
 template <typename R>

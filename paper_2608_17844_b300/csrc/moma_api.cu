@@ -841,14 +841,20 @@ void finish_preconditioner(moma_array *a) {
   while ((xs * sizeof(C)) % 16) ++xs;
   a->x_stride = xs;
   a->Xinv.ensure((size_t)a->nel * xs * sizeof(C), a->dev_bytes);
-  a->timed(PK_TRINV, [&] { launch_tri_inverse<R>(a->Lpk.as<double2>(), a->nel, a->b, a->Xinv.p, xs, a->st); });
-  check_launch(a);
   // c64: also P_e^{-1} = X_e^H X_e in the blocked layout of the streaming apply.
   a->xblk_ready = false;
-  if (std::is_same<R, float>::value && !a->no_blk_precond && precond_blk_supported(a->b, 1, 2, 0)) {
-    a->Xblk.ensure((size_t)a->nel * xblk_entries(a->b) * sizeof(float2), a->dev_bytes);
-    a->timed(PK_TRINV, [&] { launch_pinv_pack(a->Xinv.p, a->x_stride, a->nel, a->b, a->Xblk.p, a->st); });
-    check_launch(a);
+  const bool blk = std::is_same<R, float>::value && !a->no_blk_precond && precond_blk_supported(a->b, 1, 2, 0);
+  if (blk) a->Xblk.ensure((size_t)a->nel * xblk_entries(a->b) * sizeof(float2), a->dev_bytes);
+  bool q_done = false;
+  a->timed(PK_TRINV, [&] {
+    q_done = launch_tri_inverse<R>(a->Lpk.as<double2>(), a->nel, a->b, a->Xinv.p, xs, a->st, blk ? a->Xblk.p : nullptr);
+  });
+  check_launch(a);
+  if (blk) {
+    if (!q_done) {
+      a->timed(PK_TRINV, [&] { launch_pinv_pack(a->Xinv.p, a->x_stride, a->nel, a->b, a->Xblk.p, a->st); });
+      check_launch(a);
+    }
     a->xblk_ready = true;
   }
 }

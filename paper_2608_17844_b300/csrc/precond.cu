@@ -99,6 +99,15 @@ template void launch_gram<double>(const void *, int, int, int, double2 *, cudaSt
 constexpr int CH_NB = 8;
 
 MOMA_HD int colbase(int k, int b) { return k * b - k * (k - 1) / 2; }  // start of column k (packed)
+// Column k of packed column-major entry t: colbase(k) <= t < colbase(k + 1).
+MOMA_DEV int packed_col(int t, int b) {
+  const float c = (float)(2 * b + 1);
+  int k = (int)((c - sqrtf(c * c - 8.0f * (float)t)) * 0.5f);
+  k = max(0, min(k, b - 1));
+  while (k > 0 && colbase(k, b) > t) --k;
+  while (k + 1 < b && colbase(k + 1, b) <= t) ++k;
+  return k;
+}
 
 // Arithmetic R: double (plain path) or dfl, double-FP32 pairs of ~48 bits
 // (mixed path, where B300's FP64 rate would bound the factorisation; the
@@ -447,11 +456,22 @@ __global__ void __launch_bounds__(512, MINB) box_cholesky_kernel(const double2 *
   // the rest into shared memory (into global memory as well while the
   // first panels still update them).
   const C *src = reinterpret_cast<const C *>(Pbox) + (size_t)e * npk;  // stored in the working precision
-  for (int t = tid; t < npk; t += blockDim.x) {
-    const int i = tri_row(t), k = t - i * (i + 1) / 2;
-    const C v = src[t];
-    if (j0 > 0) Tg.col(k)[i] = v;
-    else Ts.col(k)[i] = v;
+  for (int t0 = tid; t0 < npk; t0 += 8 * blockDim.x) {  // batches of 8 loads in flight per thread
+    C v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int t = t0 + u * blockDim.x;
+      v[u] = t < npk ? src[t] : czero<C>();
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int t = t0 + u * blockDim.x;
+      if (t < npk) {
+        const int i = tri_row(t), k = t - i * (i + 1) / 2;
+        if (j0 > 0) Tg.col(k)[i] = v[u];
+        else Ts.col(k)[i] = v[u];
+      }
+    }
   }
   __syncthreads();
   if (j0 > 0) {
@@ -599,9 +619,165 @@ __global__ void __launch_bounds__(256) tri_inverse_kernel(const double2 *__restr
   }
 }
 
+// Blocked c64 inverse factor for b a multiple of 8 (b <= 160): L (FP32)
+// and X in shared memory as 8 x 8 blocks of the lower triangle (block
+// (p, q), q <= p, at p (p + 1) / 2 + q, row-major inside).  (1) every
+// diagonal block is inverted (one lane per column, forward substitution);
+// (2) block column j of X follows from X_jj = L_jj^{-1} and, down the
+// column, X_ij = -L_ii^{-1} sum_{k=j}^{i-1} L_ik X_kj -- the sum as 8 x 8 x 8
+// block products, lane (r, c) holding entries (r, c) and (r + 4, c).  Warp w
+// owns block columns w and P - 1 - w, whose block products add up to the
+// same count for every warp.  X is written packed column-major and, if Qb is
+// set, (3) Q = X^H X as well, in the blocked layout of the streaming apply
+// (precond_blk.cu): Q_pq = sum_{k >= p} X_kp^H X_kq, blocks dealt to the
+// warps round-robin.
+constexpr int TIB_MAXP = 20;
+
+template <int NB>
+__global__ void __launch_bounds__(32 * (TIB_MAXP / 2)) tri_inverse_blocked_kernel(const double2 *__restrict__ Lpk,
+                                                                                    int b, float2 *X,
+                                                                                    size_t x_stride, float2 *Qb,
+                                                                                    size_t qbs) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int P = b / NB, nblk = P * (P + 1) / 2;
+  float2 *Lb = reinterpret_cast<float2 *>(smraw);  // [nblk][64]
+  float2 *Xb = Lb + (size_t)nblk * 64;              // [nblk][64]
+  float2 *Db = Xb + (size_t)nblk * 64;              // [P][64] diagonal-block inverses
+  float2 *Sw = Db + (size_t)P * 64;                 // [warps][64] scratch
+  const int e = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
+  const size_t npk = (size_t)b * (b + 1) / 2;
+  const double2 *Le = Lpk + (size_t)e * npk;
+  float2 *Xe = X + (size_t)e * x_stride;
+  auto blk = [&](int p, int q) { return (p * (p + 1) / 2 + q) * 64; };
+  // Load L (columns by warps, coalesced); zero the diagonal blocks' upper parts.
+  for (int p = w; p < P; p += nw)
+    for (int t = lane; t < 64; t += 32)
+      if ((t & 7) > (t >> 3)) Lb[blk(p, p) + t] = make_float2(0.f, 0.f);
+  // One flat pass over the packed entries in batches of 16 per thread: the
+  // batch's loads are all issued before any index arithmetic, so they are
+  // in flight together.
+  for (int t0 = tid; t0 < (int)npk; t0 += 16 * blockDim.x) {
+    double2 v[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int t = t0 + u * blockDim.x;
+      v[u] = t < (int)npk ? Le[t] : make_double2(0, 0);
+    }
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int t = t0 + u * blockDim.x;
+      if (t < (int)npk) {
+        const int k = packed_col(t, b), i = k + t - colbase(k, b);
+        Lb[blk(i / NB, k / NB) + (i % NB) * NB + k % NB] = cvt<float2>(v[u]);
+      }
+    }
+  }
+  for (size_t q = npk + tid; q < x_stride; q += blockDim.x) Xe[q] = make_float2(0.f, 0.f);  // pad
+  __syncthreads();
+  // (1) Diagonal-block inverses: lane c < 8 of a warp solves column c.
+  for (int p = w; p < P; p += nw) {
+    const float2 *L = Lb + blk(p, p);
+    float2 *D = Db + p * 64;
+    if (lane < NB) {
+      const int c = lane;
+      float2 x[NB];
+#pragma unroll
+      for (int r = 0; r < NB; ++r) {
+        float2 v = make_float2(r == c ? 1.f : 0.f, 0.f);
+#pragma unroll
+        for (int t = 0; t < NB; ++t)
+          if (t < r) v = csub(v, cmul(L[r * NB + t], x[t]));
+        x[r] = r < c ? make_float2(0.f, 0.f) : cscale(v, 1.0f / L[r * NB + r].x);
+      }
+#pragma unroll
+      for (int r = 0; r < NB; ++r) D[r * NB + c] = x[r];
+    }
+  }
+  __syncthreads();
+  // (2) Block columns.
+  const int r0 = lane >> 3, c = lane & 7;
+  float2 *S = Sw + w * 64;
+  for (int pass = 0; pass < 2; ++pass) {
+    const int j = pass == 0 ? w : P - 1 - w;
+    if (j >= P || (pass == 1 && j <= w)) continue;
+    for (int rr = r0; rr < NB; rr += 4) Xb[blk(j, j) + rr * NB + c] = Db[j * 64 + rr * NB + c];
+    __syncwarp();
+    for (int i = j + 1; i < P; ++i) {
+      float2 a0 = make_float2(0.f, 0.f), a1 = a0;
+      for (int k = j; k < i; ++k) {
+        const float2 *Lik = Lb + blk(i, k), *Xkj = Xb + blk(k, j);
+#pragma unroll
+        for (int t = 0; t < NB; ++t) {
+          const float2 xv = Xkj[t * NB + c];
+          a0 = cfma(Lik[r0 * NB + t], xv, a0);
+          a1 = cfma(Lik[(r0 + 4) * NB + t], xv, a1);
+        }
+      }
+      S[r0 * NB + c] = a0;
+      S[(r0 + 4) * NB + c] = a1;
+      __syncwarp();
+      const float2 *D = Db + i * 64;
+      float2 y0 = make_float2(0.f, 0.f), y1 = y0;
+#pragma unroll
+      for (int t = 0; t < NB; ++t) {
+        const float2 sv = S[t * NB + c];
+        y0 = cfma(D[r0 * NB + t], sv, y0);  // D is lower triangular: zeros above its diagonal
+        y1 = cfma(D[(r0 + 4) * NB + t], sv, y1);
+      }
+      Xb[blk(i, j) + r0 * NB + c] = make_float2(-y0.x, -y0.y);
+      Xb[blk(i, j) + (r0 + 4) * NB + c] = make_float2(-y1.x, -y1.y);
+      __syncwarp();  // S reused, X_ij read by the next block row
+    }
+  }
+  __syncthreads();
+  // X packed column-major (coalesced).
+  for (int t = tid; t < (int)npk; t += blockDim.x) {
+    const int k = packed_col(t, b), i = k + t - colbase(k, b);
+    Xe[t] = Xb[blk(i / NB, k / NB) + (i % NB) * NB + k % NB];
+  }
+  if (!Qb) return;
+  // (3) Q = X^H X, entry (r, c) of block (p, q) at c * 8 + (r ^ c).
+  float2 *Qe = Qb + (size_t)e * qbs;
+  for (int bq = w; bq < nblk; bq += nw) {
+    int p = 0;
+    while ((p + 1) * (p + 2) / 2 <= bq) ++p;
+    const int q = bq - p * (p + 1) / 2;
+    float2 a0 = make_float2(0.f, 0.f), a1 = a0;
+    for (int k = p; k < P; ++k) {
+      const float2 *Xkp = Xb + blk(k, p), *Xkq = Xb + blk(k, q);
+#pragma unroll
+      for (int t = 0; t < NB; ++t) {
+        const float2 xq = Xkq[t * NB + c];
+        a0 = cfmac(Xkp[t * NB + r0], xq, a0);
+        a1 = cfmac(Xkp[t * NB + r0 + 4], xq, a1);
+      }
+    }
+    Qe[(size_t)bq * 64 + c * 8 + (r0 ^ c)] = a0;
+    Qe[(size_t)bq * 64 + c * 8 + ((r0 + 4) ^ c)] = a1;
+  }
+}
+
+size_t tri_inverse_blocked_smem(int b) {
+  const int P = b / 8;
+  return ((size_t)2 * P * (P + 1) / 2 * 64 + (size_t)P * 64 + (size_t)((P + 1) / 2) * 64) * sizeof(float2);
+}
+
 template <typename R>
-void launch_tri_inverse(const double2 *Lpk, int nel, int b, void *X, size_t x_stride, cudaStream_t st) {
+bool launch_tri_inverse(const double2 *Lpk, int nel, int b, void *X, size_t x_stride, cudaStream_t st, void *Qb) {
   using C = typename Cplx<R>::T;
+  if constexpr (std::is_same<R, float>::value) {
+    if (b % 8 == 0 && b / 8 <= TIB_MAXP && tri_inverse_blocked_smem(b) <= 220 * 1024) {
+      const int P = b / 8;
+      static bool configured = false;
+      if (!configured) {
+        cudaFuncSetAttribute(tri_inverse_blocked_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        configured = true;
+      }
+      tri_inverse_blocked_kernel<8><<<nel, 32 * ((P + 1) / 2), tri_inverse_blocked_smem(b), st>>>(
+          Lpk, b, reinterpret_cast<float2 *>(X), x_stride, reinterpret_cast<float2 *>(Qb), (size_t)P * (P + 1) / 2 * 64);
+      return true;
+    }
+  }
   const size_t head = ((size_t)b * sizeof(R) + 15) & ~size_t(15);
   const size_t bytes = (size_t)b * (b + 1) / 2 * sizeof(C);
   const bool in_smem = head + bytes <= 200 * 1024;
@@ -618,9 +794,10 @@ void launch_tri_inverse(const double2 *Lpk, int nel, int b, void *X, size_t x_st
   } else {
     go(tri_inverse_kernel<R, 8, false>);
   }
+  return false;
 }
-template void launch_tri_inverse<float>(const double2 *, int, int, void *, size_t, cudaStream_t);
-template void launch_tri_inverse<double>(const double2 *, int, int, void *, size_t, cudaStream_t);
+template bool launch_tri_inverse<float>(const double2 *, int, int, void *, size_t, cudaStream_t, void *);
+template bool launch_tri_inverse<double>(const double2 *, int, int, void *, size_t, cudaStream_t, void *);
 
 // ------------------------------------------------------------ apply ------
 // y_e = X_e^H (X_e x_e), X_e = L_e^{-1} packed column-major.  One CTA per
