@@ -64,6 +64,7 @@ __global__ void __launch_bounds__(RC_THREADS, MINB) bin_rc_kernel(RcArgs A) {
   uint64_t *full = reinterpret_cast<uint64_t *>(sm);
   uint64_t *empty = full + NS;
   volatile int *abort_flag = reinterpret_cast<volatile int *>(empty + NS);
+  uint64_t *red_free = empty + NS + 1;  // redC read out by the slice-0 column warps
   float2 *stage0 = reinterpret_cast<float2 *>(sm + 256);
   const size_t stage_elems = (size_t)RC_TR * lds;
   float2 *xbuf = stage0 + NS * stage_elems;      // [2 buffers][R | C][NR][b]
@@ -80,6 +81,7 @@ __global__ void __launch_bounds__(RC_THREADS, MINB) bin_rc_kernel(RcArgs A) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], RC_CONS);
     }
+    mbar_init(red_free, (b / 2 + 31) / 32);  // one arrival per slice-0 column warp
     *abort_flag = 0;
     fence_mbar_init();
   }
@@ -235,6 +237,19 @@ __global__ void __launch_bounds__(RC_THREADS, MINB) bin_rc_kernel(RcArgs A) {
     if (lane == 0) rc_arrive(&empty[s]);
 
     if (t == ntile - 1) {
+      // The other slices' warps overwrite redC only once the slice-0 warps
+      // have read the previous pair's sums (a lazy wait instead of a second
+      // barrier of all consumers).
+      if (col_active && slice > 0 && pk > 0) {
+        int okw = 1;
+        if (lane == 0 && !mbar_wait_bounded(red_free, (uint32_t)((pk - 1) & 1), RC_WAIT_NS)) {
+          if (!*abort_flag) atomicOr(P.err, DEVERR_TIMEOUT);
+          *abort_flag = 1;
+          okw = 0;
+        }
+        okw = __shfl_sync(0xffffffffu, okw, 0);
+        (void)okw;
+      }
       if (col_active && !selfp && cc < b)
 #pragma unroll
         for (int h = 0; h < 2; ++h)
@@ -242,21 +257,24 @@ __global__ void __launch_bounds__(RC_THREADS, MINB) bin_rc_kernel(RcArgs A) {
           for (int qq = 0; qq < NR; ++qq) redC[(((size_t)kw * 32 + lane) * 2 + h) * NR + qq] = accC[h][qq];
       rc_cp_async_wait_all();  // this thread's prefetch of the next pair's x has landed
       rc_consumer_bar();       // redC complete; orders the prefetch before its use
-      if (col_active && slice == 0 && !selfp && cc < b && !*abort_flag) {
+      if (col_active && slice == 0) {
+        if (!selfp && cc < b && !*abort_flag) {
 #pragma unroll
-        for (int h = 0; h < 2; ++h)
+          for (int h = 0; h < 2; ++h)
 #pragma unroll
-          for (int qq = 0; qq < NR; ++qq) {
-            float2 v = make_float2(0.f, 0.f);
-            for (int sl = 0; sl < nslice; ++sl) {
-              const float2 u = redC[((((size_t)(sl * G + cgrp)) * 32 + lane) * 2 + h) * NR + qq];
-              v.x += u.x;
-              v.y += u.y;
+            for (int qq = 0; qq < NR; ++qq) {
+              float2 v = make_float2(0.f, 0.f);
+              for (int sl = 0; sl < nslice; ++sl) {
+                const float2 u = redC[((((size_t)(sl * G + cgrp)) * 32 + lane) * 2 + h) * NR + qq];
+                v.x += u.x;
+                v.y += u.y;
+              }
+              if (q0 + qq < nr) Y[((size_t)kC * nr + q0 + qq) * b + cc + h] = v;
             }
-            if (q0 + qq < nr) Y[((size_t)kC * nr + q0 + qq) * b + cc + h] = v;
-          }
+        }
+        __syncwarp();
+        if (lane == 0) rc_arrive(red_free);
       }
-      rc_consumer_bar();  // redC may be rewritten by the next pair
     }
   }
 }
