@@ -15,9 +15,13 @@
 // Precision: 3xTF32.  Both operands are split v = hi + lo with hi, lo
 // exact TF32 values; the accumulator receives hi*hi + hi*lo + lo*hi in FP32
 // (tcgen05.mma kind::tf32, FP32 accumulate), which keeps the product close
-// to FP32 accuracy (relative error ~1e-6 instead of TF32's ~1e-3).  The
-// A splits are made once per array (tc_split_*_kernel); B' is built and
-// split in shared memory per K chunk.
+// to FP32 accuracy (relative error ~1e-6 instead of TF32's ~1e-3).  B' is
+// built and split in shared memory per K chunk.  A is either pre-split
+// (the preconditioner factors, tc_split_factor) or read unsplit ("raw": the
+// c64 pair store of the bins and its transpose, or the offset blocks of the
+// Gram products) and split in shared memory by the same warps that build
+// B', in place for hi and into the tile's second slot for lo -- the TMA
+// then moves the c64 bytes once, not the two split copies.
 //
 // The same kernel applies the block preconditioner for many RHS: the
 // items are then the lattice elements, A = X_e = L_e^{-1} and A = X_e^H
@@ -63,8 +67,11 @@ struct MmaArgs {
   const int *amap;
   int T, b, nr, conj;
   int nmt, nkc, nrtiles, NS, acc_bufs, tmem_cols;
+  int nmu;  // M-tile groups per item: a unit is (item, RHS tile, group of nmt M tiles)
   unsigned *err;
   const int *live;
+  int rawA, check;  // A tiles arrive unsplit (hi slots) and are split by warps 2-5; check their finiteness
+  int Tmap;         // raw A: matrices per map (items >= Tmap come from the second map)
 };
 
 MOMA_DEV float tf32_hi(float v) {
@@ -195,7 +202,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)NS * stage_bytes);
   uint64_t *fullA = bars, *fullB = bars + NS, *empty = bars + 2 * NS;
   uint64_t *accf = bars + 3 * NS, *acce = accf + 2, *drain = acce + 2;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
+  uint64_t *fullS = drain + 1;  // [NS] raw A: the lo slots are written
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(fullS + NS);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -203,6 +211,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     for (int s = 0; s < NS; ++s) {
       mbar_init(&fullA[s], 1);
       mbar_init(&fullB[s], 4);
+      mbar_init(&fullS[s], 4);
       mbar_init(&empty[s], 1);
     }
     for (int i = 0; i < 2; ++i) {
@@ -223,8 +232,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const int units = P.T * P.nrtiles;
+  const int units = P.T * P.nrtiles * P.nmu;
   const int acc_cols = nmt * NP;
+  // Unit u: item u / (nrtiles nmu), RHS tile (u / nmu) % nrtiles, M tiles
+  // from (u % nmu) nmt on.
 
   if (warp == 0) {
     // ---------------------------------------------------------- TMA --
@@ -236,17 +247,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       int issued_in[8];
       for (int s = 0; s < 8; ++s) issued_in[s] = -1;
       for (int u = blockIdx.x; u < units && !*abort_flag; u += gridDim.x) {
-        const int t = u / P.nrtiles, j0 = (u % P.nrtiles) * NRT;
+        const int t = u / (P.nrtiles * P.nmu), j0 = ((u / P.nmu) % P.nrtiles) * NRT, m0 = (u % P.nmu) * nmt;
         const int ai = P.amap ? P.amap[t] : t;
+        // Raw A: one unsplit tile per M tile, from hi (items < T) or lo.
+        const CUtensorMap *rmap = ai < P.Tmap ? &map_hi : &map_lo;
+        const int ri = ai < P.Tmap ? ai : ai - P.Tmap;
         for (int kc = 0; kc < nkc; ++kc, ++g) {
           const int s = g % NS;
           const uint32_t ph = (uint32_t)(g / NS) & 1u;
           if (!wait_or_abort(&empty[s], ph ^ 1u, abort_flag, P.err)) break;
           unsigned char *st = smem + (size_t)s * stage_bytes;
-          mbar_expect_tx(&fullA[s], (uint32_t)(nmt * 2 * TC_ATILE + XTILE));
+          mbar_expect_tx(&fullA[s], (uint32_t)(nmt * (P.rawA ? 1 : 2) * TC_ATILE + XTILE));
           for (int mt = 0; mt < nmt; ++mt) {
-            tma_load_3d(st + (size_t)(2 * mt) * TC_ATILE, &map_hi, kc * TC_KC, mt * TC_M, ai, &fullA[s]);
-            tma_load_3d(st + (size_t)(2 * mt + 1) * TC_ATILE, &map_lo, kc * TC_KC, mt * TC_M, ai, &fullA[s]);
+            if (P.rawA) {
+              tma_load_3d(st + (size_t)(2 * mt) * TC_ATILE, rmap, kc * TC_KC, (m0 + mt) * TC_M, ri, &fullA[s]);
+            } else {
+              tma_load_3d(st + (size_t)(2 * mt) * TC_ATILE, &map_hi, kc * TC_KC, (m0 + mt) * TC_M, ai, &fullA[s]);
+              tma_load_3d(st + (size_t)(2 * mt + 1) * TC_ATILE, &map_lo, kc * TC_KC, (m0 + mt) * TC_M, ai,
+                          &fullA[s]);
+            }
           }
           // Raw RHS chunk: rows j0 .. j0+NRT-1 (past nr read as zeros).
           tma_load_3d(st + (size_t)nmt * 2 * TC_ATILE + 2 * BTILE, &map_x, kc * TC_KC, t, j0, &fullA[s]);
@@ -279,15 +298,45 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           tc_fence_after();
           const uint32_t st = smem_u32(smem + (size_t)s * stage_bytes);
           const uint32_t bhi = st + (uint32_t)(nmt * 2 * TC_ATILE), blo = bhi + BTILE;
-          for (int mt = 0; mt < nmt; ++mt) {
-            const uint32_t d = tmem + (uint32_t)(ab * acc_cols + mt * NP);
-            const uint32_t ahi = st + (uint32_t)(2 * mt) * TC_ATILE, alo = ahi + TC_ATILE;
+          if (!P.rawA) {
+            for (int mt = 0; mt < nmt; ++mt) {
+              const uint32_t d = tmem + (uint32_t)(ab * acc_cols + mt * NP);
+              const uint32_t ahi = st + (uint32_t)(2 * mt) * TC_ATILE, alo = ahi + TC_ATILE;
 #pragma unroll
-            for (int k = 0; k < TC_KC / 8; ++k) {
-              const uint32_t ko = (uint32_t)k * 32u;  // 8 TF32 values
-              mma_tf32(d, sw128_desc(ahi + ko), sw128_desc(bhi + ko), idesc, (kc | k) ? 1u : 0u);
-              mma_tf32(d, sw128_desc(ahi + ko), sw128_desc(blo + ko), idesc, 1u);
-              mma_tf32(d, sw128_desc(alo + ko), sw128_desc(bhi + ko), idesc, 1u);
+              for (int k = 0; k < TC_KC / 8; ++k) {
+                const uint32_t ko = (uint32_t)k * 32u;  // 8 TF32 values
+                mma_tf32(d, sw128_desc(ahi + ko), sw128_desc(bhi + ko), idesc, (kc | k) ? 1u : 0u);
+                mma_tf32(d, sw128_desc(ahi + ko), sw128_desc(blo + ko), idesc, 1u);
+                mma_tf32(d, sw128_desc(alo + ko), sw128_desc(bhi + ko), idesc, 1u);
+              }
+            }
+          } else {
+            // Raw A: its FP32 values serve as A_hi as they landed (the MMA
+            // reads the TF32 bits of each FP32 value, dropping the low 13),
+            // so hi*hi and hi*lo start at once; lo*hi waits for the split.
+            for (int mt = 0; mt < nmt; ++mt) {
+              const uint32_t d = tmem + (uint32_t)(ab * acc_cols + mt * NP);
+              const uint32_t ahi = st + (uint32_t)(2 * mt) * TC_ATILE;
+#pragma unroll
+              for (int k = 0; k < TC_KC / 8; ++k) {
+                const uint32_t ko = (uint32_t)k * 32u;
+                mma_tf32(d, sw128_desc(ahi + ko), sw128_desc(bhi + ko), idesc, (kc | k) ? 1u : 0u);
+                mma_tf32(d, sw128_desc(ahi + ko), sw128_desc(blo + ko), idesc, 1u);
+              }
+            }
+            if (!wait_or_abort(&fullS[s], ph, abort_flag, P.err)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            for (int mt = 0; mt < nmt; ++mt) {
+              const uint32_t d = tmem + (uint32_t)(ab * acc_cols + mt * NP);
+              const uint32_t alo = st + (uint32_t)(2 * mt + 1) * TC_ATILE;
+#pragma unroll
+              for (int k = 0; k < TC_KC / 8; ++k) {
+                const uint32_t ko = (uint32_t)k * 32u;
+                mma_tf32(d, sw128_desc(alo + ko), sw128_desc(bhi + ko), idesc, 1u);
+              }
             }
           }
           mma_commit(&empty[s]);  // stage s free once these MMAs have read it
@@ -343,6 +392,31 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         fence_proxy_async();  // generic-proxy writes -> visible to the tensor cores
         __syncwarp();
         if (lane == 0) arrive(&fullB[s]);
+        if (P.rawA) {
+          // lo = v - trunc(v) of the unsplit A tiles into each tile's second
+          // slot (an elementwise map: the swizzled positions carry over); the
+          // raw tile itself stands for hi = trunc(v).
+          bool bad = false;
+          for (int mt = 0; mt < nmt; ++mt) {
+            const float4 *ah =
+                reinterpret_cast<const float4 *>(smem + (size_t)s * stage_bytes + (size_t)(2 * mt) * TC_ATILE);
+            float4 *al = const_cast<float4 *>(ah) + TC_ATILE / 16;
+            for (int idx = bt; idx < TC_ATILE / 16; idx += 128) {
+              const float4 v = ah[idx];
+              bad |= !isfinite(v.x) || !isfinite(v.y) || !isfinite(v.z) || !isfinite(v.w);
+              float4 l;
+              l.x = tf32_trunc(v.x - tf32_trunc(v.x));
+              l.y = tf32_trunc(v.y - tf32_trunc(v.y));
+              l.z = tf32_trunc(v.z - tf32_trunc(v.z));
+              l.w = tf32_trunc(v.w - tf32_trunc(v.w));
+              al[idx] = l;
+            }
+          }
+          if (P.check && __any_sync(0xffffffffu, bad) && lane == 0) atomicOr(P.err, DEVERR_NONFINITE);
+          fence_proxy_async();
+          __syncwarp();
+          if (lane == 0) arrive(&fullS[s]);
+        }
       }
       if (!ok) break;
     }
@@ -351,14 +425,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int q = warp & 3;  // tensor-memory lane quarter this warp may access
     int lu = 0;
     for (int u = blockIdx.x; u < units && !warp_aborted(abort_flag); u += gridDim.x, ++lu) {
-      const int t = u / P.nrtiles, j0 = (u % P.nrtiles) * NRT;
+      const int t = u / (P.nrtiles * P.nmu), j0 = ((u / P.nmu) % P.nrtiles) * NRT, m0 = (u % P.nmu) * nmt;
       const int ab = lu % P.acc_bufs;
       const uint32_t aph = (uint32_t)(lu / P.acc_bufs) & 1u;
       if (!warp_wait(&accf[ab], aph, abort_flag, P.err)) break;
       tc_fence_after();
       float2 *yt = P.y + (size_t)t * P.y_ts;
       for (int mt = 0; mt < nmt; ++mt) {
-        const int i = mt * TC_M + q * 32 + lane;
+        const int i = (m0 + mt) * TC_M + q * 32 + lane;
         const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * acc_cols + mt * NP);
 #pragma unroll
         for (int jc = 0; jc < NRT; jc += LW) {
@@ -385,9 +459,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(P.tmem_cols) : "memory");
 }
 
-// A_hi / A_lo of every bin from the pair storage: bin k reads its stored
-// block directly (mode 0, 2) or transposed (mode 1).  Output row i of bin k
-// is interleaved complex (2b floats) in both arrays.
+// One complex value split into TF32 pairs at position o of hi and lo.
 MOMA_DEV void put_split(float *hi, float *lo, size_t o, float2 v) {
   float2 h, l;
   h.x = tf32_hi(v.x);
@@ -396,42 +468,6 @@ MOMA_DEV void put_split(float *hi, float *lo, size_t o, float2 v) {
   l.y = tf32_trunc(v.y - h.y);
   reinterpret_cast<float2 *>(hi)[o] = h;
   reinterpret_cast<float2 *>(lo)[o] = l;
-}
-
-__global__ void tc_split_bins_kernel(const float2 *Z, int b, int ldb, const int2 *bin_slot, float *Ahi, float *Alo) {
-  __shared__ float2 tile[32][33];
-  const int k = blockIdx.z;
-  const int2 bs = bin_slot[k];
-  const float2 *Zs = Z + (size_t)bs.x * b * ldb;
-  const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  if (bs.y == 1) {
-    // A[i][j] = Zs[j][i]: stage the transposed tile.
-    for (int r = ty; r < 32; r += 8) {
-      const int jj = j0 + r, ii = i0 + tx;
-      tile[r][tx] = (jj < b && ii < b) ? Zs[(size_t)jj * ldb + ii] : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-  }
-  for (int r = ty; r < 32; r += 8) {
-    const int i = i0 + r, j = j0 + tx;
-    if (i >= b || j >= b) continue;
-    const float2 v = bs.y == 1 ? tile[tx][r] : Zs[(size_t)i * ldb + j];
-    put_split(Ahi, Alo, ((size_t)k * b + i) * b + j, v);
-  }
-}
-
-// Elementwise split of T whole c64 b x b matrices (row-major) into hi / lo.
-// Also the finiteness check of the blocks it reads (err: DEVERR_NONFINITE),
-// so that the set-up does not read the blocks once more just for it.
-__global__ void tc_split_plain_kernel(const float2 *Z, size_t n, float *hi, float *lo, unsigned *err) {
-  bool bad = false;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const float2 v = Z[i];
-    bad |= !isfinite(v.x) || !isfinite(v.y);
-    put_split(hi, lo, i, v);
-  }
-  if (err && __syncthreads_or(bad) && threadIdx.x == 0) atomicOr(err, DEVERR_NONFINITE);
 }
 
 // Full X_e = L_e^{-1} (zero above the diagonal) from the packed column-major
@@ -503,7 +539,7 @@ void encode_maps(TcMats &m) {
 template <int NRT>
 size_t smem_bytes(int nmt, int NS) {
   const size_t stage = (size_t)nmt * 2 * TC_ATILE + 2 * (size_t)(2 * NRT) * 128 + (size_t)NRT * 128;
-  return 1024 + NS * stage + (3 * NS + 5) * sizeof(uint64_t) + 16;
+  return 1024 + NS * stage + (4 * NS + 5) * sizeof(uint64_t) + 16;
 }
 
 template <int NRT>
@@ -514,8 +550,14 @@ void launch_nrt(const TcMats &m, const TcProduct &P, int num_sms, cudaStream_t s
   a.y = static_cast<float2 *>(P.y);
   a.x_ts = P.x_ts; a.x_rs = P.x_rs; a.y_ts = P.y_ts; a.y_rs = P.y_rs;
   a.amap = P.amap;
-  a.T = m.T; a.b = b; a.nr = P.nr; a.conj = P.conj;
+  const int items = P.items > 0 ? P.items : m.T;
+  a.T = items; a.b = b; a.nr = P.nr; a.conj = P.conj;
+  a.Tmap = m.T;
+  // All M tiles of an item in one unit (units of one M tile each, which fit
+  // three stages with raw A at b = 256, measured slower: 578 vs 551 us at
+  // 24 x 24, b = 256, 64 RHS, from building B' and loading x twice).
   a.nmt = (b + TC_M - 1) / TC_M;
+  a.nmu = 1;
   a.nkc = (2 * b + TC_KC - 1) / TC_KC;
   a.nrtiles = (P.nr + NRT - 1) / NRT;
   const int per_buf = a.nmt * 2 * NRT;
@@ -525,6 +567,8 @@ void launch_nrt(const TcMats &m, const TcProduct &P, int num_sms, cudaStream_t s
   a.tmem_cols = cols;
   a.err = P.err;
   a.live = P.live;
+  a.rawA = m.raw ? 1 : 0;
+  a.check = m.raw && P.check_finite ? 1 : 0;
   int NS = 4;
   while (NS > 2 && smem_bytes<NRT>(a.nmt, NS) > 220 * 1024) --NS;
   a.NS = NS;
@@ -543,7 +587,7 @@ void launch_nrt(const TcMats &m, const TcProduct &P, int num_sms, cudaStream_t s
   {
     auto fn = encode_fn();
     if (!fn) throw std::runtime_error("cuTensorMapEncodeTiled is not available");
-    const cuuint64_t dims[3] = {(cuuint64_t)(2 * b), (cuuint64_t)m.T, (cuuint64_t)P.nr};
+    const cuuint64_t dims[3] = {(cuuint64_t)(2 * b), (cuuint64_t)items, (cuuint64_t)P.nr};
     const cuuint64_t strides[2] = {(cuuint64_t)P.x_ts * 8, (cuuint64_t)P.x_rs * 8};
     const cuuint32_t box[3] = {TC_KC, 1, (cuuint32_t)NRT};
     const cuuint32_t estr[3] = {1, 1, 1};
@@ -552,9 +596,9 @@ void launch_nrt(const TcMats &m, const TcProduct &P, int num_sms, cudaStream_t s
                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) throw std::runtime_error("cuTensorMapEncodeTiled (x) failed: " + std::to_string((int)r));
   }
-  const int units = a.T * a.nrtiles;
+  const int units = a.T * a.nrtiles * a.nmu;
   const int grid = std::min(units, num_sms);
-  kern<<<grid, TC_THREADS, smem, st>>>(m.map_hi, m.map_lo, map_x, a);
+  kern<<<grid, TC_THREADS, smem, st>>>(m.map_hi, (m.raw && !m.lo) ? m.map_hi : m.map_lo, map_x, a);
 }
 
 }  // namespace
@@ -563,19 +607,51 @@ bool tc_supported(int b) { return b >= 128 && b <= 256 && b % 2 == 0; }
 
 size_t tc_bytes(int T, int b) { return 2 * (size_t)T * b * 2 * b * sizeof(float); }
 
-void tc_split_bins(TcMats &m, const void *Z64, int ldb, const int2 *bin_slot, cudaStream_t st) {
+// Raw maps over [T][b][ld] c64 viewed as floats: the same boxes as
+// encode_maps (rows past b and floats past 2b read as zeros).
+void tc_raw(TcMats &m, const void *Z64, const void *Z64T, int ld) {
+  auto fn = encode_fn();
+  if (!fn) throw std::runtime_error("cuTensorMapEncodeTiled is not available");
+  m.raw = true;
+  m.ld = ld;
+  m.hi = reinterpret_cast<float *>(const_cast<void *>(Z64));
+  m.lo = reinterpret_cast<float *>(const_cast<void *>(Z64T));
   const int b = m.b;
-  dim3 grid((b + 31) / 32, (b + 31) / 32, m.T), block(32, 8);
-  tc_split_bins_kernel<<<grid, block, 0, st>>>(static_cast<const float2 *>(Z64), b, ldb, bin_slot, m.hi, m.lo);
-  encode_maps(m);
+  const cuuint64_t dims[3] = {(cuuint64_t)(2 * b), (cuuint64_t)b, (cuuint64_t)m.T};
+  const cuuint64_t strides[2] = {(cuuint64_t)(2 * ld) * sizeof(float), (cuuint64_t)(2 * ld) * b * sizeof(float)};
+  const cuuint32_t box[3] = {TC_KC, TC_M, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  float *bases[2] = {m.hi, m.lo};
+  CUtensorMap *maps[2] = {&m.map_hi, &m.map_lo};
+  for (int h = 0; h < 2; ++h) {
+    if (!bases[h]) continue;
+    const CUresult r = fn(maps[h], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, bases[h], dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) throw std::runtime_error("cuTensorMapEncodeTiled (raw) failed: " + std::to_string((int)r));
+  }
 }
 
-void tc_split_plain(TcMats &m, const void *Z64, cudaStream_t st, unsigned *err) {
-  const size_t n = (size_t)m.T * m.b * m.b;
-  size_t g = (n + 255) / 256;
-  if (g > 16384) g = 16384;
-  tc_split_plain_kernel<<<(int)g, 256, 0, st>>>(static_cast<const float2 *>(Z64), n, m.hi, m.lo, err);
-  encode_maps(m);
+// Z64T[s][i][j] = Z64[s][j][i], 32 x 32 tiles through shared memory.
+__global__ void transpose_pairs_kernel(const float2 *__restrict__ Z, float2 *__restrict__ ZT, int b, int ld) {
+  __shared__ float2 tile[32][33];
+  const size_t base = (size_t)blockIdx.z * b * ld;
+  const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32, tx = threadIdx.x, ty = threadIdx.y;
+  for (int r = ty; r < 32; r += 8) {
+    const int i = i0 + r, j = j0 + tx;
+    tile[r][tx] = (i < b && j < b) ? Z[base + (size_t)i * ld + j] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int j = j0 + r, i = i0 + tx;
+    if (i < b && j < b) ZT[base + (size_t)j * ld + i] = tile[tx][r];
+  }
+}
+
+void tc_transpose_pairs(const void *Z64, void *Z64T, int Bp, int b, int ld, cudaStream_t st) {
+  dim3 grid((b + 31) / 32, (b + 31) / 32, Bp), block(32, 8);
+  transpose_pairs_kernel<<<grid, block, 0, st>>>(static_cast<const float2 *>(Z64), static_cast<float2 *>(Z64T), b,
+                                                 ld);
 }
 
 void tc_split_factor(TcMats &X, TcMats &XH, const void *Xpk, size_t x_stride, cudaStream_t st) {

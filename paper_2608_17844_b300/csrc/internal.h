@@ -109,10 +109,15 @@ void launch_bin_rc(const BinProduct &p, int num_sms, cudaStream_t st);
 // Tensor-core products (tcgen05, 3xTF32) for many right-hand sides.  A
 // TcMats holds T complex b x b matrices, each split into exact TF32 pairs
 // (hi, lo: [T][b][2b] floats, interleaved complex rows), with TMA maps.
+// raw: hi (and lo, if set) are instead plain c64 matrices [T][b][ld] that the
+// kernel splits in shared memory; an item t >= T of the product's amap
+// selects matrix t - T of lo (the pair store and its transpose).
 struct TcMats {
   int b = 0, T = 0;
   float *hi = nullptr, *lo = nullptr;
   CUtensorMap map_hi{}, map_lo{};
+  bool raw = false;
+  int ld = 0;
 };
 // y_t[j] = op(A_{amap(t)}) x_t[j] for items t < T, RHS j < nr; op = conj
 // if conj.  x_t[j][k] at x + t*x_ts + j*x_rs + k (complex64), same for y.
@@ -124,14 +129,16 @@ struct TcProduct {
   const int *amap = nullptr;  // nullptr = identity
   unsigned *err = nullptr;
   const int *live = nullptr;
+  int check_finite = 0;       // raw A: DEVERR_NONFINITE into err for a non-finite entry of A
+  int items = 0;              // items t of x and y (0: the TcMats' T; amap indexes the matrices)
 };
 bool tc_supported(int b);
+// Raw c64 matrices (rows of ld complex values) as the A operand, split in
+// shared memory: hi = Z64 (items < T), lo = Z64T (items T .. 2T-1) or null.
+void tc_raw(TcMats &m, const void *Z64, const void *Z64T, int ld);
+// Z64T[s] = Z64[s]^T for the Bp stored b x b blocks (row stride ld).
+void tc_transpose_pairs(const void *Z64, void *Z64T, int Bp, int b, int ld, cudaStream_t st);
 size_t tc_bytes(int T, int b);  // hi + lo
-// Every bin's full block from the pair storage (transposed for the partner).
-void tc_split_bins(TcMats &m, const void *Z64, int ldb, const int2 *bin_slot, cudaStream_t st);
-// T whole row-major c64 matrices (e.g. offset blocks), split elementwise;
-// err (if set) receives DEVERR_NONFINITE for a non-finite input value.
-void tc_split_plain(TcMats &m, const void *Z64, cudaStream_t st, unsigned *err = nullptr);
 // X_e and X_e^H from the packed inverse factors (c64).
 void tc_split_factor(TcMats &X, TcMats &XH, const void *Xpk, size_t x_stride, cudaStream_t st);
 void launch_tc_product(const TcMats &m, const TcProduct &P, int num_sms, cudaStream_t st);

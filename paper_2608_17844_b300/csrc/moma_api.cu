@@ -160,6 +160,7 @@ struct moma_array {
   // the partner table, split X_e and X_e^H; built on first use after
   // set_blocks.
   DevBuf tcA, tcP, partner;
+  DevBuf tamap;  // tensor-core A item of every bin: [B] for Z, [B] for Z^H (pair store, or its transpose at + Bp)
   TcMats tcZ, tcX, tcXH;
   bool tc_ready = false;
   bool no_tensor = false;
@@ -173,7 +174,7 @@ struct moma_array {
   const double2 *pbox = nullptr;  // the box sums P_e (lower triangles), in S or Wb
   bool pbox_df = false;           // ... stored as double-FP32 pairs
   cudaStream_t cs = nullptr;  // host-to-device copies of the blocks
-  DevBuf gramA, gramY;        // tensor-core Gram products: split blocks, reflected products
+  DevBuf gramY;               // tensor-core Gram products of the reflected offsets
   bool tgram = false;         // this set-up's Gram products ran on the tensor cores
   cudaEvent_t ev_cs0 = nullptr, ev_chunk[8] = {};
   // solve workspace
@@ -345,6 +346,14 @@ void build_tables(moma_array *a) {
       part[ky * a->Mx + kx] = ((a->My - ky) % a->My) * a->Mx + ((a->Mx - kx) % a->Mx);
   a->partner.ensure(part.size() * sizeof(int), a->dev_bytes);
   CK(cudaMemcpy(a->partner.p, part.data(), part.size() * sizeof(int), cudaMemcpyHostToDevice));
+  // Tensor-core A operand of bin k: its stored block (the lower member of a
+  // pair) or the transpose of its partner's (item Bp + slot); Z^H reads the
+  // partner's operand, conjugated (Eq. 6 with reciprocity).
+  std::vector<int> am(2 * a->B);
+  for (int k = 0; k < a->B; ++k) am[k] = slot[k] >= 0 ? slot[k] : a->Bp + slot[part[k]];
+  for (int k = 0; k < a->B; ++k) am[a->B + k] = am[part[k]];
+  a->tamap.ensure(am.size() * sizeof(int), a->dev_bytes);
+  CK(cudaMemcpy(a->tamap.p, am.data(), am.size() * sizeof(int), cudaMemcpyHostToDevice));
   a->pairs.ensure(pr.size() * sizeof(int2), a->dev_bytes);
   a->slot_of.ensure(slot.size() * sizeof(int), a->dev_bytes);
   CK(cudaMemcpy(a->pairs.p, pr.data(), pr.size() * sizeof(int2), cudaMemcpyHostToDevice));
@@ -456,7 +465,8 @@ void binprod(moma_array *a, int nr, const void *x, void *y, int herm) {
   if (!is64<R>() && a->tc_ready && nr >= a->tc_min_nr) {
     // Bins [B][nr][b]; Z^H reads the partner bin, conjugated (Eq. 6).
     TcProduct T;
-    T.x = x; T.y = y; T.nr = nr; T.conj = herm; T.amap = herm ? a->partner.as<int>() : nullptr;
+    T.x = x; T.y = y; T.nr = nr; T.conj = herm; T.amap = a->tamap.as<int>() + (herm ? a->B : 0);
+    T.items = a->B;
     T.x_ts = T.y_ts = (long long)nr * a->b; T.x_rs = T.y_rs = a->b;
     T.err = a->err; T.live = a->live;
     a->timed(PK_BINTC, [&] { launch_tc_product(a->tcZ, T, a->num_sms, a->st); });
@@ -768,21 +778,23 @@ void ensure_tc(moma_array *a, int nr) {
   if (a->tc_ready || a->no_tensor || a->prec != MOMA_PREC_MIXED || nr < a->tc_min_nr || !tc_supported(a->b)) return;
   drop_graphs(a);
   const int b = a->b;
-  const size_t zb = tc_bytes(a->B, b), xb = tc_bytes(a->nel, b);
-  a->tcA.ensure(zb, a->dev_bytes);
+  // Bins: the c64 pair store and its transpose, split into TF32 pairs by
+  // the kernel as it reads them.  Factors: X_e and X_e^H whole, pre-split.
+  const size_t zt = (size_t)a->Bp * b * a->ldb * sizeof(float2), xb = tc_bytes(a->nel, b);
+  a->tcA.ensure(zt, a->dev_bytes);
   a->tcP.ensure(2 * xb, a->dev_bytes);
-  unsigned char *pz = a->tcA.as<unsigned char>(), *px = a->tcP.as<unsigned char>();
+  unsigned char *px = a->tcP.as<unsigned char>();
   a->tcZ = TcMats{};
-  a->tcZ.b = b; a->tcZ.T = a->B;
-  a->tcZ.hi = reinterpret_cast<float *>(pz); a->tcZ.lo = reinterpret_cast<float *>(pz + zb / 2);
+  a->tcZ.b = b; a->tcZ.T = a->Bp;
   a->tcX = TcMats{};
   a->tcX.b = b; a->tcX.T = a->nel;
   a->tcX.hi = reinterpret_cast<float *>(px); a->tcX.lo = reinterpret_cast<float *>(px + xb / 2);
   a->tcXH = a->tcX;
   a->tcXH.hi = reinterpret_cast<float *>(px + xb); a->tcXH.lo = reinterpret_cast<float *>(px + xb + xb / 2);
   try {
-    a->timed(PK_BLOCKFFT, [&] { tc_split_bins(a->tcZ, a->Z64.p, a->ldb, a->bin_slot.as<int2>(), a->st); });
+    a->timed(PK_BLOCKFFT, [&] { tc_transpose_pairs(a->Z64.p, a->tcA.p, a->Bp, b, a->ldb, a->st); });
     check_launch(a);
+    tc_raw(a->tcZ, a->Z64.p, a->tcA.p, a->ldb);
     a->timed(PK_TRINV, [&] { tc_split_factor(a->tcX, a->tcXH, a->Xinv.p, a->x_stride, a->st); });
     check_launch(a);
   } catch (const std::runtime_error &e) {
@@ -925,18 +937,18 @@ void set_blocks_impl(moma_array *a, const void *blocks, int dtype) {
       // gives y_D[j][i] = sum_k conj(Z_D[i][k]) Z_D[j][k], which by
       // reciprocity is G_{-D}[i][j]; the box-sum pass reads it back
       // reflected and conjugated.
+      // The blocks are read unsplit (split into TF32 pairs in shared memory,
+      // where their finiteness is checked too).
       TcMats mA;
       mA.b = a->b; mA.T = nd;
-      mA.hi = a->gramA.as<float>() + (size_t)d0 * a->b * 2 * a->b;
-      mA.lo = mA.hi + (size_t)nD * a->b * 2 * a->b;
       const float2 *zb = reinterpret_cast<const float2 *>(blk) + (size_t)d0 * bb;
       TcProduct P;
       P.x = zb; P.y = a->gramY.as<float2>() + (size_t)d0 * bb;
       P.x_ts = P.y_ts = bb; P.x_rs = P.y_rs = a->b; P.nr = a->b; P.conj = 1; P.err = a->err;
+      P.check_finite = 1;
       a->timed(PK_GRAM, [&] {
         try {
-          tc_split_plain(mA, zb, a->st, a->err);
-          check_launch(a);
+          tc_raw(mA, zb, nullptr, a->b);
           launch_tc_product(mA, P, a->num_sms, a->st);
         } catch (const std::runtime_error &e) {
           throw MomaError(MOMA_ERR_CUDA, e.what());
@@ -952,11 +964,10 @@ void set_blocks_impl(moma_array *a, const void *blocks, int dtype) {
   const int nrows = ndy - r0;
   // Gram products on the tensor cores (3xTF32) for c64 blocks in the mixed
   // path when the block size suits the MMA kernel.
-  a->tgram = a->prec == MOMA_PREC_MIXED && dtype == MOMA_C64 && !a->no_tensor && tc_supported(a->b);
-  if (a->tgram) {
-    a->gramA.ensure(tc_bytes(nD, a->b), a->dev_bytes);
-    a->gramY.ensure((size_t)nD * bb * sizeof(float2), a->dev_bytes);
-  }
+  // The kernel reads the blocks with TMA, which needs a 16-byte aligned base.
+  a->tgram = a->prec == MOMA_PREC_MIXED && dtype == MOMA_C64 && !a->no_tensor && tc_supported(a->b) &&
+             reinterpret_cast<uintptr_t>(blk) % 16 == 0;
+  if (a->tgram) a->gramY.ensure((size_t)nD * bb * sizeof(float2), a->dev_bytes);
   for (int c = 0; c < nchunk; ++c) {
     const int y0 = r0 + (int)((long long)nrows * c / nchunk), y1 = r0 + (int)((long long)nrows * (c + 1) / nchunk);
     if (y1 <= y0) continue;
@@ -1609,7 +1620,7 @@ void destroy_impl(moma_array *a) {
   DevBuf *bufs[] = {&a->tabs, &a->pairs, &a->slot_of, &a->bin_slot, &a->tri, &a->tri_in, &a->Z128, &a->Z64, &a->Xinv, &a->blk, &a->T, &a->S,
                     &a->Lpk, &a->lat_in, &a->lat_tmp, &a->t1, &a->bx, &a->by, &a->Vk, &a->Iw, &a->Vw,
                     &a->rw, &a->yw, &a->kbuf, &a->errbuf, &a->one_blk, &a->portsb, &a->zp_V, &a->zp_I, &a->zp_Y, &a->zp_tmp,
-                    &a->tcA, &a->tcP, &a->partner, &a->Xblk, &a->gramA, &a->gramY, &a->lat_u, &a->mZB128,
+                    &a->tcA, &a->tcP, &a->partner, &a->Xblk, &a->gramY, &a->tamap, &a->lat_u, &a->mZB128,
                     &a->mZC128, &a->mZB64, &a->mZC64, &a->mP, &a->mL, &a->mX, &a->Wb};
   for (DevBuf *b : bufs) b->release(a->dev_bytes);
   if (a->cs) {
@@ -2209,7 +2220,6 @@ moma_status moma_release_setup(moma_array *a) {
   return guarded([&] {
     CK(cudaStreamSynchronize(a->st));
     a->blk.release(a->dev_bytes);
-    a->gramA.release(a->dev_bytes);
     a->gramY.release(a->dev_bytes);
     a->T.release(a->dev_bytes);
     a->S.release(a->dev_bytes);
@@ -2232,7 +2242,7 @@ size_t moma_estimate_bytes(int nx, int ny, int b, const moma_options *opt, int n
   size_t bytes = Bp * b * ldb * c + (prec == MOMA_PREC_MIXED ? Bp * b * ldb * 8 : 0);  // stored bins
   bytes += nel * (nt + 2) * esz;                                                        // inverse factors
   if (prec == MOMA_PREC_MIXED) bytes += nel * xblk_entries(b) * 8;                    // blocked c64 P_e^{-1}
-  bytes += B * 16 + nt * 12 + 4096;                                                     // tables
+  bytes += B * 24 + nt * 12 + 4096;                                                     // tables
   const size_t nr = (size_t)nrhs, nch = (N + 1023) / 1024;
   bytes += nr * N * c * 6 + nr * ny * Mx * b * c + 2 * B * nr * b * c;                 // solve vectors
   bytes += (size_t)(m + 1) * nr * N * esz + nr * nch * (m + 1) * c + nr * m * (m + 1) * c;  // Krylov
@@ -2240,11 +2250,11 @@ size_t moma_estimate_bytes(int nx, int ny, int b, const moma_options *opt, int n
   if (with_setup) bytes += nD * b * b * (c + 8) + (size_t)(2 * ny - 1) * Mx * nt * c + nel * nt * c;
   if (with_setup) bytes += box_window_entries(nx, ny, b) * c;                           // box-sum windows
   const bool tens_setup = prec == MOMA_PREC_MIXED && !(opt && (opt->flags & MOMA_FLAG_NO_TENSOR)) && tc_supported(b);
-  if (with_setup && tens_setup) bytes += tc_bytes((int)nD, b) + nD * b * b * 8;  // tensor-core Gram scratch
+  if (with_setup && tens_setup) bytes += nD * b * b * 8;  // tensor-core Gram products
   const bool tensor = !(opt && (opt->flags & MOMA_FLAG_NO_TENSOR));
   const int tmin = (opt && (opt->flags & MOMA_FLAG_TENSOR_ALWAYS)) ? 1 : 16;
   if (prec == MOMA_PREC_MIXED && tensor && nrhs >= tmin && tc_supported(b))
-    bytes += tc_bytes((int)B, b) + 2 * tc_bytes((int)nel, b);  // split bins and factors
+    bytes += Bp * b * ldb * 8 + 2 * tc_bytes((int)nel, b);  // transposed pair store, split factors
   return bytes;
 }
 
