@@ -433,6 +433,12 @@ void launch_bin_product(const BinProduct &P, int num_sms, cudaStream_t st) {
       return;
     }
   }
+  if constexpr (std::is_same<R, dfl>::value) {
+    if (bin_rc_dfl_supported(P.b) && P.ldb == P.b) {
+      launch_bin_rc_dfl(P, num_sms, st);
+      return;
+    }
+  }
   // RHS are processed in chunks of up to NRMAX columns (the kernel masks
   // columns past nr); each chunk streams the bins once.
   constexpr int NRMAX = sizeof(R) == 4 ? 4 : 2;

@@ -1,4 +1,6 @@
-// The c64 per-bin product of Eq. 3 for b a multiple of 32 (64 <= b <= 256):
+// The per-bin product of Eq. 3 for b a multiple of 32 (64 <= b <= 256), in
+// c64 for the inner solve and in double-FP32 (b <= 160, two RHS per
+// launch) for the refinement residual:
 // y_ka = Zhat x_ka and y_kb = Zhat^T x_kb from one stored block per pair
 // {k, -k} (reciprocity, Sec. II-D), or conj(Zhat) and conj(Zhat)^T for Z^H
 // (Eq. 6), as in binprod.cu, with a different split of the work that needs
@@ -53,9 +55,76 @@ MOMA_DEV float2 rc_sum4(float2 v) {  // the four lanes of a row (lane bits 3 and
   v.y += __shfl_xor_sync(0xffffffffu, v.y, 16);
   return v;
 }
+MOMA_DEV void rc_cp_async16(void *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
 
-template <int NR, bool HERM, int MINB>
+// Arithmetic of the kernel: c64 (E = float2, FP32 accumulators) for the
+// inner solve, and double-FP32 (E = dfl2, unnormalised two-float
+// accumulators whose additions are exact two-sums) for the refinement
+// residual of the mixed path.
+struct RcF32 {
+  using E = float2;
+  struct Acc {
+    float2 v;
+  };
+  MOMA_DEV static Acc zero() { return Acc{make_float2(0.f, 0.f)}; }
+  MOMA_DEV static E ezero() { return make_float2(0.f, 0.f); }
+  MOMA_DEV static void load2(const E *row, int c, E &z0, E &z1) {  // entries c, c + 1 (one 16-byte load)
+    const float4 z4 = *reinterpret_cast<const float4 *>(row + c);
+    z0 = make_float2(z4.x, z4.y);
+    z1 = make_float2(z4.z, z4.w);
+  }
+  MOMA_DEV static E conj(E z) { return make_float2(z.x, -z.y); }
+  MOMA_DEV static void fma(Acc &a, E z, E x) { a.v = cfma(z, x, a.v); }
+  MOMA_DEV static Acc sum4(Acc a) { return Acc{rc_sum4(a.v)}; }
+  MOMA_DEV static E value(const Acc &a) { return a.v; }
+  MOMA_DEV static void add(Acc &a, const E &u) {
+    a.v.x += u.x;
+    a.v.y += u.y;
+  }
+  MOMA_DEV static void copy_async(E *dst, const E *src) { rc_cp_async8(dst, src); }
+};
+struct RcDfl {
+  using E = dfl2;
+  struct Acc {
+    DfAcc re, im;
+  };
+  MOMA_DEV static Acc zero() { return Acc{DfAcc{0.f, 0.f}, DfAcc{0.f, 0.f}}; }
+  MOMA_DEV static E ezero() { return dfl2{dfl(0.f), dfl(0.f)}; }
+  MOMA_DEV static void load2(const E *row, int c, E &z0, E &z1) {
+    z0 = row[c];
+    z1 = row[c + 1];
+  }
+  MOMA_DEV static E conj(E z) { return dfl2{z.x, -z.y}; }
+  MOMA_DEV static void fma(Acc &a, E z, E x) {  // a += z x
+    dfacc_fma(a.re, z.x, x.x);
+    dfacc_fma(a.re, -z.y, x.y);
+    dfacc_fma(a.im, z.x, x.y);
+    dfacc_fma(a.im, z.y, x.x);
+  }
+  MOMA_DEV static DfAcc shfl_add(DfAcc a, int m) {
+    DfAcc o{__shfl_xor_sync(0xffffffffu, a.s, m), __shfl_xor_sync(0xffffffffu, a.t, m)};
+    dfacc_add(a, o);
+    return a;
+  }
+  MOMA_DEV static Acc sum4(Acc a) {
+    a.re = shfl_add(shfl_add(a.re, 8), 16);
+    a.im = shfl_add(shfl_add(a.im, 8), 16);
+    return a;
+  }
+  MOMA_DEV static E value(const Acc &a) { return dfl2{dfacc_value(a.re), dfacc_value(a.im)}; }
+  MOMA_DEV static void add(Acc &a, const E &u) {
+    dfacc_add(a.re, DfAcc{u.x.hi, u.x.lo});
+    dfacc_add(a.im, DfAcc{u.y.hi, u.y.lo});
+  }
+  MOMA_DEV static void copy_async(E *dst, const E *src) { rc_cp_async16(dst, src); }
+};
+
+template <typename AR, int NR, bool HERM, int MINB>
 __global__ void __launch_bounds__(RC_THREADS, MINB) bin_rc_kernel(RcArgs A) {
+  using E = typename AR::E;
+  using Acc = typename AR::Acc;
   extern __shared__ __align__(128) unsigned char sm[];
   const BinProduct &P = A.P;
   if (P.live && *P.live == 0) return;
@@ -65,13 +134,13 @@ __global__ void __launch_bounds__(RC_THREADS, MINB) bin_rc_kernel(RcArgs A) {
   uint64_t *empty = full + NS;
   volatile int *abort_flag = reinterpret_cast<volatile int *>(empty + NS);
   uint64_t *red_free = empty + NS + 1;  // redC read out by the slice-0 column warps
-  float2 *stage0 = reinterpret_cast<float2 *>(sm + 256);
+  E *stage0 = reinterpret_cast<E *>(sm + 256);
   const size_t stage_elems = (size_t)RC_TR * lds;
-  float2 *xbuf = stage0 + NS * stage_elems;      // [2 buffers][R | C][NR][b]
-  float2 *redC = xbuf + (size_t)4 * NR * b;      // [4 column warps][32 lanes][2][NR]
-  const float2 *Z = reinterpret_cast<const float2 *>(P.Z);
-  const float2 *X = reinterpret_cast<const float2 *>(P.x);
-  float2 *Y = reinterpret_cast<float2 *>(P.y);
+  E *xbuf = stage0 + NS * stage_elems;      // [2 buffers][R | C][NR][b]
+  E *redC = xbuf + (size_t)4 * NR * b;      // [4 column warps][32 lanes][2][NR]
+  const E *Z = reinterpret_cast<const E *>(P.Z);
+  const E *X = reinterpret_cast<const E *>(P.x);
+  E *Y = reinterpret_cast<E *>(P.y);
   const int ntile = b / RC_TR;
   const int npair = (P.Bp - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
   const int total = npair * ntile;
@@ -91,7 +160,7 @@ __global__ void __launch_bounds__(RC_THREADS, MINB) bin_rc_kernel(RcArgs A) {
     // ------------------------------------------------------------ producer --
     if (lane != 0) return;
     int issued = 0;
-    const uint32_t row_bytes = (uint32_t)(ldb * sizeof(float2));
+    const uint32_t row_bytes = (uint32_t)(ldb * sizeof(E));
     for (int i = 0; i < total; ++i) {
       const int s = i % NS;
       const uint32_t par = (uint32_t)(((i / NS) & 1) ^ 1);
@@ -110,8 +179,8 @@ __global__ void __launch_bounds__(RC_THREADS, MINB) bin_rc_kernel(RcArgs A) {
       }
       const int pk = i / ntile, t = i % ntile;
       const long long p = (long long)blockIdx.x + (long long)pk * gridDim.x;
-      const float2 *src = Z + ((size_t)p * b + (size_t)t * RC_TR) * ldb;
-      float2 *dst = stage0 + (size_t)s * stage_elems;
+      const E *src = Z + ((size_t)p * b + (size_t)t * RC_TR) * ldb;
+      E *dst = stage0 + (size_t)s * stage_elems;
       fence_proxy_async();
       mbar_expect_tx(&full[s], row_bytes * RC_TR);
       for (int rr = 0; rr < RC_TR; ++rr) bulk_g2s(dst + (size_t)rr * lds, src + (size_t)rr * ldb, row_bytes, &full[s]);
@@ -127,14 +196,14 @@ __global__ void __launch_bounds__(RC_THREADS, MINB) bin_rc_kernel(RcArgs A) {
     const int p = (int)blockIdx.x + pk * (int)gridDim.x;
     const int2 pr = P.pairs[p];
     const int kR = HERM ? pr.y : pr.x, kC = HERM ? pr.x : pr.y;
-    float2 *xr_s = xbuf + (size_t)buf * 2 * NR * b;
-    float2 *xc_s = xr_s + (size_t)NR * b;
+    E *xr_s = xbuf + (size_t)buf * 2 * NR * b;
+    E *xc_s = xr_s + (size_t)NR * b;
     for (int idx = tid; idx < NR * b; idx += RC_CONS * 32) {
       const int qq = idx / b, c = idx % b, q = q0 + qq;
-      if (q < nr) rc_cp_async8(&xr_s[idx], &X[((size_t)kR * nr + q) * b + c]);
-      else xr_s[idx] = make_float2(0.f, 0.f);
-      if (q < nr && pr.x != pr.y) rc_cp_async8(&xc_s[idx], &X[((size_t)kC * nr + q) * b + c]);
-      else xc_s[idx] = make_float2(0.f, 0.f);
+      if (q < nr) AR::copy_async(&xr_s[idx], &X[((size_t)kR * nr + q) * b + c]);
+      else xr_s[idx] = AR::ezero();
+      if (q < nr && pr.x != pr.y) AR::copy_async(&xc_s[idx], &X[((size_t)kC * nr + q) * b + c]);
+      else xc_s[idx] = AR::ezero();
     }
   };
   load_x(0, 0);
@@ -148,10 +217,10 @@ __global__ void __launch_bounds__(RC_THREADS, MINB) bin_rc_kernel(RcArgs A) {
   const int cpair = 32 * cgrp + lane, cc = 2 * cpair;
   const int r8 = lane & 7, c4 = lane >> 3;
 
-  float2 accC[2][NR];
+  Acc accC[2][NR];
   int kR = 0, kC = 0;
   bool selfp = false;
-  const float2 *xr_s = xbuf, *xc_s = xbuf + (size_t)NR * b;
+  const E *xr_s = xbuf, *xc_s = xbuf + (size_t)NR * b;
 
   for (int i = 0; i < total; ++i) {
     const int pk = i / ntile, t = i % ntile, buf = pk & 1;
@@ -166,7 +235,7 @@ __global__ void __launch_bounds__(RC_THREADS, MINB) bin_rc_kernel(RcArgs A) {
 #pragma unroll
       for (int h = 0; h < 2; ++h)
 #pragma unroll
-        for (int qq = 0; qq < NR; ++qq) accC[h][qq] = make_float2(0.f, 0.f);
+        for (int qq = 0; qq < NR; ++qq) accC[h][qq] = AR::zero();
       if (pk + 1 < npair) load_x(pk + 1, buf ^ 1);  // overlaps this pair's tiles
     }
     const int s = i % NS;
@@ -186,49 +255,49 @@ __global__ void __launch_bounds__(RC_THREADS, MINB) bin_rc_kernel(RcArgs A) {
         }
       }
     }
-    const float2 *tile = stage0 + (size_t)s * stage_elems;
+    const E *tile = stage0 + (size_t)s * stage_elems;
     const int r0 = t * RC_TR;
     if (ok) {
       if (w < 4) {
         // Row leg: row rl of the tile, columns 8i + 2 c4 (+1).
         const int rl = 8 * w + r8;
-        const float2 *zrow = tile + (size_t)rl * lds;
-        float2 acc[NR];
+        const E *zrow = tile + (size_t)rl * lds;
+        Acc acc[NR];
 #pragma unroll
-        for (int qq = 0; qq < NR; ++qq) acc[qq] = make_float2(0.f, 0.f);
+        for (int qq = 0; qq < NR; ++qq) acc[qq] = AR::zero();
         for (int c = 2 * c4; c < b; c += 8) {
-          const float4 z4 = *reinterpret_cast<const float4 *>(zrow + c);
-          float2 z0 = make_float2(z4.x, z4.y), z1 = make_float2(z4.z, z4.w);
+          E z0, z1;
+          AR::load2(zrow, c, z0, z1);
           if (HERM) {
-            z0.y = -z0.y;
-            z1.y = -z1.y;
+            z0 = AR::conj(z0);
+            z1 = AR::conj(z1);
           }
 #pragma unroll
           for (int qq = 0; qq < NR; ++qq) {
-            acc[qq] = cfma(z0, xr_s[qq * b + c], acc[qq]);
-            acc[qq] = cfma(z1, xr_s[qq * b + c + 1], acc[qq]);
+            AR::fma(acc[qq], z0, xr_s[qq * b + c]);
+            AR::fma(acc[qq], z1, xr_s[qq * b + c + 1]);
           }
         }
 #pragma unroll
-        for (int qq = 0; qq < NR; ++qq) acc[qq] = rc_sum4(acc[qq]);
+        for (int qq = 0; qq < NR; ++qq) acc[qq] = AR::sum4(acc[qq]);
         if (c4 == 0)
 #pragma unroll
           for (int qq = 0; qq < NR; ++qq)
-            if (q0 + qq < nr) Y[((size_t)kR * nr + q0 + qq) * b + r0 + rl] = acc[qq];
+            if (q0 + qq < nr) Y[((size_t)kR * nr + q0 + qq) * b + r0 + rl] = AR::value(acc[qq]);
       } else if (col_active && !selfp && cc < b) {
         // Column leg: column pair cc, rows of this warp's slice.
         for (int rl = slice * rps; rl < (slice + 1) * rps; ++rl) {
-          const float4 z4 = *reinterpret_cast<const float4 *>(tile + (size_t)rl * lds + cc);
-          float2 z0 = make_float2(z4.x, z4.y), z1 = make_float2(z4.z, z4.w);
+          E z0, z1;
+          AR::load2(tile + (size_t)rl * lds, cc, z0, z1);
           if (HERM) {
-            z0.y = -z0.y;
-            z1.y = -z1.y;
+            z0 = AR::conj(z0);
+            z1 = AR::conj(z1);
           }
 #pragma unroll
           for (int qq = 0; qq < NR; ++qq) {
-            const float2 xc = xc_s[qq * b + r0 + rl];
-            accC[0][qq] = cfma(z0, xc, accC[0][qq]);
-            accC[1][qq] = cfma(z1, xc, accC[1][qq]);
+            const E xc = xc_s[qq * b + r0 + rl];
+            AR::fma(accC[0][qq], z0, xc);
+            AR::fma(accC[1][qq], z1, xc);
           }
         }
       }
@@ -254,7 +323,7 @@ __global__ void __launch_bounds__(RC_THREADS, MINB) bin_rc_kernel(RcArgs A) {
 #pragma unroll
         for (int h = 0; h < 2; ++h)
 #pragma unroll
-          for (int qq = 0; qq < NR; ++qq) redC[(((size_t)kw * 32 + lane) * 2 + h) * NR + qq] = accC[h][qq];
+          for (int qq = 0; qq < NR; ++qq) redC[(((size_t)kw * 32 + lane) * 2 + h) * NR + qq] = AR::value(accC[h][qq]);
       rc_cp_async_wait_all();  // this thread's prefetch of the next pair's x has landed
       rc_consumer_bar();       // redC complete; orders the prefetch before its use
       if (col_active && slice == 0) {
@@ -263,13 +332,9 @@ __global__ void __launch_bounds__(RC_THREADS, MINB) bin_rc_kernel(RcArgs A) {
           for (int h = 0; h < 2; ++h)
 #pragma unroll
             for (int qq = 0; qq < NR; ++qq) {
-              float2 v = make_float2(0.f, 0.f);
-              for (int sl = 0; sl < nslice; ++sl) {
-                const float2 u = redC[((((size_t)(sl * G + cgrp)) * 32 + lane) * 2 + h) * NR + qq];
-                v.x += u.x;
-                v.y += u.y;
-              }
-              if (q0 + qq < nr) Y[((size_t)kC * nr + q0 + qq) * b + cc + h] = v;
+              Acc v = AR::zero();
+              for (int sl = 0; sl < nslice; ++sl) AR::add(v, redC[((((size_t)(sl * G + cgrp)) * 32 + lane) * 2 + h) * NR + qq]);
+              if (q0 + qq < nr) Y[((size_t)kC * nr + q0 + qq) * b + cc + h] = AR::value(v);
             }
         }
         __syncwarp();
@@ -279,28 +344,29 @@ __global__ void __launch_bounds__(RC_THREADS, MINB) bin_rc_kernel(RcArgs A) {
   }
 }
 
-size_t rc_smem(int b, int NR, int NS) {
-  return 256 + (size_t)NS * RC_TR * (b + 2) * sizeof(float2) + (size_t)4 * NR * b * sizeof(float2) +
-         (size_t)4 * 32 * 2 * NR * sizeof(float2);
+size_t rc_smem(int b, int NR, int NS, size_t esz) {
+  return 256 + (size_t)NS * RC_TR * (b + 2) * esz + (size_t)4 * NR * b * esz + (size_t)4 * 32 * 2 * NR * esz;
 }
 
-template <int NR, bool HERM>
+template <typename AR, int NR, bool HERM>
 void rc_launch(const BinProduct &P, int num_sms, cudaStream_t st, int q0) {
-  int occ = P.occ == 2 ? 2 : 1;
+  constexpr size_t esz = sizeof(typename AR::E);
+  // Two CTAs per SM only for c64 (double-FP32 stages are twice as large).
+  int occ = (P.occ == 2 && esz == 8) ? 2 : 1;
   const size_t cap = occ == 2 ? 110 * 1024 : 225 * 1024;
   int NS = (P.NS >= 2 && P.NS <= 6) ? P.NS : 4;
-  while (NS > 2 && rc_smem(P.b, NR, NS) > cap) --NS;
-  if (rc_smem(P.b, NR, NS) > cap) {  // two CTAs do not fit: one CTA per SM
+  while (NS > 2 && rc_smem(P.b, NR, NS, esz) > cap) --NS;
+  if (rc_smem(P.b, NR, NS, esz) > cap) {  // two CTAs do not fit: one CTA per SM
     occ = 1;
     NS = std::min(NS, 3);
-    while (NS > 2 && rc_smem(P.b, NR, NS) > 225 * 1024) --NS;
+    while (NS > 2 && rc_smem(P.b, NR, NS, esz) > 225 * 1024) --NS;
   }
-  const size_t smem = rc_smem(P.b, NR, NS);
+  const size_t smem = rc_smem(P.b, NR, NS, esz);
   int grid = num_sms * occ;
   if (grid > P.Bp) grid = P.Bp;
   RcArgs a{P, NS, q0, P.b + 2};
   if (occ == 2) {
-    auto kern = bin_rc_kernel<NR, HERM, 2>;
+    auto kern = bin_rc_kernel<AR, NR, HERM, 2>;
     static int configured = 0;
     if (!configured) {
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 112 * 1024);
@@ -308,7 +374,7 @@ void rc_launch(const BinProduct &P, int num_sms, cudaStream_t st, int q0) {
     }
     kern<<<grid, RC_THREADS, smem, st>>>(a);
   } else {
-    auto kern = bin_rc_kernel<NR, HERM, 1>;
+    auto kern = bin_rc_kernel<AR, NR, HERM, 1>;
     static int configured = 0;
     if (!configured) {
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
@@ -318,22 +384,37 @@ void rc_launch(const BinProduct &P, int num_sms, cudaStream_t st, int q0) {
   }
 }
 
-template <int NR>
+template <typename AR, int NR>
 void rc_launch_h(const BinProduct &P, int num_sms, cudaStream_t st, int q0) {
-  if (P.herm) rc_launch<NR, true>(P, num_sms, st, q0);
-  else rc_launch<NR, false>(P, num_sms, st, q0);
+  if (P.herm) rc_launch<AR, NR, true>(P, num_sms, st, q0);
+  else rc_launch<AR, NR, false>(P, num_sms, st, q0);
 }
+
+// Double-FP32 RHS per launch: two (their accumulators are twice the c64
+// ones').
+constexpr int RC_DFL_NR = 2;
 
 }  // namespace
 
 bool bin_rc_supported(int b) { return b % 32 == 0 && b >= 64 && b <= 256; }
 
+bool bin_rc_dfl_supported(int b) {
+  return bin_rc_supported(b) && rc_smem(b, RC_DFL_NR, 2, sizeof(dfl2)) <= 225 * 1024;
+}
+
 void launch_bin_rc(const BinProduct &P, int num_sms, cudaStream_t st) {
   for (int q0 = 0; q0 < P.nr; q0 += 4) {
     const int left = P.nr - q0;
-    if (left == 1) rc_launch_h<1>(P, num_sms, st, q0);
-    else if (left == 2) rc_launch_h<2>(P, num_sms, st, q0);
-    else rc_launch_h<4>(P, num_sms, st, q0);
+    if (left == 1) rc_launch_h<RcF32, 1>(P, num_sms, st, q0);
+    else if (left == 2) rc_launch_h<RcF32, 2>(P, num_sms, st, q0);
+    else rc_launch_h<RcF32, 4>(P, num_sms, st, q0);
+  }
+}
+
+void launch_bin_rc_dfl(const BinProduct &P, int num_sms, cudaStream_t st) {
+  for (int q0 = 0; q0 < P.nr; q0 += RC_DFL_NR) {
+    if (P.nr - q0 == 1) rc_launch_h<RcDfl, 1>(P, num_sms, st, q0);
+    else rc_launch_h<RcDfl, RC_DFL_NR>(P, num_sms, st, q0);
   }
 }
 

@@ -78,6 +78,31 @@ MOMA_DEV dfl dsqrt(dfl a) {
   return df_fast_two_sum(s, __fdiv_rn(r, __fmul_rn(2.0f, s)));
 }
 MOMA_DEV dfl &operator+=(dfl &a, dfl b) { return a = a + b; }
+// Unnormalised double-FP32 accumulator (value s + t) for sums of products:
+// each product's high part joins s through an exact two-sum, the rounding
+// error of that sum and the product's error (FMA two-product) gather in t,
+// and one two-sum at the end renormalises.  Against a renormalised `fma`
+// per term this saves a fast two-sum per term; every step that was exact
+// stays exact.
+struct DfAcc {
+  float s, t;
+};
+MOMA_DEV DfAcc dfacc(dfl c) { return DfAcc{c.hi, c.lo}; }
+MOMA_DEV void dfacc_fma(DfAcc &acc, dfl a, dfl b) {  // acc += a b
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+  const dfl q = df_two_sum(acc.s, p);
+  acc.s = q.hi;
+  acc.t = __fadd_rn(acc.t, __fadd_rn(q.lo, e));
+}
+MOMA_DEV void dfacc_add(DfAcc &acc, DfAcc b) {  // acc += b
+  const dfl q = df_two_sum(acc.s, b.s);
+  acc.s = q.hi;
+  acc.t = __fadd_rn(acc.t, __fadd_rn(q.lo, b.t));
+}
+MOMA_DEV dfl dfacc_value(DfAcc acc) { return df_two_sum(acc.s, acc.t); }
+
 MOMA_DEV dfl &operator*=(dfl &a, dfl b) { return a = a * b; }
 #endif
 

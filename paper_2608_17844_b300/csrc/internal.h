@@ -105,6 +105,10 @@ void launch_bin_product(const BinProduct &p, int num_sms, cudaStream_t st);
 // (binprod_rc.cu); launch_bin_product<float> takes it for those sizes.
 bool bin_rc_supported(int b);
 void launch_bin_rc(const BinProduct &p, int num_sms, cudaStream_t st);
+// The same in double-FP32 (stored bins and vectors dfl2) where its stages
+// fit shared memory (b <= 160); launch_bin_product<dfl> takes it there.
+bool bin_rc_dfl_supported(int b);
+void launch_bin_rc_dfl(const BinProduct &p, int num_sms, cudaStream_t st);
 
 // Tensor-core products (tcgen05, 3xTF32) for many right-hand sides.  A
 // TcMats holds T complex b x b matrices, each split into exact TF32 pairs

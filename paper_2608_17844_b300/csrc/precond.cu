@@ -117,25 +117,6 @@ MOMA_DEV double real_part(dfl2 v) { return (double)v.x; }
 MOMA_DEV double rsqrt_root(double d, double *l) { *l = sqrt(d); return 1.0 / *l; }
 MOMA_DEV dfl rsqrt_root(dfl d, dfl *l) { *l = dsqrt(d); return dfl(1.0f) / *l; }
 
-// Unnormalised double-FP32 accumulator (value s + t) for the CH_NB terms a
-// trailing-update entry receives from one panel: each product's high part
-// joins s through an exact two-sum, the rounding error of that sum and the
-// product's error (FMA two-product) gather in t, and one two-sum at the end
-// renormalises.  Against a renormalised `fma` per term this saves a
-// fast two-sum per term; every step that was exact stays exact.
-struct DfAcc {
-  float s, t;
-};
-MOMA_DEV DfAcc dfacc(dfl c) { return DfAcc{c.hi, c.lo}; }
-MOMA_DEV void dfacc_fma(DfAcc &acc, dfl a, dfl b) {  // acc += a b
-  const float p = __fmul_rn(a.hi, b.hi);
-  float e = __fmaf_rn(a.hi, b.hi, -p);
-  e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
-  const dfl q = df_two_sum(acc.s, p);
-  acc.s = q.hi;
-  acc.t = __fadd_rn(acc.t, __fadd_rn(q.lo, e));
-}
-MOMA_DEV dfl dfacc_value(DfAcc acc) { return df_two_sum(acc.s, acc.t); }
 // acc -= a conj(b) (the Cholesky update term), on the real and imaginary parts.
 MOMA_DEV void dfacc_fms_conj(DfAcc &re, DfAcc &im, const dfl2 &a, const dfl2 &b) {
   dfacc_fma(re, -a.x, b.x);
@@ -490,9 +471,9 @@ __global__ void __launch_bounds__(512, MINB) box_cholesky_kernel(const double2 *
   // FP64 output: the global-memory columns in place (each thread converts
   // the entries it reads), the shared-memory triangle copied out.
   double2 *dst = Lpk + (size_t)e * npk;
-  for (int k = 0; k < b; ++k) {
-    const C *ck = k < j0 ? Tg.col(k) : Ts.col(k);
-    for (int i = k + tid; i < b; i += blockDim.x) dst[colbase(k, b) + i - k] = cvt<double2>(ck[i]);
+  for (int t = tid; t < npk; t += blockDim.x) {  // packed column-major, coalesced
+    const int k = packed_col(t, b), i = k + t - colbase(k, b);
+    dst[t] = cvt<double2>(k < j0 ? Tg.col(k)[i] : Ts.col(k)[i]);
   }
 }
 
