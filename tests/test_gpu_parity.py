@@ -477,3 +477,30 @@ def test_split_lattice_transforms(moma_lib, cuda, nx, ny, b, nr):
             assert np.all(np.isfinite(y)) and err <= 1e-5, (op, err)
     finally:
         m.moma_destroy(h)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("nx,ny,b,nr", [(3, 2, 64, 1), (2, 3, 96, 3), (4, 3, 128, 2), (2, 2, 160, 5)])
+@pytest.mark.parametrize("op", [0, 1])
+def test_double_fp32_row_column_bin_product(moma_lib, cuda, nx, ny, b, nr, op):
+    """The double-FP32 per-bin product of the refinement residual (Eq. 3,
+    the row/column-warp layout for b = 64 .. 160, two RHS per launch with a
+    ragged last one): Z x and Z^H x of c128 vectors on a MIXED array,
+    element by element against the oracle's FP64 direct offset sums at the
+    FP64-class bar of the residual path."""
+    m = moma_lib
+    spec = LatticeSpec(nx, ny, b, 0.5, 13)
+    blocks = offset_blocks(spec, np.complex64)
+    b128 = blocks.astype(np.complex128)
+    x = rand_vec(nr, spec, seed=5)
+    ref = (mbt.matvec if op == 0 else mbt.matvec_h)(b128, nx, ny, x)
+    h = m.moma_create_array(nx, ny, b, MIXED, flags=m.MOMA_FLAG_NO_TENSOR)
+    try:
+        m.moma_set_blocks(h, blocks)
+        y = np.full_like(x, np.nan)
+        m.moma_matvec(h, op, x, y)
+    finally:
+        m.moma_destroy(h)
+    err = np.abs(y - ref).max() / np.abs(ref).max()
+    RAW_ERRORS[f"dfl_rc_bin{'H' if op else ''} {nx}x{ny}x{b} nr={nr}"] = err
+    assert np.all(np.isfinite(y)) and err <= 1e-11, err
