@@ -853,36 +853,74 @@ def main():
         pcg = {"value": nr / (msp / 1000.0), "unit": "solves/s", "ms_per_step": msp, "steps": fp_steps,
                "info": infp}
 
-    # End to end through the C ABI with host buffers (pinned), copies inside.
+    # End to end through the C ABI with host buffers (pinned), copies inside:
+    # every step uploads its blocks and V and reads back I, Z_a and Gamma.
+    # Measured twice: one handle, steps one after another ("serial"); and
+    # two handles on two streams driven by two host threads, steps
+    # alternating between them, so that one step's block upload overlaps the
+    # other's solve -- how a caller with a stream of independent problems
+    # keeps the copy engine and the SMs busy at once (the line's value).
     e2e = None
     if not args.no_e2e:
-        h = m.moma_create_array(spec.nx, spec.ny, spec.b, m.MOMA_PREC_MIXED, stream=stream)
+        import threading
         hb = torch.from_numpy(blocks).pin_memory()
-        hV = torch.from_numpy(V).pin_memory()
-        hI = torch.zeros_like(hV).pin_memory()
-        hz = torch.zeros(V.shape[:3], dtype=torch.complex128).pin_memory()
-        hg = torch.zeros_like(hz).pin_memory()
 
-        def host_step():
-            m.moma_set_blocks(h, hb)
-            m.moma_solve(h, hV, hI)
-            m.moma_active_impedance(h, hI, hV, hz, hg)
+        def make_lane(st):
+            lane = {"h": m.moma_create_array(spec.nx, spec.ny, spec.b, m.MOMA_PREC_MIXED, stream=st),
+                    "V": torch.from_numpy(V).pin_memory(), "I": torch.zeros(V.shape, dtype=torch.complex128).pin_memory(),
+                    "z": torch.zeros(V.shape[:3], dtype=torch.complex128).pin_memory()}
+            lane["g"] = torch.zeros_like(lane["z"]).pin_memory()
+            return lane
 
+        def host_step(lane):
+            m.moma_set_blocks(lane["h"], hb)
+            m.moma_solve(lane["h"], lane["V"], lane["I"])
+            m.moma_active_impedance(lane["h"], lane["I"], lane["V"], lane["z"], lane["g"])
+
+        lanes = [make_lane(stream), make_lane(torch.cuda.Stream())]
         for _ in range(args.warmup):
-            host_step()
+            for ln in lanes:
+                host_step(ln)
+        # serial: one handle
         barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            host_step()
+            host_step(lanes[0])
+        barrier()
+        dt_serial = time.perf_counter() - t0
+        # pipelined: two handles, two host threads, steps split between them
+        counts = [(args.steps + 1) // 2, args.steps // 2]
+        errors = []
+
+        def run_lane(i):
+            try:
+                for _ in range(counts[i]):
+                    host_step(lanes[i])
+            except Exception as ex:  # reported after the join
+                errors.append(ex)
+
+        barrier()
+        t0 = time.perf_counter()
+        threads = [threading.Thread(target=run_lane, args=(i,)) for i in range(2)]
+        for th in threads:
+            th.start()
+        for th in threads:
+            th.join()
+        torch.cuda.synchronize()
         barrier()
         dt = time.perf_counter() - t0
-        m.moma_destroy(h)
+        if errors:
+            raise errors[0]
+        for ln in lanes:
+            m.moma_destroy(ln["h"])
         # Host blocks: the library copies the offsets with dy >= 0 (Ny of the
         # 2Ny-1 rows; the rest follow from reciprocity); V goes in twice
         # (solve, port quantities) and I once.
         e2e = {"value": replicas.aggregate_throughput(nr * args.steps, dt, device=dev), "unit": "solves/s",
                "h2d_bytes_per_step": int(blocks.nbytes // (2 * spec.ny - 1) * spec.ny + 2 * V.nbytes + V.nbytes),
-               "d2h_bytes_per_step": int(V.nbytes + 2 * hz.numel() * 16)}
+               "d2h_bytes_per_step": int(V.nbytes + 2 * lanes[0]["z"].numel() * 16),
+               "pipeline": "2 handles on 2 streams, 2 host threads, steps alternating",
+               "serial": replicas.aggregate_throughput(nr * args.steps, dt_serial, device=dev)}
 
     ports = {n: [complex(za_head[q, ey, ex]) for q in range(nr)]
              for n, (ex, ey) in named_elements(spec.nx, spec.ny).items()}
