@@ -1,6 +1,6 @@
 // The per-bin product of Eq. 3 for b a multiple of 32 (64 <= b <= 256), in
-// c64 for the inner solve and in double-FP32 (b <= 160, two RHS per
-// launch) for the refinement residual:
+// c64 for the inner solve and in double-FP32 (two RHS per launch; 16-row
+// tiles above b = 160) for the refinement residual:
 // y_ka = Zhat x_ka and y_kb = Zhat^T x_kb from one stored block per pair
 // {k, -k} (reciprocity, Sec. II-D), or conj(Zhat) and conj(Zhat)^T for Z^H
 // (Eq. 6), as in binprod.cu, with a different split of the work that needs
@@ -77,7 +77,11 @@ struct RcF32 {
   }
   MOMA_DEV static E conj(E z) { return make_float2(z.x, -z.y); }
   MOMA_DEV static void fma(Acc &a, E z, E x) { a.v = cfma(z, x, a.v); }
-  MOMA_DEV static Acc sum4(Acc a) { return Acc{rc_sum4(a.v)}; }
+  template <int RPW>
+  MOMA_DEV static Acc sum_row(Acc a) {  // the lanes of a row: lane bits log2(RPW) .. 4
+    static_assert(RPW == 8, "c64 tiles have 32 rows");
+    return Acc{rc_sum4(a.v)};
+  }
   MOMA_DEV static E value(const Acc &a) { return a.v; }
   MOMA_DEV static void add(Acc &a, const E &u) {
     a.v.x += u.x;
@@ -108,9 +112,13 @@ struct RcDfl {
     dfacc_add(a, o);
     return a;
   }
-  MOMA_DEV static Acc sum4(Acc a) {
-    a.re = shfl_add(shfl_add(a.re, 8), 16);
-    a.im = shfl_add(shfl_add(a.im, 8), 16);
+  template <int RPW>
+  MOMA_DEV static Acc sum_row(Acc a) {  // the lanes of a row: lane bits log2(RPW) .. 4
+#pragma unroll
+    for (int m = RPW; m < 32; m <<= 1) {
+      a.re = shfl_add(a.re, m);
+      a.im = shfl_add(a.im, m);
+    }
     return a;
   }
   MOMA_DEV static E value(const Acc &a) { return dfl2{dfacc_value(a.re), dfacc_value(a.im)}; }
@@ -121,10 +129,14 @@ struct RcDfl {
   MOMA_DEV static void copy_async(E *dst, const E *src) { rc_cp_async16(dst, src); }
 };
 
-template <typename AR, int NR, bool HERM, int MINB>
+template <typename AR, int NR, bool HERM, int MINB, int TR>
 __global__ void __launch_bounds__(RC_THREADS, MINB) bin_rc_kernel(RcArgs A) {
   using E = typename AR::E;
   using Acc = typename AR::Acc;
+  // TR rows per tile: 32, or 16 for double-FP32 blocks wider than 160 (whose
+  // 32-row stages would not fit twice).  A row warp owns RPW = TR / 4 rows
+  // with 32 / RPW lanes on each.
+  constexpr int RPW = TR / 4, LPR = 32 / RPW;
   extern __shared__ __align__(128) unsigned char sm[];
   const BinProduct &P = A.P;
   if (P.live && *P.live == 0) return;
@@ -135,13 +147,13 @@ __global__ void __launch_bounds__(RC_THREADS, MINB) bin_rc_kernel(RcArgs A) {
   volatile int *abort_flag = reinterpret_cast<volatile int *>(empty + NS);
   uint64_t *red_free = empty + NS + 1;  // redC read out by the slice-0 column warps
   E *stage0 = reinterpret_cast<E *>(sm + 256);
-  const size_t stage_elems = (size_t)RC_TR * lds;
+  const size_t stage_elems = (size_t)TR * lds;
   E *xbuf = stage0 + NS * stage_elems;      // [2 buffers][R | C][NR][b]
   E *redC = xbuf + (size_t)4 * NR * b;      // [4 column warps][32 lanes][2][NR]
   const E *Z = reinterpret_cast<const E *>(P.Z);
   const E *X = reinterpret_cast<const E *>(P.x);
   E *Y = reinterpret_cast<E *>(P.y);
-  const int ntile = b / RC_TR;
+  const int ntile = b / TR;
   const int npair = (P.Bp - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
   const int total = npair * ntile;
   if (total <= 0) return;
@@ -179,11 +191,11 @@ __global__ void __launch_bounds__(RC_THREADS, MINB) bin_rc_kernel(RcArgs A) {
       }
       const int pk = i / ntile, t = i % ntile;
       const long long p = (long long)blockIdx.x + (long long)pk * gridDim.x;
-      const E *src = Z + ((size_t)p * b + (size_t)t * RC_TR) * ldb;
+      const E *src = Z + ((size_t)p * b + (size_t)t * TR) * ldb;
       E *dst = stage0 + (size_t)s * stage_elems;
       fence_proxy_async();
-      mbar_expect_tx(&full[s], row_bytes * RC_TR);
-      for (int rr = 0; rr < RC_TR; ++rr) bulk_g2s(dst + (size_t)rr * lds, src + (size_t)rr * ldb, row_bytes, &full[s]);
+      mbar_expect_tx(&full[s], row_bytes * TR);
+      for (int rr = 0; rr < TR; ++rr) bulk_g2s(dst + (size_t)rr * lds, src + (size_t)rr * ldb, row_bytes, &full[s]);
       issued = i + 1;
     }
     for (int i = max(0, issued - NS); i < issued; ++i)
@@ -211,11 +223,11 @@ __global__ void __launch_bounds__(RC_THREADS, MINB) bin_rc_kernel(RcArgs A) {
   rc_consumer_bar();
 
   // Column warps: G groups of 32 column pairs, 4 / G row slices per tile.
-  const int G = (b / 2 + 31) / 32, nslice = 4 / G, rps = RC_TR / nslice;
+  const int G = (b / 2 + 31) / 32, nslice = 4 / G, rps = TR / nslice;
   const int kw = w - 4, cgrp = kw % G, slice = kw / G;
   const bool col_active = w >= 4 && kw < G * nslice;
   const int cpair = 32 * cgrp + lane, cc = 2 * cpair;
-  const int r8 = lane & 7, c4 = lane >> 3;
+  const int r8 = lane % RPW, c4 = lane / RPW;  // row in the warp's rows, lane of the row
 
   Acc accC[2][NR];
   int kR = 0, kC = 0;
@@ -256,16 +268,16 @@ __global__ void __launch_bounds__(RC_THREADS, MINB) bin_rc_kernel(RcArgs A) {
       }
     }
     const E *tile = stage0 + (size_t)s * stage_elems;
-    const int r0 = t * RC_TR;
+    const int r0 = t * TR;
     if (ok) {
       if (w < 4) {
-        // Row leg: row rl of the tile, columns 8i + 2 c4 (+1).
-        const int rl = 8 * w + r8;
+        // Row leg: row rl of the tile, columns 2 LPR i + 2 c4 (+1).
+        const int rl = RPW * w + r8;
         const E *zrow = tile + (size_t)rl * lds;
         Acc acc[NR];
 #pragma unroll
         for (int qq = 0; qq < NR; ++qq) acc[qq] = AR::zero();
-        for (int c = 2 * c4; c < b; c += 8) {
+        for (int c = 2 * c4; c < b; c += 2 * LPR) {
           E z0, z1;
           AR::load2(zrow, c, z0, z1);
           if (HERM) {
@@ -279,7 +291,7 @@ __global__ void __launch_bounds__(RC_THREADS, MINB) bin_rc_kernel(RcArgs A) {
           }
         }
 #pragma unroll
-        for (int qq = 0; qq < NR; ++qq) acc[qq] = AR::sum4(acc[qq]);
+        for (int qq = 0; qq < NR; ++qq) acc[qq] = AR::template sum_row<RPW>(acc[qq]);
         if (c4 == 0)
 #pragma unroll
           for (int qq = 0; qq < NR; ++qq)
@@ -344,29 +356,29 @@ __global__ void __launch_bounds__(RC_THREADS, MINB) bin_rc_kernel(RcArgs A) {
   }
 }
 
-size_t rc_smem(int b, int NR, int NS, size_t esz) {
-  return 256 + (size_t)NS * RC_TR * (b + 2) * esz + (size_t)4 * NR * b * esz + (size_t)4 * 32 * 2 * NR * esz;
+size_t rc_smem(int b, int NR, int NS, size_t esz, int TR = RC_TR) {
+  return 256 + (size_t)NS * TR * (b + 2) * esz + (size_t)4 * NR * b * esz + (size_t)4 * 32 * 2 * NR * esz;
 }
 
-template <typename AR, int NR, bool HERM>
+template <typename AR, int NR, bool HERM, int TR>
 void rc_launch(const BinProduct &P, int num_sms, cudaStream_t st, int q0) {
   constexpr size_t esz = sizeof(typename AR::E);
   // Two CTAs per SM only for c64 (double-FP32 stages are twice as large).
   int occ = (P.occ == 2 && esz == 8) ? 2 : 1;
   const size_t cap = occ == 2 ? 110 * 1024 : 225 * 1024;
   int NS = (P.NS >= 2 && P.NS <= 6) ? P.NS : 4;
-  while (NS > 2 && rc_smem(P.b, NR, NS, esz) > cap) --NS;
-  if (rc_smem(P.b, NR, NS, esz) > cap) {  // two CTAs do not fit: one CTA per SM
+  while (NS > 2 && rc_smem(P.b, NR, NS, esz, TR) > cap) --NS;
+  if (rc_smem(P.b, NR, NS, esz, TR) > cap) {  // two CTAs do not fit: one CTA per SM
     occ = 1;
     NS = std::min(NS, 3);
-    while (NS > 2 && rc_smem(P.b, NR, NS, esz) > 225 * 1024) --NS;
+    while (NS > 2 && rc_smem(P.b, NR, NS, esz, TR) > 225 * 1024) --NS;
   }
-  const size_t smem = rc_smem(P.b, NR, NS, esz);
+  const size_t smem = rc_smem(P.b, NR, NS, esz, TR);
   int grid = num_sms * occ;
   if (grid > P.Bp) grid = P.Bp;
   RcArgs a{P, NS, q0, P.b + 2};
   if (occ == 2) {
-    auto kern = bin_rc_kernel<AR, NR, HERM, 2>;
+    auto kern = bin_rc_kernel<AR, NR, HERM, 2, TR>;
     static int configured = 0;
     if (!configured) {
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 112 * 1024);
@@ -374,7 +386,7 @@ void rc_launch(const BinProduct &P, int num_sms, cudaStream_t st, int q0) {
     }
     kern<<<grid, RC_THREADS, smem, st>>>(a);
   } else {
-    auto kern = bin_rc_kernel<AR, NR, HERM, 1>;
+    auto kern = bin_rc_kernel<AR, NR, HERM, 1, TR>;
     static int configured = 0;
     if (!configured) {
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
@@ -384,10 +396,10 @@ void rc_launch(const BinProduct &P, int num_sms, cudaStream_t st, int q0) {
   }
 }
 
-template <typename AR, int NR>
+template <typename AR, int NR, int TR = RC_TR>
 void rc_launch_h(const BinProduct &P, int num_sms, cudaStream_t st, int q0) {
-  if (P.herm) rc_launch<AR, NR, true>(P, num_sms, st, q0);
-  else rc_launch<AR, NR, false>(P, num_sms, st, q0);
+  if (P.herm) rc_launch<AR, NR, true, TR>(P, num_sms, st, q0);
+  else rc_launch<AR, NR, false, TR>(P, num_sms, st, q0);
 }
 
 // Double-FP32 RHS per launch: two (their accumulators are twice the c64
@@ -398,8 +410,12 @@ constexpr int RC_DFL_NR = 2;
 
 bool bin_rc_supported(int b) { return b % 32 == 0 && b >= 64 && b <= 256; }
 
+// Tile height of the double-FP32 kernel: 32 rows where two such stages fit,
+// else 16.
+int rc_dfl_tr(int b) { return rc_smem(b, RC_DFL_NR, 2, sizeof(dfl2), 32) <= 225 * 1024 ? 32 : 16; }
+
 bool bin_rc_dfl_supported(int b) {
-  return bin_rc_supported(b) && rc_smem(b, RC_DFL_NR, 2, sizeof(dfl2)) <= 225 * 1024;
+  return bin_rc_supported(b) && rc_smem(b, RC_DFL_NR, 2, sizeof(dfl2), rc_dfl_tr(b)) <= 225 * 1024;
 }
 
 void launch_bin_rc(const BinProduct &P, int num_sms, cudaStream_t st) {
@@ -412,9 +428,15 @@ void launch_bin_rc(const BinProduct &P, int num_sms, cudaStream_t st) {
 }
 
 void launch_bin_rc_dfl(const BinProduct &P, int num_sms, cudaStream_t st) {
+  const bool tall = rc_dfl_tr(P.b) == 32;
   for (int q0 = 0; q0 < P.nr; q0 += RC_DFL_NR) {
-    if (P.nr - q0 == 1) rc_launch_h<RcDfl, 1>(P, num_sms, st, q0);
-    else rc_launch_h<RcDfl, RC_DFL_NR>(P, num_sms, st, q0);
+    if (P.nr - q0 == 1) {
+      if (tall) rc_launch_h<RcDfl, 1, 32>(P, num_sms, st, q0);
+      else rc_launch_h<RcDfl, 1, 16>(P, num_sms, st, q0);
+    } else {
+      if (tall) rc_launch_h<RcDfl, RC_DFL_NR, 32>(P, num_sms, st, q0);
+      else rc_launch_h<RcDfl, RC_DFL_NR, 16>(P, num_sms, st, q0);
+    }
   }
 }
 

@@ -480,12 +480,14 @@ def test_split_lattice_transforms(moma_lib, cuda, nx, ny, b, nr):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("nx,ny,b,nr", [(3, 2, 64, 1), (2, 3, 96, 3), (4, 3, 128, 2), (2, 2, 160, 5)])
+@pytest.mark.parametrize("nx,ny,b,nr", [(3, 2, 64, 1), (2, 3, 96, 3), (4, 3, 128, 2), (2, 2, 160, 5),
+                                         (2, 2, 192, 3), (1, 2, 224, 1), (2, 1, 256, 2)])
 @pytest.mark.parametrize("op", [0, 1])
 def test_double_fp32_row_column_bin_product(moma_lib, cuda, nx, ny, b, nr, op):
     """The double-FP32 per-bin product of the refinement residual (Eq. 3,
-    the row/column-warp layout for b = 64 .. 160, two RHS per launch with a
-    ragged last one): Z x and Z^H x of c128 vectors on a MIXED array,
+    the row/column-warp layout: 32-row tiles for b = 64 .. 160, 16-row tiles
+    above; two RHS per launch with a ragged last one): Z x and Z^H x of c128
+    vectors on a MIXED array,
     element by element against the oracle's FP64 direct offset sums at the
     FP64-class bar of the residual path."""
     m = moma_lib
