@@ -14,7 +14,7 @@ LIB = os.path.join(PKG, "libmoma.so")
 BUILD_DIR = os.path.join(PKG, "_build")
 
 SOURCES = ["fft.cu", "binprod.cu", "precond.cu", "krylov.cu", "moma_api.cu", "server.cu", "ports.cu", "binmma.cu",
-           "predict.cu", "margin.cu", "lattice2d.cu", "precond_blk.cu", "binprod_rc.cu", "fftreg.cu"]
+           "predict.cu", "margin.cu", "lattice2d.cu", "precond_blk.cu", "binprod_rc.cu", "fftreg.cu", "lattice_cluster.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -83,6 +83,24 @@ struct Lattice2D {
 };
 template <typename R>
 bool lattice2d_fits(int Mx, int My, int J);
+
+// The same three c64 transforms on thread-block clusters (lattice_cluster.cu):
+// square M x M grids (M = 32, 48, 64), eight CTAs per group of eight basis
+// indices exchanging the half-transformed grid in distributed shared memory.
+// PX, PY: lanes per x / y line, those of the per-axis register passes for
+// the same geometry (lanes_per_line), which makes the results bitwise equal
+// to theirs.
+struct LatticeCluster {
+  int mode = 0;  // 0 F2, 1 I2, 2 I2MF2 (as Lattice2D)
+  const void *in = nullptr;
+  void *out = nullptr;
+  int nx = 0, ny = 0, b = 0, nr = 0;
+  long long ldv = 0;
+  const int *live = nullptr;  // if set and *live == 0 the transform does nothing
+  int PX = 0, PY = 0;
+};
+bool lattice_cluster_supported(int Mx, int My, int nx, int ny, int PX, int PY);
+void launch_lattice_cluster(const LatticeCluster &p, const FftTables &fx, const FftTables &fy, cudaStream_t st);
 template <typename R>
 void launch_lattice2d(const Lattice2D &p, const FftTables &fx, const FftTables &fy, cudaStream_t st);
 

@@ -568,6 +568,33 @@ void l2d(moma_array *a, int mode, int nr, const void *in, void *out) {
   check_launch(a);
 }
 
+// c64 transforms on thread-block clusters (one launch per 2D transform)
+// where the grid is square and the lane splits that the per-axis passes
+// would take for this RHS count are ones the cluster kernels implement.
+template <typename R>
+bool use_cluster(moma_array *a, int nr, int &PX, int &PY) {
+  if constexpr (!std::is_same<R, float>::value) return false;
+  else {
+    if (a->axis_fft || a->Mx != a->My) return false;
+    AxisPass probe;
+    probe.in_c128 = probe.out_c128 = 0;
+    if (!axis_reg_supported(probe, a->Mx)) return false;
+    PX = lanes_per_line(pass_fx(a, nr, nullptr, nullptr, 0, 0), a->Mx);
+    PY = lanes_per_line(pass_fy(a, nr, nullptr, nullptr, 0), a->My);
+    return lattice_cluster_supported(a->Mx, a->My, a->nx, a->ny, PX, PY);
+  }
+}
+template <typename R>
+bool cluster_transform(moma_array *a, int mode, int nr, const void *in, void *out) {
+  LatticeCluster p;
+  if (!use_cluster<R>(a, nr, p.PX, p.PY)) return false;
+  p.mode = mode; p.in = in; p.out = out; p.nx = a->nx; p.ny = a->ny; p.b = a->b; p.nr = nr; p.ldv = a->ldv;
+  p.live = a->live;
+  a->timed(PK_FFT64, [&] { launch_lattice_cluster(p, a->fx, a->fy, a->st); });
+  check_launch(a);
+  return true;
+}
+
 // lattice -> bins (Fx then Fy); in may be c128 when R is double.
 template <typename R>
 void lattice_to_bins(moma_array *a, int nr, const void *in, int in128) {
@@ -575,6 +602,7 @@ void lattice_to_bins(moma_array *a, int nr, const void *in, int in128) {
     l2d<R>(a, 0, nr, in, a->bx.p);
     return;
   }
+  if (!in128 && cluster_transform<R>(a, 0, nr, in, a->bx.p)) return;
   axis<R>(a, pass_fx(a, nr, in, a->t1.p, in128, st_code<R>()), a->fx);
   axis<R>(a, pass_fy(a, nr, a->t1.p, a->bx.p, st_code<R>()), a->fy);
 }
@@ -584,6 +612,7 @@ void bins_to_lattice(moma_array *a, int nr, const void *bins, void *out) {
     l2d<R>(a, 1, nr, bins, out);
     return;
   }
+  if (cluster_transform<R>(a, 1, nr, bins, out)) return;
   axis<R>(a, pass_iy(a, nr, bins, a->t1.p, st_code<R>()), a->fy);
   axis<R>(a, pass_ix(a, nr, a->t1.p, out, st_code<R>(), false, lat_code<R>()), a->fx);
 }
@@ -594,6 +623,7 @@ void mask_between_legs(moma_array *a, int nr) {
     l2d<R>(a, 2, nr, a->by.p, a->bx.p);
     return;
   }
+  if (cluster_transform<R>(a, 2, nr, a->by.p, a->bx.p)) return;
   axis<R>(a, pass_iy(a, nr, a->by.p, a->t1.p, is64<R>()), a->fy);
   axis<R>(a, pass_ix(a, nr, a->t1.p, a->t1.p, is64<R>(), true), a->fx);
   axis<R>(a, pass_fy(a, nr, a->t1.p, a->bx.p, is64<R>()), a->fy);
@@ -1689,6 +1719,9 @@ moma_status moma_create_array(int nx, int ny, int b, const moma_options *opt, vo
     CK(cudaGetDevice(&a->dev));
     CK(cudaDeviceGetAttribute(&a->num_sms, cudaDevAttrMultiProcessorCount, a->dev));
     build_tables(a);
+    // The cluster transforms' fit on this device is queried once per kernel
+    // shape; do it here, outside any graph capture.
+    for (int py : {2, 4}) lattice_cluster_supported(mx, my, nx, ny, 4, py);
     a->Z128.ensure((size_t)a->Bp * b * a->ldb * sizeof(double2), a->dev_bytes);
     CK(cudaMemsetAsync(a->Z128.p, 0, a->Z128.cap, a->st));  // stream-ordered (see ensure_ws)
     if (prec == MOMA_PREC_MIXED) {

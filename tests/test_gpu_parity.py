@@ -480,6 +480,52 @@ def test_split_lattice_transforms(moma_lib, cuda, nx, ny, b, nr):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("nx,ny,b,nr,M", [(3, 3, 24, 1, 64), (32, 32, 8, 2, 0), (5, 4, 20, 3, 48), (4, 4, 12, 2, 32),
+                                           (3, 3, 128, 4, 64), (24, 24, 8, 1, 0)])
+def test_cluster_lattice_transforms(moma_lib, cuda, nx, ny, b, nr, M):
+    """The c64 2D lattice transforms on thread-block clusters (F2, I2 and the
+    inverse / mask / forward pass between the Z and Z^H legs, Eq. 2, Eq. 3,
+    Sec. III-A) on square circulants M = 64, 48, 32: Z x, Z^H x and
+    P^{-1} Z^H Z x bitwise equal to the per-axis passes (MOMA_FLAG_AXIS_FFT:
+    the same line transforms, handed over through L2 between launches) and
+    element by element against the oracle's direct offset sums.  b = 20 and
+    12 leave the last group of eight basis indices ragged; four RHS at
+    b = 128 take two lanes per y line."""
+    m = moma_lib
+    spec = LatticeSpec(nx, ny, b, 0.5, 14)
+    blocks = offset_blocks(spec, np.complex64)
+    b128 = blocks.astype(np.complex128)
+    x = rand_vec(nr, spec, seed=23, dtype=np.complex64)
+    xo = x.astype(np.complex128)
+    p = mbt.precond_blocks(b128, nx, ny)
+    ref = {0: mbt.matvec(b128, nx, ny, xo), 1: mbt.matvec_h(b128, nx, ny, xo),
+           2: mbt.normal_operator(b128, nx, ny, xo, p)}
+    out = {}
+    for name, flags in (("cluster", m.MOMA_FLAG_NO_TENSOR), ("axis", m.MOMA_FLAG_NO_TENSOR | m.MOMA_FLAG_AXIS_FFT)):
+        h = m.moma_create_array(nx, ny, b, MIXED, mx=M, my=M, flags=flags)
+        try:
+            m.moma_set_blocks(h, blocks)
+            m.moma_profile(h, 1)
+            for op in (0, 1, 2):
+                n0 = m.moma_kernel_stats(h, "fft_c64")[0]
+                y = np.full_like(x, np.nan)
+                m.moma_matvec(h, op, x, y)
+                out[name, op] = y
+                # Lattice-transform launches of the c64 product: one per 2D
+                # transform on the clusters, one per axis pass otherwise.
+                nt = m.moma_kernel_stats(h, "fft_c64")[0] - n0
+                assert nt == {"cluster": (2, 2, 3), "axis": (4, 4, 7)}[name][op], (name, op, nt)
+        finally:
+            m.moma_destroy(h)
+    for op in (0, 1, 2):
+        y = out["cluster", op]
+        err = np.abs(y - ref[op]).max() / np.abs(ref[op]).max()
+        RAW_ERRORS[f"cluster_fft op{op} {nx}x{ny}x{b} M={M} nr={nr}"] = err
+        assert np.all(np.isfinite(y)) and err <= 1e-5, (op, err)
+        assert np.array_equal(y, out["axis", op]), op
+
+
+@pytest.mark.gpu
 @pytest.mark.parametrize("nx,ny,b,nr", [(3, 2, 64, 1), (2, 3, 96, 3), (4, 3, 128, 2), (2, 2, 160, 5),
                                          (2, 2, 192, 3), (1, 2, 224, 1), (2, 1, 256, 2)])
 @pytest.mark.parametrize("op", [0, 1])
