@@ -129,7 +129,7 @@ struct RcDfl {
   MOMA_DEV static void copy_async(E *dst, const E *src) { rc_cp_async16(dst, src); }
 };
 
-template <typename AR, int NR, bool HERM, int MINB, int TR>
+template <typename AR, int NR, bool HERM, int MINB, int TR, int BB>
 __global__ void __launch_bounds__(RC_THREADS, MINB) bin_rc_kernel(RcArgs A) {
   using E = typename AR::E;
   using Acc = typename AR::Acc;
@@ -140,7 +140,10 @@ __global__ void __launch_bounds__(RC_THREADS, MINB) bin_rc_kernel(RcArgs A) {
   extern __shared__ __align__(128) unsigned char sm[];
   const BinProduct &P = A.P;
   if (P.live && *P.live == 0) return;
-  const int b = P.b, ldb = P.ldb, nr = P.nr, q0 = A.q0, NS = A.NS, lds = A.lds;
+  // BB > 0: the block order as a compile-time constant (loops unrolled,
+  // strides folded); the row/column kernels run with ldb = b.
+  const int b = BB > 0 ? BB : P.b, ldb = BB > 0 ? BB : P.ldb, lds = BB > 0 ? BB + 2 : A.lds;
+  const int nr = P.nr, q0 = A.q0, NS = A.NS;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   uint64_t *full = reinterpret_cast<uint64_t *>(sm);
   uint64_t *empty = full + NS;
@@ -173,9 +176,11 @@ __global__ void __launch_bounds__(RC_THREADS, MINB) bin_rc_kernel(RcArgs A) {
     if (lane != 0) return;
     int issued = 0;
     const uint32_t row_bytes = (uint32_t)(ldb * sizeof(E));
+    int s = 0, t = 0;  // stage, tile of the pair (counters: no division per tile)
+    uint32_t ph = 0;   // ring pass parity
+    long long p = blockIdx.x;
     for (int i = 0; i < total; ++i) {
-      const int s = i % NS;
-      const uint32_t par = (uint32_t)(((i / NS) & 1) ^ 1);
+      const uint32_t par = ph ^ 1u;
       bool ok = mbar_try_wait(&empty[s], par);
       if (!ok) {
         const uint64_t t0 = global_ns();
@@ -189,14 +194,20 @@ __global__ void __launch_bounds__(RC_THREADS, MINB) bin_rc_kernel(RcArgs A) {
         *abort_flag = 1;
         break;
       }
-      const int pk = i / ntile, t = i % ntile;
-      const long long p = (long long)blockIdx.x + (long long)pk * gridDim.x;
       const E *src = Z + ((size_t)p * b + (size_t)t * TR) * ldb;
       E *dst = stage0 + (size_t)s * stage_elems;
       fence_proxy_async();
       mbar_expect_tx(&full[s], row_bytes * TR);
       for (int rr = 0; rr < TR; ++rr) bulk_g2s(dst + (size_t)rr * lds, src + (size_t)rr * ldb, row_bytes, &full[s]);
       issued = i + 1;
+      if (++t == ntile) {
+        t = 0;
+        p += gridDim.x;
+      }
+      if (++s == NS) {
+        s = 0;
+        ph ^= 1u;
+      }
     }
     for (int i = max(0, issued - NS); i < issued; ++i)
       mbar_wait_bounded(&full[i % NS], (uint32_t)((i / NS) & 1), RC_WAIT_NS);
@@ -234,8 +245,10 @@ __global__ void __launch_bounds__(RC_THREADS, MINB) bin_rc_kernel(RcArgs A) {
   bool selfp = false;
   const E *xr_s = xbuf, *xc_s = xbuf + (size_t)NR * b;
 
+  int s = 0, t = 0, pk = 0;  // stage, tile of the pair, pair (counters: no division per tile)
+  uint32_t ph = 0;           // ring pass parity
   for (int i = 0; i < total; ++i) {
-    const int pk = i / ntile, t = i % ntile, buf = pk & 1;
+    const int buf = pk & 1;
     if (t == 0) {
       const int p = (int)blockIdx.x + pk * (int)gridDim.x;
       const int2 pr = P.pairs[p];
@@ -250,10 +263,9 @@ __global__ void __launch_bounds__(RC_THREADS, MINB) bin_rc_kernel(RcArgs A) {
         for (int qq = 0; qq < NR; ++qq) accC[h][qq] = AR::zero();
       if (pk + 1 < npair) load_x(pk + 1, buf ^ 1);  // overlaps this pair's tiles
     }
-    const int s = i % NS;
     bool ok = false;
     if (!*abort_flag) {
-      const uint32_t par = (uint32_t)((i / NS) & 1);
+      const uint32_t par = ph;
       ok = mbar_try_wait(&full[s], par);
       if (!ok) {
         const uint64_t t0 = global_ns();
@@ -353,6 +365,14 @@ __global__ void __launch_bounds__(RC_THREADS, MINB) bin_rc_kernel(RcArgs A) {
         if (lane == 0) rc_arrive(red_free);
       }
     }
+    if (++t == ntile) {
+      t = 0;
+      ++pk;
+    }
+    if (++s == NS) {
+      s = 0;
+      ph ^= 1u;
+    }
   }
 }
 
@@ -360,7 +380,7 @@ size_t rc_smem(int b, int NR, int NS, size_t esz, int TR = RC_TR) {
   return 256 + (size_t)NS * TR * (b + 2) * esz + (size_t)4 * NR * b * esz + (size_t)4 * 32 * 2 * NR * esz;
 }
 
-template <typename AR, int NR, bool HERM, int TR>
+template <typename AR, int NR, bool HERM, int TR, int BB>
 void rc_launch(const BinProduct &P, int num_sms, cudaStream_t st, int q0) {
   constexpr size_t esz = sizeof(typename AR::E);
   // Two CTAs per SM only for c64 (double-FP32 stages are twice as large).
@@ -378,7 +398,7 @@ void rc_launch(const BinProduct &P, int num_sms, cudaStream_t st, int q0) {
   if (grid > P.Bp) grid = P.Bp;
   RcArgs a{P, NS, q0, P.b + 2};
   if (occ == 2) {
-    auto kern = bin_rc_kernel<AR, NR, HERM, 2, TR>;
+    auto kern = bin_rc_kernel<AR, NR, HERM, 2, TR, BB>;
     static int configured = 0;
     if (!configured) {
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 112 * 1024);
@@ -386,7 +406,7 @@ void rc_launch(const BinProduct &P, int num_sms, cudaStream_t st, int q0) {
     }
     kern<<<grid, RC_THREADS, smem, st>>>(a);
   } else {
-    auto kern = bin_rc_kernel<AR, NR, HERM, 1, TR>;
+    auto kern = bin_rc_kernel<AR, NR, HERM, 1, TR, BB>;
     static int configured = 0;
     if (!configured) {
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
@@ -396,10 +416,17 @@ void rc_launch(const BinProduct &P, int num_sms, cudaStream_t st, int q0) {
   }
 }
 
+// b = 128 (the benchmark's block order) as a compile-time constant, any
+// other multiple of 32 at run time.
 template <typename AR, int NR, int TR = RC_TR>
 void rc_launch_h(const BinProduct &P, int num_sms, cudaStream_t st, int q0) {
-  if (P.herm) rc_launch<AR, NR, true, TR>(P, num_sms, st, q0);
-  else rc_launch<AR, NR, false, TR>(P, num_sms, st, q0);
+  if (P.b == 128) {
+    if (P.herm) rc_launch<AR, NR, true, TR, 128>(P, num_sms, st, q0);
+    else rc_launch<AR, NR, false, TR, 128>(P, num_sms, st, q0);
+    return;
+  }
+  if (P.herm) rc_launch<AR, NR, true, TR, 0>(P, num_sms, st, q0);
+  else rc_launch<AR, NR, false, TR, 0>(P, num_sms, st, q0);
 }
 
 // Double-FP32 RHS per launch: two (their accumulators are twice the c64
