@@ -416,17 +416,26 @@ void rc_launch(const BinProduct &P, int num_sms, cudaStream_t st, int q0) {
   }
 }
 
-// b = 128 (the benchmark's block order) as a compile-time constant, any
-// other multiple of 32 at run time.
+template <typename AR, int NR, int TR, int BB>
+void rc_launch_hb(const BinProduct &P, int num_sms, cudaStream_t st, int q0) {
+  if (P.herm) rc_launch<AR, NR, true, TR, BB>(P, num_sms, st, q0);
+  else rc_launch<AR, NR, false, TR, BB>(P, num_sms, st, q0);
+}
+
+// The block orders of the benchmark workloads (b = 96, 128, 256) as
+// compile-time constants, any other multiple of 32 at run time.  (A
+// double-FP32 launch takes 16-row tiles exactly when b > 160.)
 template <typename AR, int NR, int TR = RC_TR>
 void rc_launch_h(const BinProduct &P, int num_sms, cudaStream_t st, int q0) {
-  if (P.b == 128) {
-    if (P.herm) rc_launch<AR, NR, true, TR, 128>(P, num_sms, st, q0);
-    else rc_launch<AR, NR, false, TR, 128>(P, num_sms, st, q0);
-    return;
+  constexpr bool dfl_tiles = std::is_same<AR, RcDfl>::value;
+  if constexpr (!dfl_tiles || TR == 32) {
+    if (P.b == 128) return rc_launch_hb<AR, NR, TR, 128>(P, num_sms, st, q0);
+    if (P.b == 96) return rc_launch_hb<AR, NR, TR, 96>(P, num_sms, st, q0);
   }
-  if (P.herm) rc_launch<AR, NR, true, TR, 0>(P, num_sms, st, q0);
-  else rc_launch<AR, NR, false, TR, 0>(P, num_sms, st, q0);
+  if constexpr (!dfl_tiles || TR == 16) {
+    if (P.b == 256) return rc_launch_hb<AR, NR, TR, 256>(P, num_sms, st, q0);
+  }
+  rc_launch_hb<AR, NR, TR, 0>(P, num_sms, st, q0);
 }
 
 // Double-FP32 RHS per launch: two (their accumulators are twice the c64
