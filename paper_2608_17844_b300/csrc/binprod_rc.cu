@@ -229,6 +229,11 @@ __global__ void __launch_bounds__(RC_THREADS, MINB) bin_rc_kernel(RcArgs A) {
       else xc_s[idx] = AR::ezero();
     }
   };
+  // Launched as a programmatic dependent of the kernel that writes the bin
+  // vectors: the producer streams the pair store from the start, the
+  // consumers read x only once that kernel has completed.  (A plain launch
+  // passes this wait at once.)
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   load_x(0, 0);
   rc_cp_async_wait_all();
   rc_consumer_bar();
@@ -376,6 +381,24 @@ __global__ void __launch_bounds__(RC_THREADS, MINB) bin_rc_kernel(RcArgs A) {
   }
 }
 
+// Launch with programmatic stream serialisation: the kernel may begin
+// while the previous kernel in the stream is finishing (see the consumers'
+// griddepcontrol.wait).
+template <typename K>
+void rc_launch_pdl(K kern, int grid, size_t smem, cudaStream_t st, const RcArgs &a) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(RC_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at;
+  at.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at.val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = &at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kern, a);
+}
+
 size_t rc_smem(int b, int NR, int NS, size_t esz, int TR = RC_TR) {
   return 256 + (size_t)NS * TR * (b + 2) * esz + (size_t)4 * NR * b * esz + (size_t)4 * 32 * 2 * NR * esz;
 }
@@ -404,7 +427,7 @@ void rc_launch(const BinProduct &P, int num_sms, cudaStream_t st, int q0) {
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 112 * 1024);
       configured = 1;
     }
-    kern<<<grid, RC_THREADS, smem, st>>>(a);
+    rc_launch_pdl(kern, grid, smem, st, a);
   } else {
     auto kern = bin_rc_kernel<AR, NR, HERM, 1, TR, BB>;
     static int configured = 0;
@@ -412,7 +435,7 @@ void rc_launch(const BinProduct &P, int num_sms, cudaStream_t st, int q0) {
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
       configured = 1;
     }
-    kern<<<grid, RC_THREADS, smem, st>>>(a);
+    rc_launch_pdl(kern, grid, smem, st, a);
   }
 }
 

@@ -120,6 +120,9 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(ClShape<M, PX, PY>
   const float2 *tw = A.tw.w;
   const float inv_m = 1.0f / (float)M;
   const float2 zero = make_float2(0.f, 0.f);
+  // A bin product launched as a programmatic dependent may start now (it
+  // streams the pair store and waits for this grid before reading bins).
+  if (MODE != 1) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   cl_arrive_relaxed();  // every CTA of the cluster has started once the matching wait returns
 
   // ---- y lines: (column colL, basis jj), kx = c + 8 colL ----
