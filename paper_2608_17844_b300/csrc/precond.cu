@@ -416,10 +416,10 @@ MOMA_DEV bool chol_panels(const Tri<C> T, int b, int jfirst, int jlast, R *inv_d
 // global memory (the element's Lpk slot, in the working precision), the
 // rest with the trailing triangle of order b - j0 in shared memory: j0 is
 // the smallest panel boundary at which that triangle fits the launch's
-// shared-memory budget, chosen so that two CTAs share an SM (j0 = 0: the
+// shared-memory budget, chosen so that MINB CTAs share an SM (j0 = 0: the
 // whole factorisation in shared memory; j0 = b: none of it).
 template <typename R, int MINB>
-__global__ void __launch_bounds__(512, MINB) box_cholesky_kernel(const double2 *__restrict__ Pbox, int b, int j0,
+__global__ void __launch_bounds__(MINB == 4 ? 256 : 512, MINB) box_cholesky_kernel(const double2 *__restrict__ Pbox, int b, int j0,
                                                                  double2 *__restrict__ Lpk, unsigned *err) {
   using C = typename Cplx<R>::T;
   static_assert(sizeof(C) == sizeof(double2), "the factor is stored in place of its FP64 output");
@@ -479,15 +479,25 @@ __global__ void __launch_bounds__(512, MINB) box_cholesky_kernel(const double2 *
 
 template <typename R>
 static void launch_chol_typed(const double2 *Pbox, int nel, int b, double2 *Lpk, unsigned *err, cudaStream_t st) {
-  // Two CTAs per SM where the trailing triangle of the later panels fits
-  // 110 KB of shared memory; the first panels then run in global memory.
-  constexpr size_t kHalf = 110 * 1024, kWhole = 210 * 1024;
+  // Four CTAs of 256 threads per SM where the trailing triangle fits 54 KB
+  // of shared memory with at most half the columns factored in global
+  // memory (b <= 128: one element's serial panel work overlaps three
+  // others' trailing updates); else two CTAs of 512 threads where it fits
+  // 110 KB; else one CTA with up to 210 KB.
+  constexpr size_t kQuarter = 54 * 1024, kHalf = 110 * 1024, kWhole = 210 * 1024;
   auto tri_bytes = [](int n) { return (size_t)n * (n + 1) / 2 * sizeof(double2); };
   static int configured = 0;
   if (!configured) {
+    cudaFuncSetAttribute(box_cholesky_kernel<R, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kQuarter);
     cudaFuncSetAttribute(box_cholesky_kernel<R, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHalf);
     cudaFuncSetAttribute(box_cholesky_kernel<R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWhole);
     configured = 1;
+  }
+  int jq = 0;
+  while (jq < b && tri_bytes(b - jq) > kQuarter) jq += CH_NB;
+  if (jq < b && 2 * jq <= b) {
+    box_cholesky_kernel<R, 4><<<nel, 256, tri_bytes(b - jq), st>>>(Pbox, b, jq, Lpk, err);
+    return;
   }
   int j0 = 0;
   while (j0 < b && tri_bytes(b - j0) > kHalf) j0 += CH_NB;

@@ -121,9 +121,15 @@ def test_matvec_fp64_and_c64(moma_lib, cuda, nx, ny, b, op, prec):
         m.moma_destroy(h)
 
 
-@pytest.mark.parametrize("nx,ny,b", [(1, 1, 3), (3, 2, 4), (4, 4, 32), (5, 3, 7), (6, 6, 33)])
+@pytest.mark.parametrize("nx,ny,b", [(1, 1, 3), (3, 2, 4), (4, 4, 32), (5, 3, 7), (6, 6, 33), (3, 1, 96), (2, 2, 128),
+                                      (1, 2, 160), (1, 1, 256)])
 @pytest.mark.parametrize("prec", [FP64, MIXED])
 def test_preconditioner_blocks_and_apply(moma_lib, cuda, nx, ny, b, prec):
+    """Every P_e (Eq. 37) and the apply of P^{-1} against the oracle, for
+    each launch shape of the block factorisation: the whole triangle in
+    shared memory (b <= 33), four CTAs per SM with the first 24 / 48 / 80
+    columns factored in global memory (b = 96, 128, 160), one CTA per SM
+    (b = 256)."""
     m = moma_lib
     spec, blocks, h = make(m, nx, ny, b, prec)
     try:
