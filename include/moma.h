@@ -96,7 +96,10 @@ enum {
                                     ~1/58 of FP32; results agree to ~1e-13) */
     MOMA_FLAG_AXIS_FFT = 32,     /* lattice transforms of the c64 / FP64 products as one launch per
                                     lattice axis instead of one 2D launch per transform (the 2D
-                                    kernels are the default where the grid fits shared memory) */
+                                    launches are the default: on thread-block clusters for square
+                                    c64 grids of 32, 48 or 64 per axis, whose results are bitwise
+                                    those of the per-axis passes; in shared memory where a larger
+                                    grid fits it) */
     MOMA_FLAG_PRECOND_PER_ELEMENT = 64, /* c64 preconditioner apply with one CTA per element instead of
                                     the streaming kernel (default for even b <= 160 and fewer
                                     than 16 RHS) */
