@@ -34,30 +34,11 @@
 #include <stdexcept>
 
 #include "internal.h"
-#include "fftreg.cuh"
+#include "lattice_cluster.cuh"
 
 namespace moma {
 
 namespace {
-
-constexpr int kCl = 8;            // CTAs per cluster
-constexpr int kClJ = 8;           // basis indices per cluster
-constexpr int kColJ = kClJ + 4;   // Bcol: stride of consecutive rows of a column
-constexpr int kRowJ = kClJ + 1;   // Brow: stride of consecutive columns of a row
-
-template <int M, int PX, int PY>
-struct ClShape {
-  static constexpr int YMAX = (M + 1) / 2;            // lattice rows at most (M >= 2 Ny - 1)
-  static constexpr int RPC = (YMAX + kCl - 1) / kCl;  // rows per CTA at most
-  static constexpr int CPC = M / kCl;                 // columns per CTA
-  static constexpr int NXT = RPC * kClJ * PX, NYT = CPC * kClJ * PY;
-  static constexpr int NT = ((NXT > NYT ? NXT : NYT) + 31) / 32 * 32;
-  static constexpr int QX = M / PX, QY = M / PY, QMAX = QX > QY ? QX : QY;
-  static constexpr int XBUF = (NT / 32) * QMAX * kLaneLd;  // per-warp exchange buffers
-  static constexpr int BCOL = CPC * YMAX * kColJ;
-  static constexpr int BROW = RPC * M * kRowJ;
-  static_assert(M % kCl == 0, "grid columns are dealt to the cluster's CTAs in turn");
-};
 
 struct ClTw {
   float2 w[kRegMaxM];
@@ -126,14 +107,12 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(ClShape<M, PX, PY>
   cl_arrive_relaxed();  // every CTA of the cluster has started once the matching wait returns
 
   // ---- y lines: (column colL, basis jj), kx = c + 8 colL ----
-  constexpr int LY = 32 / PY;
-  const int sy = lane % PY, ly = lane / PY, lny = warp * LY + ly;
-  const int colL = lny / kClJ, jjy = lny % kClJ, kx = c + kCl * colL;
+  const ClLine ty = cl_line<PY>(c, tid);
+  const int sy = ty.s, ly = ty.l, colL = ty.loc, jjy = ty.jj, kx = ty.g;
   const bool acty = colL < S::CPC && j0 + jjy < b;
   // ---- x lines: (row rowL, basis jj), y = c + 8 rowL ----
-  constexpr int LX = 32 / PX;
-  const int sx = lane % PX, lx = lane / PX, lnx = warp * LX + lx;
-  const int rowL = lnx / kClJ, jjx = lnx % kClJ, yx = c + kCl * rowL;
+  const ClLine tx = cl_line<PX>(c, tid);
+  const int sx = tx.s, lx = tx.l, rowL = tx.loc, jjx = tx.jj, yx = tx.g;
   const bool rowx = rowL < S::RPC && yx < ny;
   const bool actx = rowx && j0 + jjx < b;
 
@@ -154,7 +133,7 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(ClShape<M, PX, PY>
 #pragma unroll
       for (int q = 0; q < S::QX; ++q) {
         const int k = sx + PX * q;
-        cl_store(cl_map(bcol + (k / kCl) * (S::YMAX * kColJ) + yx * kColJ + jjx, k % kCl), v[q]);
+        cl_store(cl_map(bcol + cl_bcol_off<M, PX, PY>(k, yx, jjx), cl_owner(k)), v[q]);
       }
     cl_sync();
   } else {
@@ -177,7 +156,7 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(ClShape<M, PX, PY>
 #pragma unroll
       for (int q = 0; q < S::QY; ++q) {
         const int y = sy + PY * q;
-        if (y < ny) cl_store(cl_map(brow + (y / kCl) * (M * kRowJ) + kx * kRowJ + jjy, y % kCl), v[q]);
+        if (y < ny) cl_store(cl_map(brow + cl_brow_off<M>(y, kx, jjy), cl_owner(y)), v[q]);
       }
     cl_sync();
 
@@ -187,7 +166,7 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(ClShape<M, PX, PY>
     float2 u[S::QX];
 #pragma unroll
     for (int q = 0; q < S::QX; ++q) {
-      float2 t = rowx ? brow[rowL * (M * kRowJ) + (sx + PX * q) * kRowJ + jjx] : zero;
+      float2 t = rowx ? brow[cl_brow_off<M>(yx, sx + PX * q, jjx)] : zero;
       t.y = -t.y;
       u[q] = t;
     }
@@ -214,7 +193,7 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(ClShape<M, PX, PY>
 #pragma unroll
         for (int q = 0; q < S::QX; ++q) {
           const int k = sx + PX * q;
-          cl_store(cl_map(bcol + (k / kCl) * (S::YMAX * kColJ) + yx * kColJ + jjx, k % kCl), u[q]);
+          cl_store(cl_map(bcol + cl_bcol_off<M, PX, PY>(k, yx, jjx), cl_owner(k)), u[q]);
         }
       cl_sync();
     }
@@ -228,7 +207,7 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(ClShape<M, PX, PY>
 #pragma unroll
     for (int q = 0; q < S::QY; ++q) {
       const int y = sy + PY * q;
-      v[q] = (colL < S::CPC && y < ny) ? bcol[colL * (S::YMAX * kColJ) + y * kColJ + jjy] : zero;
+      v[q] = (colL < S::CPC && y < ny) ? bcol[cl_bcol_off<M, PX, PY>(kx, y, jjy)] : zero;
     }
     cl_line_fft<M, PY>(v, xb, lane, sy, ly, w, tw);
     if (acty) {
