@@ -29,8 +29,12 @@
 // stride kColJ = 12 (the y lines' loads of four rows by eight basis indices
 // cover 32 distinct banks pairs), Brow[row][kx][jj] with the column stride
 // kRowJ = 9 (the x lines' loads of eight columns by four basis indices are
-// nearly conflict-free).  Every CTA of a cluster passes every cluster
-// barrier (no thread leaves early), so the barriers always complete.
+// nearly conflict-free); the work split and the offsets are those of
+// lattice_cluster.cuh.  Every CTA of a cluster passes every cluster barrier
+// (no thread leaves early), so the barriers always complete.  F2 and I2MF2
+// let the next kernel launch at their start: the bin product that follows
+// is launched as a programmatic dependent and streams its pair store while
+// the transform finishes.
 #include <stdexcept>
 
 #include "internal.h"
