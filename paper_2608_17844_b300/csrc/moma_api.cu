@@ -538,8 +538,11 @@ void precond(moma_array *a, int nr, const void *x, void *y) {
   precond_margin<R>(a, nr, x, y);
 }
 
-// The 2D lattice transforms (one launch per transform) serve the c64 and
-// FP64 products; the double-FP32 residual path keeps the per-axis passes.
+// The shared-memory 2D lattice transforms (one launch per transform) serve
+// the c64 and FP64 products on grids the register passes do not take; c64
+// grids up to 64 per axis use the cluster transforms (square grids) or the
+// register per-axis passes, and the double-FP32 residual path keeps the
+// per-axis passes.
 template <typename R> bool use_l2d(const moma_array *a) {
   if constexpr (std::is_same<R, dfl>::value) return false;
   else {
